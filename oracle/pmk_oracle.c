@@ -22,8 +22,10 @@
  *
  * Readings where the paper is silent or garbled (kept identical on the
  * product side, which implements them independently):
- *   - random source: SplitMix64 (Steele, Lea, Flood 2014), seeded by the
- *     caller, instead of /dev/random;
+ *   - random source: SplitMix64 (Steele, Lea, Flood 2014) instead of
+ *     /dev/random; key k draws from its own stream, seeded with the k-th
+ *     output of a master SplitMix64 stream seeded by the caller, so the K
+ *     keys can be generated in parallel as Section 3.3 does with OpenMP;
  *   - primes have exactly n/2 bits with the two top bits set (so N has
  *     exactly n bits), bit 0 set; candidates are rejected by trial division
  *     by the odd primes below 2000, then unless gcd(e, cand-1) = 1, then by
@@ -436,7 +438,7 @@ int oracle_keygen(uint32_t K, uint32_t nbits, uint64_t e, uint64_t seed, uint32_
       if (c % f == 0) { pr = 0; break; }
     if (pr) small[nsmall++] = c;
   }
-  uint64_t rng = seed;
+  uint64_t master = seed;
   limb_t *one = calloc((size_t)h, 4), *pm1 = calloc((size_t)h, 4), *qm1 = calloc((size_t)h, 4);
   limb_t *phi = calloc((size_t)s, 4), *ew = calloc((size_t)s, 4);
   one[0] = 1;
@@ -444,6 +446,7 @@ int oracle_keygen(uint32_t K, uint32_t nbits, uint64_t e, uint64_t seed, uint32_
   ew[1] = (limb_t)(e >> 32);
   for (uint32_t k = 0; k < K; k++) {
     limb_t *pk = p + (size_t)k * h, *qk = q + (size_t)k * h;
+    uint64_t rng = splitmix64(&master);   /* this key's own stream */
     gen_prime(&rng, (int)nbits / 2, e, small, nsmall, pk);
     do {
       gen_prime(&rng, (int)nbits / 2, e, small, nsmall, qk);
