@@ -1,0 +1,389 @@
+"""Benchmark of the PMKRSA hot path on GB300.
+
+One step = one pass of the whole hot path over one message that is already
+resident in HBM: split -> encrypt (e = 65537) -> decrypt (full d) -> join,
+all in this library's kernels on one stream.  Workload: a 1 MiB uniformly
+random file, K = 8 key pairs of 2048 bits, 255-byte chunks (4,113 chunks),
+chunk t bound to key t mod K.  The headline value is 2048-bit decrypt
+chunk-modexps per second of whole-step time; the inputs are smaller than L2,
+so L2 is flushed (a 256 MiB write) between timed steps, outside the timed
+intervals.  The CRT form of decryption is timed the same way and reported
+beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun every rank processes its own message (weak scaling); rank 0
+prints one JSON line.  ``--impl reference`` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2111_11924_gb300 import workloads as W  # noqa: E402
+
+WORKLOAD = W.FILE_1MIB_2048
+METRIC = "2048-bit decrypt chunk-modexps/s"
+UNIT = "chunk-modexps/s"
+L2_FLUSH_BYTES = 256 << 20
+KERNELS_PER_STEP = 6  # split, range check + modexp (encrypt), range check + modexp (decrypt), join
+
+# DRAM traffic of the full-d decryption kernel from one ncu capture, valid only
+# for the kernel sources it was measured on (see profiles/).
+TRAFFIC_SOURCES = ["paper_2111_11924_gb300/csrc/modexp_core.cuh", "paper_2111_11924_gb300/csrc/modexp_kernels.cuh"]
+TRAFFIC_MEASURED = {}  # source digest -> bytes per launch
+
+
+def sources_digest() -> str:
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def algorithmic_montmuls(nbits: int) -> float:
+    """Montgomery products of one full-d decryption, fixed at the w = 5
+    sliding-window count: (n - 1) squarings + n/6 multiplies + 16 table
+    entries + 2 domain conversions."""
+    return (nbits - 1) + nbits / 6 + 16 + 2
+
+
+def macs_per_montmul(nbits: int) -> int:
+    s = nbits // 32
+    return 2 * s * s + s  # CIOS: s rows of (s + s) MACs plus the q products
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.reader = threading.Thread(target=self._read, daemon=True)
+            self.reader.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend, init_method="env://")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- CPU oracle arm
+
+_ORACLE_CACHE: dict = {}
+
+def oracle_sample(n_sample: int, threads: int) -> dict:
+    """Time the oracle (as it stands) on a bounded sample of the workload's
+    chunks: oracle split, encrypt, full-d decrypt; rate in chunks/s."""
+    import oracle
+
+    w = WORKLOAD
+    if "keys" not in _ORACLE_CACHE:
+        _ORACLE_CACHE["keys"] = oracle.keygen(w.K, w.nbits, w.e, w.key_seed)
+        _ORACLE_CACHE["msg"] = w.message()
+    keys = _ORACLE_CACHE["keys"]
+    msg = _ORACLE_CACHE["msg"][: n_sample * w.payload]
+    t0 = time.perf_counter()
+    m = oracle.split(msg, w.nbits)
+    c = oracle.encrypt_chunks(m, keys, threads=threads)
+    d = oracle.decrypt_chunks(c, keys, threads=threads)
+    back = oracle.join(d, len(msg), w.nbits)
+    dt = time.perf_counter() - t0
+    assert back == msg.tobytes()
+    return {"value": len(m) / dt, "seconds": dt, "chunks": len(m)}
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return 0
+    threads = os.cpu_count() or 1
+    n_sample = args.ref_sample
+    for _ in range(args.warmup):
+        oracle_sample(max(threads, 16), threads)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        r = oracle_sample(n_sample, threads)
+        vals.append(r["value"])
+        secs.append(r["seconds"])
+    value = len(vals) * n_sample / sum(secs)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(secs),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": WORKLOAD.describe() | {"step": f"oracle split+encrypt+decrypt(full d)+join of {n_sample} chunks"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"first {n_sample} chunks of the workload per step, all host cores"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    import paper_2111_11924_gb300 as P
+
+    w = WORKLOAD
+    ctx = P.Context(local)
+    ks = ctx.keygen(w.K, w.nbits, w.e, w.key_seed)
+    msg_np = W.Workload(w.id + 1000 * rank, w.name, w.msg_bytes, w.K, w.nbits).message() if rank else w.message()
+    d_msg = torch.from_numpy(msg_np).cuda()
+    n = w.n_chunks
+    chunks = torch.empty((n, w.limbs), dtype=torch.int32, device="cuda")
+    cipher = torch.empty_like(chunks)
+    plain = torch.empty_like(chunks)
+    back = torch.empty_like(d_msg)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def step(use_crt: bool, ev=None):
+        if ev:
+            ev[0].record()
+        ctx.split(w.nbits, d_msg, out=chunks)
+        if ev:
+            ev[1].record()
+        ctx.encrypt_chunks(ks, chunks, out=cipher)
+        if ev:
+            ev[2].record()
+        ctx.decrypt_chunks(ks, cipher, use_crt=use_crt, out=plain)
+        if ev:
+            ev[3].record()
+        ctx.join(w.nbits, plain, w.msg_bytes, out=back)
+        if ev:
+            ev[4].record()
+
+    def timed(use_crt: bool, steps: int, warmup: int):
+        for _ in range(warmup):
+            step(use_crt)
+        torch.cuda.synchronize()
+        ctx.check()
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(steps)]
+        barrier(world)
+        torch.cuda.synchronize()
+        for i in range(steps):
+            flush.zero_()  # evict L2 between steps, outside the timed intervals
+            step(use_crt, evs[i])
+        torch.cuda.synchronize()
+        barrier(world)
+        ctx.check()
+        ph = np.array([[evs[i][j].elapsed_time(evs[i][j + 1]) for j in range(4)] for i in range(steps)])
+        return ph  # ms: split, encrypt, decrypt, join
+
+    peak = ctx.measure_int_peak()
+    with ClockSampler(local) as clocks:
+        ph = timed(False, args.steps, args.warmup)
+    torch.cuda.synchronize()
+    assert torch.equal(back, d_msg), "round trip failed"
+    ph_crt = timed(True, max(3, args.steps // 2), 3)
+    assert torch.equal(back, d_msg), "CRT round trip failed"
+
+    step_ms = ph.sum(axis=1)
+    t_step = max_over_ranks(float(step_ms.mean()), world, "cuda")
+    value = world * n / (t_step / 1e3)
+    dec_ms = float(ph[:, 2].mean())
+    enc_ms = float(ph[:, 1].mean())
+    split_ms, join_ms = float(ph[:, 0].mean()), float(ph[:, 3].mean())
+    crt_step = float(ph_crt.sum(axis=1).mean())
+    crt_dec = float(ph_crt[:, 2].mean())
+
+    clk = clocks.summary()
+    sms = peak["num_sms"]
+    max_mhz = clk["sm_max_mhz"] or 2070.0
+    peak_tmacs = peak["macs_per_clk_per_sm"] * sms * max_mhz * 1e6 / 1e12
+    alg_macs = algorithmic_montmuls(w.nbits) * macs_per_montmul(w.nbits) * n
+    achieved = alg_macs / (dec_ms / 1e3) / 1e12
+    digest = sources_digest()
+
+    # end to end through the C ABI on pinned host buffers
+    h_msg = torch.from_numpy(msg_np).pin_memory()
+    h_cipher = torch.empty((n, w.limbs), dtype=torch.int32).pin_memory()
+    h_back = torch.empty(w.msg_bytes, dtype=torch.uint8).pin_memory()
+    for _ in range(2):
+        ctx.encrypt_message_host(ks, h_msg, h_cipher)
+        ctx.decrypt_message_host(ks, h_cipher, h_back)
+    barrier(world)
+    e2e_t = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        ctx.encrypt_message_host(ks, h_msg, h_cipher)
+        ctx.decrypt_message_host(ks, h_cipher, h_back)
+        e2e_t.append(time.perf_counter() - t0)
+    barrier(world)
+    assert torch.equal(h_back, h_msg), "host round trip failed"
+    e2e_s = max_over_ranks(statistics.mean(e2e_t), world, "cuda")
+    cipher_bytes = n * w.limbs * 4
+
+    mb = w.msg_bytes / 2**20
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": w.describe() | {"step": "split+encrypt+decrypt(full d)+join, message resident in HBM",
+                                  "l2": "flushed (256 MiB write) between timed steps", "parallelism": f"replicas{world}"},
+        "phases_ms": {"split": split_ms, "encrypt": enc_ms, "decrypt": dec_ms, "join": join_ms},
+        "decrypt_only": {"value": n / (dec_ms / 1e3), "unit": UNIT},
+        "encrypt_only": {"value": n / (enc_ms / 1e3), "unit": UNIT},
+        "throughput_MBps": {"encrypt": mb / (enc_ms / 1e3), "decrypt": mb / (dec_ms / 1e3),
+                            "round_trip": mb / (t_step / 1e3)},
+        "crt": {"value": world * n / (crt_step / 1e3), "unit": UNIT, "ms_per_step": crt_step,
+                "decrypt_ms": crt_dec, "decrypt_only": n / (crt_dec / 1e3)},
+        "split_join_GBps": {"split": (w.msg_bytes + cipher_bytes) / (split_ms / 1e3) / 1e9,
+                            "join": (w.msg_bytes + cipher_bytes) / (join_ms / 1e3) / 1e9},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tmacs, "unit": "TMAC/s",
+                     "frac": achieved / peak_tmacs, "traffic": TRAFFIC_MEASURED.get(digest),
+                     "kernel": "k_modexp<64,8,false> (full-d decrypt; interval includes its 4 us range check)",
+                     "peak_basis": f"{peak['macs_per_clk_per_sm']:.2f} MAC/clk/SM measured x {sms} SMs x {max_mhz:.0f} MHz",
+                     "frac_at_observed_clock": (achieved / (peak["macs_per_clk_per_sm"] * sms * clk["sm_mhz"] * 1e-6)
+                                                if clk["sm_mhz"] else None)},
+        "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+        "e2e": {"value": world * n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": w.msg_bytes + cipher_bytes,
+                "d2h_bytes_per_step": cipher_bytes + w.msg_bytes},
+        "gpu_launches": KERNELS_PER_STEP * args.steps,
+        "source_digest": digest,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        r = oracle_sample(args.ref_sample, threads)
+        line["cpu_baseline"] = {"value": r["value"], "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": f"first {r['chunks']} chunks of the workload (oracle split+encrypt+"
+                                          f"decrypt+join), {r['seconds']:.1f} s on {threads} threads"}
+    if rank == 0:
+        print(json.dumps(line))
+    ks.free()
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def run_profile(args):
+    """A short, fixed launch sequence for ncu captures: keygen, split,
+    encrypt, two full-d decryptions, one CRT decryption, join, checked."""
+    import torch
+
+    import paper_2111_11924_gb300 as P
+
+    w = WORKLOAD
+    ctx = P.Context(0)
+    ks = ctx.keygen(w.K, w.nbits, w.e, w.key_seed)
+    d_msg = torch.from_numpy(w.message()).cuda()
+    chunks = ctx.split(w.nbits, d_msg)
+    cipher = ctx.encrypt_chunks(ks, chunks)
+    for _ in range(2):
+        plain = ctx.decrypt_chunks(ks, cipher)
+    plain_crt = ctx.decrypt_chunks(ks, cipher, use_crt=True)
+    back = ctx.join(w.nbits, plain, w.msg_bytes)
+    ctx.check()
+    assert torch.equal(plain, chunks) and torch.equal(plain_crt, chunks) and torch.equal(back, d_msg)
+    print("profile sequence ok")
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--ref-sample", type=int, default=512, help="chunks per oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="run the fixed launch sequence used for ncu captures and exit")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.profile:
+        return run_profile(args)
+    return run_reference(args) if args.impl == "reference" else run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,171 @@
+/*
+ * pmkrsa.h -- C ABI of the GB300 (sm_103a) PMKRSA library.
+ *
+ * PMKRSA ("A Variant RSA Acceleration with Parallelization", arXiv
+ * 2111.11924) splits a message into chunks and binds chunk t to one of K RSA
+ * key pairs; every chunk is then an independent modular exponentiation
+ * (Section 3.1, Algorithm 1).  This library runs that hot path on one GPU:
+ * split, encrypt (c = m^e mod N_k), decrypt (m = c^d mod N_k, full d or
+ * CRT) and join, as hand-written CUDA kernels on the caller's stream.
+ *
+ * Conventions shared by every call:
+ *   - Return value: PMK_OK (0) or a negative PMK_E* code.  Nothing aborts.
+ *   - d_* pointers are DEVICE pointers on the context's device, owned by the
+ *     caller (for example torch CUDA tensors); h_* pointers are HOST
+ *     pointers owned by the caller (pinned memory gives asynchronous copies).
+ *   - Device work is enqueued on `stream` (a cudaStream_t; NULL = legacy
+ *     default stream) and returns before it finishes.  Errors detected on
+ *     the device (an input chunk >= its modulus) are recorded in the
+ *     context and reported by pmk_status().
+ *   - Chunk buffers hold n_chunks x nbits/32 little-endian uint32 limbs,
+ *     chunk-major ("limb buffer").  Chunk t is bound to key t mod K, the
+ *     row-per-key reshape of the i x j plaintext matrix (Section 3.1).
+ *   - Calls on one context are not thread-safe; use one context per thread.
+ */
+#ifndef PMKRSA_H
+#define PMKRSA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PMK_OK 0
+#define PMK_EINVAL (-1)       /* null pointer, size mismatch, unsupported width, K = 0, even e ... */
+#define PMK_ERANGE (-2)       /* an input chunk was >= its modulus (device-detected) */
+#define PMK_ENOMEM (-3)       /* a device or host allocation failed */
+#define PMK_ECUDA (-4)        /* a CUDA runtime call failed */
+#define PMK_EUNSUPPORTED (-5) /* key width not compiled into this build */
+
+typedef struct pmk_ctx pmk_ctx;         /* one GPU: device status word, staging buffers */
+typedef struct pmk_keyset pmk_keyset;   /* K key pairs: host copy + device-resident tables */
+
+/* Create a context bound to CUDA device `cuda_device`.  Allocates a small
+ * device status word.  *out is set only on success. */
+int pmk_ctx_create(int cuda_device, pmk_ctx **out);
+/* Release the context and its device memory.  NULL is ignored. */
+void pmk_ctx_destroy(pmk_ctx *ctx);
+
+/*
+ * Key initialisation (Section 1.1 steps 1a-1c; Algorithm 1 "Initialization").
+ * For each of K keys: primes p != q of exactly nbits/2 bits (two top bits
+ * set), N = pq, d = e^-1 mod (p-1)(q-1), plus the CRT values dp = d mod (p-1),
+ * dq = d mod (q-1), qinv = q^-1 mod p.  Randomness is SplitMix64 seeded with
+ * `seed`; candidates pass trial division by the odd primes below 2000,
+ * gcd(e, p-1) = 1 and 40 Miller-Rabin rounds with bases (splitmix64()>>1)+2.
+ * Runs on the host; then uploads the key tables to the context's device.
+ *   nbits: 128..4096, a multiple of 128 (EUNSUPPORTED if not built).
+ *   e: odd, 3 <= e < 2^32.
+ */
+int pmk_keygen(pmk_ctx *ctx, uint32_t K, uint32_t nbits, uint64_t e, uint64_t seed, pmk_keyset **out);
+
+/*
+ * The same key initialisation as pmk_keygen, on the host only (no device,
+ * no context): writes the key material to caller-owned host arrays with the
+ * layout of pmk_keyset_export.  Any output pointer may be NULL.
+ */
+int pmk_keygen_host(uint32_t K, uint32_t nbits, uint64_t e, uint64_t seed, uint32_t *N, uint32_t *d, uint32_t *p,
+                    uint32_t *q, uint32_t *dp, uint32_t *dq, uint32_t *qinv);
+
+/*
+ * Build a key set from given primes (K x nbits/64 limbs each, key-major,
+ * little-endian): derives N, d, dp, dq, qinv and the device tables.  The
+ * caller guarantees p, q prime, p != q, each exactly nbits/2 bits with the
+ * top two bits set, gcd(e, p-1) = gcd(e, q-1) = 1 (EINVAL if a cheap check fails).
+ */
+int pmk_keyset_from_primes(pmk_ctx *ctx, uint32_t K, uint32_t nbits, uint64_t e, const uint32_t *p,
+                           const uint32_t *q, pmk_keyset **out);
+
+/* Copy the key material out (host arrays, key-major, little-endian limbs):
+ * N, d: K x nbits/32;  p, q, dp, dq, qinv: K x nbits/64.  Any pointer may be NULL. */
+int pmk_keyset_export(const pmk_keyset *ks, uint32_t *N, uint32_t *d, uint32_t *p, uint32_t *q, uint32_t *dp,
+                      uint32_t *dq, uint32_t *qinv);
+uint32_t pmk_keyset_num_keys(const pmk_keyset *ks);
+uint32_t pmk_keyset_nbits(const pmk_keyset *ks);
+uint64_t pmk_keyset_e(const pmk_keyset *ks);
+/* Release host and device memory of the key set.  NULL is ignored. */
+void pmk_keyset_free(pmk_keyset *ks);
+
+/* Plaintext bytes per chunk, nbits/8 - 1 (so every chunk is < N), and the
+ * chunk count ceil(msg_len / payload) of a message (Section 3.1 split). */
+size_t pmk_payload_bytes(uint32_t nbits);
+size_t pmk_num_chunks(size_t msg_len, uint32_t nbits);
+
+/*
+ * Split (Section 3.1): chunk t = message bytes [tP, min((t+1)P, L)) read as
+ * a little-endian integer, zero-extended to nbits/32 limbs.
+ *   d_msg: msg_len bytes (device).  d_chunks: n_chunks x nbits/32 uint32
+ *   (device), n_chunks must equal pmk_num_chunks(msg_len, nbits).
+ */
+int pmk_split(pmk_ctx *ctx, uint32_t nbits, const uint8_t *d_msg, size_t msg_len, uint32_t *d_chunks,
+              size_t n_chunks, void *stream);
+
+/*
+ * Join (the "merge and output" step of Section 3.3): inverse of pmk_split.
+ * Writes the low P bytes of every chunk, concatenated and cut to msg_len.
+ */
+int pmk_join(pmk_ctx *ctx, uint32_t nbits, const uint32_t *d_chunks, size_t n_chunks, uint8_t *d_msg,
+             size_t msg_len, void *stream);
+
+/*
+ * Encryption (Algorithm 1 "Encryption", c = m^e mod N; Algorithm 2 over
+ * Algorithm 3 Montgomery products): d_out[t] = d_in[t]^e mod N_{t mod K}.
+ * d_in, d_out: n_chunks limb buffers (device); they may be the same buffer.
+ * A chunk >= N is reported as PMK_ERANGE by pmk_status().
+ */
+int pmk_encrypt_chunks(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_in, uint32_t *d_out,
+                       size_t n_chunks, void *stream);
+
+/*
+ * Decryption (Algorithm 1 "Decryption", m = c^d mod N):
+ * d_out[t] = d_in[t]^{d_k} mod N_k, k = t mod K.  use_crt = 0: one
+ * full-width exponentiation; use_crt = 1: the CRT form of Section 2.1
+ * (two half-width exponentiations and Garner's recombination), bit-identical.
+ * With use_crt = 1, d_in and d_out must not overlap.
+ */
+int pmk_decrypt_chunks(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_in, uint32_t *d_out,
+                       size_t n_chunks, int use_crt, void *stream);
+
+/*
+ * Whole-message calls on HOST buffers: copy in, split/encrypt (or
+ * decrypt/join) on the device, copy out, synchronise the stream.  The
+ * context keeps grow-only device staging buffers between calls.
+ *   h_cipher: n_chunks x nbits/32 uint32 with n_chunks = pmk_num_chunks(msg_len, nbits).
+ * Returns the device status as pmk_status() would.
+ */
+int pmk_encrypt_message_host(pmk_ctx *ctx, const pmk_keyset *ks, const uint8_t *h_msg, size_t msg_len,
+                             uint32_t *h_cipher, size_t n_chunks, void *stream);
+int pmk_decrypt_message_host(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *h_cipher, size_t n_chunks,
+                             uint8_t *h_msg, size_t msg_len, int use_crt, void *stream);
+
+/* Synchronise `stream`, then return (and clear) the first device-side error
+ * recorded since the last call: PMK_OK or PMK_ERANGE; PMK_ECUDA if a CUDA
+ * call fails. */
+int pmk_status(pmk_ctx *ctx, void *stream);
+
+/* Static description of an error code. */
+const char *pmk_strerror(int code);
+
+/*
+ * Integer-pipe peak of this GPU, measured by the library's own
+ * dependency-free 32x32->64 multiply-accumulate loop: MACs per clock per SM,
+ * the SM clock seen during the loop (MHz) and the SM count.  Used as the
+ * roofline denominator of the modular-exponentiation kernels.
+ */
+int pmk_measure_int_peak(pmk_ctx *ctx, double *macs_per_clk_per_sm, double *sm_mhz, int *num_sms);
+
+/*
+ * Launch geometry of the exponentiation kernels for one limb count
+ * (nbits/32 for full-width, nbits/64 for CRT halves): threads per
+ * instance, a power of two dividing 32 and the limb count.  0 restores the
+ * default.  Returns EUNSUPPORTED if that pair is not built.
+ */
+int pmk_set_threads_per_instance(pmk_ctx *ctx, uint32_t limbs, uint32_t tpi);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PMKRSA_H */

@@ -1,0 +1,447 @@
+// C ABI of the PMKRSA library (include/pmkrsa.h): argument checks, key-set
+// upload, and the order of kernel launches for each call.
+#include <cstring>
+#include <map>
+#include <new>
+
+#include "pmk_internal.h"
+
+struct pmk_ctx {
+  int device = 0;
+  uint32_t *d_status = nullptr;            // device-side error bits (pmk::kStatusRange)
+  uint8_t *d_msg = nullptr;                // staging of the *_host calls (grow-only)
+  size_t msg_cap = 0;
+  uint32_t *d_a = nullptr, *d_b = nullptr;
+  size_t a_cap = 0, b_cap = 0;             // in words
+  std::map<uint32_t, uint32_t> tpi;        // limb count -> threads per instance override
+};
+
+struct pmk_keyset {
+  int device = 0;
+  uint32_t K = 0, nbits = 0;
+  uint64_t e = 0;
+  std::vector<pmk::HostKey> keys;
+  uint32_t *d_blob = nullptr;              // every key's limbs and schedules
+  pmk::KeyDev *d_keys = nullptr;           // K device key views into d_blob
+};
+
+namespace {
+
+using pmk::HostKey;
+using pmk::KeyDev;
+
+// Makes the context's device current for the duration of a call.
+class DeviceGuard {
+ public:
+  explicit DeviceGuard(int dev) {
+    ok_ = cudaGetDevice(&prev_) == cudaSuccess && (prev_ == dev || cudaSetDevice(dev) == cudaSuccess);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (ok_ && cudaGetDevice(&cur) == cudaSuccess && cur != prev_) cudaSetDevice(prev_);
+  }
+  bool ok() const { return ok_; }
+
+ private:
+  int prev_ = 0;
+  bool ok_ = false;
+};
+
+cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+bool overlap(const void *a, size_t na, const void *b, size_t nb) {
+  const char *x = static_cast<const char *>(a), *y = static_cast<const char *>(b);
+  return x < y + nb && y < x + na;
+}
+
+int grow(void **buf, size_t *cap, size_t bytes) {
+  if (*cap >= bytes) return PMK_OK;
+  if (*buf) cudaFree(*buf);
+  *buf = nullptr;
+  *cap = 0;
+  if (cudaMalloc(buf, bytes) != cudaSuccess) return PMK_ENOMEM;
+  *cap = bytes;
+  return PMK_OK;
+}
+
+// Threads per instance for an exponentiation over `limbs` limbs: the
+// context's override when that geometry is built for this mode, else the default.
+uint32_t tpi_for(const pmk_ctx *ctx, uint32_t limbs, bool crt) {
+  auto it = ctx->tpi.find(limbs);
+  if (it != ctx->tpi.end() && pmk::modexp_built(limbs, it->second, crt)) return it->second;
+  return pmk::default_tpi(limbs);
+}
+
+size_t push(std::vector<uint32_t> &blob, const std::vector<uint32_t> &v) {
+  while (blob.size() % 4) blob.push_back(0);  // 16-byte alignment for vector loads
+  const size_t off = blob.size();
+  blob.insert(blob.end(), v.begin(), v.end());
+  return off;
+}
+
+int upload(pmk_keyset *ks) {
+  std::vector<uint32_t> blob;
+  struct Offs {
+    size_t N, R2, se, sd, P[2], R2h[2], R3h[2], sh[2], qm;
+  };
+  std::vector<Offs> offs(ks->K);
+  for (uint32_t k = 0; k < ks->K; k++) {
+    const HostKey &h = ks->keys[k];
+    Offs &o = offs[k];
+    o.N = push(blob, h.N);
+    o.R2 = push(blob, h.R2);
+    o.se = push(blob, h.sched_e.steps);
+    o.sd = push(blob, h.sched_d.steps);
+    o.P[0] = push(blob, h.p);
+    o.P[1] = push(blob, h.q);
+    for (int i = 0; i < 2; i++) {
+      o.R2h[i] = push(blob, h.R2h[i]);
+      o.R3h[i] = push(blob, h.R3h[i]);
+      o.sh[i] = push(blob, h.sched_h[i].steps);
+    }
+    o.qm = push(blob, h.qinv_m);
+  }
+  if (cudaMalloc(&ks->d_blob, blob.size() * 4) != cudaSuccess) return PMK_ENOMEM;
+  if (cudaMemcpy(ks->d_blob, blob.data(), blob.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) return PMK_ECUDA;
+  std::vector<KeyDev> kd(ks->K);
+  for (uint32_t k = 0; k < ks->K; k++) {
+    const HostKey &h = ks->keys[k];
+    const Offs &o = offs[k];
+    KeyDev &d = kd[k];
+    const uint32_t *b = ks->d_blob;
+    d.N = b + o.N;
+    d.R2 = b + o.R2;
+    d.sched_e = b + o.se;
+    d.sched_d = b + o.sd;
+    d.qinv_m = b + o.qm;
+    d.n0 = h.n0;
+    d.nsteps_e = (uint32_t)h.sched_e.steps.size();
+    d.nsteps_d = (uint32_t)h.sched_d.steps.size();
+    d.maxidx_e = h.sched_e.maxidx;
+    d.maxidx_d = h.sched_d.maxidx;
+    for (int i = 0; i < 2; i++) {
+      d.P[i] = b + o.P[i];
+      d.R2h[i] = b + o.R2h[i];
+      d.R3h[i] = b + o.R3h[i];
+      d.sched_h[i] = b + o.sh[i];
+      d.n0h[i] = h.n0h[i];
+      d.nsteps_h[i] = (uint32_t)h.sched_h[i].steps.size();
+      d.maxidx_h[i] = h.sched_h[i].maxidx;
+    }
+  }
+  if (cudaMalloc(&ks->d_keys, sizeof(KeyDev) * ks->K) != cudaSuccess) return PMK_ENOMEM;
+  if (cudaMemcpy(ks->d_keys, kd.data(), sizeof(KeyDev) * ks->K, cudaMemcpyHostToDevice) != cudaSuccess)
+    return PMK_ECUDA;
+  return PMK_OK;
+}
+
+int finish_keyset(pmk_ctx *ctx, pmk_keyset *ks, pmk_keyset **out) {
+  DeviceGuard g(ctx->device);
+  int rc = g.ok() ? upload(ks) : PMK_ECUDA;
+  if (rc != PMK_OK) {
+    pmk_keyset_free(ks);
+    return rc;
+  }
+  *out = ks;
+  return PMK_OK;
+}
+
+bool width_built(uint32_t nbits) {
+  return pmk::default_tpi(nbits / 32) != 0 && pmk::default_tpi(nbits / 64) != 0;
+}
+
+int check_chunk_call(const pmk_ctx *ctx, const pmk_keyset *ks, const void *in, const void *out) {
+  if (!ctx || !ks) return PMK_EINVAL;
+  if (ks->device != ctx->device) return PMK_EINVAL;
+  if (!in || !out || !aligned16(in) || !aligned16(out)) return PMK_EINVAL;
+  return PMK_OK;
+}
+
+int enqueue_encrypt(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *in, uint32_t *out, size_t n, cudaStream_t st) {
+  const uint32_t S = ks->nbits / 32;
+  int rc = pmk::launch_range_check(ks->d_keys, ks->K, S, in, n, ctx->d_status, st);
+  if (rc == PMK_OK) rc = pmk::launch_modexp(pmk::ExpMode::kEncrypt, S, tpi_for(ctx, S, false), ks->d_keys, ks->K, in, out, n, st);
+  return rc;
+}
+
+int enqueue_decrypt(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *in, uint32_t *out, size_t n, int use_crt,
+                    cudaStream_t st) {
+  const uint32_t S = ks->nbits / 32;
+  int rc = pmk::launch_range_check(ks->d_keys, ks->K, S, in, n, ctx->d_status, st);
+  if (rc != PMK_OK) return rc;
+  if (!use_crt) return pmk::launch_modexp(pmk::ExpMode::kDecrypt, S, tpi_for(ctx, S, false), ks->d_keys, ks->K, in, out, n, st);
+  const uint32_t H = S / 2;
+  rc = pmk::launch_modexp(pmk::ExpMode::kCrtHalf, H, tpi_for(ctx, H, true), ks->d_keys, ks->K, in, out, n, st);
+  if (rc == PMK_OK) rc = pmk::launch_garner(H, ks->d_keys, ks->K, out, n, st);
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pmk_ctx_create(int cuda_device, pmk_ctx **out) {
+  if (!out) return PMK_EINVAL;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess) return PMK_ECUDA;
+  if (cuda_device < 0 || cuda_device >= count) return PMK_EINVAL;
+  pmk_ctx *ctx = new (std::nothrow) pmk_ctx();
+  if (!ctx) return PMK_ENOMEM;
+  ctx->device = cuda_device;
+  DeviceGuard g(cuda_device);
+  if (!g.ok()) {
+    delete ctx;
+    return PMK_ECUDA;
+  }
+  if (cudaMalloc(&ctx->d_status, sizeof(uint32_t)) != cudaSuccess ||
+      cudaMemset(ctx->d_status, 0, sizeof(uint32_t)) != cudaSuccess) {
+    pmk_ctx_destroy(ctx);
+    return PMK_ENOMEM;
+  }
+  *out = ctx;
+  return PMK_OK;
+}
+
+void pmk_ctx_destroy(pmk_ctx *ctx) {
+  if (!ctx) return;
+  DeviceGuard g(ctx->device);
+  cudaFree(ctx->d_status);
+  cudaFree(ctx->d_msg);
+  cudaFree(ctx->d_a);
+  cudaFree(ctx->d_b);
+  delete ctx;
+}
+
+int pmk_keygen(pmk_ctx *ctx, uint32_t K, uint32_t nbits, uint64_t e, uint64_t seed, pmk_keyset **out) {
+  if (!ctx || !out) return PMK_EINVAL;
+  if (K == 0 || nbits < 128 || nbits > 4096 || nbits % 128 || e < 3 || !(e & 1) || (e >> 32)) return PMK_EINVAL;
+  if (!width_built(nbits)) return PMK_EUNSUPPORTED;
+  try {
+    pmk_keyset *ks = new pmk_keyset();
+    ks->device = ctx->device;
+    ks->K = K;
+    ks->nbits = nbits;
+    ks->e = e;
+    int rc = pmk::host_keygen(K, nbits, e, seed, ks->keys);
+    if (rc != PMK_OK) {
+      delete ks;
+      return rc;
+    }
+    return finish_keyset(ctx, ks, out);
+  } catch (const std::bad_alloc &) {
+    return PMK_ENOMEM;
+  }
+}
+
+int pmk_keygen_host(uint32_t K, uint32_t nbits, uint64_t e, uint64_t seed, uint32_t *N, uint32_t *d, uint32_t *p,
+                    uint32_t *q, uint32_t *dp, uint32_t *dq, uint32_t *qinv) {
+  if (K == 0 || nbits < 128 || nbits > 4096 || nbits % 128 || e < 3 || !(e & 1) || (e >> 32)) return PMK_EINVAL;
+  try {
+    pmk_keyset ks;
+    ks.K = K;
+    ks.nbits = nbits;
+    ks.e = e;
+    int rc = pmk::host_keygen(K, nbits, e, seed, ks.keys);
+    if (rc != PMK_OK) return rc;
+    return pmk_keyset_export(&ks, N, d, p, q, dp, dq, qinv);
+  } catch (const std::bad_alloc &) {
+    return PMK_ENOMEM;
+  }
+}
+
+int pmk_keyset_from_primes(pmk_ctx *ctx, uint32_t K, uint32_t nbits, uint64_t e, const uint32_t *p,
+                           const uint32_t *q, pmk_keyset **out) {
+  if (!ctx || !out || !p || !q || K == 0) return PMK_EINVAL;
+  if (nbits < 128 || nbits > 4096 || nbits % 128 || e < 3 || !(e & 1) || (e >> 32)) return PMK_EINVAL;
+  if (!width_built(nbits)) return PMK_EUNSUPPORTED;
+  try {
+    pmk_keyset *ks = new pmk_keyset();
+    ks->device = ctx->device;
+    ks->K = K;
+    ks->nbits = nbits;
+    ks->e = e;
+    ks->keys.resize(K);
+    const size_t h = nbits / 64;
+    for (uint32_t k = 0; k < K; k++) {
+      int rc = pmk::host_from_primes(nbits, e, p + k * h, q + k * h, ks->keys[k]);
+      if (rc != PMK_OK) {
+        delete ks;
+        return rc;
+      }
+    }
+    return finish_keyset(ctx, ks, out);
+  } catch (const std::bad_alloc &) {
+    return PMK_ENOMEM;
+  }
+}
+
+int pmk_keyset_export(const pmk_keyset *ks, uint32_t *N, uint32_t *d, uint32_t *p, uint32_t *q, uint32_t *dp,
+                      uint32_t *dq, uint32_t *qinv) {
+  if (!ks) return PMK_EINVAL;
+  const size_t s = ks->nbits / 32, h = s / 2;
+  for (uint32_t k = 0; k < ks->K; k++) {
+    const HostKey &x = ks->keys[k];
+    if (N) std::memcpy(N + k * s, x.N.data(), s * 4);
+    if (d) std::memcpy(d + k * s, x.d.data(), s * 4);
+    if (p) std::memcpy(p + k * h, x.p.data(), h * 4);
+    if (q) std::memcpy(q + k * h, x.q.data(), h * 4);
+    if (dp) std::memcpy(dp + k * h, x.dp.data(), h * 4);
+    if (dq) std::memcpy(dq + k * h, x.dq.data(), h * 4);
+    if (qinv) std::memcpy(qinv + k * h, x.qinv.data(), h * 4);
+  }
+  return PMK_OK;
+}
+
+uint32_t pmk_keyset_num_keys(const pmk_keyset *ks) { return ks ? ks->K : 0; }
+uint32_t pmk_keyset_nbits(const pmk_keyset *ks) { return ks ? ks->nbits : 0; }
+uint64_t pmk_keyset_e(const pmk_keyset *ks) { return ks ? ks->e : 0; }
+
+void pmk_keyset_free(pmk_keyset *ks) {
+  if (!ks) return;
+  {
+    DeviceGuard g(ks->device);
+    cudaFree(ks->d_blob);
+    cudaFree(ks->d_keys);
+  }
+  delete ks;
+}
+
+size_t pmk_payload_bytes(uint32_t nbits) { return nbits >= 16 ? nbits / 8 - 1 : 0; }
+
+size_t pmk_num_chunks(size_t msg_len, uint32_t nbits) {
+  const size_t P = pmk_payload_bytes(nbits);
+  return P ? (msg_len + P - 1) / P : 0;
+}
+
+int pmk_split(pmk_ctx *ctx, uint32_t nbits, const uint8_t *d_msg, size_t msg_len, uint32_t *d_chunks, size_t n_chunks,
+              void *stream) {
+  if (!ctx || nbits < 128 || nbits % 128 || nbits > 4096) return PMK_EINVAL;
+  if (n_chunks != pmk_num_chunks(msg_len, nbits)) return PMK_EINVAL;
+  if (n_chunks == 0) return PMK_OK;
+  if (!d_msg || !d_chunks) return PMK_EINVAL;
+  DeviceGuard g(ctx->device);
+  if (!g.ok()) return PMK_ECUDA;
+  return pmk::launch_split(nbits, d_msg, msg_len, d_chunks, n_chunks, as_stream(stream));
+}
+
+int pmk_join(pmk_ctx *ctx, uint32_t nbits, const uint32_t *d_chunks, size_t n_chunks, uint8_t *d_msg, size_t msg_len,
+             void *stream) {
+  if (!ctx || nbits < 128 || nbits % 128 || nbits > 4096) return PMK_EINVAL;
+  if (n_chunks != pmk_num_chunks(msg_len, nbits)) return PMK_EINVAL;
+  if (msg_len == 0) return PMK_OK;
+  if (!d_msg || !d_chunks) return PMK_EINVAL;
+  DeviceGuard g(ctx->device);
+  if (!g.ok()) return PMK_ECUDA;
+  return pmk::launch_join(nbits, d_chunks, n_chunks, d_msg, msg_len, as_stream(stream));
+}
+
+int pmk_encrypt_chunks(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_in, uint32_t *d_out, size_t n_chunks,
+                       void *stream) {
+  if (n_chunks == 0) return (ctx && ks) ? PMK_OK : PMK_EINVAL;
+  int rc = check_chunk_call(ctx, ks, d_in, d_out);
+  if (rc != PMK_OK) return rc;
+  DeviceGuard g(ctx->device);
+  if (!g.ok()) return PMK_ECUDA;
+  return enqueue_encrypt(ctx, ks, d_in, d_out, n_chunks, as_stream(stream));
+}
+
+int pmk_decrypt_chunks(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_in, uint32_t *d_out, size_t n_chunks,
+                       int use_crt, void *stream) {
+  if (n_chunks == 0) return (ctx && ks) ? PMK_OK : PMK_EINVAL;
+  int rc = check_chunk_call(ctx, ks, d_in, d_out);
+  if (rc != PMK_OK) return rc;
+  const size_t bytes = n_chunks * (ks->nbits / 8);
+  if (use_crt && overlap(d_in, bytes, d_out, bytes)) return PMK_EINVAL;
+  DeviceGuard g(ctx->device);
+  if (!g.ok()) return PMK_ECUDA;
+  return enqueue_decrypt(ctx, ks, d_in, d_out, n_chunks, use_crt, as_stream(stream));
+}
+
+int pmk_status(pmk_ctx *ctx, void *stream) {
+  if (!ctx) return PMK_EINVAL;
+  DeviceGuard g(ctx->device);
+  if (!g.ok()) return PMK_ECUDA;
+  if (cudaStreamSynchronize(as_stream(stream)) != cudaSuccess) return PMK_ECUDA;
+  uint32_t st = 0;
+  if (cudaMemcpy(&st, ctx->d_status, sizeof st, cudaMemcpyDeviceToHost) != cudaSuccess) return PMK_ECUDA;
+  if (st == 0) return PMK_OK;
+  if (cudaMemset(ctx->d_status, 0, sizeof st) != cudaSuccess) return PMK_ECUDA;
+  return (st & pmk::kStatusRange) ? PMK_ERANGE : PMK_ECUDA;
+}
+
+int pmk_encrypt_message_host(pmk_ctx *ctx, const pmk_keyset *ks, const uint8_t *h_msg, size_t msg_len,
+                             uint32_t *h_cipher, size_t n_chunks, void *stream) {
+  if (!ctx || !ks || ks->device != ctx->device) return PMK_EINVAL;
+  if (n_chunks != pmk_num_chunks(msg_len, ks->nbits)) return PMK_EINVAL;
+  if (n_chunks == 0) return PMK_OK;
+  if (!h_msg || !h_cipher) return PMK_EINVAL;
+  DeviceGuard g(ctx->device);
+  if (!g.ok()) return PMK_ECUDA;
+  const size_t words = n_chunks * (ks->nbits / 32);
+  int rc = grow(reinterpret_cast<void **>(&ctx->d_msg), &ctx->msg_cap, msg_len);
+  if (rc == PMK_OK) rc = grow(reinterpret_cast<void **>(&ctx->d_a), &ctx->a_cap, words * 4);
+  if (rc != PMK_OK) return rc;
+  cudaStream_t st = as_stream(stream);
+  if (cudaMemcpyAsync(ctx->d_msg, h_msg, msg_len, cudaMemcpyHostToDevice, st) != cudaSuccess) return PMK_ECUDA;
+  rc = pmk::launch_split(ks->nbits, ctx->d_msg, msg_len, ctx->d_a, n_chunks, st);
+  if (rc == PMK_OK) rc = enqueue_encrypt(ctx, ks, ctx->d_a, ctx->d_a, n_chunks, st);
+  if (rc != PMK_OK) return rc;
+  if (cudaMemcpyAsync(h_cipher, ctx->d_a, words * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) return PMK_ECUDA;
+  return pmk_status(ctx, stream);
+}
+
+int pmk_decrypt_message_host(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *h_cipher, size_t n_chunks,
+                             uint8_t *h_msg, size_t msg_len, int use_crt, void *stream) {
+  if (!ctx || !ks || ks->device != ctx->device) return PMK_EINVAL;
+  if (n_chunks != pmk_num_chunks(msg_len, ks->nbits)) return PMK_EINVAL;
+  if (n_chunks == 0) return PMK_OK;
+  if (!h_msg || !h_cipher) return PMK_EINVAL;
+  DeviceGuard g(ctx->device);
+  if (!g.ok()) return PMK_ECUDA;
+  const size_t words = n_chunks * (ks->nbits / 32);
+  int rc = grow(reinterpret_cast<void **>(&ctx->d_msg), &ctx->msg_cap, msg_len);
+  if (rc == PMK_OK) rc = grow(reinterpret_cast<void **>(&ctx->d_a), &ctx->a_cap, words * 4);
+  if (rc == PMK_OK) rc = grow(reinterpret_cast<void **>(&ctx->d_b), &ctx->b_cap, words * 4);
+  if (rc != PMK_OK) return rc;
+  cudaStream_t st = as_stream(stream);
+  if (cudaMemcpyAsync(ctx->d_a, h_cipher, words * 4, cudaMemcpyHostToDevice, st) != cudaSuccess) return PMK_ECUDA;
+  rc = enqueue_decrypt(ctx, ks, ctx->d_a, ctx->d_b, n_chunks, use_crt, st);
+  if (rc == PMK_OK) rc = pmk::launch_join(ks->nbits, ctx->d_b, n_chunks, ctx->d_msg, msg_len, st);
+  if (rc != PMK_OK) return rc;
+  if (cudaMemcpyAsync(h_msg, ctx->d_msg, msg_len, cudaMemcpyDeviceToHost, st) != cudaSuccess) return PMK_ECUDA;
+  return pmk_status(ctx, stream);
+}
+
+const char *pmk_strerror(int code) {
+  switch (code) {
+    case PMK_OK: return "ok";
+    case PMK_EINVAL: return "invalid argument";
+    case PMK_ERANGE: return "input chunk not below its modulus";
+    case PMK_ENOMEM: return "out of memory";
+    case PMK_ECUDA: return "CUDA runtime error";
+    case PMK_EUNSUPPORTED: return "key width or launch geometry not built";
+    default: return "unknown error";
+  }
+}
+
+int pmk_measure_int_peak(pmk_ctx *ctx, double *macs_per_clk_per_sm, double *sm_mhz, int *num_sms) {
+  if (!ctx || !macs_per_clk_per_sm || !sm_mhz || !num_sms) return PMK_EINVAL;
+  DeviceGuard g(ctx->device);
+  if (!g.ok()) return PMK_ECUDA;
+  return pmk::measure_int_peak(macs_per_clk_per_sm, sm_mhz, num_sms);
+}
+
+int pmk_set_threads_per_instance(pmk_ctx *ctx, uint32_t limbs, uint32_t tpi) {
+  if (!ctx) return PMK_EINVAL;
+  if (tpi == 0) {
+    ctx->tpi.erase(limbs);
+    return PMK_OK;
+  }
+  if (!pmk::modexp_supported(limbs, tpi)) return PMK_EUNSUPPORTED;
+  ctx->tpi[limbs] = tpi;
+  return PMK_OK;
+}
+
+}  // extern "C"

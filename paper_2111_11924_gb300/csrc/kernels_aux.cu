@@ -1,0 +1,251 @@
+// Split / join (HBM-bound byte <-> limb repacking), the input range check and
+// Garner's CRT recombination, plus the launcher of the exponentiation kernels.
+#include <algorithm>
+#include <mutex>
+#include <set>
+#include <utility>
+
+#include "modexp_kernels.cuh"
+
+namespace pmk {
+namespace {
+
+constexpr int kAuxThreads = 256;
+
+// Split (Section 3.1): word j of chunk t holds message bytes t P + 4j .. +3
+// (little-endian), zero past the chunk payload P or the message end L.
+// One thread per output word; a warp reads a contiguous byte range.
+__global__ void __launch_bounds__(kAuxThreads) k_split(const uint8_t *__restrict__ msg, long long L, int P, int S,
+                                                       uint32_t *__restrict__ chunks, long long nwords) {
+  long long w = (long long)blockIdx.x * kAuxThreads + threadIdx.x;
+  const long long stride = (long long)gridDim.x * kAuxThreads;
+  for (; w < nwords; w += stride) {
+    const long long t = w / S;
+    const int b0 = (int)(w - t * S) * 4;
+    uint32_t v = 0;
+    if (b0 < P) {
+      const long long o = t * P + b0;
+      const int cnt = (int)min((long long)min(4, P - b0), max(0LL, L - o));
+      for (int i = 0; i < cnt; i++) v |= (uint32_t)__ldg(msg + o + i) << (8 * i);
+    }
+    chunks[w] = v;
+  }
+}
+
+// Join: byte b of the message is byte (b mod P) of chunk b / P.  One thread
+// per 4 output bytes.
+__global__ void __launch_bounds__(kAuxThreads) k_join(const uint32_t *__restrict__ chunks, int P, int S,
+                                                      uint8_t *__restrict__ msg, long long L) {
+  long long q = (long long)blockIdx.x * kAuxThreads + threadIdx.x;
+  const long long stride = (long long)gridDim.x * kAuxThreads;
+  for (; 4 * q < L; q += stride) {
+    for (int i = 0; i < 4; i++) {
+      const long long b = 4 * q + i;
+      if (b >= L) break;
+      const long long t = b / P;
+      const int k = (int)(b - t * P);
+      msg[b] = (uint8_t)(__ldg(chunks + t * S + k / 4) >> (8 * (k % 4)));
+    }
+  }
+}
+
+// Flags chunks whose value is >= the modulus of their key (t mod K).
+__global__ void __launch_bounds__(kAuxThreads) k_range(const KeyDev *__restrict__ keys, uint32_t K, int S,
+                                                       const uint32_t *__restrict__ in, long long n,
+                                                       uint32_t *__restrict__ status) {
+  const long long t = (long long)blockIdx.x * kAuxThreads + threadIdx.x;
+  if (t >= n) return;
+  const uint32_t *x = in + t * S;
+  const uint32_t *N = keys[t % K].N;
+  int ge = 1;  // x == N counts as out of range
+  for (int i = S - 1; i >= 0; i--) {
+    const uint32_t xi = __ldg(x + i), ni = __ldg(N + i);
+    if (xi != ni) {
+      ge = xi > ni;
+      break;
+    }
+  }
+  if (ge) atomicOr(status, kStatusRange);
+}
+
+// Garner's recombination (Section 2.1 CRT equations): with m_p in the low half
+// of out[t] and m_q in the high half, out[t] <- m_q + q ((m_p - m_q) qinv mod p).
+// One thread per chunk; arrays sit in local memory (this kernel is a
+// negligible share of the CRT decryption).
+__global__ void __launch_bounds__(kAuxThreads) k_garner(const KeyDev *__restrict__ keys, uint32_t K, int H,
+                                                        uint32_t *__restrict__ out, long long n) {
+  const long long t = (long long)blockIdx.x * kAuxThreads + threadIdx.x;
+  if (t >= n) return;
+  const KeyDev &kd = keys[t % K];
+  const uint32_t *p = kd.P[0], *q = kd.P[1], *qm = kd.qinv_m;
+  const uint32_t n0 = kd.n0h[0];
+  uint32_t *o = out + t * 2 * H;
+  uint32_t mq[64], d[64], acc[128];
+  // mq mod p: m_q < q < 2p, so at most one subtraction
+  uint32_t borrow = 0;
+  for (int i = 0; i < H; i++) {
+    const uint64_t s = (uint64_t)o[H + i] - p[i] - borrow;
+    d[i] = (uint32_t)s;
+    borrow = (uint32_t)(s >> 63);
+    mq[i] = o[H + i];
+  }
+  if (!borrow)
+    for (int i = 0; i < H; i++) mq[i] = d[i];
+  // d = (m_p - (m_q mod p)) mod p
+  borrow = 0;
+  for (int i = 0; i < H; i++) {
+    const uint64_t s = (uint64_t)o[i] - mq[i] - borrow;
+    d[i] = (uint32_t)s;
+    borrow = (uint32_t)(s >> 63);
+  }
+  if (borrow) {
+    uint64_t c = 0;
+    for (int i = 0; i < H; i++) {
+      c += (uint64_t)d[i] + p[i];
+      d[i] = (uint32_t)c;
+      c >>= 32;
+    }
+  }
+  // h = MontMul(d, qinv R mod p) = d qinv mod p  (CIOS, single thread)
+  for (int i = 0; i < H + 2; i++) acc[i] = 0;
+  for (int i = 0; i < H; i++) {
+    uint64_t c = 0;
+    for (int j = 0; j < H; j++) {
+      c += (uint64_t)d[j] * qm[i] + acc[j];
+      acc[j] = (uint32_t)c;
+      c >>= 32;
+    }
+    c += acc[H];
+    acc[H] = (uint32_t)c;
+    acc[H + 1] = (uint32_t)(c >> 32);
+    const uint32_t m = acc[0] * n0;
+    c = ((uint64_t)m * p[0] + acc[0]) >> 32;
+    for (int j = 1; j < H; j++) {
+      c += (uint64_t)m * p[j] + acc[j];
+      acc[j - 1] = (uint32_t)c;
+      c >>= 32;
+    }
+    c += acc[H];
+    acc[H - 1] = (uint32_t)c;
+    acc[H] = acc[H + 1] + (uint32_t)(c >> 32);
+  }
+  // conditional subtraction -> h < p, into d
+  borrow = 0;
+  for (int i = 0; i < H; i++) {
+    const uint64_t s = (uint64_t)acc[i] - p[i] - borrow;
+    d[i] = (uint32_t)s;
+    borrow = (uint32_t)(s >> 63);
+  }
+  if (acc[H] == 0 && borrow)
+    for (int i = 0; i < H; i++) d[i] = acc[i];
+  // out = m_q + h q  (m_q re-read: it is the original high half)
+  for (int i = 0; i < 2 * H; i++) acc[i] = i < H ? o[H + i] : 0;
+  for (int i = 0; i < H; i++) {
+    uint64_t c = 0;
+    for (int j = 0; j < H; j++) {
+      c += (uint64_t)d[i] * q[j] + acc[i + j];
+      acc[i + j] = (uint32_t)c;
+      c >>= 32;
+    }
+    for (int j = i + H; j < 2 * H && c; j++) {
+      c += acc[j];
+      acc[j] = (uint32_t)c;
+      c >>= 32;
+    }
+  }
+  for (int i = 0; i < 2 * H; i++) o[i] = acc[i];
+}
+
+int grid_for(long long work, int threads) {
+  long long b = (work + threads - 1) / threads;
+  return (int)std::max(1LL, std::min(b, 152LL * 64));
+}
+
+int cuda_rc(cudaError_t e) { return e == cudaSuccess ? PMK_OK : PMK_ECUDA; }
+
+const ModexpEntry *find_entry(uint32_t limbs, uint32_t tpi, bool crt) {
+  int n = 0;
+  const ModexpEntry *list = crt ? modexp_entries_crt(&n) : modexp_entries_full(&n);
+  for (int i = 0; i < n; i++)
+    if (list[i].limbs == (int)limbs && list[i].tpi == (int)tpi) return &list[i];
+  return nullptr;
+}
+
+}  // namespace
+
+int launch_split(uint32_t nbits, const uint8_t *msg, size_t len, uint32_t *chunks, size_t n, cudaStream_t st) {
+  const int P = (int)(nbits / 8 - 1), S = (int)(nbits / 32);
+  const long long nw = (long long)n * S;
+  if (nw == 0) return PMK_OK;
+  k_split<<<grid_for(nw, kAuxThreads), kAuxThreads, 0, st>>>(msg, (long long)len, P, S, chunks, nw);
+  return cuda_rc(cudaGetLastError());
+}
+
+int launch_join(uint32_t nbits, const uint32_t *chunks, size_t n, uint8_t *msg, size_t len, cudaStream_t st) {
+  (void)n;
+  const int P = (int)(nbits / 8 - 1), S = (int)(nbits / 32);
+  if (len == 0) return PMK_OK;
+  k_join<<<grid_for(((long long)len + 3) / 4, kAuxThreads), kAuxThreads, 0, st>>>(chunks, P, S, msg, (long long)len);
+  return cuda_rc(cudaGetLastError());
+}
+
+int launch_range_check(const KeyDev *keys, uint32_t K, uint32_t s, const uint32_t *in, size_t n, uint32_t *status,
+                       cudaStream_t st) {
+  if (n == 0) return PMK_OK;
+  k_range<<<(unsigned)((n + kAuxThreads - 1) / kAuxThreads), kAuxThreads, 0, st>>>(keys, K, (int)s, in, (long long)n,
+                                                                                   status);
+  return cuda_rc(cudaGetLastError());
+}
+
+int launch_garner(uint32_t half_limbs, const KeyDev *keys, uint32_t K, uint32_t *out, size_t n, cudaStream_t st) {
+  if (n == 0) return PMK_OK;
+  if (half_limbs > 64) return PMK_EUNSUPPORTED;
+  k_garner<<<(unsigned)((n + kAuxThreads - 1) / kAuxThreads), kAuxThreads, 0, st>>>(keys, K, (int)half_limbs, out,
+                                                                                    (long long)n);
+  return cuda_rc(cudaGetLastError());
+}
+
+bool modexp_built(uint32_t limbs, uint32_t tpi, bool crt) { return find_entry(limbs, tpi, crt) != nullptr; }
+
+bool modexp_supported(uint32_t limbs, uint32_t tpi) {
+  return find_entry(limbs, tpi, false) != nullptr || find_entry(limbs, tpi, true) != nullptr;
+}
+
+uint32_t default_tpi(uint32_t limbs) {
+  switch (limbs) {
+    case 2: case 4: case 8: case 16: return 2;
+    case 32: return 4;
+    case 48: case 64: case 96: return 8;
+    case 128: return 16;
+    default: return 0;
+  }
+}
+
+int launch_modexp(ExpMode mode, uint32_t limbs, uint32_t tpi, const KeyDev *keys, uint32_t K, const uint32_t *in,
+                  uint32_t *out, size_t n, cudaStream_t st) {
+  if (n == 0) return PMK_OK;
+  const bool crt = mode == ExpMode::kCrtHalf;
+  const ModexpEntry *e = find_entry(limbs, tpi, crt);
+  if (!e) return PMK_EUNSUPPORTED;
+  static std::mutex mu;
+  static std::set<std::pair<const void *, int>> configured;  // (kernel, device) with the smem limit raised
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PMK_ECUDA;
+    if (!configured.count({e->fn, dev})) {
+      cudaError_t err = cudaFuncSetAttribute(e->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e->smem);
+      if (err != cudaSuccess) return PMK_ECUDA;
+      configured.insert({e->fn, dev});
+    }
+  }
+  const long long per_key = ((long long)n + K - 1) / K;
+  const int ipb = dev::kThreads / e->tpi;
+  dim3 grid((unsigned)((per_key + ipb - 1) / ipb), crt ? 2 * K : K);
+  long long nl = (long long)n;
+  int enc = mode == ExpMode::kEncrypt ? 1 : 0;
+  void *args[] = {(void *)&keys, (void *)&K, (void *)&in, (void *)&out, (void *)&nl, (void *)&enc};
+  return cuda_rc(cudaLaunchKernel(e->fn, grid, dim3(dev::kThreads), args, e->smem, st));
+}
+
+}  // namespace pmk

@@ -1,0 +1,433 @@
+// Host key initialisation for PMKRSA (Section 1.1 steps 1a-1c and Algorithm 1
+// "Initialization"), the Montgomery constants the kernels need, and the
+// sliding-window exponent schedules.
+//
+// Arithmetic here is the library's own: 64-bit limbs with 128-bit products,
+// Montgomery multiplication for Miller-Rabin and Fermat inversion, and the
+// small-exponent identity d = (k phi + 1) / e for the private exponent.  It
+// needs no general division routine.
+//
+// Reading of the unspecified parts of key generation (the paper draws from
+// /dev/random, Section 3.3): SplitMix64 (Steele, Lea, Flood 2014); key k uses
+// its own stream seeded by the k-th output of a master stream seeded by the
+// caller, so keys are generated in parallel (Section 3.3 uses OpenMP).  A
+// prime candidate is nbits/128 SplitMix64 words, little-endian, with its top
+// two bits and bit 0 set; it is rejected if an odd prime below 2000 divides
+// it, then if gcd(e, cand - 1) != 1, then by 40 Miller-Rabin rounds with bases
+// (splitmix64() >> 1) + 2.  q is redrawn while q == p.
+#include <algorithm>
+#include <cstring>
+#include <thread>
+
+#include "pmk_internal.h"
+
+namespace pmk {
+namespace {
+
+using u64 = uint64_t;
+using u128 = unsigned __int128;
+
+u64 splitmix64(u64 &state) {
+  u64 z = (state += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// ---- fixed-width unsigned arithmetic on n 64-bit limbs ----
+
+int cmp(const u64 *a, const u64 *b, int n) {
+  for (int i = n - 1; i >= 0; i--)
+    if (a[i] != b[i]) return a[i] < b[i] ? -1 : 1;
+  return 0;
+}
+
+u64 sub(u64 *r, const u64 *a, const u64 *b, int n) {
+  u64 borrow = 0;
+  for (int i = 0; i < n; i++) {
+    u128 d = (u128)a[i] - b[i] - borrow;
+    r[i] = (u64)d;
+    borrow = (u64)(d >> 127);
+  }
+  return borrow;
+}
+
+u64 mod_small(const u64 *a, int n, u64 m) {
+  u128 r = 0;
+  for (int i = n - 1; i >= 0; i--) r = ((r << 64) | a[i]) % m;
+  return (u64)r;
+}
+
+// r = 2 r mod m (r < m)
+void dbl_mod(u64 *r, const u64 *m, int n) {
+  u64 top = r[n - 1] >> 63;
+  for (int i = n - 1; i > 0; i--) r[i] = (r[i] << 1) | (r[i - 1] >> 63);
+  r[0] <<= 1;
+  if (top || cmp(r, m, n) >= 0) sub(r, r, m, n);
+}
+
+// Montgomery arithmetic modulo an odd m with R = 2^(64 n).
+struct Mont {
+  int n;
+  std::vector<u64> m, r2;  // r2 = R^2 mod m
+  u64 m0inv;               // -m^-1 mod 2^64
+  explicit Mont(const std::vector<u64> &mod) : n((int)mod.size()), m(mod), r2(mod.size(), 0) {
+    u64 inv = m[0];  // Newton: inv = m^-1 mod 2^64
+    for (int i = 0; i < 6; i++) inv *= 2 - m[0] * inv;
+    m0inv = (u64)0 - inv;
+    r2[0] = 1;
+    for (int i = 0; i < 128 * n; i++) dbl_mod(r2.data(), m.data(), n);
+  }
+  // out = a b R^-1 mod m  (CIOS, a, b < m)
+  void mul(u64 *out, const u64 *a, const u64 *b) const {
+    std::vector<u64> t(n + 2, 0);
+    for (int i = 0; i < n; i++) {
+      u128 c = 0;
+      for (int j = 0; j < n; j++) {
+        c += (u128)a[j] * b[i] + t[j];
+        t[j] = (u64)c;
+        c >>= 64;
+      }
+      c += t[n];
+      t[n] = (u64)c;
+      t[n + 1] = (u64)(c >> 64);
+      u64 q = t[0] * m0inv;
+      c = ((u128)q * m[0] + t[0]) >> 64;
+      for (int j = 1; j < n; j++) {
+        c += (u128)q * m[j] + t[j];
+        t[j - 1] = (u64)c;
+        c >>= 64;
+      }
+      c += t[n];
+      t[n - 1] = (u64)c;
+      t[n] = t[n + 1] + (u64)(c >> 64);
+    }
+    if (t[n] || cmp(t.data(), m.data(), n) >= 0) sub(t.data(), t.data(), m.data(), n);
+    std::memcpy(out, t.data(), sizeof(u64) * n);
+  }
+  void to_mont(u64 *out, const u64 *a) const { mul(out, a, r2.data()); }
+  void from_mont(u64 *out, const u64 *a) const {
+    std::vector<u64> one(n, 0);
+    one[0] = 1;
+    mul(out, a, one.data());
+  }
+  // out = b^x mod m, plain left-to-right binary over the bits of x (nx limbs)
+  void pow(u64 *out, const u64 *b, const u64 *x, int nx) const {
+    std::vector<u64> base(n), acc(n), one(n, 0);
+    one[0] = 1;
+    to_mont(base.data(), b);
+    to_mont(acc.data(), one.data());
+    for (int i = 64 * nx - 1; i >= 0; i--) {
+      mul(acc.data(), acc.data(), acc.data());
+      if ((x[i / 64] >> (i % 64)) & 1) mul(acc.data(), acc.data(), base.data());
+    }
+    from_mont(out, acc.data());
+  }
+};
+
+bool miller_rabin_round(const Mont &mt, u64 base) {
+  int n = mt.n;
+  std::vector<u64> n1(mt.m), one(n, 0), d(n), x(n), b(n, 0);
+  one[0] = 1;
+  sub(n1.data(), mt.m.data(), one.data(), n);
+  int s = 0;
+  while (!((n1[s / 64] >> (s % 64)) & 1)) s++;
+  for (int i = 0; i < n; i++) {  // d = (m - 1) >> s
+    int bit = s + 64 * i, w = bit / 64, sh = bit % 64;
+    u64 lo = w < n ? n1[w] >> sh : 0;
+    u64 hi = (w + 1 < n && sh) ? n1[w + 1] << (64 - sh) : 0;
+    d[i] = lo | hi;
+  }
+  b[0] = base;
+  mt.pow(x.data(), b.data(), d.data(), n);
+  if (cmp(x.data(), one.data(), n) == 0 || cmp(x.data(), n1.data(), n) == 0) return true;
+  std::vector<u64> xm(n), n1m(n);
+  mt.to_mont(xm.data(), x.data());
+  mt.to_mont(n1m.data(), n1.data());
+  std::vector<u64> onem(n);
+  mt.to_mont(onem.data(), one.data());
+  for (int i = 1; i < s; i++) {
+    mt.mul(xm.data(), xm.data(), xm.data());
+    if (cmp(xm.data(), n1m.data(), n) == 0) return true;
+    if (cmp(xm.data(), onem.data(), n) == 0) return false;
+  }
+  return false;
+}
+
+u64 gcd64(u64 a, u64 b) {
+  while (b) {
+    u64 t = a % b;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+const std::vector<u64> &small_primes() {
+  static const std::vector<u64> primes = [] {
+    std::vector<bool> comp(2000, false);
+    std::vector<u64> v;
+    for (int i = 2; i < 2000; i++) {
+      if (comp[i]) continue;
+      if (i > 2) v.push_back(i);
+      for (int j = i * i; j < 2000; j += i) comp[j] = true;
+    }
+    return v;
+  }();
+  return primes;
+}
+
+std::vector<u64> gen_prime(u64 &rng, int bits, u64 e) {
+  int n = bits / 64;
+  std::vector<u64> p(n);
+  for (;;) {
+    for (int w = 0; w < n; w++) p[w] = splitmix64(rng);
+    p[n - 1] |= 0xC000000000000000ull;
+    p[0] |= 1;
+    bool composite = false;
+    for (u64 sp : small_primes())
+      if (mod_small(p.data(), n, sp) == 0) {
+        composite = true;
+        break;
+      }
+    if (composite) continue;
+    u64 r = mod_small(p.data(), n, e);           // (p - 1) mod e
+    r = (r + e - 1) % e;
+    if (gcd64(e, r) != 1) continue;
+    Mont mt(p);
+    bool ok = true;
+    for (int round = 0; round < 40 && ok; round++) ok = miller_rabin_round(mt, (splitmix64(rng) >> 1) + 2);
+    if (ok) return p;
+  }
+}
+
+// inverse of a modulo m (gcd 1), small word-size values
+u64 inv_small(u64 a, u64 m) {
+  __int128 t0 = 0, t1 = 1, r0 = m, r1 = a % m;
+  while (r1) {
+    __int128 q = r0 / r1, tmp;
+    tmp = r0 - q * r1; r0 = r1; r1 = tmp;
+    tmp = t0 - q * t1; t0 = t1; t1 = tmp;
+  }
+  if (t0 < 0) t0 += m;
+  return (u64)t0;
+}
+
+// x^-1 mod phi for a small x (here the public exponent), via
+// x^-1 = (k phi + 1) / x with k = -phi^-1 mod x.  phi has n limbs.
+std::vector<u64> inv_of_small(u64 x, const std::vector<u64> &phi) {
+  int n = (int)phi.size();
+  u64 k = (x - inv_small(mod_small(phi.data(), n, x), x)) % x;
+  std::vector<u64> t(n + 1, 0);
+  u128 c = 1;  // t = k phi + 1
+  for (int i = 0; i < n; i++) {
+    c += (u128)k * phi[i];
+    t[i] = (u64)c;
+    c >>= 64;
+  }
+  t[n] = (u64)c;
+  u128 rem = 0;  // exact division by x
+  for (int i = n; i >= 0; i--) {
+    u128 cur = (rem << 64) | t[i];
+    t[i] = (u64)(cur / x);
+    rem = cur % x;
+  }
+  t.resize(n);
+  return t;
+}
+
+std::vector<uint32_t> to32(const std::vector<u64> &a, size_t nlimbs32) {
+  std::vector<uint32_t> r(nlimbs32, 0);
+  for (size_t i = 0; i < a.size() && 2 * i < nlimbs32; i++) {
+    r[2 * i] = (uint32_t)a[i];
+    if (2 * i + 1 < nlimbs32) r[2 * i + 1] = (uint32_t)(a[i] >> 32);
+  }
+  return r;
+}
+
+std::vector<u64> to64(const uint32_t *a, size_t nlimbs32) {
+  std::vector<u64> r((nlimbs32 + 1) / 2, 0);
+  for (size_t i = 0; i < nlimbs32; i++) r[i / 2] |= (u64)a[i] << (32 * (i % 2));
+  return r;
+}
+
+std::vector<u64> mul_full(const std::vector<u64> &a, const std::vector<u64> &b) {
+  std::vector<u64> r(a.size() + b.size(), 0);
+  for (size_t i = 0; i < b.size(); i++) {
+    u128 c = 0;
+    for (size_t j = 0; j < a.size(); j++) {
+      c += (u128)a[j] * b[i] + r[i + j];
+      r[i + j] = (u64)c;
+      c >>= 64;
+    }
+    r[i + a.size()] = (u64)c;
+  }
+  return r;
+}
+
+std::vector<u64> minus_one(std::vector<u64> a) {
+  for (auto &w : a)
+    if (w-- != 0) break;
+  return a;
+}
+
+uint32_t neg_inv32(uint32_t m0) {
+  uint32_t inv = m0;
+  for (int i = 0; i < 5; i++) inv *= 2 - m0 * inv;
+  return 0u - inv;
+}
+
+// 2^(32 k) mod m for k = ks[...], by repeated doubling (m odd, n limbs)
+void pow2_mod(const std::vector<u64> &m, int bits_a, int bits_b, std::vector<u64> &ra, std::vector<u64> &rb) {
+  int n = (int)m.size();
+  std::vector<u64> r(n, 0);
+  r[0] = 1;
+  for (int i = 1; i <= std::max(bits_a, bits_b); i++) {
+    dbl_mod(r.data(), m.data(), n);
+    if (i == bits_a) ra = r;
+    if (i == bits_b) rb = r;
+  }
+}
+
+void finish_key(uint32_t nbits, u64 e, const std::vector<u64> &p, const std::vector<u64> &q, HostKey &k) {
+  size_t s = nbits / 32, h = s / 2;
+  std::vector<u64> p1 = minus_one(p), q1 = minus_one(q);
+  std::vector<u64> N = mul_full(p, q), phi = mul_full(p1, q1);
+  std::vector<u64> d = inv_of_small(e, phi);
+  std::vector<u64> dp = inv_of_small(e, p1), dq = inv_of_small(e, q1);  // = d mod (p-1), d mod (q-1)
+  // qinv = q^(p-2) mod p (Fermat); q < 2p, so q mod p is one conditional subtraction
+  int n = (int)p.size();
+  std::vector<u64> qm(q), pm2(p), qinv(n);
+  if (cmp(qm.data(), p.data(), n) >= 0) sub(qm.data(), qm.data(), p.data(), n);
+  std::vector<u64> two(n, 0);
+  two[0] = 2;
+  sub(pm2.data(), p.data(), two.data(), n);
+  Mont mp(p);
+  mp.pow(qinv.data(), qm.data(), pm2.data(), n);
+  k.N = to32(N, s);
+  k.d = to32(d, s);
+  k.p = to32(p, h);
+  k.q = to32(q, h);
+  k.dp = to32(dp, h);
+  k.dq = to32(dq, h);
+  k.qinv = to32(qinv, h);
+  // Montgomery constants (32-bit limb view)
+  k.n0 = neg_inv32(k.N[0]);
+  k.n0h[0] = neg_inv32(k.p[0]);
+  k.n0h[1] = neg_inv32(k.q[0]);
+  std::vector<u64> r2, unused;
+  pow2_mod(N, (int)(64 * s), (int)(64 * s), r2, unused);
+  k.R2 = to32(r2, s);
+  const std::vector<u64> *pq[2] = {&p, &q};
+  for (int i = 0; i < 2; i++) {
+    std::vector<u64> a, b;
+    pow2_mod(*pq[i], (int)(64 * h), (int)(96 * h), a, b);
+    k.R2h[i] = to32(a, h);
+    k.R3h[i] = to32(b, h);
+  }
+  std::vector<u64> qm_r(qinv);  // qinv * R_h mod p
+  for (size_t i = 0; i < 32 * h; i++) dbl_mod(qm_r.data(), p.data(), n);
+  k.qinv_m = to32(qm_r, h);
+  uint32_t ev[2] = {(uint32_t)e, (uint32_t)(e >> 32)};
+  k.sched_e = make_schedule(ev, 2);
+  k.sched_d = make_schedule(k.d.data(), (int)s);
+  k.sched_h[0] = make_schedule(k.dp.data(), (int)h);
+  k.sched_h[1] = make_schedule(k.dq.data(), (int)h);
+}
+
+bool valid_width(uint32_t nbits) { return nbits >= 128 && nbits <= 4096 && nbits % 128 == 0; }
+
+}  // namespace
+
+// Sliding-window recoding of an exponent, scanned from its top bit.  The
+// window width w <= 5 (at most 16 odd powers) minimises the product count
+// (table entries + multiplies) for this exponent.
+Schedule make_schedule(const uint32_t *exp, int nlimbs) {
+  int top = -1;
+  for (int i = 32 * nlimbs - 1; i >= 0; i--)
+    if ((exp[i / 32] >> (i % 32)) & 1) {
+      top = i;
+      break;
+    }
+  Schedule best;
+  size_t best_cost = ~(size_t)0;
+  if (top < 0) return best;  // exponent 0: empty schedule (callers reject it)
+  auto bit = [&](int i) { return (exp[i / 32] >> (i % 32)) & 1; };
+  for (int w = 1; w <= 5; w++) {
+    Schedule sc;
+    int i = top, pending = 0;
+    bool first = true;
+    size_t muls = 0;
+    while (i >= 0) {
+      if (!bit(i)) {
+        pending++;
+        i--;
+        continue;
+      }
+      int j = std::max(i - w + 1, 0);
+      while (!bit(j)) j++;
+      uint32_t v = 0;
+      for (int b = i; b >= j; b--) v = (v << 1) | bit(b);
+      uint32_t idx = (v - 1) / 2;
+      if (first) {
+        sc.steps.push_back(idx);
+        first = false;
+      } else {
+        sc.steps.push_back(((uint32_t)(pending + (i - j + 1)) << 8) | idx);
+        muls++;
+      }
+      sc.maxidx = std::max(sc.maxidx, idx);
+      pending = 0;
+      i = j - 1;
+    }
+    if (pending) sc.steps.push_back(((uint32_t)pending << 8) | 0xFFu);
+    size_t cost = muls + sc.maxidx + (sc.maxidx ? 1 : 0);
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = sc;
+    }
+  }
+  return best;
+}
+
+int host_keygen(uint32_t K, uint32_t nbits, uint64_t e, uint64_t seed, std::vector<HostKey> &out) {
+  if (K == 0 || !valid_width(nbits) || e < 3 || !(e & 1) || e >> 32) return PMK_EINVAL;
+  std::vector<u64> seeds(K);
+  u64 master = seed;
+  for (uint32_t k = 0; k < K; k++) seeds[k] = splitmix64(master);
+  out.assign(K, HostKey());
+  auto work = [&](uint32_t k) {
+    u64 rng = seeds[k];
+    std::vector<u64> p = gen_prime(rng, (int)nbits / 2, e), q;
+    do {
+      q = gen_prime(rng, (int)nbits / 2, e);
+    } while (cmp(p.data(), q.data(), (int)p.size()) == 0);
+    finish_key(nbits, e, p, q, out[k]);
+  };
+  unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  unsigned nt = std::min<unsigned>(hw, K);
+  std::vector<std::thread> pool;
+  for (unsigned t = 0; t < nt; t++)
+    pool.emplace_back([&, t] {
+      for (uint32_t k = t; k < K; k += nt) work(k);
+    });
+  for (auto &th : pool) th.join();
+  return PMK_OK;
+}
+
+int host_from_primes(uint32_t nbits, uint64_t e, const uint32_t *p32, const uint32_t *q32, HostKey &out) {
+  if (!valid_width(nbits) || e < 3 || !(e & 1) || e >> 32) return PMK_EINVAL;
+  size_t h = nbits / 64;
+  std::vector<u64> p = to64(p32, h), q = to64(q32, h);
+  int n = (int)p.size();
+  for (const auto *f : {&p, &q}) {
+    if (!((*f)[0] & 1) || ((*f)[n - 1] >> 62) != 3) return PMK_EINVAL;
+    u64 r = (mod_small(f->data(), n, e) + e - 1) % e;
+    if (gcd64(e, r) != 1) return PMK_EINVAL;
+  }
+  if (cmp(p.data(), q.data(), n) == 0) return PMK_EINVAL;
+  finish_key(nbits, e, p, q, out);
+  return PMK_OK;
+}
+
+}  // namespace pmk

@@ -1,0 +1,117 @@
+// Exponentiation kernels built on modexp_core.cuh, and the table that maps a
+// (mode, limb count, threads per instance) triple to an instantiation.
+#pragma once
+
+#include "modexp_core.cuh"
+
+namespace pmk {
+namespace dev {
+
+// Grid: blockIdx.y selects the key (full width) or key * 2 + half (CRT);
+// blockIdx.x * IPB + instance slot selects the j-th chunk of that key, chunk
+// t = key + j K.  Every block therefore serves one key: schedules, modulus and
+// control flow are uniform across it.
+//
+// FULL: out[t] = in[t]^E mod N_key, E = e (enc != 0) or d, S = nbits / 32.
+// CRT:  out[t][half] = in[t]^{d_p | d_q} mod (p | q) over S = nbits / 64
+//       limbs, input reduced via in mod p = hi R + lo -> MontMul(hi, R^3) +
+//       MontMul(lo, R^2) = in R mod p.  Garner combines the halves afterwards.
+template <int S, int TPI, bool CRT>
+__global__ void __launch_bounds__(kThreads) k_modexp(const KeyDev *__restrict__ keys, uint32_t K,
+                                                     const uint32_t *__restrict__ in, uint32_t *__restrict__ out,
+                                                     long long n, int enc) {
+  constexpr int L = S / TPI;
+  constexpr int IPB = kThreads / TPI;
+  constexpr int ROW = Layout<S>::kRow;
+  constexpr int INST = Layout<S>::kInst;
+  constexpr int W = CRT ? 2 * S : S;  // limbs per chunk in memory
+  extern __shared__ __align__(16) uint32_t smem[];
+  uint32_t *sR2 = smem, *sOne = smem + ROW, *sR3 = smem + 2 * ROW;
+  const uint32_t r = threadIdx.x % TPI, g = threadIdx.x / TPI;
+  uint32_t *tbl = smem + Layout<S>::kConstRows * ROW + g * INST;
+  uint32_t *ybuf = tbl + kTableMax * ROW;
+
+  const uint32_t key = CRT ? blockIdx.y >> 1 : blockIdx.y;
+  const uint32_t half = CRT ? blockIdx.y & 1 : 0;
+  const long long first = key + (long long)blockIdx.x * IPB * K;
+  if (first >= n) return;  // block-uniform: no instance of this block has a chunk
+  const KeyDev &kd = keys[key];
+  const uint32_t *M = CRT ? kd.P[half] : kd.N;
+  const uint32_t *R2 = CRT ? kd.R2h[half] : kd.R2;
+  const uint32_t *sched = CRT ? kd.sched_h[half] : (enc ? kd.sched_e : kd.sched_d);
+  const uint32_t nsteps = CRT ? kd.nsteps_h[half] : (enc ? kd.nsteps_e : kd.nsteps_d);
+  const uint32_t maxidx = CRT ? kd.maxidx_h[half] : (enc ? kd.maxidx_e : kd.maxidx_d);
+  const uint32_t n0 = CRT ? kd.n0h[half] : kd.n0;
+
+  for (int i = threadIdx.x; i < S; i += kThreads) {
+    sR2[i] = __ldg(R2 + i);
+    sOne[i] = (i == 0);
+    if (CRT) sR3[i] = __ldg(kd.R3h[half] + i);
+  }
+  __syncthreads();
+
+  const long long t = first + (long long)g * K;
+  const bool active = t < n;
+  uint32_t nn[L], a[L];
+  load_slice_global<L>(nn, M, r);
+  if (!CRT) {
+    if (active) {
+      load_slice_global<L>(a, in + t * W, r);
+    } else {
+#pragma unroll
+      for (int j = 0; j < L; j++) a[j] = 0;
+    }
+    mont_mul<S, TPI>(a, sR2, nn, n0, r);  // x R mod N
+  } else {
+    uint32_t lo[L];
+    if (active) {
+      load_slice_global<L>(lo, in + t * W, r);
+      load_slice_global<L>(a, in + t * W + S, r);
+    } else {
+#pragma unroll
+      for (int j = 0; j < L; j++) lo[j] = a[j] = 0;
+    }
+    mont_mul<S, TPI>(a, sR3, nn, n0, r);   // hi R^2 mod p
+    mont_mul<S, TPI>(lo, sR2, nn, n0, r);  // lo R mod p
+    mod_add<L, TPI>(a, lo, nn, r);         // (hi R + lo) R mod p
+  }
+  exp_window<S, TPI>(a, tbl, ybuf, sched, nsteps, maxidx, nn, n0, r);
+  mont_mul<S, TPI>(a, sOne, nn, n0, r);  // leave the Montgomery domain
+  if (active) {
+    uint32_t *o = out + t * W + (CRT ? half * S : 0) + r * L;
+    if constexpr (L % 4 == 0) {
+#pragma unroll
+      for (int j = 0; j < L; j += 4) *reinterpret_cast<uint4 *>(o + j) = make_uint4(a[j], a[j + 1], a[j + 2], a[j + 3]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < L; j++) o[j] = a[j];
+    }
+  }
+}
+
+template <int S>
+constexpr size_t modexp_smem_bytes(int tpi) {
+  return sizeof(uint32_t) * ((size_t)Layout<S>::kConstRows * Layout<S>::kRow + (size_t)(kThreads / tpi) * Layout<S>::kInst);
+}
+
+}  // namespace dev
+
+// One compiled instantiation.
+struct ModexpEntry {
+  int limbs, tpi;
+  bool crt;
+  const void *fn;
+  size_t smem;
+};
+
+template <int S, int TPI, bool CRT>
+ModexpEntry make_entry() {
+  return ModexpEntry{S, TPI, CRT, reinterpret_cast<const void *>(&dev::k_modexp<S, TPI, CRT>),
+                     dev::modexp_smem_bytes<S>(TPI)};
+}
+
+// Instantiation lists live in separate translation units (compiled in parallel).
+const ModexpEntry *modexp_entries_full(int *count);
+const ModexpEntry *modexp_entries_crt(int *count);
+
+}  // namespace pmk

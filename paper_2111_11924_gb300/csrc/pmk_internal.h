@@ -1,0 +1,73 @@
+// Internal declarations shared by the host code and the CUDA kernels of the
+// PMKRSA library.  Nothing here is part of the C ABI (include/pmkrsa.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "pmkrsa.h"
+
+namespace pmk {
+
+// Error bits written by kernels into the context's device status word.
+enum : uint32_t { kStatusRange = 1u };
+
+// Exponent schedule for left-to-right sliding-window exponentiation.
+// steps[0] = index of the first odd power (a load, no squaring);
+// steps[i>0] = (nsq << 8) | idx : nsq squarings, then a multiply by the odd
+// power table entry idx (x^(2 idx + 1)); idx = 0xFF means no multiply.
+struct Schedule {
+  std::vector<uint32_t> steps;
+  uint32_t maxidx = 0;  // table entries 0..maxidx are needed
+};
+
+// One key pair on the host, 32-bit little-endian limbs.
+struct HostKey {
+  std::vector<uint32_t> N, d, p, q, dp, dq, qinv;  // N, d: s limbs; the rest s/2
+  // Montgomery data, R = 2^(32 s) for N and R_h = 2^(32 s/2) for p, q.
+  uint32_t n0 = 0, n0h[2] = {0, 0};                 // -M^-1 mod 2^32
+  std::vector<uint32_t> R2;                          // R^2 mod N
+  std::vector<uint32_t> R2h[2], R3h[2];              // R_h^2, R_h^3 mod p | q
+  std::vector<uint32_t> qinv_m;                      // qinv * R_h mod p
+  Schedule sched_e, sched_d, sched_h[2];             // e, d, dp, dq
+};
+
+// Device view of one key (pointers into the key set's device blob).
+struct KeyDev {
+  const uint32_t *N;
+  const uint32_t *R2;
+  const uint32_t *sched_e;
+  const uint32_t *sched_d;
+  const uint32_t *P[2];
+  const uint32_t *R2h[2];
+  const uint32_t *R3h[2];
+  const uint32_t *sched_h[2];
+  const uint32_t *qinv_m;
+  uint32_t n0, n0h[2];
+  uint32_t nsteps_e, nsteps_d, nsteps_h[2];
+  uint32_t maxidx_e, maxidx_d, maxidx_h[2];
+};
+
+// Host keygen (keygen.cpp).
+int host_keygen(uint32_t K, uint32_t nbits, uint64_t e, uint64_t seed, std::vector<HostKey> &out);
+int host_from_primes(uint32_t nbits, uint64_t e, const uint32_t *p, const uint32_t *q, HostKey &out);
+Schedule make_schedule(const uint32_t *exp, int nlimbs);
+
+// Kernel launchers (kernels_*.cu).  All return PMK_* codes.
+enum class ExpMode : int { kEncrypt = 0, kDecrypt = 1, kCrtHalf = 2 };
+int launch_split(uint32_t nbits, const uint8_t *msg, size_t len, uint32_t *chunks, size_t n, cudaStream_t st);
+int launch_join(uint32_t nbits, const uint32_t *chunks, size_t n, uint8_t *msg, size_t len, cudaStream_t st);
+int launch_range_check(const KeyDev *keys, uint32_t K, uint32_t s, const uint32_t *in, size_t n,
+                       uint32_t *status, cudaStream_t st);
+int launch_modexp(ExpMode mode, uint32_t limbs, uint32_t tpi, const KeyDev *keys, uint32_t K, const uint32_t *in,
+                  uint32_t *out, size_t n, cudaStream_t st);
+int launch_garner(uint32_t half_limbs, const KeyDev *keys, uint32_t K, uint32_t *out, size_t n, cudaStream_t st);
+bool modexp_supported(uint32_t limbs, uint32_t tpi);
+bool modexp_built(uint32_t limbs, uint32_t tpi, bool crt);
+uint32_t default_tpi(uint32_t limbs);
+int measure_int_peak(double *macs_per_clk_per_sm, double *sm_mhz, int *num_sms);
+
+}  // namespace pmk

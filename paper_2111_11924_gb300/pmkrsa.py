@@ -1,0 +1,276 @@
+"""ctypes binding of libpmkrsa.so: one Python call per C-ABI entry point.
+
+Device buffers are torch CUDA tensors (limb buffers as int32 tensors holding
+uint32 bit patterns, messages as uint8 tensors); the CUDA stream is torch's
+current stream on the context's device unless one is given.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import _native_build
+
+PMK_OK, PMK_EINVAL, PMK_ERANGE, PMK_ENOMEM, PMK_ECUDA, PMK_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
+
+_lib = None
+
+
+class PMKError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code})" if what else f"{strerror(code)} ({code})")
+
+
+def load_library() -> ctypes.CDLL:
+    """Load the in-tree native library; raise if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _native_build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"native PMKRSA library not built ({path}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P32 = ctypes.POINTER(ctypes.c_uint32)
+    vp, u32, u64, sz, i = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_size_t, ctypes.c_int
+    sig = {
+        "pmk_ctx_create": (i, [i, ctypes.POINTER(vp)]),
+        "pmk_ctx_destroy": (None, [vp]),
+        "pmk_keygen": (i, [vp, u32, u32, u64, u64, ctypes.POINTER(vp)]),
+        "pmk_keygen_host": (i, [u32, u32, u64, u64, P32, P32, P32, P32, P32, P32, P32]),
+        "pmk_keyset_from_primes": (i, [vp, u32, u32, u64, P32, P32, ctypes.POINTER(vp)]),
+        "pmk_keyset_export": (i, [vp, P32, P32, P32, P32, P32, P32, P32]),
+        "pmk_keyset_num_keys": (u32, [vp]),
+        "pmk_keyset_nbits": (u32, [vp]),
+        "pmk_keyset_e": (u64, [vp]),
+        "pmk_keyset_free": (None, [vp]),
+        "pmk_payload_bytes": (sz, [u32]),
+        "pmk_num_chunks": (sz, [sz, u32]),
+        "pmk_split": (i, [vp, u32, vp, sz, vp, sz, vp]),
+        "pmk_join": (i, [vp, u32, vp, sz, vp, sz, vp]),
+        "pmk_encrypt_chunks": (i, [vp, vp, vp, vp, sz, vp]),
+        "pmk_decrypt_chunks": (i, [vp, vp, vp, vp, sz, i, vp]),
+        "pmk_encrypt_message_host": (i, [vp, vp, vp, sz, vp, sz, vp]),
+        "pmk_decrypt_message_host": (i, [vp, vp, vp, sz, vp, sz, i, vp]),
+        "pmk_status": (i, [vp, vp]),
+        "pmk_strerror": (ctypes.c_char_p, [i]),
+        "pmk_measure_int_peak": (i, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(i)]),
+        "pmk_set_threads_per_instance": (i, [vp, u32, u32]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def strerror(code: int) -> str:
+    return load_library().pmk_strerror(code).decode()
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != PMK_OK:
+        raise PMKError(rc, what)
+
+
+def payload_bytes(nbits: int) -> int:
+    return int(load_library().pmk_payload_bytes(nbits))
+
+
+def num_chunks(msg_len: int, nbits: int) -> int:
+    return int(load_library().pmk_num_chunks(msg_len, nbits))
+
+
+def _p32(a: np.ndarray):
+    assert a.dtype == np.uint32 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
+
+
+_KEY_FIELDS = ("N", "d", "p", "q", "dp", "dq", "qinv")
+
+
+def _key_arrays(K: int, nbits: int) -> dict:
+    s, h = nbits // 32, nbits // 64
+    return {f: np.zeros((K, s if f in ("N", "d") else h), np.uint32) for f in _KEY_FIELDS}
+
+
+def keygen_host(K: int, nbits: int, e: int = 65537, seed: int = 0) -> dict:
+    """Key initialisation on the host only (no GPU): dict of (K, limbs) uint32 arrays."""
+    arrs = _key_arrays(K, nbits)
+    _check(load_library().pmk_keygen_host(K, nbits, e, seed & (2**64 - 1), *[_p32(arrs[f]) for f in _KEY_FIELDS]),
+           "pmk_keygen_host")
+    return arrs
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+class KeySet:
+    """K key pairs resident on the context's device (pmk_keyset)."""
+
+    def __init__(self, ctx: "Context", handle: ctypes.c_void_p):
+        self._ctx = ctx
+        self._h = handle
+        lib = load_library()
+        self.K = int(lib.pmk_keyset_num_keys(handle))
+        self.nbits = int(lib.pmk_keyset_nbits(handle))
+        self.e = int(lib.pmk_keyset_e(handle))
+        self.limbs = self.nbits // 32
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise ValueError("key set freed")
+        return self._h
+
+    def export(self) -> dict:
+        arrs = _key_arrays(self.K, self.nbits)
+        _check(load_library().pmk_keyset_export(self.handle, *[_p32(arrs[f]) for f in _KEY_FIELDS]), "export")
+        return arrs
+
+    def free(self) -> None:
+        if self._h:
+            load_library().pmk_keyset_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Context:
+    """A pmk_ctx bound to one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise PMKError(PMK_ECUDA, "no CUDA device: the PMKRSA path runs only on the GPU")
+        self.device = int(device)
+        torch.cuda.init()
+        h = ctypes.c_void_p()
+        _check(load_library().pmk_ctx_create(self.device, ctypes.byref(h)), "pmk_ctx_create")
+        self._h = h
+
+    # ------------------------------------------------------------ plumbing
+    @property
+    def handle(self):
+        if not self._h:
+            raise ValueError("context closed")
+        return self._h
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            load_library().pmk_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def stream_handle(self, stream=None) -> int:
+        torch = _torch()
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        return int(s.cuda_stream)
+
+    def _dev(self, t, dtype, what):
+        torch = _torch()
+        if not isinstance(t, torch.Tensor) or t.device.type != "cuda" or t.device.index != self.device:
+            raise ValueError(f"{what} must be a CUDA tensor on device {self.device}")
+        if t.dtype != dtype or not t.is_contiguous():
+            raise ValueError(f"{what} must be a contiguous {dtype} tensor")
+        return ctypes.c_void_p(t.data_ptr())
+
+    # ------------------------------------------------------------ keys
+    def keygen(self, K: int, nbits: int, e: int = 65537, seed: int = 0) -> KeySet:
+        h = ctypes.c_void_p()
+        _check(load_library().pmk_keygen(self.handle, K, nbits, e, seed & (2**64 - 1), ctypes.byref(h)), "pmk_keygen")
+        return KeySet(self, h)
+
+    def keyset_from_primes(self, nbits: int, e: int, p: np.ndarray, q: np.ndarray) -> KeySet:
+        p = np.ascontiguousarray(p, np.uint32)
+        q = np.ascontiguousarray(q, np.uint32)
+        K = p.shape[0]
+        h = ctypes.c_void_p()
+        _check(load_library().pmk_keyset_from_primes(self.handle, K, nbits, e, _p32(p), _p32(q), ctypes.byref(h)),
+               "pmk_keyset_from_primes")
+        return KeySet(self, h)
+
+    # ------------------------------------------------------------ hot path
+    def split(self, nbits: int, msg, out=None, stream=None):
+        torch = _torch()
+        n = num_chunks(msg.numel(), nbits)
+        if out is None:
+            out = torch.empty((n, nbits // 32), dtype=torch.int32, device=msg.device)
+        _check(load_library().pmk_split(self.handle, nbits, self._dev(msg, torch.uint8, "msg"), msg.numel(),
+                                        self._dev(out, torch.int32, "chunks"), n, self.stream_handle(stream)),
+               "pmk_split")
+        return out
+
+    def join(self, nbits: int, chunks, msg_len: int, out=None, stream=None):
+        torch = _torch()
+        if out is None:
+            out = torch.empty(msg_len, dtype=torch.uint8, device=chunks.device)
+        _check(load_library().pmk_join(self.handle, nbits, self._dev(chunks, torch.int32, "chunks"), chunks.shape[0],
+                                       self._dev(out, torch.uint8, "msg"), msg_len, self.stream_handle(stream)),
+               "pmk_join")
+        return out
+
+    def encrypt_chunks(self, ks: KeySet, chunks, out=None, stream=None):
+        torch = _torch()
+        if out is None:
+            out = torch.empty_like(chunks)
+        _check(load_library().pmk_encrypt_chunks(self.handle, ks.handle, self._dev(chunks, torch.int32, "in"),
+                                                 self._dev(out, torch.int32, "out"), chunks.shape[0],
+                                                 self.stream_handle(stream)), "pmk_encrypt_chunks")
+        return out
+
+    def decrypt_chunks(self, ks: KeySet, chunks, use_crt: bool = False, out=None, stream=None):
+        torch = _torch()
+        if out is None:
+            out = torch.empty_like(chunks)
+        _check(load_library().pmk_decrypt_chunks(self.handle, ks.handle, self._dev(chunks, torch.int32, "in"),
+                                                 self._dev(out, torch.int32, "out"), chunks.shape[0], int(use_crt),
+                                                 self.stream_handle(stream)), "pmk_decrypt_chunks")
+        return out
+
+    def encrypt_message_host(self, ks: KeySet, h_msg, h_cipher, stream=None) -> None:
+        """Host buffers (torch CPU tensors, ideally pinned): uint8 message -> int32 limb buffer."""
+        n = h_cipher.shape[0]
+        _check(load_library().pmk_encrypt_message_host(self.handle, ks.handle, ctypes.c_void_p(h_msg.data_ptr()),
+                                                       h_msg.numel(), ctypes.c_void_p(h_cipher.data_ptr()), n,
+                                                       self.stream_handle(stream)), "pmk_encrypt_message_host")
+
+    def decrypt_message_host(self, ks: KeySet, h_cipher, h_msg, use_crt: bool = False, stream=None) -> None:
+        n = h_cipher.shape[0]
+        _check(load_library().pmk_decrypt_message_host(self.handle, ks.handle, ctypes.c_void_p(h_cipher.data_ptr()), n,
+                                                       ctypes.c_void_p(h_msg.data_ptr()), h_msg.numel(), int(use_crt),
+                                                       self.stream_handle(stream)), "pmk_decrypt_message_host")
+
+    def status(self, stream=None) -> int:
+        """Synchronise and return (and clear) the device-side error code."""
+        return int(load_library().pmk_status(self.handle, self.stream_handle(stream)))
+
+    def check(self, stream=None) -> None:
+        _check(self.status(stream), "device status")
+
+    # ------------------------------------------------------------ tuning / measurement
+    def measure_int_peak(self) -> dict:
+        m, mhz, sms = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+        _check(load_library().pmk_measure_int_peak(self.handle, ctypes.byref(m), ctypes.byref(mhz), ctypes.byref(sms)),
+               "pmk_measure_int_peak")
+        return {"macs_per_clk_per_sm": m.value, "sm_mhz": mhz.value, "num_sms": sms.value}
+
+    def set_threads_per_instance(self, limbs: int, tpi: int) -> None:
+        _check(load_library().pmk_set_threads_per_instance(self.handle, limbs, tpi), "pmk_set_threads_per_instance")

@@ -1,0 +1,270 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle, element by element.
+
+Integer results are compared bit-exactly: a modular exponentiation has one
+correct residue.  Key material on the oracle side comes from the oracle's own
+keygen and is checked equal to the library's.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2111_11924_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_2111_11924_gb300 as P
+
+    return P
+
+
+@pytest.fixture(scope="module")
+def ctx(P):
+    c = P.Context(0)
+    yield c
+    c.close()
+
+
+def dev(a: np.ndarray):
+    return torch.from_numpy(np.ascontiguousarray(a, np.uint32).view(np.int32)).cuda()
+
+
+def host(t) -> np.ndarray:
+    torch.cuda.synchronize()
+    return t.cpu().numpy().view(np.uint32)
+
+
+_keys = {}
+
+
+def keys_for(ctx, K, nbits, seed, e=65537):
+    """(library key set, oracle keys) for the same seeded key initialisation."""
+    k = (K, nbits, seed, e)
+    if k not in _keys:
+        ks = ctx.keygen(K, nbits, e, seed)
+        ok = oracle.keygen(K, nbits, e, seed)
+        ex = ks.export()
+        for f in ok.a:
+            assert np.array_equal(ex[f], ok.a[f]), f"keygen mismatch in {f}"
+        _keys[k] = (ks, ok)
+    return _keys[k]
+
+
+# ------------------------------------------------------------------ split / join
+
+@pytest.mark.parametrize("nbits", [128, 1024, 2048, 4096])
+def test_split_join_parity(ctx, nbits):
+    P = nbits // 8 - 1
+    rng = np.random.default_rng(nbits)
+    for L in [1, 2, 3, P - 1, P, P + 1, 3 * P + 7, 4099, 32768]:
+        msg = rng.integers(0, 256, L, dtype=np.uint8)
+        d_msg = torch.from_numpy(msg).cuda()
+        ch = ctx.split(nbits, d_msg)
+        assert np.array_equal(host(ch), oracle.split(msg, nbits)), L
+        back = ctx.join(nbits, dev(oracle.split(msg, nbits)), L)
+        assert bytes(back.cpu().numpy()) == msg.tobytes()
+        assert bytes(ctx.join(nbits, ch, L).cpu().numpy()) == msg.tobytes()
+
+
+def test_split_join_empty(ctx, P):
+    d_msg = torch.empty(0, dtype=torch.uint8, device="cuda")
+    ch = ctx.split(2048, d_msg)
+    assert ch.shape == (0, 64)
+    assert ctx.join(2048, ch, 0).numel() == 0
+
+
+def test_split_join_full_1mib(ctx):
+    w = W.FILE_1MIB_2048
+    msg = w.message()
+    ch = ctx.split(w.nbits, torch.from_numpy(msg).cuda())
+    assert np.array_equal(host(ch), oracle.split(msg, w.nbits))
+    assert bytes(ctx.join(w.nbits, ch, len(msg)).cpu().numpy()) == msg.tobytes()
+
+
+# ------------------------------------------------------------------ small widths, edge values
+
+@pytest.mark.parametrize("nbits,K", [(128, 3), (256, 2), (512, 2)])
+def test_edge_values_small_widths(ctx, nbits, K):
+    ks, ok = keys_for(ctx, K, nbits, seed=900 + nbits)
+    s = nbits // 32
+    Ns = ok.ints("N")
+    rng = np.random.default_rng(nbits)
+    vals = []
+    for t in range(24 * K):
+        N = Ns[t % K]
+        pick = t // K
+        special = [0, 1, 2, N - 1, N - 2, N // 2, (1 << (nbits - 1)) % N, ok.key(t % K)["p"], ok.key(t % K)["q"]]
+        vals.append(special[pick] if pick < len(special) else W.random_below(rng, N))
+    m = np.stack([oracle.to_limbs(v, s) for v in vals])
+    c_ref = oracle.encrypt_chunks(m, ok)
+    c = ctx.encrypt_chunks(ks, dev(m))
+    assert np.array_equal(host(c), c_ref)
+    for use_crt in (False, True):
+        ref = oracle.decrypt_chunks(c_ref, ok, use_crt=use_crt)
+        got = ctx.decrypt_chunks(ks, dev(c_ref), use_crt=use_crt)
+        assert np.array_equal(host(got), ref), use_crt
+        assert np.array_equal(ref, m)  # the oracle's own round trip
+    assert ctx.status() == 0
+
+
+# ------------------------------------------------------------------ the 32 KiB / 1024-bit workload, every chunk
+
+def test_small_workload_every_chunk(ctx):
+    w = W.SMALL_1024
+    ks, ok = keys_for(ctx, w.K, w.nbits, w.key_seed)
+    msg = w.message()
+    m = oracle.split(msg, w.nbits)
+    assert m.shape[0] == w.n_chunks == 259
+    d_m = ctx.split(w.nbits, torch.from_numpy(msg).cuda())
+    c = ctx.encrypt_chunks(ks, d_m)
+    c_ref = oracle.encrypt_chunks(m, ok, threads=8)
+    assert np.array_equal(host(c), c_ref)
+    for use_crt in (False, True):
+        d = ctx.decrypt_chunks(ks, c, use_crt=use_crt)
+        assert np.array_equal(host(d), oracle.decrypt_chunks(c_ref, ok, use_crt=use_crt, threads=8)), use_crt
+        assert bytes(ctx.join(w.nbits, d, len(msg)).cpu().numpy()) == msg.tobytes()
+    assert ctx.status() == 0
+
+
+# ------------------------------------------------------------------ the 1 MiB / 2048-bit workload (bench configuration)
+
+def test_1mib_2048_encrypt_all_decrypt_sampled(ctx):
+    w = W.FILE_1MIB_2048
+    ks, ok = keys_for(ctx, w.K, w.nbits, w.key_seed)
+    msg = w.message()
+    m = oracle.split(msg, w.nbits)
+    d_m = ctx.split(w.nbits, torch.from_numpy(msg).cuda())
+    c = ctx.encrypt_chunks(ks, d_m)
+    c_host = host(c)
+    assert np.array_equal(c_host, oracle.encrypt_chunks(m, ok, threads=8))   # every chunk
+    d_full = ctx.decrypt_chunks(ks, c, use_crt=False)
+    d_crt = ctx.decrypt_chunks(ks, c, use_crt=True)
+    full_h, crt_h = host(d_full), host(d_crt)
+    assert np.array_equal(full_h, m)        # round trip on every chunk
+    assert np.array_equal(crt_h, full_h)    # CRT identical to full-d on every chunk
+    # sampled chunks through the oracle's own decryption (both forms), incl. the ragged last chunk
+    rng = np.random.default_rng(7)
+    idx = np.unique(np.concatenate([rng.choice(w.n_chunks, 56, replace=False), [0, 1, w.n_chunks - 1]]))
+    sub = np.ascontiguousarray(c_host[idx])
+    # keep each chunk bound to its own key: build a K-row key table per sampled chunk
+    for use_crt, got in ((False, full_h), (True, crt_h)):
+        for t in idx[:24] if use_crt else idx:
+            k = int(t) % w.K
+            kd = ok.key(k)
+            cv = oracle.from_limbs(c_host[t])
+            ref = oracle.crt(cv, kd["dp"], kd["dq"], kd["p"], kd["q"], kd["qinv"]) if use_crt else \
+                oracle.modexp(cv, kd["d"], kd["N"])
+            assert oracle.from_limbs(got[t]) == ref, (t, use_crt)
+    assert sub.shape[0] == len(idx)
+    assert ctx.status() == 0
+
+
+# ------------------------------------------------------------------ launch geometries
+
+@pytest.mark.parametrize("nbits,limbs,tpis", [(2048, 64, [4, 8, 16]), (1024, 32, [4, 8]), (2048, 32, [4, 8])])
+def test_threads_per_instance_variants(ctx, nbits, limbs, tpis):
+    K = 3
+    ks, ok = keys_for(ctx, K, nbits, seed=4242)
+    rng = np.random.default_rng(1)
+    Ns = ok.ints("N")
+    n = 37  # ragged: several blocks per key and a partial one
+    c = np.stack([oracle.to_limbs(W.random_below(rng, Ns[t % K]), nbits // 32) for t in range(n)])
+    ref_full = oracle.decrypt_chunks(c[:9], ok)
+    outs = []
+    for tpi in tpis:
+        ctx.set_threads_per_instance(limbs, tpi)
+        try:
+            use_crt = limbs != nbits // 32
+            outs.append(host(ctx.decrypt_chunks(ks, dev(c), use_crt=use_crt)))
+        finally:
+            ctx.set_threads_per_instance(limbs, 0)
+    for o in outs:
+        assert np.array_equal(o[:9], ref_full)
+        assert np.array_equal(o, outs[0])
+
+
+@pytest.mark.parametrize("nbits", [3072, 4096])
+def test_wide_keys(ctx, nbits):
+    ks, ok = keys_for(ctx, 2, nbits, seed=77 + nbits)
+    rng = np.random.default_rng(nbits)
+    Ns = ok.ints("N")
+    m = np.stack([oracle.to_limbs(W.random_below(rng, Ns[t % 2]), nbits // 32) for t in range(6)])
+    c = ctx.encrypt_chunks(ks, dev(m))
+    c_ref = oracle.encrypt_chunks(m, ok)
+    assert np.array_equal(host(c), c_ref)
+    assert np.array_equal(host(ctx.decrypt_chunks(ks, c)), m)
+    assert np.array_equal(host(ctx.decrypt_chunks(ks, c, use_crt=True)), m)
+    d0 = ok.key(0)
+    assert oracle.from_limbs(host(ctx.decrypt_chunks(ks, c))[0]) == oracle.modexp(oracle.from_limbs(c_ref[0]), d0["d"], d0["N"])
+
+
+# ------------------------------------------------------------------ degenerate cases and errors
+
+def test_degenerate_counts_and_inplace(ctx):
+    ks, ok = keys_for(ctx, 5, 512, seed=31)
+    Ns = ok.ints("N")
+    rng = np.random.default_rng(3)
+    for n in (1, 3, 5, 6):  # fewer chunks than keys, exactly K, K + 1
+        m = np.stack([oracle.to_limbs(W.random_below(rng, Ns[t % 5]), 16) for t in range(n)])
+        d_m = dev(m)
+        ctx.encrypt_chunks(ks, d_m, out=d_m)  # in place
+        assert np.array_equal(host(d_m), oracle.encrypt_chunks(m, ok))
+        ctx.decrypt_chunks(ks, d_m, out=d_m)  # in place, full d
+        assert np.array_equal(host(d_m), m)
+    empty = torch.empty((0, 16), dtype=torch.int32, device="cuda")
+    ctx.encrypt_chunks(ks, empty)
+    ctx.decrypt_chunks(ks, empty, use_crt=True)
+    assert ctx.status() == 0
+
+
+def test_out_of_range_chunk_reported(ctx, P):
+    ks, ok = keys_for(ctx, 2, 256, seed=8)
+    Ns = ok.ints("N")
+    vals = [5, Ns[1], 7, (1 << 256) - 1, Ns[0] - 1, Ns[1] + 1]
+    m = np.stack([oracle.to_limbs(v, 8) for v in vals])
+    out = ctx.decrypt_chunks(ks, dev(m))
+    assert ctx.status() == P.pmkrsa.PMK_ERANGE
+    assert ctx.status() == 0  # cleared
+    got = host(out)
+    for t in (0, 2, 4):
+        kd = ok.key(t % 2)
+        assert oracle.from_limbs(got[t]) == oracle.modexp(vals[t], kd["d"], kd["N"])
+    ctx.encrypt_chunks(ks, dev(m[:2]))
+    assert ctx.status() == P.pmkrsa.PMK_ERANGE
+
+
+def test_argument_errors(ctx, P):
+    ks, _ = keys_for(ctx, 2, 256, seed=8)
+    m = torch.zeros((4, 8), dtype=torch.int32, device="cuda")
+    with pytest.raises(P.PMKError):
+        ctx.decrypt_chunks(ks, m, use_crt=True, out=m)  # CRT in place is rejected
+    with pytest.raises(P.PMKError):
+        ctx.keygen(1, 200)  # width not a multiple of 128
+    with pytest.raises(P.PMKError):
+        ctx.keygen(1, 256, e=4)
+    lib = P.load_library()
+    import ctypes
+    assert lib.pmk_split(ctx.handle, 2048, ctypes.c_void_p(m.data_ptr()), 1000, ctypes.c_void_p(m.data_ptr()), 3,
+                         None) == P.pmkrsa.PMK_EINVAL  # 1000 bytes need 4 chunks
+
+
+def test_host_buffer_calls_and_from_primes(ctx):
+    w = W.SMALL_1024
+    ks, ok = keys_for(ctx, w.K, w.nbits, w.key_seed)
+    msg = torch.from_numpy(w.message()).pin_memory()
+    cipher = torch.empty((w.n_chunks, w.limbs), dtype=torch.int32).pin_memory()
+    ctx.encrypt_message_host(ks, msg, cipher)
+    ref = oracle.encrypt_chunks(oracle.split(msg.numpy(), w.nbits), ok, threads=8)
+    assert np.array_equal(cipher.numpy().view(np.uint32), ref)
+    back = torch.empty(w.msg_bytes, dtype=torch.uint8).pin_memory()
+    for use_crt in (False, True):
+        back.zero_()
+        ctx.decrypt_message_host(ks, cipher, back, use_crt=use_crt)
+        assert torch.equal(back, msg)
+    ks2 = ctx.keyset_from_primes(w.nbits, w.e, ok.a["p"], ok.a["q"])
+    ex = ks2.export()
+    assert all(np.array_equal(ex[f], ok.a[f]) for f in ok.a)
