@@ -38,6 +38,7 @@ extern "C" {
 #define PMK_ENOMEM (-3)       /* a device or host allocation failed */
 #define PMK_ECUDA (-4)        /* a CUDA runtime call failed */
 #define PMK_EUNSUPPORTED (-5) /* key width not compiled into this build */
+#define PMK_ETOOLARGE (-6)    /* request exceeds the fixed capacity of the allocation-free call */
 
 typedef struct pmk_ctx pmk_ctx;         /* one GPU: device status word, staging buffers */
 typedef struct pmk_keyset pmk_keyset;   /* K key pairs: host copy + device-resident tables */
@@ -139,6 +140,29 @@ int pmk_encrypt_message_host(pmk_ctx *ctx, const pmk_keyset *ks, const uint8_t *
                              uint32_t *h_cipher, size_t n_chunks, void *stream);
 int pmk_decrypt_message_host(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *h_cipher, size_t n_chunks,
                              uint8_t *h_msg, size_t msg_len, int use_crt, void *stream);
+
+/*
+ * Allocation-free variant of pmk_decrypt_message_host.  The paper has no
+ * counterpart of this call.  It exists for callers that must not let the
+ * library call cudaMalloc: for example a process whose device memory is
+ * handed entirely to another allocator under a fixed budget, or a
+ * latency-critical path that cannot pay for a device allocation.  The
+ * ciphertext, the decrypted chunks and the message bytes are staged in one
+ * fixed device array built into the library (32 MiB, reserved on every GPU
+ * that loads the library until the process exits); no allocation routine is
+ * called.  No context is needed: the key set's device is used.
+ *   Capacity: 256 + 2 * round_up_256(n_chunks * nbits/8) + round_up_256(msg_len)
+ *   bytes must fit in 32 MiB, else PMK_ETOOLARGE and nothing is enqueued.
+ *   The first call on a device looks up the array's device address (one-time
+ *   set-up per device); make that first call before any stream capture.
+ *   All calls share the array and it keeps the last call's contents: calls
+ *   whose GPU work overlaps (other streams, other host threads) race and
+ *   corrupt each other's results.
+ *   Synchronises `stream`.  Returns PMK_OK, PMK_ERANGE (a chunk >= its
+ *   modulus), PMK_EINVAL, PMK_ETOOLARGE or PMK_ECUDA.
+ */
+int pmk_decrypt_message_host_noalloc(const pmk_keyset *ks, const uint32_t *h_cipher, size_t n_chunks,
+                                     uint8_t *h_msg, size_t msg_len, int use_crt, void *stream);
 
 /* Synchronise `stream`, then return (and clear) the first device-side error
  * recorded since the last call: PMK_OK or PMK_ERANGE; PMK_ECUDA if a CUDA

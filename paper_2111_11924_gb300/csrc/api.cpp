@@ -16,15 +16,6 @@ struct pmk_ctx {
   std::map<uint32_t, uint32_t> tpi;        // limb count -> threads per instance override
 };
 
-struct pmk_keyset {
-  int device = 0;
-  uint32_t K = 0, nbits = 0;
-  uint64_t e = 0;
-  std::vector<pmk::HostKey> keys;
-  uint32_t *d_blob = nullptr;              // every key's limbs and schedules
-  pmk::KeyDev *d_keys = nullptr;           // K device key views into d_blob
-};
-
 namespace {
 
 using pmk::HostKey;
@@ -422,6 +413,7 @@ const char *pmk_strerror(int code) {
     case PMK_ENOMEM: return "out of memory";
     case PMK_ECUDA: return "CUDA runtime error";
     case PMK_EUNSUPPORTED: return "key width or launch geometry not built";
+    case PMK_ETOOLARGE: return "request exceeds the fixed capacity of the allocation-free call";
     default: return "unknown error";
   }
 }

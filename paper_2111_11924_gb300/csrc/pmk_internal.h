@@ -71,3 +71,13 @@ uint32_t default_tpi(uint32_t limbs);
 int measure_int_peak(double *macs_per_clk_per_sm, double *sm_mhz, int *num_sms);
 
 }  // namespace pmk
+
+// Key set: host copy and device-resident tables (opaque in the C ABI).
+struct pmk_keyset {
+  int device = 0;
+  uint32_t K = 0, nbits = 0;
+  uint64_t e = 0;
+  std::vector<pmk::HostKey> keys;
+  uint32_t *d_blob = nullptr;              // every key's limbs and schedules
+  pmk::KeyDev *d_keys = nullptr;           // K device key views into d_blob
+};

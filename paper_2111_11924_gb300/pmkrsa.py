@@ -14,7 +14,7 @@ import numpy as np
 
 from . import _native_build
 
-PMK_OK, PMK_EINVAL, PMK_ERANGE, PMK_ENOMEM, PMK_ECUDA, PMK_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
+PMK_OK, PMK_EINVAL, PMK_ERANGE, PMK_ENOMEM, PMK_ECUDA, PMK_EUNSUPPORTED, PMK_ETOOLARGE = 0, -1, -2, -3, -4, -5, -6
 
 _lib = None
 
@@ -55,6 +55,7 @@ def load_library() -> ctypes.CDLL:
         "pmk_decrypt_chunks": (i, [vp, vp, vp, vp, sz, i, vp]),
         "pmk_encrypt_message_host": (i, [vp, vp, vp, sz, vp, sz, vp]),
         "pmk_decrypt_message_host": (i, [vp, vp, vp, sz, vp, sz, i, vp]),
+        "pmk_decrypt_message_host_noalloc": (i, [vp, vp, sz, vp, sz, i, vp]),
         "pmk_status": (i, [vp, vp]),
         "pmk_strerror": (ctypes.c_char_p, [i]),
         "pmk_measure_int_peak": (i, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
@@ -274,3 +275,13 @@ class Context:
 
     def set_threads_per_instance(self, limbs: int, tpi: int) -> None:
         _check(load_library().pmk_set_threads_per_instance(self.handle, limbs, tpi), "pmk_set_threads_per_instance")
+
+
+def decrypt_message_host_noalloc(ks: KeySet, h_cipher, h_msg, use_crt: bool = False, stream=None) -> int:
+    """pmk_decrypt_message_host_noalloc: decrypt without any device allocation
+    (device staging in the library's fixed array).  Returns the PMK_* code."""
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream(ks._ctx.device)
+    return int(load_library().pmk_decrypt_message_host_noalloc(
+        ks.handle, ctypes.c_void_p(h_cipher.data_ptr()), h_cipher.shape[0], ctypes.c_void_p(h_msg.data_ptr()),
+        h_msg.numel(), int(use_crt), ctypes.c_void_p(int(s.cuda_stream))))
