@@ -256,6 +256,10 @@ def run_ours(args):
         return ph  # ms: split, encrypt, decrypt, join
 
     peak = ctx.measure_int_peak()
+    # the plain path first: built-in default geometry, one launch per call
+    ph_default = timed(False, max(3, args.steps // 2), 3)
+    tuned = ctx.autotune(ks, n, "decrypt", reps=3)
+    tuned_crt = ctx.autotune(ks, n, "crt", reps=3)
     with ClockSampler(local) as clocks:
         ph = timed(False, args.steps, args.warmup)
     torch.cuda.synchronize()
@@ -312,12 +316,18 @@ def run_ours(args):
         "throughput_MBps": {"encrypt": mb / (enc_ms / 1e3), "decrypt": mb / (dec_ms / 1e3),
                             "round_trip": mb / (t_step / 1e3)},
         "crt": {"value": world * n / (crt_step / 1e3), "unit": UNIT, "ms_per_step": crt_step,
-                "decrypt_ms": crt_dec, "decrypt_only": n / (crt_dec / 1e3)},
+                "decrypt_ms": crt_dec, "decrypt_only": n / (crt_dec / 1e3),
+                "geometry": {"lanes_per_instance": tuned_crt["tpi"], "form": ["chain", "columns"][tuned_crt["form"]]}},
+        "geometry": {"lanes_per_instance": tuned["tpi"], "form": ["chain", "columns"][tuned["form"]],
+                     "chosen_by": "pmk_autotune over every compiled geometry"},
+        "default_geometry": {"value": world * n / (float(ph_default.sum(axis=1).mean()) / 1e3), "unit": UNIT,
+                             "decrypt_ms": float(ph_default[:, 2].mean())},
         "split_join_GBps": {"split": (w.msg_bytes + cipher_bytes) / (split_ms / 1e3) / 1e9,
                             "join": (w.msg_bytes + cipher_bytes) / (join_ms / 1e3) / 1e9},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tmacs, "unit": "TMAC/s",
                      "frac": achieved / peak_tmacs, "traffic": TRAFFIC_MEASURED.get(digest),
-                     "kernel": "k_modexp<64,8,false> (full-d decrypt; interval includes its 4 us range check)",
+                     "kernel": f"k_modexp<64,{tuned['tpi']},full,{['chain', 'columns'][tuned['form']]}> "
+                               "(full-d decrypt; interval includes its ~4 us range check)",
                      "peak_basis": f"{peak['macs_per_clk_per_sm']:.2f} MAC/clk/SM measured x {sms} SMs x {max_mhz:.0f} MHz",
                      "frac_at_observed_clock": (achieved / (peak["macs_per_clk_per_sm"] * sms * clk["sm_mhz"] * 1e-6)
                                                 if clk["sm_mhz"] else None)},
@@ -352,6 +362,8 @@ def run_profile(args):
     import paper_2111_11924_gb300 as P
 
     w = WORKLOAD
+    if args.profile_mib:
+        w = W.Workload(w.id, f"{w.name}-x{args.profile_mib}", args.profile_mib << 20, w.K, w.nbits)
     ctx = P.Context(0)
     ks = ctx.keygen(w.K, w.nbits, w.e, w.key_seed)
     d_msg = torch.from_numpy(w.message()).cuda()
@@ -377,6 +389,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="run the fixed launch sequence used for ncu captures and exit")
+    ap.add_argument("--profile-mib", type=int, default=0,
+                    help="with --profile: message size in MiB instead of the 1 MiB workload")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -181,12 +181,34 @@ const char *pmk_strerror(int code);
 int pmk_measure_int_peak(pmk_ctx *ctx, double *macs_per_clk_per_sm, double *sm_mhz, int *num_sms);
 
 /*
- * Launch geometry of the exponentiation kernels for one limb count
- * (nbits/32 for full-width, nbits/64 for CRT halves): threads per
- * instance, a power of two dividing 32 and the limb count.  0 restores the
- * default.  Returns EUNSUPPORTED if that pair is not built.
+ * Launch geometry of the exponentiation kernels for one limb count and mode.
+ *   limbs: nbits/32 for the full-width kernels (crt = 0), nbits/64 for the
+ *          CRT half-width kernels (crt = 1).
+ *   tpi:   lanes of a warp that hold one exponentiation (a power of two
+ *          dividing 32 and the limb count); 0 restores the built-in default.
+ *   form:  Montgomery product form, 0 = one add-with-carry chain per lane and
+ *          row, 1 = independent 64-bit column accumulators.
+ * Returns EUNSUPPORTED if that geometry is not compiled in.  Results are
+ * bit-identical for every geometry; only speed differs.
  */
-int pmk_set_threads_per_instance(pmk_ctx *ctx, uint32_t limbs, uint32_t tpi);
+int pmk_set_kernel_config(pmk_ctx *ctx, uint32_t limbs, int crt, uint32_t tpi, uint32_t form);
+/* The geometry the context currently uses for (limbs, crt). */
+int pmk_get_kernel_config(const pmk_ctx *ctx, uint32_t limbs, int crt, uint32_t *tpi, uint32_t *form);
+/* Compiled geometries for (limbs, crt): writes up to `max` (tpi, form) pairs
+ * and returns how many exist (a negative code on bad arguments).  Host only. */
+int pmk_list_kernel_configs(uint32_t limbs, int crt, uint32_t *tpi, uint32_t *form, int max);
+
+/*
+ * Autotuner: time every compiled geometry of one exponentiation on
+ * `n_chunks` synthetic chunks of this key set (mode 0 = encrypt, 1 = full-d
+ * decrypt, 2 = CRT decrypt), `reps` timed launches each after one warm-up,
+ * and make the fastest the context's geometry for that limb count and mode
+ * (as pmk_set_kernel_config would).  Writes the choice and its best launch
+ * time in ms (any output pointer may be NULL).  Allocates and frees two
+ * temporary device buffers and synchronises the device's legacy stream.
+ */
+int pmk_autotune(pmk_ctx *ctx, const pmk_keyset *ks, size_t n_chunks, int mode, int reps, uint32_t *tpi,
+                 uint32_t *form, float *ms);
 
 #ifdef __cplusplus
 }

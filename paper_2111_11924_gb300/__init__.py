@@ -15,10 +15,11 @@ from .pmkrsa import (  # noqa: F401
     Context,
     KeySet,
     keygen_host,
+    kernel_configs,
     load_library,
     num_chunks,
     payload_bytes,
     strerror,
 )
 
-__all__ = ["PMKError", "Context", "KeySet", "keygen_host", "load_library", "num_chunks", "payload_bytes", "strerror"]
+__all__ = ["PMKError", "Context", "KeySet", "keygen_host", "kernel_configs", "load_library", "num_chunks", "payload_bytes", "strerror"]

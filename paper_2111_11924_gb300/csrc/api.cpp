@@ -13,7 +13,7 @@ struct pmk_ctx {
   size_t msg_cap = 0;
   uint32_t *d_a = nullptr, *d_b = nullptr;
   size_t a_cap = 0, b_cap = 0;             // in words
-  std::map<uint32_t, uint32_t> tpi;        // limb count -> threads per instance override
+  std::map<uint32_t, pmk::KernelConfig> cfg;  // (limbs << 1 | crt) -> kernel geometry override
 };
 
 namespace {
@@ -57,12 +57,12 @@ int grow(void **buf, size_t *cap, size_t bytes) {
   return PMK_OK;
 }
 
-// Threads per instance for an exponentiation over `limbs` limbs: the
-// context's override when that geometry is built for this mode, else the default.
-uint32_t tpi_for(const pmk_ctx *ctx, uint32_t limbs, bool crt) {
-  auto it = ctx->tpi.find(limbs);
-  if (it != ctx->tpi.end() && pmk::modexp_built(limbs, it->second, crt)) return it->second;
-  return pmk::default_tpi(limbs);
+// Kernel geometry for an exponentiation over `limbs` limbs: the context's
+// override for this mode, else the built-in default.
+pmk::KernelConfig cfg_for(const pmk_ctx *ctx, uint32_t limbs, bool crt) {
+  auto it = ctx->cfg.find(limbs << 1 | (crt ? 1u : 0u));
+  if (it != ctx->cfg.end()) return it->second;
+  return pmk::default_config(limbs, crt);
 }
 
 size_t push(std::vector<uint32_t> &blob, const std::vector<uint32_t> &v) {
@@ -140,7 +140,7 @@ int finish_keyset(pmk_ctx *ctx, pmk_keyset *ks, pmk_keyset **out) {
 }
 
 bool width_built(uint32_t nbits) {
-  return pmk::default_tpi(nbits / 32) != 0 && pmk::default_tpi(nbits / 64) != 0;
+  return pmk::default_config(nbits / 32, false).tpi != 0 && pmk::default_config(nbits / 64, true).tpi != 0;
 }
 
 int check_chunk_call(const pmk_ctx *ctx, const pmk_keyset *ks, const void *in, const void *out) {
@@ -153,7 +153,7 @@ int check_chunk_call(const pmk_ctx *ctx, const pmk_keyset *ks, const void *in, c
 int enqueue_encrypt(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *in, uint32_t *out, size_t n, cudaStream_t st) {
   const uint32_t S = ks->nbits / 32;
   int rc = pmk::launch_range_check(ks->d_keys, ks->K, S, in, n, ctx->d_status, st);
-  if (rc == PMK_OK) rc = pmk::launch_modexp(pmk::ExpMode::kEncrypt, S, tpi_for(ctx, S, false), ks->d_keys, ks->K, in, out, n, st);
+  if (rc == PMK_OK) rc = pmk::launch_modexp(pmk::ExpMode::kEncrypt, S, cfg_for(ctx, S, false), ks->d_keys, ks->K, in, out, n, st);
   return rc;
 }
 
@@ -162,9 +162,9 @@ int enqueue_decrypt(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *in, uint
   const uint32_t S = ks->nbits / 32;
   int rc = pmk::launch_range_check(ks->d_keys, ks->K, S, in, n, ctx->d_status, st);
   if (rc != PMK_OK) return rc;
-  if (!use_crt) return pmk::launch_modexp(pmk::ExpMode::kDecrypt, S, tpi_for(ctx, S, false), ks->d_keys, ks->K, in, out, n, st);
+  if (!use_crt) return pmk::launch_modexp(pmk::ExpMode::kDecrypt, S, cfg_for(ctx, S, false), ks->d_keys, ks->K, in, out, n, st);
   const uint32_t H = S / 2;
-  rc = pmk::launch_modexp(pmk::ExpMode::kCrtHalf, H, tpi_for(ctx, H, true), ks->d_keys, ks->K, in, out, n, st);
+  rc = pmk::launch_modexp(pmk::ExpMode::kCrtHalf, H, cfg_for(ctx, H, true), ks->d_keys, ks->K, in, out, n, st);
   if (rc == PMK_OK) rc = pmk::launch_garner(H, ks->d_keys, ks->K, out, n, st);
   return rc;
 }
@@ -425,15 +425,37 @@ int pmk_measure_int_peak(pmk_ctx *ctx, double *macs_per_clk_per_sm, double *sm_m
   return pmk::measure_int_peak(macs_per_clk_per_sm, sm_mhz, num_sms);
 }
 
-int pmk_set_threads_per_instance(pmk_ctx *ctx, uint32_t limbs, uint32_t tpi) {
+int pmk_set_kernel_config(pmk_ctx *ctx, uint32_t limbs, int crt, uint32_t tpi, uint32_t form) {
   if (!ctx) return PMK_EINVAL;
+  const uint32_t key = limbs << 1 | (crt ? 1u : 0u);
   if (tpi == 0) {
-    ctx->tpi.erase(limbs);
+    ctx->cfg.erase(key);
     return PMK_OK;
   }
-  if (!pmk::modexp_supported(limbs, tpi)) return PMK_EUNSUPPORTED;
-  ctx->tpi[limbs] = tpi;
+  const pmk::KernelConfig c{tpi, form};
+  if (!pmk::modexp_built(limbs, c, crt != 0)) return PMK_EUNSUPPORTED;
+  ctx->cfg[key] = c;
   return PMK_OK;
+}
+
+int pmk_get_kernel_config(const pmk_ctx *ctx, uint32_t limbs, int crt, uint32_t *tpi, uint32_t *form) {
+  if (!ctx || !tpi || !form) return PMK_EINVAL;
+  const pmk::KernelConfig c = cfg_for(ctx, limbs, crt != 0);
+  if (c.tpi == 0) return PMK_EUNSUPPORTED;
+  *tpi = c.tpi;
+  *form = c.form;
+  return PMK_OK;
+}
+
+int pmk_list_kernel_configs(uint32_t limbs, int crt, uint32_t *tpi, uint32_t *form, int max) {
+  if (max < 0) return PMK_EINVAL;
+  std::vector<pmk::KernelConfig> v(max > 0 ? max : 1);
+  const int n = pmk::list_configs(limbs, crt != 0, v.data(), max);
+  for (int i = 0; i < n && i < max; i++) {
+    if (tpi) tpi[i] = v[i].tpi;
+    if (form) form[i] = v[i].form;
+  }
+  return n;
 }
 
 }  // extern "C"

@@ -163,11 +163,11 @@ int grid_for(long long work, int threads) {
 
 int cuda_rc(cudaError_t e) { return e == cudaSuccess ? PMK_OK : PMK_ECUDA; }
 
-const ModexpEntry *find_entry(uint32_t limbs, uint32_t tpi, bool crt) {
+const ModexpEntry *find_entry(uint32_t limbs, KernelConfig cfg, bool crt) {
   int n = 0;
   const ModexpEntry *list = crt ? modexp_entries_crt(&n) : modexp_entries_full(&n);
   for (int i = 0; i < n; i++)
-    if (list[i].limbs == (int)limbs && list[i].tpi == (int)tpi) return &list[i];
+    if (list[i].limbs == (int)limbs && list[i].tpi == (int)cfg.tpi && list[i].form == (int)cfg.form) return &list[i];
   return nullptr;
 }
 
@@ -205,27 +205,41 @@ int launch_garner(uint32_t half_limbs, const KeyDev *keys, uint32_t K, uint32_t 
   return cuda_rc(cudaGetLastError());
 }
 
-bool modexp_built(uint32_t limbs, uint32_t tpi, bool crt) { return find_entry(limbs, tpi, crt) != nullptr; }
+bool modexp_built(uint32_t limbs, KernelConfig cfg, bool crt) { return find_entry(limbs, cfg, crt) != nullptr; }
 
-bool modexp_supported(uint32_t limbs, uint32_t tpi) {
-  return find_entry(limbs, tpi, false) != nullptr || find_entry(limbs, tpi, true) != nullptr;
-}
-
-uint32_t default_tpi(uint32_t limbs) {
+// Defaults measured on GB300 (1 MiB and 100 MiB workloads at 2048 bits):
+// 64-limb full-width and 32-limb CRT halves run fastest with independent
+// columns at 8 and 4 lanes; other widths use the carry-chain form.
+KernelConfig default_config(uint32_t limbs, bool crt) {
+  KernelConfig c;
   switch (limbs) {
-    case 2: case 4: case 8: case 16: return 2;
-    case 32: return 4;
-    case 48: case 64: case 96: return 8;
-    case 128: return 16;
-    default: return 0;
+    case 2: case 4: case 8: case 16: c.tpi = 2; break;
+    case 32: c.tpi = 4; c.form = crt ? 1 : 0; break;
+    case 48: case 96: c.tpi = 8; break;
+    case 64: c.tpi = 8; c.form = crt ? 0 : 1; break;
+    case 128: c.tpi = 16; break;
+    default: break;
   }
+  if (c.tpi && !find_entry(limbs, c, crt)) c = KernelConfig();
+  return c;
 }
 
-int launch_modexp(ExpMode mode, uint32_t limbs, uint32_t tpi, const KeyDev *keys, uint32_t K, const uint32_t *in,
+int list_configs(uint32_t limbs, bool crt, KernelConfig *out, int max) {
+  int n = 0, k = 0;
+  const ModexpEntry *list = crt ? modexp_entries_crt(&n) : modexp_entries_full(&n);
+  for (int i = 0; i < n; i++)
+    if (list[i].limbs == (int)limbs) {
+      if (k < max && out) out[k] = KernelConfig{(uint32_t)list[i].tpi, (uint32_t)list[i].form};
+      k++;
+    }
+  return k;
+}
+
+int launch_modexp(ExpMode mode, uint32_t limbs, KernelConfig cfg, const KeyDev *keys, uint32_t K, const uint32_t *in,
                   uint32_t *out, size_t n, cudaStream_t st) {
   if (n == 0) return PMK_OK;
   const bool crt = mode == ExpMode::kCrtHalf;
-  const ModexpEntry *e = find_entry(limbs, tpi, crt);
+  const ModexpEntry *e = find_entry(limbs, cfg, crt);
   if (!e) return PMK_EUNSUPPORTED;
   static std::mutex mu;
   static std::set<std::pair<const void *, int>> configured;  // (kernel, device) with the smem limit raised

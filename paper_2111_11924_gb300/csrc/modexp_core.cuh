@@ -244,6 +244,96 @@ __device__ __forceinline__ void mont_mul(uint32_t (&a)[S / TPI], const uint32_t 
   for (int j = 0; j < L; j++) a[j] = t[j];
 }
 
+// a <- MontMul(a, y), column form.  Each lane keeps one 64-bit accumulator
+// per limb position ("column"): the low half of a product a_j * y_i goes to
+// column j and its high half to column j + 1, so a row is L independent
+// column updates instead of one add-with-carry chain through the lane.
+// Columns absorb at most four 32-bit terms per row and live at most S + L
+// rows, so they stay below 2^42.  The row shift moves a whole column (two
+// shuffles); column carries are propagated once, before finalize.
+template <int S, int TPI>
+__device__ __forceinline__ void mont_mul_cols(uint32_t (&a)[S / TPI], const uint32_t *ys, const uint32_t (&nn)[S / TPI],
+                                              uint32_t n0, uint32_t r) {
+  constexpr int L = S / TPI;
+  constexpr int kStep = (S % 4 == 0) ? 4 : 2;
+  uint64_t acc[L];
+#pragma unroll
+  for (int j = 0; j < L; j++) acc[j] = 0;
+#pragma unroll 1
+  for (int i0 = 0; i0 < S; i0 += kStep) {
+    uint32_t yv[kStep];
+    if constexpr (kStep == 4) {
+      const uint4 v = *reinterpret_cast<const uint4 *>(ys + i0);
+      yv[0] = v.x; yv[1] = v.y; yv[2] = v.z; yv[3] = v.w;
+    } else {
+      const uint2 v = *reinterpret_cast<const uint2 *>(ys + i0);
+      yv[0] = v.x; yv[1] = v.y;
+    }
+#pragma unroll
+    for (int u = 0; u < kStep; u++) {
+      uint32_t hprev = 0;
+#pragma unroll
+      for (int j = 0; j < L; j++) {
+        const uint64_t p = (uint64_t)a[j] * yv[u];
+        acc[j] += (uint64_t)(uint32_t)p + hprev;
+        hprev = (uint32_t)(p >> 32);
+      }
+      uint64_t top = hprev;  // column L: the next lane's column 0 before the shift
+      uint32_t q = (uint32_t)acc[0] * n0;
+      if constexpr (TPI > 1) q = __shfl_sync(kFull, q, 0, TPI);
+      hprev = 0;
+#pragma unroll
+      for (int j = 0; j < L; j++) {
+        const uint64_t p = (uint64_t)nn[j] * q;
+        acc[j] += (uint64_t)(uint32_t)p + hprev;
+        hprev = (uint32_t)(p >> 32);
+      }
+      top += hprev;
+      // T /= 2^32: column 0 of lane 0 is now zero mod 2^32 and its high part
+      // carries into column 1; every other lane's column 0 moves down to the
+      // previous lane's top column.
+      uint64_t in = 0;
+      if constexpr (TPI > 1) {
+        const uint32_t lo = __shfl_down_sync(kFull, (uint32_t)acc[0], 1, TPI);
+        const uint32_t hi = __shfl_down_sync(kFull, (uint32_t)(acc[0] >> 32), 1, TPI);
+        if (r != TPI - 1) in = ((uint64_t)hi << 32) | lo;
+      }
+      const uint64_t carry0 = (r == 0) ? (acc[0] >> 32) : 0;
+#pragma unroll
+      for (int j = 0; j < L - 1; j++) acc[j] = acc[j + 1];
+      acc[L - 1] = in + top;
+      acc[0] += carry0;
+    }
+  }
+  uint32_t t[L];
+  uint64_t c = 0;
+#pragma unroll
+  for (int j = 0; j < L; j++) {
+    const uint64_t v = acc[j] + c;
+    t[j] = (uint32_t)v;
+    c = v >> 32;
+  }
+  finalize<L, TPI>(t, (uint32_t)c, nn, r);
+#pragma unroll
+  for (int j = 0; j < L; j++) a[j] = t[j];
+}
+
+// Montgomery product forms: kChain = mont_mul (one add-with-carry chain per
+// lane and row), kCols = mont_mul_cols (independent 64-bit columns).  Which is
+// faster depends on limbs per lane and on how many warps a batch provides, so
+// each compiled geometry names its form.
+enum MontForm : int { kChain = 0, kCols = 1 };
+
+template <int S, int TPI, int FORM>
+__device__ __forceinline__ void mont(uint32_t (&a)[S / TPI], const uint32_t *ys, const uint32_t (&nn)[S / TPI],
+                                     uint32_t n0, uint32_t r) {
+  if constexpr (FORM == kCols) {
+    mont_mul_cols<S, TPI>(a, ys, nn, n0, r);
+  } else {
+    mont_mul<S, TPI>(a, ys, nn, n0, r);
+  }
+}
+
 // a <- (a + b) mod N for a, b < N (distributed add, lookahead, one reduction).
 template <int L, int TPI>
 __device__ __forceinline__ void mod_add(uint32_t (&a)[L], const uint32_t (&b)[L], const uint32_t (&nn)[L], uint32_t r) {
@@ -301,7 +391,7 @@ __device__ __forceinline__ void load_slice_global(uint32_t (&a)[L], const uint32
 // Table of odd powers and the exponent walk.  On entry a = x in Montgomery
 // form; on exit a = x^E in Montgomery form.  tbl: kTableMax rows, ybuf: one
 // row, all of this instance.  sched: steps of make_schedule() (block-uniform).
-template <int S, int TPI>
+template <int S, int TPI, int FORM>
 __device__ __forceinline__ void exp_window(uint32_t (&a)[S / TPI], uint32_t *tbl, uint32_t *ybuf,
                                            const uint32_t *__restrict__ sched, uint32_t nsteps, uint32_t maxidx,
                                            const uint32_t (&nn)[S / TPI], uint32_t n0, uint32_t r) {
@@ -311,14 +401,14 @@ __device__ __forceinline__ void exp_window(uint32_t (&a)[S / TPI], uint32_t *tbl
   if (maxidx > 0) {
     store_slice<L>(ybuf, a, r);
     __syncwarp();
-    mont_mul<S, TPI>(a, ybuf, nn, n0, r);  // x^2
+    mont<S, TPI, FORM>(a, ybuf, nn, n0, r);  // x^2
     __syncwarp();
     store_slice<L>(ybuf, a, r);
     load_slice<L>(a, tbl, r);
     __syncwarp();
 #pragma unroll 1
     for (uint32_t k = 1; k <= maxidx; k++) {  // T[k] = T[k-1] x^2 = x^(2k+1)
-      mont_mul<S, TPI>(a, ybuf, nn, n0, r);
+      mont<S, TPI, FORM>(a, ybuf, nn, n0, r);
       store_slice<L>(tbl + k * ROW, a, r);
     }
     __syncwarp();
@@ -333,9 +423,9 @@ __device__ __forceinline__ void exp_window(uint32_t (&a)[S / TPI], uint32_t *tbl
       __syncwarp();
       store_slice<L>(ybuf, a, r);
       __syncwarp();
-      mont_mul<S, TPI>(a, ybuf, nn, n0, r);
+      mont<S, TPI, FORM>(a, ybuf, nn, n0, r);
     }
-    if (idx != 0xffu) mont_mul<S, TPI>(a, tbl + idx * ROW, nn, n0, r);
+    if (idx != 0xffu) mont<S, TPI, FORM>(a, tbl + idx * ROW, nn, n0, r);
   }
 }
 

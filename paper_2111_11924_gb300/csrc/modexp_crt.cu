@@ -3,11 +3,16 @@
 
 namespace pmk {
 
+using dev::kChain;
+using dev::kCols;
+
 const ModexpEntry *modexp_entries_crt(int *count) {
   static const ModexpEntry entries[] = {
-      make_entry<2, 2, true>(),  make_entry<4, 2, true>(),  make_entry<8, 2, true>(),
-      make_entry<16, 2, true>(), make_entry<32, 4, true>(), make_entry<32, 8, true>(),
-      make_entry<48, 8, true>(), make_entry<64, 8, true>(), make_entry<64, 16, true>(),
+      make_entry<2, 2, true, kChain>(),  make_entry<4, 2, true, kChain>(),  make_entry<8, 2, true, kChain>(),
+      make_entry<16, 2, true, kChain>(), make_entry<32, 4, true, kChain>(), make_entry<32, 8, true, kChain>(),
+      make_entry<32, 4, true, kCols>(),  make_entry<32, 8, true, kCols>(),  make_entry<48, 8, true, kChain>(),
+      make_entry<48, 8, true, kCols>(),  make_entry<64, 8, true, kChain>(), make_entry<64, 16, true, kChain>(),
+      make_entry<64, 8, true, kCols>(),  make_entry<64, 16, true, kCols>(),
   };
   *count = (int)(sizeof(entries) / sizeof(entries[0]));
   return entries;

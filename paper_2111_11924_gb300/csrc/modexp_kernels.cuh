@@ -16,7 +16,7 @@ namespace dev {
 // CRT:  out[t][half] = in[t]^{d_p | d_q} mod (p | q) over S = nbits / 64
 //       limbs, input reduced via in mod p = hi R + lo -> MontMul(hi, R^3) +
 //       MontMul(lo, R^2) = in R mod p.  Garner combines the halves afterwards.
-template <int S, int TPI, bool CRT>
+template <int S, int TPI, bool CRT, int FORM>
 __global__ void __launch_bounds__(kThreads) k_modexp(const KeyDev *__restrict__ keys, uint32_t K,
                                                      const uint32_t *__restrict__ in, uint32_t *__restrict__ out,
                                                      long long n, int enc) {
@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(kThreads) k_modexp(const KeyDev *__restrict__ 
 #pragma unroll
       for (int j = 0; j < L; j++) a[j] = 0;
     }
-    mont_mul<S, TPI>(a, sR2, nn, n0, r);  // x R mod N
+    mont<S, TPI, FORM>(a, sR2, nn, n0, r);  // x R mod N
   } else {
     uint32_t lo[L];
     if (active) {
@@ -71,12 +71,12 @@ __global__ void __launch_bounds__(kThreads) k_modexp(const KeyDev *__restrict__ 
 #pragma unroll
       for (int j = 0; j < L; j++) lo[j] = a[j] = 0;
     }
-    mont_mul<S, TPI>(a, sR3, nn, n0, r);   // hi R^2 mod p
-    mont_mul<S, TPI>(lo, sR2, nn, n0, r);  // lo R mod p
+    mont<S, TPI, FORM>(a, sR3, nn, n0, r);   // hi R^2 mod p
+    mont<S, TPI, FORM>(lo, sR2, nn, n0, r);  // lo R mod p
     mod_add<L, TPI>(a, lo, nn, r);         // (hi R + lo) R mod p
   }
-  exp_window<S, TPI>(a, tbl, ybuf, sched, nsteps, maxidx, nn, n0, r);
-  mont_mul<S, TPI>(a, sOne, nn, n0, r);  // leave the Montgomery domain
+  exp_window<S, TPI, FORM>(a, tbl, ybuf, sched, nsteps, maxidx, nn, n0, r);
+  mont<S, TPI, FORM>(a, sOne, nn, n0, r);  // leave the Montgomery domain
   if (active) {
     uint32_t *o = out + t * W + (CRT ? half * S : 0) + r * L;
     if constexpr (L % 4 == 0) {
@@ -96,17 +96,19 @@ constexpr size_t modexp_smem_bytes(int tpi) {
 
 }  // namespace dev
 
-// One compiled instantiation.
+// One compiled instantiation: limb count, lanes per instance, CRT or full
+// width, Montgomery form (dev::kChain / dev::kCols).
 struct ModexpEntry {
   int limbs, tpi;
   bool crt;
+  int form;
   const void *fn;
   size_t smem;
 };
 
-template <int S, int TPI, bool CRT>
+template <int S, int TPI, bool CRT, int FORM>
 ModexpEntry make_entry() {
-  return ModexpEntry{S, TPI, CRT, reinterpret_cast<const void *>(&dev::k_modexp<S, TPI, CRT>),
+  return ModexpEntry{S, TPI, CRT, FORM, reinterpret_cast<const void *>(&dev::k_modexp<S, TPI, CRT, FORM>),
                      dev::modexp_smem_bytes<S>(TPI)};
 }
 

@@ -85,9 +85,9 @@ extern "C" int pmk_decrypt_message_host_noalloc(const pmk_keyset *ks, const uint
     }
     rc = launch_range_check(ks->d_keys, ks->K, S, d_cipher, n_chunks, d_status, st);
     if (rc == PMK_OK && !use_crt)
-      rc = launch_modexp(ExpMode::kDecrypt, S, default_tpi(S), ks->d_keys, ks->K, d_cipher, d_plain, n_chunks, st);
+      rc = launch_modexp(ExpMode::kDecrypt, S, default_config(S, false), ks->d_keys, ks->K, d_cipher, d_plain, n_chunks, st);
     if (rc == PMK_OK && use_crt) {
-      rc = launch_modexp(ExpMode::kCrtHalf, H, default_tpi(H), ks->d_keys, ks->K, d_cipher, d_plain, n_chunks, st);
+      rc = launch_modexp(ExpMode::kCrtHalf, H, default_config(H, true), ks->d_keys, ks->K, d_cipher, d_plain, n_chunks, st);
       if (rc == PMK_OK) rc = launch_garner(H, ks->d_keys, ks->K, d_plain, n_chunks, st);
     }
     if (rc == PMK_OK) rc = launch_join(ks->nbits, d_plain, n_chunks, d_msg, msg_len, st);

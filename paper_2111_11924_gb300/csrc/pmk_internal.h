@@ -62,12 +62,17 @@ int launch_split(uint32_t nbits, const uint8_t *msg, size_t len, uint32_t *chunk
 int launch_join(uint32_t nbits, const uint32_t *chunks, size_t n, uint8_t *msg, size_t len, cudaStream_t st);
 int launch_range_check(const KeyDev *keys, uint32_t K, uint32_t s, const uint32_t *in, size_t n,
                        uint32_t *status, cudaStream_t st);
-int launch_modexp(ExpMode mode, uint32_t limbs, uint32_t tpi, const KeyDev *keys, uint32_t K, const uint32_t *in,
+// Launch geometry of an exponentiation kernel: lanes per instance and
+// Montgomery form (0 = one carry chain per lane, 1 = independent columns).
+struct KernelConfig {
+  uint32_t tpi = 0, form = 0;
+};
+int launch_modexp(ExpMode mode, uint32_t limbs, KernelConfig cfg, const KeyDev *keys, uint32_t K, const uint32_t *in,
                   uint32_t *out, size_t n, cudaStream_t st);
 int launch_garner(uint32_t half_limbs, const KeyDev *keys, uint32_t K, uint32_t *out, size_t n, cudaStream_t st);
-bool modexp_supported(uint32_t limbs, uint32_t tpi);
-bool modexp_built(uint32_t limbs, uint32_t tpi, bool crt);
-uint32_t default_tpi(uint32_t limbs);
+bool modexp_built(uint32_t limbs, KernelConfig cfg, bool crt);
+KernelConfig default_config(uint32_t limbs, bool crt);  // tpi == 0: limb count not built
+int list_configs(uint32_t limbs, bool crt, KernelConfig *out, int max);
 int measure_int_peak(double *macs_per_clk_per_sm, double *sm_mhz, int *num_sms);
 
 }  // namespace pmk

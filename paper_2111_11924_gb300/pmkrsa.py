@@ -60,7 +60,10 @@ def load_library() -> ctypes.CDLL:
         "pmk_strerror": (ctypes.c_char_p, [i]),
         "pmk_measure_int_peak": (i, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(i)]),
-        "pmk_set_threads_per_instance": (i, [vp, u32, u32]),
+        "pmk_set_kernel_config": (i, [vp, u32, i, u32, u32]),
+        "pmk_get_kernel_config": (i, [vp, u32, i, P32, P32]),
+        "pmk_list_kernel_configs": (i, [u32, i, P32, P32, i]),
+        "pmk_autotune": (i, [vp, vp, sz, i, i, P32, P32, ctypes.POINTER(ctypes.c_float)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -273,8 +276,35 @@ class Context:
                "pmk_measure_int_peak")
         return {"macs_per_clk_per_sm": m.value, "sm_mhz": mhz.value, "num_sms": sms.value}
 
-    def set_threads_per_instance(self, limbs: int, tpi: int) -> None:
-        _check(load_library().pmk_set_threads_per_instance(self.handle, limbs, tpi), "pmk_set_threads_per_instance")
+    def set_kernel_config(self, limbs: int, crt: bool, tpi: int, form: int = 0) -> None:
+        """Lanes per instance and Montgomery form for (limbs, crt); tpi = 0 restores the default."""
+        _check(load_library().pmk_set_kernel_config(self.handle, limbs, int(crt), tpi, form), "pmk_set_kernel_config")
+
+    def autotune(self, ks: KeySet, n_chunks: int, mode: str = "decrypt", reps: int = 3) -> dict:
+        """Time every compiled geometry for this key set and batch size; keep the fastest.
+        mode: "encrypt", "decrypt" (full d) or "crt"."""
+        m = {"encrypt": 0, "decrypt": 1, "crt": 2}[mode]
+        tpi, form, ms = np.zeros(1, np.uint32), np.zeros(1, np.uint32), ctypes.c_float()
+        _check(load_library().pmk_autotune(self.handle, ks.handle, n_chunks, m, reps, _p32(tpi), _p32(form),
+                                           ctypes.byref(ms)), "pmk_autotune")
+        return {"tpi": int(tpi[0]), "form": int(form[0]), "ms": ms.value}
+
+    def get_kernel_config(self, limbs: int, crt: bool) -> tuple:
+        tpi, form = np.zeros(1, np.uint32), np.zeros(1, np.uint32)
+        _check(load_library().pmk_get_kernel_config(self.handle, limbs, int(crt), _p32(tpi), _p32(form)),
+               "pmk_get_kernel_config")
+        return int(tpi[0]), int(form[0])
+
+
+def kernel_configs(limbs: int, crt: bool) -> list:
+    """Compiled (tpi, form) geometries for an exponentiation over `limbs` limbs."""
+    lib = load_library()
+    n = lib.pmk_list_kernel_configs(limbs, int(crt), None, None, 0)
+    if n <= 0:
+        return []
+    tpi, form = np.zeros(n, np.uint32), np.zeros(n, np.uint32)
+    lib.pmk_list_kernel_configs(limbs, int(crt), _p32(tpi), _p32(form), n)
+    return list(zip(tpi.tolist(), form.tolist()))
 
 
 def decrypt_message_host_noalloc(ks: KeySet, h_cipher, h_msg, use_crt: bool = False, stream=None) -> int:

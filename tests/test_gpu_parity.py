@@ -165,26 +165,31 @@ def test_1mib_2048_encrypt_all_decrypt_sampled(ctx):
 
 # ------------------------------------------------------------------ launch geometries
 
-@pytest.mark.parametrize("nbits,limbs,tpis", [(2048, 64, [4, 8, 16]), (1024, 32, [4, 8]), (2048, 32, [4, 8])])
-def test_threads_per_instance_variants(ctx, nbits, limbs, tpis):
+@pytest.mark.parametrize("nbits,crt", [(2048, False), (2048, True), (1024, False), (1024, True), (4096, False),
+                                       (3072, True)])
+def test_every_kernel_geometry(ctx, P, nbits, crt):
+    """Every compiled (lanes, form) geometry gives the same bit-exact result."""
     K = 3
-    ks, ok = keys_for(ctx, K, nbits, seed=4242)
+    ks, ok = keys_for(ctx, K, nbits, seed=4242 + nbits)
     rng = np.random.default_rng(1)
     Ns = ok.ints("N")
     n = 37  # ragged: several blocks per key and a partial one
     c = np.stack([oracle.to_limbs(W.random_below(rng, Ns[t % K]), nbits // 32) for t in range(n)])
-    ref_full = oracle.decrypt_chunks(c[:9], ok)
+    ref = oracle.decrypt_chunks(c[:6], ok)
+    limbs = nbits // 64 if crt else nbits // 32
+    configs = P.kernel_configs(limbs, crt)
+    assert len(configs) >= 1
     outs = []
-    for tpi in tpis:
-        ctx.set_threads_per_instance(limbs, tpi)
+    for tpi, form in configs:
+        ctx.set_kernel_config(limbs, crt, tpi, form)
         try:
-            use_crt = limbs != nbits // 32
-            outs.append(host(ctx.decrypt_chunks(ks, dev(c), use_crt=use_crt)))
+            outs.append(host(ctx.decrypt_chunks(ks, dev(c), use_crt=crt)))
         finally:
-            ctx.set_threads_per_instance(limbs, 0)
-    for o in outs:
-        assert np.array_equal(o[:9], ref_full)
-        assert np.array_equal(o, outs[0])
+            ctx.set_kernel_config(limbs, crt, 0)
+    for o, cfg in zip(outs, configs):
+        assert np.array_equal(o[:6], ref), cfg
+        assert np.array_equal(o, outs[0]), cfg
+    assert ctx.get_kernel_config(limbs, crt)[0] in {t for t, _ in configs}
 
 
 @pytest.mark.parametrize("nbits", [3072, 4096])
@@ -268,3 +273,19 @@ def test_host_buffer_calls_and_from_primes(ctx):
     ks2 = ctx.keyset_from_primes(w.nbits, w.e, ok.a["p"], ok.a["q"])
     ex = ks2.export()
     assert all(np.array_equal(ex[f], ok.a[f]) for f in ok.a)
+
+
+@pytest.mark.parametrize("mode", ["encrypt", "decrypt", "crt"])
+def test_autotune_chooses_a_built_geometry(ctx, P, mode):
+    ks, ok = keys_for(ctx, 2, 1024, seed=555)
+    res = ctx.autotune(ks, 300, mode, reps=1)
+    limbs = 16 if mode == "crt" else 32
+    assert (res["tpi"], res["form"]) in P.kernel_configs(limbs, mode == "crt")
+    assert res["ms"] > 0
+    assert ctx.get_kernel_config(limbs, mode == "crt") == (res["tpi"], res["form"])
+    rng = np.random.default_rng(9)
+    m = np.stack([oracle.to_limbs(W.random_below(rng, N), 32) for N in ok.ints("N") * 5])
+    c = ctx.encrypt_chunks(ks, dev(m))
+    assert np.array_equal(host(c), oracle.encrypt_chunks(m, ok))
+    assert np.array_equal(host(ctx.decrypt_chunks(ks, c, use_crt=(mode == "crt"))), m)
+    ctx.set_kernel_config(limbs, mode == "crt", 0)
