@@ -57,7 +57,7 @@ void pmk_ctx_destroy(pmk_ctx *ctx);
  * `seed`; candidates pass trial division by the odd primes below 2000,
  * gcd(e, p-1) = 1 and 40 Miller-Rabin rounds with bases (splitmix64()>>1)+2.
  * Runs on the host; then uploads the key tables to the context's device.
- *   nbits: 128..4096, a multiple of 128 (EUNSUPPORTED if not built).
+ *   nbits: 128..8192, a multiple of 128 (EUNSUPPORTED if not built).
  *   e: odd, 3 <= e < 2^32.
  */
 int pmk_keygen(pmk_ctx *ctx, uint32_t K, uint32_t nbits, uint64_t e, uint64_t seed, pmk_keyset **out);

@@ -207,7 +207,7 @@ void pmk_ctx_destroy(pmk_ctx *ctx) {
 
 int pmk_keygen(pmk_ctx *ctx, uint32_t K, uint32_t nbits, uint64_t e, uint64_t seed, pmk_keyset **out) {
   if (!ctx || !out) return PMK_EINVAL;
-  if (K == 0 || nbits < 128 || nbits > 4096 || nbits % 128 || e < 3 || !(e & 1) || (e >> 32)) return PMK_EINVAL;
+  if (K == 0 || nbits < 128 || nbits > 8192 || nbits % 128 || e < 3 || !(e & 1) || (e >> 32)) return PMK_EINVAL;
   if (!width_built(nbits)) return PMK_EUNSUPPORTED;
   try {
     pmk_keyset *ks = new pmk_keyset();
@@ -228,7 +228,7 @@ int pmk_keygen(pmk_ctx *ctx, uint32_t K, uint32_t nbits, uint64_t e, uint64_t se
 
 int pmk_keygen_host(uint32_t K, uint32_t nbits, uint64_t e, uint64_t seed, uint32_t *N, uint32_t *d, uint32_t *p,
                     uint32_t *q, uint32_t *dp, uint32_t *dq, uint32_t *qinv) {
-  if (K == 0 || nbits < 128 || nbits > 4096 || nbits % 128 || e < 3 || !(e & 1) || (e >> 32)) return PMK_EINVAL;
+  if (K == 0 || nbits < 128 || nbits > 8192 || nbits % 128 || e < 3 || !(e & 1) || (e >> 32)) return PMK_EINVAL;
   try {
     pmk_keyset ks;
     ks.K = K;
@@ -245,7 +245,7 @@ int pmk_keygen_host(uint32_t K, uint32_t nbits, uint64_t e, uint64_t seed, uint3
 int pmk_keyset_from_primes(pmk_ctx *ctx, uint32_t K, uint32_t nbits, uint64_t e, const uint32_t *p,
                            const uint32_t *q, pmk_keyset **out) {
   if (!ctx || !out || !p || !q || K == 0) return PMK_EINVAL;
-  if (nbits < 128 || nbits > 4096 || nbits % 128 || e < 3 || !(e & 1) || (e >> 32)) return PMK_EINVAL;
+  if (nbits < 128 || nbits > 8192 || nbits % 128 || e < 3 || !(e & 1) || (e >> 32)) return PMK_EINVAL;
   if (!width_built(nbits)) return PMK_EUNSUPPORTED;
   try {
     pmk_keyset *ks = new pmk_keyset();
@@ -308,7 +308,7 @@ size_t pmk_num_chunks(size_t msg_len, uint32_t nbits) {
 
 int pmk_split(pmk_ctx *ctx, uint32_t nbits, const uint8_t *d_msg, size_t msg_len, uint32_t *d_chunks, size_t n_chunks,
               void *stream) {
-  if (!ctx || nbits < 128 || nbits % 128 || nbits > 4096) return PMK_EINVAL;
+  if (!ctx || nbits < 128 || nbits % 128 || nbits > 8192) return PMK_EINVAL;
   if (n_chunks != pmk_num_chunks(msg_len, nbits)) return PMK_EINVAL;
   if (n_chunks == 0) return PMK_OK;
   if (!d_msg || !d_chunks) return PMK_EINVAL;
@@ -319,7 +319,7 @@ int pmk_split(pmk_ctx *ctx, uint32_t nbits, const uint8_t *d_msg, size_t msg_len
 
 int pmk_join(pmk_ctx *ctx, uint32_t nbits, const uint32_t *d_chunks, size_t n_chunks, uint8_t *d_msg, size_t msg_len,
              void *stream) {
-  if (!ctx || nbits < 128 || nbits % 128 || nbits > 4096) return PMK_EINVAL;
+  if (!ctx || nbits < 128 || nbits % 128 || nbits > 8192) return PMK_EINVAL;
   if (n_chunks != pmk_num_chunks(msg_len, nbits)) return PMK_EINVAL;
   if (msg_len == 0) return PMK_OK;
   if (!d_msg || !d_chunks) return PMK_EINVAL;

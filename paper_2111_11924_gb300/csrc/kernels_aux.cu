@@ -4,6 +4,7 @@
 #include <mutex>
 #include <set>
 #include <utility>
+#include <vector>
 
 #include "modexp_kernels.cuh"
 
@@ -80,7 +81,7 @@ __global__ void __launch_bounds__(kAuxThreads) k_garner(const KeyDev *__restrict
   const uint32_t *p = kd.P[0], *q = kd.P[1], *qm = kd.qinv_m;
   const uint32_t n0 = kd.n0h[0];
   uint32_t *o = out + t * 2 * H;
-  uint32_t mq[64], d[64], acc[128];
+  uint32_t mq[128], d[128], acc[256];
   // mq mod p: m_q < q < 2p, so at most one subtraction
   uint32_t borrow = 0;
   for (int i = 0; i < H; i++) {
@@ -163,11 +164,21 @@ int grid_for(long long work, int threads) {
 
 int cuda_rc(cudaError_t e) { return e == cudaSuccess ? PMK_OK : PMK_ECUDA; }
 
-const ModexpEntry *find_entry(uint32_t limbs, KernelConfig cfg, bool crt) {
-  int n = 0;
+// Every compiled instantiation of one mode (the wide-key list is shared).
+std::vector<ModexpEntry> entries(bool crt) {
+  int n = 0, m = 0;
   const ModexpEntry *list = crt ? modexp_entries_crt(&n) : modexp_entries_full(&n);
-  for (int i = 0; i < n; i++)
-    if (list[i].limbs == (int)limbs && list[i].tpi == (int)cfg.tpi && list[i].form == (int)cfg.form) return &list[i];
+  const ModexpEntry *wide = modexp_entries_wide(&m);
+  std::vector<ModexpEntry> v(list, list + n);
+  for (int i = 0; i < m; i++)
+    if (wide[i].crt == crt) v.push_back(wide[i]);
+  return v;
+}
+
+const ModexpEntry *find_entry(uint32_t limbs, KernelConfig cfg, bool crt) {
+  static const std::vector<ModexpEntry> full = entries(false), half = entries(true);
+  for (const ModexpEntry &e : crt ? half : full)
+    if (e.limbs == (int)limbs && e.tpi == (int)cfg.tpi && e.form == (int)cfg.form) return &e;
   return nullptr;
 }
 
@@ -199,7 +210,7 @@ int launch_range_check(const KeyDev *keys, uint32_t K, uint32_t s, const uint32_
 
 int launch_garner(uint32_t half_limbs, const KeyDev *keys, uint32_t K, uint32_t *out, size_t n, cudaStream_t st) {
   if (n == 0) return PMK_OK;
-  if (half_limbs > 64) return PMK_EUNSUPPORTED;
+  if (half_limbs > 128) return PMK_EUNSUPPORTED;
   k_garner<<<(unsigned)((n + kAuxThreads - 1) / kAuxThreads), kAuxThreads, 0, st>>>(keys, K, (int)half_limbs, out,
                                                                                     (long long)n);
   return cuda_rc(cudaGetLastError());
@@ -217,7 +228,7 @@ KernelConfig default_config(uint32_t limbs, bool crt) {
     case 32: c.tpi = 4; c.form = crt ? 1 : 0; break;
     case 48: case 96: c.tpi = 8; break;
     case 64: c.tpi = 8; c.form = crt ? 0 : 1; break;
-    case 128: c.tpi = 16; break;
+    case 128: case 192: case 256: c.tpi = 16; break;
     default: break;
   }
   if (c.tpi && !find_entry(limbs, c, crt)) c = KernelConfig();
@@ -225,11 +236,10 @@ KernelConfig default_config(uint32_t limbs, bool crt) {
 }
 
 int list_configs(uint32_t limbs, bool crt, KernelConfig *out, int max) {
-  int n = 0, k = 0;
-  const ModexpEntry *list = crt ? modexp_entries_crt(&n) : modexp_entries_full(&n);
-  for (int i = 0; i < n; i++)
-    if (list[i].limbs == (int)limbs) {
-      if (k < max && out) out[k] = KernelConfig{(uint32_t)list[i].tpi, (uint32_t)list[i].form};
+  int k = 0;
+  for (const ModexpEntry &e : entries(crt))
+    if (e.limbs == (int)limbs) {
+      if (k < max && out) out[k] = KernelConfig{(uint32_t)e.tpi, (uint32_t)e.form};
       k++;
     }
   return k;

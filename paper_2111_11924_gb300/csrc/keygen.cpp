@@ -335,13 +335,19 @@ void finish_key(uint32_t nbits, u64 e, const std::vector<u64> &p, const std::vec
   k.sched_h[1] = make_schedule(k.dq.data(), (int)h);
 }
 
-bool valid_width(uint32_t nbits) { return nbits >= 128 && nbits <= 4096 && nbits % 128 == 0; }
+bool valid_width(uint32_t nbits) { return nbits >= 128 && nbits <= 8192 && nbits % 128 == 0; }
 
 }  // namespace
 
+#ifndef PMK_TABLE_MAX
+#define PMK_TABLE_MAX 16
+#endif
+// Widest window whose odd powers fit the kernels' table (2^(w-1) entries).
+constexpr int kMaxWindow = PMK_TABLE_MAX >= 16 ? 5 : PMK_TABLE_MAX >= 8 ? 4 : PMK_TABLE_MAX >= 4 ? 3 : 2;
+
 // Sliding-window recoding of an exponent, scanned from its top bit.  The
-// window width w <= 5 (at most 16 odd powers) minimises the product count
-// (table entries + multiplies) for this exponent.
+// window width w <= kMaxWindow (at most PMK_TABLE_MAX odd powers) minimises
+// the product count (table entries + multiplies) for this exponent.
 Schedule make_schedule(const uint32_t *exp, int nlimbs) {
   int top = -1;
   for (int i = 32 * nlimbs - 1; i >= 0; i--)
@@ -353,7 +359,7 @@ Schedule make_schedule(const uint32_t *exp, int nlimbs) {
   size_t best_cost = ~(size_t)0;
   if (top < 0) return best;  // exponent 0: empty schedule (callers reject it)
   auto bit = [&](int i) { return (exp[i / 32] >> (i % 32)) & 1; };
-  for (int w = 1; w <= 5; w++) {
+  for (int w = 1; w <= kMaxWindow; w++) {
     Schedule sc;
     int i = top, pending = 0;
     bool first = true;

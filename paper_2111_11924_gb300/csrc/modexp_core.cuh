@@ -28,7 +28,10 @@ namespace pmk {
 namespace dev {
 
 constexpr int kThreads = 128;   // threads per block (4 warps)
-constexpr int kTableMax = 16;   // odd powers x^1 .. x^31 (window width <= 5)
+#ifndef PMK_TABLE_MAX
+#define PMK_TABLE_MAX 16
+#endif
+constexpr int kTableMax = PMK_TABLE_MAX;  // odd powers x^1 .. x^(2 kTableMax - 1)
 constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ void add_cc(uint32_t &r, uint32_t a, uint32_t b) {

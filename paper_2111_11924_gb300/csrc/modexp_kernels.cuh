@@ -115,5 +115,6 @@ ModexpEntry make_entry() {
 // Instantiation lists live in separate translation units (compiled in parallel).
 const ModexpEntry *modexp_entries_full(int *count);
 const ModexpEntry *modexp_entries_crt(int *count);
+const ModexpEntry *modexp_entries_wide(int *count);  // 6144/8192-bit full width, 3072/4096-bit CRT halves
 
 }  // namespace pmk

@@ -1,0 +1,22 @@
+// Wide-key instantiations: 6144- and 8192-bit full width (192 / 256 limbs)
+// and the CRT halves of 6144- and 8192-bit keys (96 / 128 limbs).
+#include "modexp_kernels.cuh"
+
+namespace pmk {
+
+using dev::kChain;
+using dev::kCols;
+
+const ModexpEntry *modexp_entries_wide(int *count) {
+  static const ModexpEntry entries[] = {
+      make_entry<192, 16, false, kChain>(), make_entry<192, 16, false, kCols>(),
+      make_entry<256, 16, false, kChain>(), make_entry<256, 16, false, kCols>(),
+      make_entry<256, 32, false, kChain>(), make_entry<96, 8, true, kChain>(),
+      make_entry<96, 16, true, kChain>(),   make_entry<96, 16, true, kCols>(),
+      make_entry<128, 16, true, kChain>(),  make_entry<128, 16, true, kCols>(),
+  };
+  *count = (int)(sizeof(entries) / sizeof(entries[0]));
+  return entries;
+}
+
+}  // namespace pmk

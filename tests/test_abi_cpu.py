@@ -70,7 +70,7 @@ def test_library_keygen_matches_oracle(P, K, nbits, e, seed):
 
 
 def test_keygen_argument_errors(P):
-    for bad in [(0, 1024, 65537), (1, 1000, 65537), (1, 1024, 4), (1, 1024, 1), (1, 8192, 65537), (1, 1024, 1 << 33)]:
+    for bad in [(0, 1024, 65537), (1, 1000, 65537), (1, 1024, 4), (1, 1024, 1), (1, 16384, 65537), (1, 1024, 1 << 33)]:
         with pytest.raises(P.PMKError):
             P.keygen_host(*bad, seed=1)
 

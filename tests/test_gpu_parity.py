@@ -289,3 +289,49 @@ def test_autotune_chooses_a_built_geometry(ctx, P, mode):
     assert np.array_equal(host(c), oracle.encrypt_chunks(m, ok))
     assert np.array_equal(host(ctx.decrypt_chunks(ks, c, use_crt=(mode == "crt"))), m)
     ctx.set_kernel_config(limbs, mode == "crt", 0)
+
+
+def _checked_wide_keys(ctx, K, nbits, seed):
+    """Library keygen at widths where the oracle's keygen takes minutes; every
+    key is verified here with Python integers instead (N = pq, e d = 1 mod phi,
+    Fermat probable primes, CRT values)."""
+    ks = ctx.keygen(K, nbits, 65537, seed)
+    ex = ks.export()
+    keys = []
+    for k in range(K):
+        v = {f: oracle.from_limbs(ex[f][k]) for f in ex}
+        p, q, N, d = v["p"], v["q"], v["N"], v["d"]
+        assert N == p * q and N.bit_length() == nbits and p != q
+        phi = (p - 1) * (q - 1)
+        assert (d * 65537) % phi == 1
+        for f in (p, q):
+            assert f.bit_length() == nbits // 2 and all(pow(b, f - 1, f) == 1 for b in (2, 3, 5, 7))
+        assert v["dp"] == d % (p - 1) and v["dq"] == d % (q - 1) and (v["qinv"] * q) % p == 1
+        keys.append(v)
+    return ks, keys
+
+
+@pytest.mark.parametrize("nbits", [6144, 8192])
+def test_6144_8192_bit_keys(ctx, P, nbits):
+    ks, keys = _checked_wide_keys(ctx, 2, nbits, seed=0x50444D4B00008000 + nbits)
+    s = nbits // 32
+    rng = np.random.default_rng(nbits)
+    vals = [W.random_below(rng, keys[t % 2]["N"]) for t in range(5)]
+    m = np.stack([oracle.to_limbs(v, s) for v in vals])
+    c = host(ctx.encrypt_chunks(ks, dev(m)))
+    for t in range(5):
+        assert oracle.from_limbs(c[t]) == oracle.modexp(vals[t], 65537, keys[t % 2]["N"]), t
+    k0 = keys[0]
+    ref0 = oracle.modexp(oracle.from_limbs(c[0]), k0["d"], k0["N"])
+    assert ref0 == vals[0]
+    for crt in (False, True):
+        limbs = s // 2 if crt else s
+        for tpi, form in P.kernel_configs(limbs, crt):
+            ctx.set_kernel_config(limbs, crt, tpi, form)
+            try:
+                got = host(ctx.decrypt_chunks(ks, dev(c), use_crt=crt))
+            finally:
+                ctx.set_kernel_config(limbs, crt, 0)
+            assert np.array_equal(got, m), (crt, tpi, form)
+            assert oracle.from_limbs(got[0]) == ref0
+    assert ctx.status() == 0
