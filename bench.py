@@ -379,6 +379,128 @@ def run_profile(args):
     return 0
 
 
+def run_widths(args):
+    """The paper's Table 2 workload at every key length: a 102,400-byte
+    random plaintext, K = 16 key pairs, split -> encrypt -> decrypt -> join,
+    full d and CRT, geometry autotuned per key length.  One JSON line per
+    width (the plain path, without the blinding matrix)."""
+    import torch
+
+    import paper_2111_11924_gb300 as P
+
+    ctx = P.Context(0)
+    for nbits in args.width_list:
+        w = W.Workload(100 + nbits, f"pmkrsa-100KB-K16-{nbits}bit", 102400, 16, nbits)
+        ks = ctx.keygen(w.K, w.nbits, w.e, w.key_seed)
+        d_msg = torch.from_numpy(w.message()).cuda()
+        n = w.n_chunks
+        tuned = {m: ctx.autotune(ks, n, m, reps=2) for m in ("encrypt", "decrypt", "crt")}
+        chunks = ctx.split(w.nbits, d_msg)
+        cipher = ctx.encrypt_chunks(ks, chunks)
+        out = torch.empty_like(chunks)
+        res = {}
+        for name, fn in (("encrypt", lambda: ctx.encrypt_chunks(ks, chunks, out=cipher)),
+                         ("decrypt", lambda: ctx.decrypt_chunks(ks, cipher, out=out)),
+                         ("decrypt_crt", lambda: ctx.decrypt_chunks(ks, cipher, use_crt=True, out=out))):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
+            ts = []
+            for i in range(args.steps):
+                ev[2 * i].record()
+                fn()
+                ev[2 * i + 1].record()
+            torch.cuda.synchronize()
+            ts = [ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(args.steps)]
+            res[name] = statistics.median(ts)
+            if name != "encrypt":
+                assert torch.equal(out, chunks)
+        ctx.check()
+        print(json.dumps({"workload": w.name, "key_bits": nbits, "chunks": n, "keys": w.K,
+                          "ms": {k: round(v, 4) for k, v in res.items()},
+                          "chunk_modexps_per_s": {k: round(n / (v / 1e3)) for k, v in res.items()},
+                          "geometry": {m: (t["tpi"], ["chain", "columns"][t["form"]]) for m, t in tuned.items()}}))
+        ks.free()
+    return 0
+
+
+def run_batched(args):
+    """Many messages of mixed sizes and key widths in one batch: 64 messages,
+    sizes log-uniform over 4 KB - 25 MB (times --batch-scale), each with its
+    own K in {2, 4, 8, 16} and key width in {1024, 2048, 3072, 4096} bits;
+    ops 70% full-d decrypt, 10% CRT decrypt, 20% encrypt.  Times the plain
+    path (one call, one launch per job, on one stream) against the batched
+    path (pmk_batch: one persistent kernel per width, graph-replayed), after
+    autotuning every (width, mode), and checks both give identical output."""
+    import torch
+
+    import paper_2111_11924_gb300 as P
+    from paper_2111_11924_gb300 import pmkrsa as B
+
+    rng = np.random.default_rng(0x50444D4B0000C000)
+    ctx = P.Context(0)
+    keysets, jobs, payload = {}, [], 0
+    for m in range(64):
+        size = int(np.exp(rng.uniform(np.log(4096), np.log(25e6))) * args.batch_scale)
+        K = int(rng.choice([2, 4, 8, 16]))
+        nbits = int(rng.choice([1024, 2048, 3072, 4096]))
+        op = int(rng.choice([B.OP_DECRYPT, B.OP_DECRYPT_CRT, B.OP_ENCRYPT], p=[0.7, 0.1, 0.2]))
+        if (K, nbits) not in keysets:
+            keysets[K, nbits] = ctx.keygen(K, nbits, 65537, 0x50444D4B0000C100 + 16 * K + nbits)
+        ks = keysets[K, nbits]
+        msg = torch.from_numpy(np.random.default_rng(m).integers(0, 256, max(size, 1), dtype=np.uint8)).cuda()
+        plain = ctx.split(nbits, msg)
+        src = plain if op == B.OP_ENCRYPT else ctx.encrypt_chunks(ks, plain)
+        jobs.append((ks, src, torch.empty_like(src), op))
+        payload += msg.numel()
+    torch.cuda.synchronize()
+    n_total = sum(j[1].shape[0] for j in jobs)
+    tuned = {}
+    for (K, nbits), ks in keysets.items():
+        for mode, op in (("encrypt", B.OP_ENCRYPT), ("decrypt", B.OP_DECRYPT), ("crt", B.OP_DECRYPT_CRT)):
+            n = sum(j[1].shape[0] for j in jobs if j[0].nbits == nbits and j[3] == op)
+            if n and (nbits, mode) not in tuned:
+                tuned[nbits, mode] = ctx.autotune(ks, min(n, 50000), mode, reps=1)
+
+    def per_call():
+        for ks, x, out, op in jobs:
+            if op == B.OP_ENCRYPT:
+                ctx.encrypt_chunks(ks, x, out=out)
+            else:
+                ctx.decrypt_chunks(ks, x, use_crt=(op == B.OP_DECRYPT_CRT), out=out)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ts = []
+        for _ in range(reps):
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    t_plain = timed(per_call, args.steps)
+    ref = [j[2].clone() for j in jobs]
+    batch = ctx.batch(jobs)
+    t_batch = timed(batch.launch, args.steps)
+    ctx.check()
+    same = all(torch.equal(j[2], r) for j, r in zip(jobs, ref))
+    line = {"mode": "batched", "messages": len(jobs), "payload_bytes": payload, "chunk_modexps": n_total,
+            "scale": args.batch_scale, "per_call_ms": t_plain, "batched_ms": t_batch,
+            "per_call_chunk_modexps_per_s": n_total / (t_plain / 1e3),
+            "batched_chunk_modexps_per_s": n_total / (t_batch / 1e3), "speedup": t_plain / t_batch,
+            "payload_MBps_batched": payload / 2**20 / (t_batch / 1e3), "identical_outputs": same,
+            "persistent_kernels": batch.n_kernels, "tasks": batch.n_tasks,
+            "geometry": {f"{nb}-{m}": [t["tpi"], ["chain", "columns"][t["form"]]] for (nb, m), t in tuned.items()}}
+    print(json.dumps(line))
+    batch.destroy()
+    return 0 if same else 1
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -389,6 +511,12 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="run the fixed launch sequence used for ncu captures and exit")
+    ap.add_argument("--batched", action="store_true",
+                    help="time the mixed-size 64-message batch (plain per-call vs persistent batch) and exit")
+    ap.add_argument("--batch-scale", type=float, default=1.0, help="scale of the batch's message sizes")
+    ap.add_argument("--widths", action="store_true",
+                    help="time the 100 KB / K=16 workload at each key length and exit")
+    ap.add_argument("--width-list", type=int, nargs="*", default=[1024, 2048, 3072, 4096, 6144, 8192])
     ap.add_argument("--profile-mib", type=int, default=0,
                     help="with --profile: message size in MiB instead of the 1 MiB workload")
     args = ap.parse_args(argv)
@@ -396,6 +524,10 @@ def main(argv=None):
         ap.error("--warmup must be >= 3")
     if args.profile:
         return run_profile(args)
+    if args.widths:
+        return run_widths(args)
+    if args.batched:
+        return run_batched(args)
     return run_reference(args) if args.impl == "reference" else run_ours(args)
 
 

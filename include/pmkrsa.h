@@ -164,6 +164,42 @@ int pmk_decrypt_message_host(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t 
 int pmk_decrypt_message_host_noalloc(const pmk_keyset *ks, const uint32_t *h_cipher, size_t n_chunks,
                                      uint8_t *h_msg, size_t msg_len, int use_crt, void *stream);
 
+/*
+ * Batched, persistent execution (the pipeline of Section 3.3 over many
+ * messages at once).  A job is one call's worth of work on a limb buffer:
+ *   op = PMK_OP_ENCRYPT (c = m^e), PMK_OP_DECRYPT (m = c^d, full d) or
+ *   PMK_OP_DECRYPT_CRT (Section 2.1 CRT form; d_in and d_out must not overlap),
+ * over n_chunks chunks, chunk t bound to key t mod K of the job's key set.
+ * Jobs may mix key sets and key widths.  pmk_batch_create plans the work:
+ *   - jobs are grouped by exponentiation width and mode; each group runs as
+ *     one persistent kernel whose warps take tasks (up to 32/TPI chunks of
+ *     one key) from a device queue, longest tasks first;
+ *   - groups run concurrently on internal streams, widest first;
+ *   - range checks, the kernels and CRT recombination are captured once into
+ *     a CUDA graph (geometry: the context's current kernel configs).
+ * pmk_batch_launch replays that graph on `stream` (asynchronous; errors via
+ * pmk_status).  The buffers named by the jobs must stay valid and keep their
+ * addresses for the batch's lifetime; their contents may change between
+ * launches.  Results are bit-identical to one pmk_*_chunks call per job.
+ */
+#define PMK_OP_ENCRYPT 0
+#define PMK_OP_DECRYPT 1
+#define PMK_OP_DECRYPT_CRT 2
+typedef struct pmk_job {
+  const pmk_keyset *ks;
+  const uint32_t *d_in;  /* n_chunks x nbits/32 limbs, 16-byte aligned */
+  uint32_t *d_out;       /* same shape */
+  size_t n_chunks;
+  int op;
+} pmk_job;
+typedef struct pmk_batch pmk_batch;
+
+int pmk_batch_create(pmk_ctx *ctx, const pmk_job *jobs, size_t n_jobs, pmk_batch **out);
+int pmk_batch_launch(pmk_batch *batch, void *stream);
+/* Tasks planned and persistent kernels per launch. */
+int pmk_batch_info(const pmk_batch *batch, size_t *n_tasks, int *n_kernels);
+void pmk_batch_destroy(pmk_batch *batch);
+
 /* Synchronise `stream`, then return (and clear) the first device-side error
  * recorded since the last call: PMK_OK or PMK_ERANGE; PMK_ECUDA if a CUDA
  * call fails. */

@@ -6,16 +6,6 @@
 
 #include "pmk_internal.h"
 
-struct pmk_ctx {
-  int device = 0;
-  uint32_t *d_status = nullptr;            // device-side error bits (pmk::kStatusRange)
-  uint8_t *d_msg = nullptr;                // staging of the *_host calls (grow-only)
-  size_t msg_cap = 0;
-  uint32_t *d_a = nullptr, *d_b = nullptr;
-  size_t a_cap = 0, b_cap = 0;             // in words
-  std::map<uint32_t, pmk::KernelConfig> cfg;  // (limbs << 1 | crt) -> kernel geometry override
-};
-
 namespace {
 
 using pmk::HostKey;

@@ -1,0 +1,222 @@
+// Batched persistent execution: plan tasks for many jobs, group them by
+// exponentiation width and mode, and capture range checks, one persistent
+// kernel per group (on forked streams) and CRT recombination into a CUDA
+// graph that pmk_batch_launch replays.
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "pmk_internal.h"
+
+struct pmk_batch {
+  int device = 0;
+  size_t n_tasks = 0;
+  int n_kernels = 0;
+  pmk::BatchTask *d_tasks = nullptr;
+  int *d_counters = nullptr;
+  cudaStream_t capture = nullptr;
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> events;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+struct Group {
+  uint32_t limbs = 0;
+  bool crt = false;
+  pmk::KernelConfig cfg;
+  std::vector<pmk::BatchTask> tasks;
+  size_t offset = 0;
+  int blocks = 0;
+};
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+bool overlap(const void *a, size_t na, const void *b, size_t nb) {
+  const char *x = static_cast<const char *>(a), *y = static_cast<const char *>(b);
+  return x < y + nb && y < x + na;
+}
+
+void release(pmk_batch *b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (cudaEvent_t e : b->events) cudaEventDestroy(e);
+  for (cudaStream_t s : b->side) cudaStreamDestroy(s);
+  if (b->capture) cudaStreamDestroy(b->capture);
+  cudaFree(b->d_tasks);
+  cudaFree(b->d_counters);
+}
+
+int plan_and_capture(pmk_ctx *ctx, const pmk_job *jobs, size_t n_jobs, pmk_batch *b) {
+  std::vector<Group> groups;
+  auto group_for = [&](uint32_t limbs, bool crt) -> Group * {
+    for (Group &g : groups)
+      if (g.limbs == limbs && g.crt == crt) return &g;
+    Group g;
+    g.limbs = limbs;
+    g.crt = crt;
+    if (pmk_get_kernel_config(ctx, limbs, crt ? 1 : 0, &g.cfg.tpi, &g.cfg.form) != PMK_OK) return nullptr;
+    groups.push_back(g);
+    return &groups.back();
+  };
+  for (size_t j = 0; j < n_jobs; j++) {
+    const pmk_job &jb = jobs[j];
+    if (jb.n_chunks == 0) continue;
+    const pmk_keyset *ks = jb.ks;
+    const bool crt = jb.op == PMK_OP_DECRYPT_CRT;
+    const uint32_t S = ks->nbits / 32, limbs = crt ? S / 2 : S;
+    Group *g = group_for(limbs, crt);
+    if (!g) return PMK_EUNSUPPORTED;
+    const uint32_t ipw = 32 / g->cfg.tpi;
+    for (uint32_t k = 0; k < ks->K && k < jb.n_chunks; k++) {
+      const long long count = ((long long)jb.n_chunks - k + ks->K - 1) / ks->K;
+      for (long long i0 = 0; i0 < count; i0 += ipw)
+        for (int half = 0; half < (crt ? 2 : 1); half++) {
+          pmk::BatchTask t;
+          t.key = ks->d_keys + k;
+          t.in = jb.d_in;
+          t.out = jb.d_out;
+          t.first = k + i0 * ks->K;
+          t.stride = ks->K;
+          t.count = (int)std::min<long long>(ipw, count - i0);
+          t.mode = crt ? 2 + half : (jb.op == PMK_OP_ENCRYPT ? 0 : 1);
+          g->tasks.push_back(t);
+        }
+    }
+  }
+  // longest work first: decryptions before encryptions within a group,
+  // widest groups launched first
+  for (Group &g : groups)
+    std::stable_sort(g.tasks.begin(), g.tasks.end(),
+                     [](const pmk::BatchTask &x, const pmk::BatchTask &y) { return (x.mode != 0) > (y.mode != 0); });
+  std::stable_sort(groups.begin(), groups.end(),
+                   [](const Group &x, const Group &y) { return x.limbs * (x.crt ? 1 : 2) > y.limbs * (y.crt ? 1 : 2); });
+  std::vector<pmk::BatchTask> all;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess) return PMK_ECUDA;
+  for (Group &g : groups) {
+    g.offset = all.size();
+    all.insert(all.end(), g.tasks.begin(), g.tasks.end());
+    const int per_sm = pmk::modexp_tasks_blocks_per_sm(g.limbs, g.cfg, g.crt);  // also raises the smem limit
+    if (per_sm <= 0) return PMK_EUNSUPPORTED;
+    const long long need = ((long long)g.tasks.size() + 3) / 4;  // four warps per block
+    g.blocks = (int)std::max<long long>(1, std::min<long long>(need, (long long)per_sm * sms));
+  }
+  b->n_tasks = all.size();
+  b->n_kernels = (int)groups.size();
+  if (!all.empty()) {
+    if (cudaMalloc(&b->d_tasks, sizeof(pmk::BatchTask) * all.size()) != cudaSuccess) return PMK_ENOMEM;
+    if (cudaMemcpy(b->d_tasks, all.data(), sizeof(pmk::BatchTask) * all.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      return PMK_ECUDA;
+  }
+  if (cudaMalloc(&b->d_counters, sizeof(int) * std::max<size_t>(1, groups.size())) != cudaSuccess) return PMK_ENOMEM;
+  if (cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking) != cudaSuccess) return PMK_ECUDA;
+  b->side.resize(groups.size(), nullptr);
+  b->events.resize(groups.size() + 1, nullptr);
+  for (auto &s : b->side)
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return PMK_ECUDA;
+  for (auto &e : b->events)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return PMK_ECUDA;
+
+  if (cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return PMK_ECUDA;
+  int rc = PMK_OK;
+  if (cudaMemsetAsync(b->d_counters, 0, sizeof(int) * std::max<size_t>(1, groups.size()), b->capture) != cudaSuccess)
+    rc = PMK_ECUDA;
+  for (size_t j = 0; j < n_jobs && rc == PMK_OK; j++)
+    if (jobs[j].n_chunks)
+      rc = pmk::launch_range_check(jobs[j].ks->d_keys, jobs[j].ks->K, jobs[j].ks->nbits / 32, jobs[j].d_in,
+                                   jobs[j].n_chunks, ctx->d_status, b->capture);
+  if (rc == PMK_OK && cudaEventRecord(b->events.back(), b->capture) != cudaSuccess) rc = PMK_ECUDA;
+  for (size_t gi = 0; gi < groups.size() && rc == PMK_OK; gi++) {
+    const Group &g = groups[gi];
+    if (cudaStreamWaitEvent(b->side[gi], b->events.back(), 0) != cudaSuccess) {
+      rc = PMK_ECUDA;
+      break;
+    }
+    rc = pmk::launch_modexp_tasks(g.limbs, g.cfg, g.crt, b->d_tasks + g.offset, (int)g.tasks.size(),
+                                  b->d_counters + gi, g.blocks, b->side[gi]);
+    if (rc == PMK_OK && (cudaEventRecord(b->events[gi], b->side[gi]) != cudaSuccess ||
+                         cudaStreamWaitEvent(b->capture, b->events[gi], 0) != cudaSuccess))
+      rc = PMK_ECUDA;
+  }
+  for (size_t j = 0; j < n_jobs && rc == PMK_OK; j++)
+    if (jobs[j].n_chunks && jobs[j].op == PMK_OP_DECRYPT_CRT)
+      rc = pmk::launch_garner(jobs[j].ks->nbits / 64, jobs[j].ks->d_keys, jobs[j].ks->K, jobs[j].d_out,
+                              jobs[j].n_chunks, b->capture);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t end = cudaStreamEndCapture(b->capture, &graph);
+  b->graph = graph;
+  if (rc != PMK_OK) return rc;
+  if (end != cudaSuccess || !graph) return PMK_ECUDA;
+  if (cudaGraphInstantiate(&b->exec, graph, 0) != cudaSuccess) return PMK_ECUDA;
+  return PMK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pmk_batch_create(pmk_ctx *ctx, const pmk_job *jobs, size_t n_jobs, pmk_batch **out) {
+  if (!ctx || !out || (n_jobs && !jobs)) return PMK_EINVAL;
+  for (size_t j = 0; j < n_jobs; j++) {
+    const pmk_job &jb = jobs[j];
+    if (!jb.ks || jb.ks->device != ctx->device || jb.op < 0 || jb.op > 2) return PMK_EINVAL;
+    if (jb.n_chunks == 0) continue;
+    if (!jb.d_in || !jb.d_out || !aligned16(jb.d_in) || !aligned16(jb.d_out)) return PMK_EINVAL;
+    const size_t bytes = jb.n_chunks * (jb.ks->nbits / 8);
+    if (jb.op == PMK_OP_DECRYPT_CRT && overlap(jb.d_in, bytes, jb.d_out, bytes)) return PMK_EINVAL;
+  }
+  pmk_batch *b = new (std::nothrow) pmk_batch();
+  if (!b) return PMK_ENOMEM;
+  b->device = ctx->device;
+  int prev = 0;
+  if (cudaGetDevice(&prev) != cudaSuccess || (prev != ctx->device && cudaSetDevice(ctx->device) != cudaSuccess)) {
+    delete b;
+    return PMK_ECUDA;
+  }
+  int rc;
+  try {
+    rc = plan_and_capture(ctx, jobs, n_jobs, b);
+  } catch (const std::bad_alloc &) {
+    rc = PMK_ENOMEM;
+  }
+  if (rc != PMK_OK) {
+    release(b);
+    delete b;
+  } else {
+    *out = b;
+  }
+  if (prev != ctx->device) cudaSetDevice(prev);
+  return rc;
+}
+
+int pmk_batch_launch(pmk_batch *b, void *stream) {
+  if (!b || !b->exec) return PMK_EINVAL;
+  int prev = 0;
+  if (cudaGetDevice(&prev) != cudaSuccess) return PMK_ECUDA;
+  if (prev != b->device && cudaSetDevice(b->device) != cudaSuccess) return PMK_ECUDA;
+  const int rc = cudaGraphLaunch(b->exec, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess ? PMK_OK : PMK_ECUDA;
+  if (prev != b->device) cudaSetDevice(prev);
+  return rc;
+}
+
+int pmk_batch_info(const pmk_batch *b, size_t *n_tasks, int *n_kernels) {
+  if (!b) return PMK_EINVAL;
+  if (n_tasks) *n_tasks = b->n_tasks;
+  if (n_kernels) *n_kernels = b->n_kernels;
+  return PMK_OK;
+}
+
+void pmk_batch_destroy(pmk_batch *b) {
+  if (!b) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != b->device) cudaSetDevice(b->device);
+  release(b);
+  if (prev != b->device) cudaSetDevice(prev);
+  delete b;
+}
+
+}  // extern "C"

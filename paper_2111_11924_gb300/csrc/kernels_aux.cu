@@ -245,6 +245,43 @@ int list_configs(uint32_t limbs, bool crt, KernelConfig *out, int max) {
   return k;
 }
 
+namespace {
+// Raise a kernel's dynamic shared-memory limit once per device.
+int configure_smem(const void *fn, size_t bytes) {
+  static std::mutex mu;
+  static std::set<std::pair<const void *, int>> done;
+  std::lock_guard<std::mutex> lock(mu);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return PMK_ECUDA;
+  if (!done.count({fn, dev})) {
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+      return PMK_ECUDA;
+    done.insert({fn, dev});
+  }
+  return PMK_OK;
+}
+}  // namespace
+
+int modexp_tasks_blocks_per_sm(uint32_t limbs, KernelConfig cfg, bool crt) {
+  const ModexpEntry *e = find_entry(limbs, cfg, crt);
+  if (!e || configure_smem(e->fn_tasks, e->smem_tasks) != PMK_OK) return 0;
+  int blocks = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, e->fn_tasks, dev::kThreads, e->smem_tasks) != cudaSuccess)
+    return 0;
+  return blocks;
+}
+
+int launch_modexp_tasks(uint32_t limbs, KernelConfig cfg, bool crt, const BatchTask *tasks, int ntasks, int *counter,
+                        int blocks, cudaStream_t st) {
+  if (ntasks == 0) return PMK_OK;
+  const ModexpEntry *e = find_entry(limbs, cfg, crt);
+  if (!e) return PMK_EUNSUPPORTED;
+  int rc = configure_smem(e->fn_tasks, e->smem_tasks);
+  if (rc != PMK_OK) return rc;
+  void *args[] = {(void *)&tasks, (void *)&ntasks, (void *)&counter};
+  return cuda_rc(cudaLaunchKernel(e->fn_tasks, dim3(blocks), dim3(dev::kThreads), args, e->smem_tasks, st));
+}
+
 int launch_modexp(ExpMode mode, uint32_t limbs, KernelConfig cfg, const KeyDev *keys, uint32_t K, const uint32_t *in,
                   uint32_t *out, size_t n, cudaStream_t st) {
   if (n == 0) return PMK_OK;

@@ -1,5 +1,6 @@
-// Wide-key instantiations: 6144- and 8192-bit full width (192 / 256 limbs)
-// and the CRT halves of 6144- and 8192-bit keys (96 / 128 limbs).
+// Wide-key instantiations: 6144- and 8192-bit full width (192 / 256 limbs),
+// the CRT halves of 6144- and 8192-bit keys (96 / 128 limbs), and geometries
+// with more lanes per instance for latency-bound small batches.
 #include "modexp_kernels.cuh"
 
 namespace pmk {
@@ -14,6 +15,10 @@ const ModexpEntry *modexp_entries_wide(int *count) {
       make_entry<256, 32, false, kChain>(), make_entry<96, 8, true, kChain>(),
       make_entry<96, 16, true, kChain>(),   make_entry<96, 16, true, kCols>(),
       make_entry<128, 16, true, kChain>(),  make_entry<128, 16, true, kCols>(),
+      // more lanes per instance: shorter exponentiation latency for small batches
+      make_entry<96, 16, false, kChain>(),  make_entry<96, 16, false, kCols>(),
+      make_entry<48, 16, true, kChain>(),   make_entry<128, 32, false, kChain>(),
+      make_entry<192, 32, false, kChain>(), make_entry<64, 32, false, kChain>(),
   };
   *count = (int)(sizeof(entries) / sizeof(entries[0]));
   return entries;

@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <map>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -51,6 +52,17 @@ struct KeyDev {
   uint32_t maxidx_e, maxidx_d, maxidx_h[2];
 };
 
+// One unit of work of the persistent batch kernels: up to 32 / TPI chunks
+// (first + i * stride, i < count) of one key, in one mode.
+struct BatchTask {
+  const KeyDev *key;
+  const uint32_t *in;
+  uint32_t *out;
+  long long first, stride;
+  int count;
+  int mode;  // 0 encrypt, 1 full-d decrypt, 2 / 3 CRT half p / q
+};
+
 // Host keygen (keygen.cpp).
 int host_keygen(uint32_t K, uint32_t nbits, uint64_t e, uint64_t seed, std::vector<HostKey> &out);
 int host_from_primes(uint32_t nbits, uint64_t e, const uint32_t *p, const uint32_t *q, HostKey &out);
@@ -73,6 +85,12 @@ int launch_garner(uint32_t half_limbs, const KeyDev *keys, uint32_t K, uint32_t 
 bool modexp_built(uint32_t limbs, KernelConfig cfg, bool crt);
 KernelConfig default_config(uint32_t limbs, bool crt);  // tpi == 0: limb count not built
 int list_configs(uint32_t limbs, bool crt, KernelConfig *out, int max);
+// Persistent batch kernel for (limbs, cfg, crt): `blocks` x 128 threads
+// drain tasks[0..ntasks) through *counter (which must start at zero).
+int launch_modexp_tasks(uint32_t limbs, KernelConfig cfg, bool crt, const BatchTask *tasks, int ntasks, int *counter,
+                        int blocks, cudaStream_t st);
+// Resident blocks per SM of that kernel (0 if not built).
+int modexp_tasks_blocks_per_sm(uint32_t limbs, KernelConfig cfg, bool crt);
 int measure_int_peak(double *macs_per_clk_per_sm, double *sm_mhz, int *num_sms);
 
 }  // namespace pmk
@@ -85,4 +103,15 @@ struct pmk_keyset {
   std::vector<pmk::HostKey> keys;
   uint32_t *d_blob = nullptr;              // every key's limbs and schedules
   pmk::KeyDev *d_keys = nullptr;           // K device key views into d_blob
+};
+
+// Context: one device, its status word, staging and kernel geometry choices.
+struct pmk_ctx {
+  int device = 0;
+  uint32_t *d_status = nullptr;            // device-side error bits (pmk::kStatusRange)
+  uint8_t *d_msg = nullptr;                // staging of the *_host calls (grow-only)
+  size_t msg_cap = 0;
+  uint32_t *d_a = nullptr, *d_b = nullptr;
+  size_t a_cap = 0, b_cap = 0;             // in words
+  std::map<uint32_t, pmk::KernelConfig> cfg;  // (limbs << 1 | crt) -> kernel geometry override
 };

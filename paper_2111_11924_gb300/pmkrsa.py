@@ -18,6 +18,14 @@ PMK_OK, PMK_EINVAL, PMK_ERANGE, PMK_ENOMEM, PMK_ECUDA, PMK_EUNSUPPORTED, PMK_ETO
 
 _lib = None
 
+OP_ENCRYPT, OP_DECRYPT, OP_DECRYPT_CRT = 0, 1, 2
+
+
+class _Job(ctypes.Structure):
+    """struct pmk_job of include/pmkrsa.h."""
+    _fields_ = [("ks", ctypes.c_void_p), ("d_in", ctypes.c_void_p), ("d_out", ctypes.c_void_p),
+                ("n_chunks", ctypes.c_size_t), ("op", ctypes.c_int)]
+
 
 class PMKError(RuntimeError):
     def __init__(self, code: int, what: str = ""):
@@ -56,6 +64,10 @@ def load_library() -> ctypes.CDLL:
         "pmk_encrypt_message_host": (i, [vp, vp, vp, sz, vp, sz, vp]),
         "pmk_decrypt_message_host": (i, [vp, vp, vp, sz, vp, sz, i, vp]),
         "pmk_decrypt_message_host_noalloc": (i, [vp, vp, sz, vp, sz, i, vp]),
+        "pmk_batch_create": (i, [vp, ctypes.POINTER(_Job), sz, ctypes.POINTER(vp)]),
+        "pmk_batch_launch": (i, [vp, vp]),
+        "pmk_batch_info": (i, [vp, ctypes.POINTER(sz), ctypes.POINTER(i)]),
+        "pmk_batch_destroy": (None, [vp]),
         "pmk_status": (i, [vp, vp]),
         "pmk_strerror": (ctypes.c_char_p, [i]),
         "pmk_measure_int_peak": (i, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
@@ -262,6 +274,18 @@ class Context:
                                                        ctypes.c_void_p(h_msg.data_ptr()), h_msg.numel(), int(use_crt),
                                                        self.stream_handle(stream)), "pmk_decrypt_message_host")
 
+    def batch(self, jobs) -> "Batch":
+        """Plan and capture a batch: jobs = [(keyset, in_tensor, out_tensor, op), ...]
+        with op one of OP_ENCRYPT, OP_DECRYPT, OP_DECRYPT_CRT."""
+        torch = _torch()
+        arr = (_Job * max(1, len(jobs)))()
+        for k, (ks, t_in, t_out, op) in enumerate(jobs):
+            arr[k] = _Job(ks.handle, self._dev(t_in, torch.int32, "in").value, self._dev(t_out, torch.int32, "out").value,
+                          t_in.shape[0], int(op))
+        h = ctypes.c_void_p()
+        _check(load_library().pmk_batch_create(self.handle, arr, len(jobs), ctypes.byref(h)), "pmk_batch_create")
+        return Batch(self, h, jobs)
+
     def status(self, stream=None) -> int:
         """Synchronise and return (and clear) the device-side error code."""
         return int(load_library().pmk_status(self.handle, self.stream_handle(stream)))
@@ -315,3 +339,28 @@ def decrypt_message_host_noalloc(ks: KeySet, h_cipher, h_msg, use_crt: bool = Fa
     return int(load_library().pmk_decrypt_message_host_noalloc(
         ks.handle, ctypes.c_void_p(h_cipher.data_ptr()), h_cipher.shape[0], ctypes.c_void_p(h_msg.data_ptr()),
         h_msg.numel(), int(use_crt), ctypes.c_void_p(int(s.cuda_stream))))
+
+
+class Batch:
+    """A planned, graph-captured batch (pmk_batch); keeps its job tensors alive."""
+
+    def __init__(self, ctx: Context, handle, jobs):
+        self._ctx, self._h, self._jobs = ctx, handle, list(jobs)
+        n, k = ctypes.c_size_t(), ctypes.c_int()
+        _check(load_library().pmk_batch_info(handle, ctypes.byref(n), ctypes.byref(k)), "pmk_batch_info")
+        self.n_tasks, self.n_kernels = n.value, k.value
+
+    def launch(self, stream=None) -> None:
+        _check(load_library().pmk_batch_launch(self._h, ctypes.c_void_p(self._ctx.stream_handle(stream))),
+               "pmk_batch_launch")
+
+    def destroy(self) -> None:
+        if self._h:
+            load_library().pmk_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
