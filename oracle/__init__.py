@@ -9,8 +9,9 @@ package never does, and this module never imports the product.
 What lives where:
   * ``pmk_oracle.c`` -- schoolbook bignum (Knuth Algorithm D division),
     Algorithm 2 square-and-multiply, the Garner form of the Section 2.1 CRT
-    equations, extended Euclid, and the seeded key initialisation of
-    Algorithm 1 (see that file's header for the readings it fixes).
+    equations, extended Euclid, the seeded key initialisation of
+    Algorithm 1, and Algorithm 1's blinded encryption / decryption with the
+    random matrix R (see that file's header for the readings it fixes).
   * this file -- ctypes marshalling, plus ``split``/``join`` written
     directly from their definitions (Section 3.1: the message is cut into
     chunks, each read as a little-endian integer; chunk t belongs to key
@@ -65,6 +66,8 @@ def _load():
                                           P, P, P, P, P, P, P]
             lib.oracle_modexp_chunks.argtypes = [P, P, i, P, i, P, i, ctypes.c_long, ctypes.c_long]
             lib.oracle_crt_chunks.argtypes = [P, P, i, P, P, P, P, P, i, ctypes.c_long, ctypes.c_long]
+            lib.oracle_blind_encrypt_chunks.argtypes = [P, P, P, P, i, P, i, P, i, ctypes.c_long, ctypes.c_long]
+            lib.oracle_blind_decrypt_chunks.argtypes = [P, P, P, i, P, i, P, i, ctypes.c_long, ctypes.c_long]
             _lib = lib
     return _lib
 
@@ -262,6 +265,45 @@ def decrypt_chunks(chunks: np.ndarray, keys: OracleKeys, use_crt: bool = False, 
                                    _ptr(A["qinv"]), keys.K, a, b)
         if rc:
             raise ValueError(f"oracle_crt_chunks rc={rc}")
+
+    _run(work, n, threads)
+    return out
+
+
+def blind_encrypt_chunks(chunks: np.ndarray, rnd: np.ndarray, keys: OracleKeys, threads: int = 1):
+    """Algorithm 1 Encryption with R: returns (C*, C_R), chunk t bound to key t mod K."""
+    m = np.ascontiguousarray(chunks, dtype=np.uint32)
+    r = np.ascontiguousarray(rnd, dtype=np.uint32)
+    n, s = m.shape
+    assert r.shape == m.shape
+    cstar, cr = np.zeros_like(m), np.zeros_like(m)
+    e = np.tile(to_limbs(keys.e, 2), (keys.K, 1))
+    M = np.ascontiguousarray(keys.a["N"])
+    lib = _load()
+
+    def work(a, b):
+        rc = lib.oracle_blind_encrypt_chunks(_ptr(m), _ptr(r), _ptr(cstar), _ptr(cr), s, _ptr(e), 2, _ptr(M), keys.K, a, b)
+        if rc:
+            raise ValueError(f"oracle_blind_encrypt_chunks rc={rc}")
+
+    _run(work, n, threads)
+    return cstar, cr
+
+
+def blind_decrypt_chunks(cstar: np.ndarray, cr: np.ndarray, keys: OracleKeys, threads: int = 1) -> np.ndarray:
+    """Algorithm 1 Decryption with R: r' = c_r^d, m* = c*^d, m' = m* r'^-1 (mod N)."""
+    c = np.ascontiguousarray(cstar, dtype=np.uint32)
+    q = np.ascontiguousarray(cr, dtype=np.uint32)
+    n, s = c.shape
+    out = np.zeros_like(c)
+    D = np.ascontiguousarray(keys.a["d"])
+    M = np.ascontiguousarray(keys.a["N"])
+    lib = _load()
+
+    def work(a, b):
+        rc = lib.oracle_blind_decrypt_chunks(_ptr(c), _ptr(q), _ptr(out), s, _ptr(D), s, _ptr(M), keys.K, a, b)
+        if rc:
+            raise ValueError(f"oracle_blind_decrypt_chunks rc={rc}")
 
     _run(work, n, threads)
     return out

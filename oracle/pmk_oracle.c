@@ -19,6 +19,9 @@
  *                      phi = (p-1)(q-1), d = e^-1 mod phi (extended Euclid).
  *   oracle_*_chunks    Algorithm 1 "Encryption"/"Decryption" loops: chunk t
  *                      is bound to key t mod K (row-per-key reshape, Sec. 3.1).
+ *   oracle_blind_*     Algorithm 1 with the random matrix R (Sec. 3.1):
+ *                      encrypt c = m^e, c* = c r^e, c_r = r^e (mod N);
+ *                      decrypt r' = c_r^d, m* = c*^d, m' = m* r'^-1 (mod N).
  *
  * Readings where the paper is silent or garbled (kept identical on the
  * product side, which implements them independently):
@@ -488,4 +491,43 @@ int oracle_crt_chunks(const uint32_t *in, uint32_t *out, int s, const uint32_t *
     if (rc) return rc;
   }
   return 0;
+}
+
+/*
+ * Algorithm 1 with blinding, chunks [t0, t1), key t mod K (s-limb values):
+ *   encrypt:  c_t = m_t^e,  c*_t = c_t r_t^e,  c_r,t = r_t^e   (mod N_k)
+ */
+int oracle_blind_encrypt_chunks(const uint32_t *m, const uint32_t *rnd, uint32_t *cstar, uint32_t *cr, int s,
+                                const uint32_t *e, int ne, const uint32_t *mods, int K, long t0, long t1) {
+  limb_t *c = (limb_t *)calloc((size_t)s, sizeof(limb_t));
+  int rc = 0;
+  for (long t = t0; t < t1 && !rc; t++) {
+    const limb_t *N = mods + (size_t)(t % K) * s;
+    rc = modexp(m + (size_t)t * s, s, e, ne, N, s, c);                          /* c = m^e */
+    if (!rc) rc = modexp(rnd + (size_t)t * s, s, e, ne, N, s, cr + (size_t)t * s); /* c_r = r^e */
+    if (!rc) bn_mulmod(c, cr + (size_t)t * s, N, s, cstar + (size_t)t * s);       /* c* = c r^e */
+  }
+  free(c);
+  return rc;
+}
+
+/*
+ *   decrypt:  r' = c_r^d,  m* = c*^d,  m' = m* r'^-1   (mod N_k)
+ * Returns -3 if some r' has no inverse modulo N_k.
+ */
+int oracle_blind_decrypt_chunks(const uint32_t *cstar, const uint32_t *cr, uint32_t *m, int s, const uint32_t *exps,
+                                int ne, const uint32_t *mods, int K, long t0, long t1) {
+  limb_t *rp = (limb_t *)calloc((size_t)s, sizeof(limb_t));
+  limb_t *ms = (limb_t *)calloc((size_t)s, sizeof(limb_t));
+  limb_t *ri = (limb_t *)calloc((size_t)s, sizeof(limb_t));
+  int rc = 0;
+  for (long t = t0; t < t1 && !rc; t++) {
+    const limb_t *N = mods + (size_t)(t % K) * s, *d = exps + (size_t)(t % K) * ne;
+    rc = modexp(cr + (size_t)t * s, s, d, ne, N, s, rp);                    /* r' = c_r^d */
+    if (!rc) rc = modexp(cstar + (size_t)t * s, s, d, ne, N, s, ms);      /* m* = c*^d */
+    if (!rc && bn_modinv(rp, N, s, ri)) rc = -3;                           /* r'^-1 */
+    if (!rc) bn_mulmod(ms, ri, N, s, m + (size_t)t * s);                   /* m' = m* r'^-1 */
+  }
+  free(rp); free(ms); free(ri);
+  return rc;
 }

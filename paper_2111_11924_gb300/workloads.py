@@ -73,3 +73,14 @@ def random_below(rng: np.random.Generator, bound: int) -> int:
         v = int.from_bytes(rng.bytes(nbytes), "little") & ((1 << bound.bit_length()) - 1)
         if v < bound:
             return v
+
+
+def blinding_values(n_chunks: int, nbits: int, seed: int) -> np.ndarray:
+    """The random matrix R of Algorithm 1 as an input: one value per chunk,
+    uniform below 2^(nbits - 8) (so below every nbits-bit modulus), as
+    (n_chunks, nbits/32) little-endian uint32 limbs."""
+    s = nbits // 32
+    nbytes = nbits // 8 - 1
+    raw = np.zeros((n_chunks, 4 * s), np.uint8)
+    raw[:, :nbytes] = np.random.default_rng(seed).integers(0, 256, (n_chunks, nbytes), dtype=np.uint8)
+    return raw.view("<u4").astype(np.uint32)

@@ -243,3 +243,36 @@ def test_pmkrsa_roundtrip_message():
     assert all(oracle.from_limbs(c[t]) < Ns[t % 3] for t in range(len(c)))
     for use_crt in (False, True):
         assert oracle.join(oracle.decrypt_chunks(c, keys, use_crt=use_crt), len(msg), 512) == msg
+
+
+def test_blinded_pmkrsa_algorithm1():
+    """Algorithm 1 with the random matrix R: pinned against Python integers
+    (c* = (m r)^e, c_r = r^e mod N) and the round trip of Section 3.1."""
+    from paper_2111_11924_gb300.workloads import blinding_values
+
+    keys = oracle.keygen(3, 512, 65537, seed=61)
+    msg = np.random.default_rng(5).integers(0, 256, 700, dtype=np.uint8).tobytes()
+    m = oracle.split(msg, 512)
+    r = blinding_values(len(m), 512, seed=9)
+    cstar, cr = oracle.blind_encrypt_chunks(m, r, keys, threads=2)
+    Ns = keys.ints("N")
+    for t in range(len(m)):
+        N, mv, rv = Ns[t % 3], oracle.from_limbs(m[t]), oracle.from_limbs(r[t])
+        assert oracle.from_limbs(cr[t]) == pow(rv, 65537, N)
+        assert oracle.from_limbs(cstar[t]) == pow(mv * rv, 65537, N)
+    back = oracle.blind_decrypt_chunks(cstar, cr, keys, threads=2)
+    assert np.array_equal(back, m)
+    assert oracle.join(back, len(msg), 512) == msg
+    # the same ciphertext chunk blinded twice gives different c* (Section 3.4's point)
+    r2 = blinding_values(len(m), 512, seed=10)
+    cstar2, _ = oracle.blind_encrypt_chunks(m, r2, keys)
+    assert not np.array_equal(cstar, cstar2)
+
+
+def test_blinded_decrypt_rejects_non_invertible_r():
+    keys = oracle.keygen(1, 256, 65537, seed=3)
+    kd = keys.key(0)
+    m = np.stack([oracle.to_limbs(5, 8)])
+    cr = np.stack([oracle.to_limbs(kd["p"] * 3 % kd["N"], 8)])  # shares the factor p with N
+    with pytest.raises(ValueError):
+        oracle.blind_decrypt_chunks(m, cr, keys)
