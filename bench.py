@@ -266,6 +266,39 @@ def run_ours(args):
     assert torch.equal(back, d_msg), "round trip failed"
     ph_crt = timed(True, max(3, args.steps // 2), 3)
     assert torch.equal(back, d_msg), "CRT round trip failed"
+    # Algorithm 1 with the random matrix R (fresh per message): split ->
+    # blinded encrypt -> blinded decrypt (full d) -> join, timed the same way
+    rnd = torch.from_numpy(W.blinding_values(n, w.nbits, w.msg_seed + 77).view(np.int32)).cuda()
+    cstar, cr = torch.empty_like(chunks), torch.empty_like(chunks)
+
+    def blinded_step(ev=None):
+        if ev:
+            ev[0].record()
+        ctx.split(w.nbits, d_msg, out=chunks)
+        if ev:
+            ev[1].record()
+        ctx.encrypt_blinded(ks, chunks, rnd, out_cstar=cstar, out_cr=cr)
+        if ev:
+            ev[2].record()
+        ctx.decrypt_blinded(ks, cstar, cr, out=plain)
+        if ev:
+            ev[3].record()
+        ctx.join(w.nbits, plain, w.msg_bytes, out=back)
+        if ev:
+            ev[4].record()
+
+    for _ in range(3):
+        blinded_step()
+    torch.cuda.synchronize()
+    bl_steps = max(3, args.steps // 2)
+    bl_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(bl_steps)]
+    for i in range(bl_steps):
+        flush.zero_()
+        blinded_step(bl_ev[i])
+    torch.cuda.synchronize()
+    ctx.check()
+    assert torch.equal(back, d_msg), "blinded round trip failed"
+    ph_bl = np.array([[bl_ev[i][j].elapsed_time(bl_ev[i][j + 1]) for j in range(4)] for i in range(bl_steps)])
 
     step_ms = ph.sum(axis=1)
     t_step = max_over_ranks(float(step_ms.mean()), world, "cuda")
@@ -318,6 +351,10 @@ def run_ours(args):
         "crt": {"value": world * n / (crt_step / 1e3), "unit": UNIT, "ms_per_step": crt_step,
                 "decrypt_ms": crt_dec, "decrypt_only": n / (crt_dec / 1e3),
                 "geometry": {"lanes_per_instance": tuned_crt["tpi"], "form": ["chain", "columns"][tuned_crt["form"]]}},
+        "blinded": {"value": world * n / (float(ph_bl.sum(axis=1).mean()) / 1e3), "unit": UNIT,
+                    "ms_per_step": float(ph_bl.sum(axis=1).mean()), "encrypt_ms": float(ph_bl[:, 1].mean()),
+                    "decrypt_ms": float(ph_bl[:, 2].mean()),
+                    "step": "split + Algorithm 1 encryption with R + decryption as (c* c_r^-1)^d + join"},
         "geometry": {"lanes_per_instance": tuned["tpi"], "form": ["chain", "columns"][tuned["form"]],
                      "chosen_by": "pmk_autotune over every compiled geometry"},
         "default_geometry": {"value": world * n / (float(ph_default.sum(axis=1).mean()) / 1e3), "unit": UNIT,
@@ -379,6 +416,13 @@ def run_profile(args):
     return 0
 
 
+# Section 4, Table 2, configuration D (P100, 16 keys, blinded PMKRSA, 102,400-byte
+# plaintext): encryption / decryption seconds, quoted as context (other hardware).
+PAPER_TABLE2 = {2048: {"encrypt": 0.9, "decrypt": 61.1}, 3072: {"encrypt": 1.4, "decrypt": 141.9},
+                4096: {"encrypt": 2.1, "decrypt": 276.3}, 6144: {"encrypt": 3.6, "decrypt": 787.3},
+                8192: {"encrypt": 6.0, "decrypt": 1666.5}}
+
+
 def run_widths(args):
     """The paper's Table 2 workload at every key length: a 102,400-byte
     random plaintext, K = 16 key pairs, split -> encrypt -> decrypt -> join,
@@ -399,9 +443,15 @@ def run_widths(args):
         cipher = ctx.encrypt_chunks(ks, chunks)
         out = torch.empty_like(chunks)
         res = {}
+        rnd = torch.from_numpy(W.blinding_values(n, nbits, w.msg_seed + 77).view(np.int32)).cuda()
+        cstar, cr = torch.empty_like(chunks), torch.empty_like(chunks)
+        ctx.encrypt_blinded(ks, chunks, rnd, out_cstar=cstar, out_cr=cr)
         for name, fn in (("encrypt", lambda: ctx.encrypt_chunks(ks, chunks, out=cipher)),
                          ("decrypt", lambda: ctx.decrypt_chunks(ks, cipher, out=out)),
-                         ("decrypt_crt", lambda: ctx.decrypt_chunks(ks, cipher, use_crt=True, out=out))):
+                         ("decrypt_crt", lambda: ctx.decrypt_chunks(ks, cipher, use_crt=True, out=out)),
+                         ("encrypt_blinded", lambda: ctx.encrypt_blinded(ks, chunks, rnd, out_cstar=cstar, out_cr=cr)),
+                         ("decrypt_blinded", lambda: ctx.decrypt_blinded(ks, cstar, cr, out=out)),
+                         ("decrypt_blinded_crt", lambda: ctx.decrypt_blinded(ks, cstar, cr, use_crt=True, out=out))):
             for _ in range(3):
                 fn()
             torch.cuda.synchronize()
@@ -414,11 +464,13 @@ def run_widths(args):
             torch.cuda.synchronize()
             ts = [ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(args.steps)]
             res[name] = statistics.median(ts)
-            if name != "encrypt":
+            if name.startswith("decrypt"):
                 assert torch.equal(out, chunks)
         ctx.check()
+        paper = PAPER_TABLE2.get(nbits)
         print(json.dumps({"workload": w.name, "key_bits": nbits, "chunks": n, "keys": w.K,
                           "ms": {k: round(v, 4) for k, v in res.items()},
+                          "paper_table2_P100_config_D_ms": paper,
                           "chunk_modexps_per_s": {k: round(n / (v / 1e3)) for k, v in res.items()},
                           "geometry": {m: (t["tpi"], ["chain", "columns"][t["form"]]) for m, t in tuned.items()}}))
         ks.free()

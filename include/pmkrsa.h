@@ -39,6 +39,7 @@ extern "C" {
 #define PMK_ECUDA (-4)        /* a CUDA runtime call failed */
 #define PMK_EUNSUPPORTED (-5) /* key width not compiled into this build */
 #define PMK_ETOOLARGE (-6)    /* request exceeds the fixed capacity of the allocation-free call */
+#define PMK_ENOINV (-7)       /* a blinding value shares a factor with its modulus (device-detected) */
 
 typedef struct pmk_ctx pmk_ctx;         /* one GPU: device status word, staging buffers */
 typedef struct pmk_keyset pmk_keyset;   /* K key pairs: host copy + device-resident tables */
@@ -130,6 +131,29 @@ int pmk_decrypt_chunks(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_in,
                        size_t n_chunks, int use_crt, void *stream);
 
 /*
+ * PMKRSA encryption with the random matrix R (Algorithm 1 "Encryption",
+ * Section 3.1): for every chunk, with k = t mod K,
+ *   c_t = m_t^e,  c*_t = c_t r_t^e,  c_r,t = r_t^e   (mod N_k).
+ * d_r holds the caller's random values r_t (< N_k, drawn fresh per message),
+ * same layout as the chunks.  Outputs d_cstar (C*) and d_cr (C_R); the four
+ * buffers must not overlap.  Chunks or r values >= N report PMK_ERANGE.
+ */
+int pmk_encrypt_blinded(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_m, const uint32_t *d_r,
+                        uint32_t *d_cstar, uint32_t *d_cr, size_t n_chunks, void *stream);
+
+/*
+ * PMKRSA decryption with R (Algorithm 1 "Decryption"): the paper computes
+ * r' = c_r^d, m* = c*^d, m' = m* r'^-1 (mod N).  This library computes the
+ * same residue as m' = (c* c_r^-1)^d: the inverse of c_r comes from two
+ * half-width Fermat exponentiations (c_r^(p-2) mod p, c_r^(q-2) mod q) and
+ * Garner's recombination, followed by one exponentiation by d (full width,
+ * or the Section 2.1 CRT form with use_crt = 1).  A c_r sharing a factor
+ * with N reports PMK_ENOINV through pmk_status.  Buffers must not overlap.
+ */
+int pmk_decrypt_blinded(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_cstar, const uint32_t *d_cr,
+                        uint32_t *d_m, size_t n_chunks, int use_crt, void *stream);
+
+/*
  * Whole-message calls on HOST buffers: copy in, split/encrypt (or
  * decrypt/join) on the device, copy out, synchronise the stream.  The
  * context keeps grow-only device staging buffers between calls.
@@ -201,8 +225,8 @@ int pmk_batch_info(const pmk_batch *batch, size_t *n_tasks, int *n_kernels);
 void pmk_batch_destroy(pmk_batch *batch);
 
 /* Synchronise `stream`, then return (and clear) the first device-side error
- * recorded since the last call: PMK_OK or PMK_ERANGE; PMK_ECUDA if a CUDA
- * call fails. */
+ * recorded since the last call: PMK_OK, PMK_ERANGE or PMK_ENOINV; PMK_ECUDA
+ * if a CUDA call fails. */
 int pmk_status(pmk_ctx *ctx, void *stream);
 
 /* Static description of an error code. */

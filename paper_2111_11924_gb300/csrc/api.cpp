@@ -65,7 +65,7 @@ size_t push(std::vector<uint32_t> &blob, const std::vector<uint32_t> &v) {
 int upload(pmk_keyset *ks) {
   std::vector<uint32_t> blob;
   struct Offs {
-    size_t N, R2, se, sd, P[2], R2h[2], R3h[2], sh[2], qm;
+    size_t N, R2, se, sd, P[2], R2h[2], R3h[2], sh[2], shi[2], qm;
   };
   std::vector<Offs> offs(ks->K);
   for (uint32_t k = 0; k < ks->K; k++) {
@@ -81,6 +81,7 @@ int upload(pmk_keyset *ks) {
       o.R2h[i] = push(blob, h.R2h[i]);
       o.R3h[i] = push(blob, h.R3h[i]);
       o.sh[i] = push(blob, h.sched_h[i].steps);
+      o.shi[i] = push(blob, h.sched_hinv[i].steps);
     }
     o.qm = push(blob, h.qinv_m);
   }
@@ -110,6 +111,9 @@ int upload(pmk_keyset *ks) {
       d.n0h[i] = h.n0h[i];
       d.nsteps_h[i] = (uint32_t)h.sched_h[i].steps.size();
       d.maxidx_h[i] = h.sched_h[i].maxidx;
+      d.sched_hinv[i] = b + o.shi[i];
+      d.nsteps_hinv[i] = (uint32_t)h.sched_hinv[i].steps.size();
+      d.maxidx_hinv[i] = h.sched_hinv[i].maxidx;
     }
   }
   if (cudaMalloc(&ks->d_keys, sizeof(KeyDev) * ks->K) != cudaSuccess) return PMK_ENOMEM;
@@ -340,6 +344,64 @@ int pmk_decrypt_chunks(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_in,
   return enqueue_decrypt(ctx, ks, d_in, d_out, n_chunks, use_crt, as_stream(stream));
 }
 
+int pmk_encrypt_blinded(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_m, const uint32_t *d_r,
+                        uint32_t *d_cstar, uint32_t *d_cr, size_t n_chunks, void *stream) {
+  if (n_chunks == 0) return (ctx && ks) ? PMK_OK : PMK_EINVAL;
+  int rc = check_chunk_call(ctx, ks, d_m, d_cstar);
+  if (rc == PMK_OK) rc = check_chunk_call(ctx, ks, d_r, d_cr);
+  if (rc != PMK_OK) return rc;
+  const size_t bytes = n_chunks * (ks->nbits / 8);
+  const void *bufs[4] = {d_m, d_r, d_cstar, d_cr};
+  for (int i = 0; i < 4; i++)
+    for (int j = i + 1; j < 4; j++)
+      if (overlap(bufs[i], bytes, bufs[j], bytes)) return PMK_EINVAL;
+  DeviceGuard g(ctx->device);
+  if (!g.ok()) return PMK_ECUDA;
+  cudaStream_t st = as_stream(stream);
+  const uint32_t S = ks->nbits / 32;
+  rc = enqueue_encrypt(ctx, ks, d_m, d_cstar, n_chunks, st);                     // c = m^e (into C*)
+  if (rc == PMK_OK) rc = enqueue_encrypt(ctx, ks, d_r, d_cr, n_chunks, st);     // c_r = r^e
+  if (rc == PMK_OK) rc = pmk::launch_mulmod(S, ks->d_keys, ks->K, d_cstar, d_cr, d_cstar, n_chunks, st);  // c* = c c_r
+  return rc;
+}
+
+int pmk_decrypt_blinded(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_cstar, const uint32_t *d_cr,
+                        uint32_t *d_m, size_t n_chunks, int use_crt, void *stream) {
+  if (n_chunks == 0) return (ctx && ks) ? PMK_OK : PMK_EINVAL;
+  int rc = check_chunk_call(ctx, ks, d_cstar, d_m);
+  if (rc == PMK_OK) rc = check_chunk_call(ctx, ks, d_cr, d_m);
+  if (rc != PMK_OK) return rc;
+  const size_t bytes = n_chunks * (ks->nbits / 8);
+  if (overlap(d_cstar, bytes, d_m, bytes) || overlap(d_cr, bytes, d_m, bytes) || overlap(d_cstar, bytes, d_cr, bytes))
+    return PMK_EINVAL;
+  DeviceGuard g(ctx->device);
+  if (!g.ok()) return PMK_ECUDA;
+  cudaStream_t st = as_stream(stream);
+  const uint32_t S = ks->nbits / 32, H = S / 2;
+  rc = pmk::launch_range_check(ks->d_keys, ks->K, S, d_cstar, n_chunks, ctx->d_status, st);
+  if (rc == PMK_OK) rc = pmk::launch_range_check(ks->d_keys, ks->K, S, d_cr, n_chunks, ctx->d_status, st);
+  // c_r^-1 mod N: Fermat inverses mod p and q, recombined (into d_m)
+  if (rc == PMK_OK)
+    rc = pmk::launch_modexp(pmk::ExpMode::kCrtInverse, H, cfg_for(ctx, H, true), ks->d_keys, ks->K, d_cr, d_m,
+                            n_chunks, st);
+  if (rc == PMK_OK) rc = pmk::launch_garner(H, ks->d_keys, ks->K, d_m, n_chunks, st, ctx->d_status);
+  // x = c* c_r^-1, in place
+  if (rc == PMK_OK) rc = pmk::launch_mulmod(S, ks->d_keys, ks->K, d_cstar, d_m, d_m, n_chunks, st);
+  if (rc != PMK_OK) return rc;
+  // m = x^d
+  if (!use_crt)
+    return pmk::launch_modexp(pmk::ExpMode::kDecrypt, S, cfg_for(ctx, S, false), ks->d_keys, ks->K, d_m, d_m,
+                              n_chunks, st);
+  rc = grow(reinterpret_cast<void **>(&ctx->d_b), &ctx->b_cap, n_chunks * S * 4);
+  if (rc == PMK_OK && cudaMemcpyAsync(ctx->d_b, d_m, n_chunks * S * 4, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    rc = PMK_ECUDA;
+  if (rc == PMK_OK)
+    rc = pmk::launch_modexp(pmk::ExpMode::kCrtHalf, H, cfg_for(ctx, H, true), ks->d_keys, ks->K, ctx->d_b, d_m,
+                            n_chunks, st);
+  if (rc == PMK_OK) rc = pmk::launch_garner(H, ks->d_keys, ks->K, d_m, n_chunks, st);
+  return rc;
+}
+
 int pmk_status(pmk_ctx *ctx, void *stream) {
   if (!ctx) return PMK_EINVAL;
   DeviceGuard g(ctx->device);
@@ -349,7 +411,8 @@ int pmk_status(pmk_ctx *ctx, void *stream) {
   if (cudaMemcpy(&st, ctx->d_status, sizeof st, cudaMemcpyDeviceToHost) != cudaSuccess) return PMK_ECUDA;
   if (st == 0) return PMK_OK;
   if (cudaMemset(ctx->d_status, 0, sizeof st) != cudaSuccess) return PMK_ECUDA;
-  return (st & pmk::kStatusRange) ? PMK_ERANGE : PMK_ECUDA;
+  if (st & pmk::kStatusRange) return PMK_ERANGE;
+  return (st & pmk::kStatusNotInvertible) ? PMK_ENOINV : PMK_ECUDA;
 }
 
 int pmk_encrypt_message_host(pmk_ctx *ctx, const pmk_keyset *ks, const uint8_t *h_msg, size_t msg_len,
@@ -404,6 +467,7 @@ const char *pmk_strerror(int code) {
     case PMK_ECUDA: return "CUDA runtime error";
     case PMK_EUNSUPPORTED: return "key width or launch geometry not built";
     case PMK_ETOOLARGE: return "request exceeds the fixed capacity of the allocation-free call";
+    case PMK_ENOINV: return "blinding value not invertible modulo its key";
     default: return "unknown error";
   }
 }

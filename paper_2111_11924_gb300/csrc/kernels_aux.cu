@@ -73,14 +73,27 @@ __global__ void __launch_bounds__(kAuxThreads) k_range(const KeyDev *__restrict_
 // of out[t] and m_q in the high half, out[t] <- m_q + q ((m_p - m_q) qinv mod p).
 // One thread per chunk; arrays sit in local memory (this kernel is a
 // negligible share of the CRT decryption).
+//
+// With `status` set, a zero half (the input was divisible by p or q, so it
+// has no inverse when the halves are Fermat inverses) is flagged as
+// kStatusNotInvertible.
 __global__ void __launch_bounds__(kAuxThreads) k_garner(const KeyDev *__restrict__ keys, uint32_t K, int H,
-                                                        uint32_t *__restrict__ out, long long n) {
+                                                        uint32_t *__restrict__ out, long long n,
+                                                        uint32_t *__restrict__ status) {
   const long long t = (long long)blockIdx.x * kAuxThreads + threadIdx.x;
   if (t >= n) return;
   const KeyDev &kd = keys[t % K];
   const uint32_t *p = kd.P[0], *q = kd.P[1], *qm = kd.qinv_m;
   const uint32_t n0 = kd.n0h[0];
   uint32_t *o = out + t * 2 * H;
+  if (status) {
+    uint32_t any_p = 0, any_q = 0;
+    for (int i = 0; i < H; i++) {
+      any_p |= o[i];
+      any_q |= o[H + i];
+    }
+    if (!any_p || !any_q) atomicOr(status, kStatusNotInvertible);
+  }
   uint32_t mq[128], d[128], acc[256];
   // mq mod p: m_q < q < 2p, so at most one subtraction
   uint32_t borrow = 0;
@@ -184,6 +197,10 @@ const ModexpEntry *find_entry(uint32_t limbs, KernelConfig cfg, bool crt) {
 
 }  // namespace
 
+namespace {
+int configure_smem(const void *fn, size_t bytes);
+}  // namespace
+
 int launch_split(uint32_t nbits, const uint8_t *msg, size_t len, uint32_t *chunks, size_t n, cudaStream_t st) {
   const int P = (int)(nbits / 8 - 1), S = (int)(nbits / 32);
   const long long nw = (long long)n * S;
@@ -208,12 +225,41 @@ int launch_range_check(const KeyDev *keys, uint32_t K, uint32_t s, const uint32_
   return cuda_rc(cudaGetLastError());
 }
 
-int launch_garner(uint32_t half_limbs, const KeyDev *keys, uint32_t K, uint32_t *out, size_t n, cudaStream_t st) {
+int launch_garner(uint32_t half_limbs, const KeyDev *keys, uint32_t K, uint32_t *out, size_t n, cudaStream_t st,
+                  uint32_t *status_if_zero_half) {
   if (n == 0) return PMK_OK;
   if (half_limbs > 128) return PMK_EUNSUPPORTED;
   k_garner<<<(unsigned)((n + kAuxThreads - 1) / kAuxThreads), kAuxThreads, 0, st>>>(keys, K, (int)half_limbs, out,
-                                                                                    (long long)n);
+                                                                                    (long long)n, status_if_zero_half);
   return cuda_rc(cudaGetLastError());
+}
+
+const MulmodEntry *mulmod_entries(int *count) {
+  static const MulmodEntry entries[] = {
+      make_mulmod<4, 2>(),   make_mulmod<8, 2>(),    make_mulmod<16, 2>(),   make_mulmod<32, 4>(),
+      make_mulmod<64, 8>(),  make_mulmod<96, 8>(),   make_mulmod<128, 16>(), make_mulmod<192, 16>(),
+      make_mulmod<256, 16>(),
+  };
+  *count = (int)(sizeof(entries) / sizeof(entries[0]));
+  return entries;
+}
+
+int launch_mulmod(uint32_t limbs, const KeyDev *keys, uint32_t K, const uint32_t *a, const uint32_t *b, uint32_t *out,
+                  size_t n, cudaStream_t st) {
+  if (n == 0) return PMK_OK;
+  int cnt = 0;
+  const MulmodEntry *list = mulmod_entries(&cnt), *e = nullptr;
+  for (int i = 0; i < cnt; i++)
+    if (list[i].limbs == (int)limbs) e = &list[i];
+  if (!e) return PMK_EUNSUPPORTED;
+  int rc = configure_smem(e->fn, e->smem);
+  if (rc != PMK_OK) return rc;
+  const long long per_key = ((long long)n + K - 1) / K;
+  const int ipb = dev::kThreads / e->tpi;
+  dim3 grid((unsigned)((per_key + ipb - 1) / ipb), K);
+  long long nl = (long long)n;
+  void *args[] = {(void *)&keys, (void *)&K, (void *)&a, (void *)&b, (void *)&out, (void *)&nl};
+  return cuda_rc(cudaLaunchKernel(e->fn, grid, dim3(dev::kThreads), args, e->smem, st));
 }
 
 bool modexp_built(uint32_t limbs, KernelConfig cfg, bool crt) { return find_entry(limbs, cfg, crt) != nullptr; }
@@ -285,27 +331,17 @@ int launch_modexp_tasks(uint32_t limbs, KernelConfig cfg, bool crt, const BatchT
 int launch_modexp(ExpMode mode, uint32_t limbs, KernelConfig cfg, const KeyDev *keys, uint32_t K, const uint32_t *in,
                   uint32_t *out, size_t n, cudaStream_t st) {
   if (n == 0) return PMK_OK;
-  const bool crt = mode == ExpMode::kCrtHalf;
+  const bool crt = mode == ExpMode::kCrtHalf || mode == ExpMode::kCrtInverse;
   const ModexpEntry *e = find_entry(limbs, cfg, crt);
   if (!e) return PMK_EUNSUPPORTED;
-  static std::mutex mu;
-  static std::set<std::pair<const void *, int>> configured;  // (kernel, device) with the smem limit raised
-  {
-    std::lock_guard<std::mutex> lock(mu);
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return PMK_ECUDA;
-    if (!configured.count({e->fn, dev})) {
-      cudaError_t err = cudaFuncSetAttribute(e->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e->smem);
-      if (err != cudaSuccess) return PMK_ECUDA;
-      configured.insert({e->fn, dev});
-    }
-  }
+  const int rc = configure_smem(e->fn, e->smem);
+  if (rc != PMK_OK) return rc;
   const long long per_key = ((long long)n + K - 1) / K;
   const int ipb = dev::kThreads / e->tpi;
   dim3 grid((unsigned)((per_key + ipb - 1) / ipb), crt ? 2 * K : K);
   long long nl = (long long)n;
-  int enc = mode == ExpMode::kEncrypt ? 1 : 0;
-  void *args[] = {(void *)&keys, (void *)&K, (void *)&in, (void *)&out, (void *)&nl, (void *)&enc};
+  int sel = (mode == ExpMode::kEncrypt || mode == ExpMode::kCrtInverse) ? 1 : 0;
+  void *args[] = {(void *)&keys, (void *)&K, (void *)&in, (void *)&out, (void *)&nl, (void *)&sel};
   return cuda_rc(cudaLaunchKernel(e->fn, grid, dim3(dev::kThreads), args, e->smem, st));
 }
 

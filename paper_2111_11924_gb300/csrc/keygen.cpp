@@ -333,6 +333,13 @@ void finish_key(uint32_t nbits, u64 e, const std::vector<u64> &p, const std::vec
   k.sched_d = make_schedule(k.d.data(), (int)s);
   k.sched_h[0] = make_schedule(k.dp.data(), (int)h);
   k.sched_h[1] = make_schedule(k.dq.data(), (int)h);
+  std::vector<u64> pm2x(p), qm2x(q), twox(n, 0);  // Fermat inverses mod p and q: exponents p - 2, q - 2
+  twox[0] = 2;
+  sub(pm2x.data(), p.data(), twox.data(), n);
+  sub(qm2x.data(), q.data(), twox.data(), n);
+  const std::vector<uint32_t> pm2_32 = to32(pm2x, h), qm2_32 = to32(qm2x, h);
+  k.sched_hinv[0] = make_schedule(pm2_32.data(), (int)h);
+  k.sched_hinv[1] = make_schedule(qm2_32.data(), (int)h);
 }
 
 bool valid_width(uint32_t nbits) { return nbits >= 128 && nbits <= 8192 && nbits % 128 == 0; }

@@ -12,14 +12,16 @@ namespace dev {
 // t = key + j K.  Every block therefore serves one key: schedules, modulus and
 // control flow are uniform across it.
 //
-// FULL: out[t] = in[t]^E mod N_key, E = e (enc != 0) or d, S = nbits / 32.
-// CRT:  out[t][half] = in[t]^{d_p | d_q} mod (p | q) over S = nbits / 64
-//       limbs, input reduced via in mod p = hi R + lo -> MontMul(hi, R^3) +
+// FULL: out[t] = in[t]^E mod N_key, E = e (sel != 0) or d, S = nbits / 32.
+// CRT:  out[t][half] = in[t]^E mod (p | q) over S = nbits / 64 limbs, with
+//       E = d_p | d_q (sel == 0), or p - 2 | q - 2 (sel != 0: inverses mod p,
+//       q by Fermat's little theorem), 
+//       input reduced via in mod p = hi R + lo -> MontMul(hi, R^3) +
 //       MontMul(lo, R^2) = in R mod p.  Garner combines the halves afterwards.
 template <int S, int TPI, bool CRT, int FORM>
 __global__ void __launch_bounds__(kThreads) k_modexp(const KeyDev *__restrict__ keys, uint32_t K,
                                                      const uint32_t *__restrict__ in, uint32_t *__restrict__ out,
-                                                     long long n, int enc) {
+                                                     long long n, int sel) {
   constexpr int L = S / TPI;
   constexpr int IPB = kThreads / TPI;
   constexpr int ROW = Layout<S>::kRow;
@@ -38,9 +40,9 @@ __global__ void __launch_bounds__(kThreads) k_modexp(const KeyDev *__restrict__ 
   const KeyDev &kd = keys[key];
   const uint32_t *M = CRT ? kd.P[half] : kd.N;
   const uint32_t *R2 = CRT ? kd.R2h[half] : kd.R2;
-  const uint32_t *sched = CRT ? kd.sched_h[half] : (enc ? kd.sched_e : kd.sched_d);
-  const uint32_t nsteps = CRT ? kd.nsteps_h[half] : (enc ? kd.nsteps_e : kd.nsteps_d);
-  const uint32_t maxidx = CRT ? kd.maxidx_h[half] : (enc ? kd.maxidx_e : kd.maxidx_d);
+  const uint32_t *sched = CRT ? (sel ? kd.sched_hinv[half] : kd.sched_h[half]) : (sel ? kd.sched_e : kd.sched_d);
+  const uint32_t nsteps = CRT ? (sel ? kd.nsteps_hinv[half] : kd.nsteps_h[half]) : (sel ? kd.nsteps_e : kd.nsteps_d);
+  const uint32_t maxidx = CRT ? (sel ? kd.maxidx_hinv[half] : kd.maxidx_h[half]) : (sel ? kd.maxidx_e : kd.maxidx_d);
   const uint32_t n0 = CRT ? kd.n0h[half] : kd.n0;
 
   for (int i = threadIdx.x; i < S; i += kThreads) {
@@ -170,6 +172,46 @@ __global__ void __launch_bounds__(kThreads) k_modexp_tasks(const BatchTask *__re
   }
 }
 
+// out[t] = a[t] b[t] mod N_key: two Montgomery products, a b R^-1 and then
+// (a b R^-1) R^2 R^-1.  Same grid mapping as k_modexp; b goes through shared
+// memory as the broadcast operand.
+template <int S, int TPI>
+__global__ void __launch_bounds__(kThreads) k_mulmod(const KeyDev *__restrict__ keys, uint32_t K,
+                                                     const uint32_t *a_in, const uint32_t *b_in, uint32_t *out,
+                                                     long long n) {
+  constexpr int L = S / TPI;
+  constexpr int IPB = kThreads / TPI;
+  constexpr int ROW = Layout<S>::kRow;
+  extern __shared__ __align__(16) uint32_t smem[];
+  const uint32_t r = threadIdx.x % TPI, g = threadIdx.x / TPI;
+  uint32_t *sR2 = smem, *yrow = smem + (1 + g) * ROW;
+  const uint32_t key = blockIdx.y;
+  const long long first = key + (long long)blockIdx.x * IPB * K;
+  if (first >= n) return;
+  const KeyDev &kd = keys[key];
+  for (int i = threadIdx.x; i < S; i += kThreads) sR2[i] = __ldg(kd.R2 + i);
+  const long long t = first + (long long)g * K;
+  const bool active = t < n;
+  uint32_t nn[L], a[L], b[L];
+  load_slice_global<L>(nn, kd.N, r);
+  if (active) {
+    load_slice_global<L>(a, a_in + t * S, r);
+    load_slice_global<L>(b, b_in + t * S, r);
+  } else {
+#pragma unroll
+    for (int j = 0; j < L; j++) a[j] = b[j] = 0;
+  }
+  store_slice<L>(yrow, b, r);
+  __syncthreads();
+  mont<S, TPI, kChain>(a, yrow, nn, kd.n0, r);
+  mont<S, TPI, kChain>(a, sR2, nn, kd.n0, r);
+  if (active) {
+    uint32_t *o = out + t * S + r * L;
+#pragma unroll
+    for (int j = 0; j < L; j++) o[j] = a[j];
+  }
+}
+
 template <int S>
 constexpr size_t modexp_smem_bytes(int tpi) {
   return sizeof(uint32_t) * ((size_t)Layout<S>::kConstRows * Layout<S>::kRow + (size_t)(kThreads / tpi) * Layout<S>::kInst);
@@ -204,5 +246,18 @@ ModexpEntry make_entry() {
 const ModexpEntry *modexp_entries_full(int *count);
 const ModexpEntry *modexp_entries_crt(int *count);
 const ModexpEntry *modexp_entries_wide(int *count);  // 6144/8192-bit full width, 3072/4096-bit CRT halves
+
+// Modular multiplication kernels, one per full-width limb count.
+struct MulmodEntry {
+  int limbs, tpi;
+  const void *fn;
+  size_t smem;
+};
+template <int S, int TPI>
+MulmodEntry make_mulmod() {
+  return MulmodEntry{S, TPI, reinterpret_cast<const void *>(&dev::k_mulmod<S, TPI>),
+                     sizeof(uint32_t) * (size_t)(1 + dev::kThreads / TPI) * dev::Layout<S>::kRow};
+}
+const MulmodEntry *mulmod_entries(int *count);
 
 }  // namespace pmk

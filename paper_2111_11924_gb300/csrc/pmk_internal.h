@@ -14,7 +14,7 @@
 namespace pmk {
 
 // Error bits written by kernels into the context's device status word.
-enum : uint32_t { kStatusRange = 1u };
+enum : uint32_t { kStatusRange = 1u, kStatusNotInvertible = 2u };
 
 // Exponent schedule for left-to-right sliding-window exponentiation.
 // steps[0] = index of the first odd power (a load, no squaring);
@@ -34,6 +34,7 @@ struct HostKey {
   std::vector<uint32_t> R2h[2], R3h[2];              // R_h^2, R_h^3 mod p | q
   std::vector<uint32_t> qinv_m;                      // qinv * R_h mod p
   Schedule sched_e, sched_d, sched_h[2];             // e, d, dp, dq
+  Schedule sched_hinv[2];                            // p - 2, q - 2 (Fermat inverses mod p, q)
 };
 
 // Device view of one key (pointers into the key set's device blob).
@@ -47,9 +48,10 @@ struct KeyDev {
   const uint32_t *R3h[2];
   const uint32_t *sched_h[2];
   const uint32_t *qinv_m;
+  const uint32_t *sched_hinv[2];
   uint32_t n0, n0h[2];
-  uint32_t nsteps_e, nsteps_d, nsteps_h[2];
-  uint32_t maxidx_e, maxidx_d, maxidx_h[2];
+  uint32_t nsteps_e, nsteps_d, nsteps_h[2], nsteps_hinv[2];
+  uint32_t maxidx_e, maxidx_d, maxidx_h[2], maxidx_hinv[2];
 };
 
 // One unit of work of the persistent batch kernels: up to 32 / TPI chunks
@@ -69,7 +71,7 @@ int host_from_primes(uint32_t nbits, uint64_t e, const uint32_t *p, const uint32
 Schedule make_schedule(const uint32_t *exp, int nlimbs);
 
 // Kernel launchers (kernels_*.cu).  All return PMK_* codes.
-enum class ExpMode : int { kEncrypt = 0, kDecrypt = 1, kCrtHalf = 2 };
+enum class ExpMode : int { kEncrypt = 0, kDecrypt = 1, kCrtHalf = 2, kCrtInverse = 3 };
 int launch_split(uint32_t nbits, const uint8_t *msg, size_t len, uint32_t *chunks, size_t n, cudaStream_t st);
 int launch_join(uint32_t nbits, const uint32_t *chunks, size_t n, uint8_t *msg, size_t len, cudaStream_t st);
 int launch_range_check(const KeyDev *keys, uint32_t K, uint32_t s, const uint32_t *in, size_t n,
@@ -81,7 +83,11 @@ struct KernelConfig {
 };
 int launch_modexp(ExpMode mode, uint32_t limbs, KernelConfig cfg, const KeyDev *keys, uint32_t K, const uint32_t *in,
                   uint32_t *out, size_t n, cudaStream_t st);
-int launch_garner(uint32_t half_limbs, const KeyDev *keys, uint32_t K, uint32_t *out, size_t n, cudaStream_t st);
+int launch_garner(uint32_t half_limbs, const KeyDev *keys, uint32_t K, uint32_t *out, size_t n, cudaStream_t st,
+                  uint32_t *status_if_zero_half = nullptr);
+// out[t] = a[t] * b[t] mod N_{t mod K} (full width; out may alias a or b)
+int launch_mulmod(uint32_t limbs, const KeyDev *keys, uint32_t K, const uint32_t *a, const uint32_t *b, uint32_t *out,
+                  size_t n, cudaStream_t st);
 bool modexp_built(uint32_t limbs, KernelConfig cfg, bool crt);
 KernelConfig default_config(uint32_t limbs, bool crt);  // tpi == 0: limb count not built
 int list_configs(uint32_t limbs, bool crt, KernelConfig *out, int max);

@@ -14,7 +14,8 @@ import numpy as np
 
 from . import _native_build
 
-PMK_OK, PMK_EINVAL, PMK_ERANGE, PMK_ENOMEM, PMK_ECUDA, PMK_EUNSUPPORTED, PMK_ETOOLARGE = 0, -1, -2, -3, -4, -5, -6
+PMK_OK, PMK_EINVAL, PMK_ERANGE, PMK_ENOMEM, PMK_ECUDA, PMK_EUNSUPPORTED, PMK_ETOOLARGE, PMK_ENOINV = (
+    0, -1, -2, -3, -4, -5, -6, -7)
 
 _lib = None
 
@@ -61,6 +62,8 @@ def load_library() -> ctypes.CDLL:
         "pmk_join": (i, [vp, u32, vp, sz, vp, sz, vp]),
         "pmk_encrypt_chunks": (i, [vp, vp, vp, vp, sz, vp]),
         "pmk_decrypt_chunks": (i, [vp, vp, vp, vp, sz, i, vp]),
+        "pmk_encrypt_blinded": (i, [vp, vp, vp, vp, vp, vp, sz, vp]),
+        "pmk_decrypt_blinded": (i, [vp, vp, vp, vp, vp, sz, i, vp]),
         "pmk_encrypt_message_host": (i, [vp, vp, vp, sz, vp, sz, vp]),
         "pmk_decrypt_message_host": (i, [vp, vp, vp, sz, vp, sz, i, vp]),
         "pmk_decrypt_message_host_noalloc": (i, [vp, vp, sz, vp, sz, i, vp]),
@@ -259,6 +262,28 @@ class Context:
         _check(load_library().pmk_decrypt_chunks(self.handle, ks.handle, self._dev(chunks, torch.int32, "in"),
                                                  self._dev(out, torch.int32, "out"), chunks.shape[0], int(use_crt),
                                                  self.stream_handle(stream)), "pmk_decrypt_chunks")
+        return out
+
+    def encrypt_blinded(self, ks: KeySet, chunks, rnd, out_cstar=None, out_cr=None, stream=None):
+        """Algorithm 1 encryption with the random matrix R: returns (C*, C_R)."""
+        torch = _torch()
+        out_cstar = torch.empty_like(chunks) if out_cstar is None else out_cstar
+        out_cr = torch.empty_like(chunks) if out_cr is None else out_cr
+        _check(load_library().pmk_encrypt_blinded(self.handle, ks.handle, self._dev(chunks, torch.int32, "m"),
+                                                  self._dev(rnd, torch.int32, "r"),
+                                                  self._dev(out_cstar, torch.int32, "cstar"),
+                                                  self._dev(out_cr, torch.int32, "cr"), chunks.shape[0],
+                                                  self.stream_handle(stream)), "pmk_encrypt_blinded")
+        return out_cstar, out_cr
+
+    def decrypt_blinded(self, ks: KeySet, cstar, cr, use_crt: bool = False, out=None, stream=None):
+        """Algorithm 1 decryption with R: m = (c* c_r^-1)^d mod N."""
+        torch = _torch()
+        out = torch.empty_like(cstar) if out is None else out
+        _check(load_library().pmk_decrypt_blinded(self.handle, ks.handle, self._dev(cstar, torch.int32, "cstar"),
+                                                  self._dev(cr, torch.int32, "cr"), self._dev(out, torch.int32, "m"),
+                                                  cstar.shape[0], int(use_crt), self.stream_handle(stream)),
+               "pmk_decrypt_blinded")
         return out
 
     def encrypt_message_host(self, ks: KeySet, h_msg, h_cipher, stream=None) -> None:

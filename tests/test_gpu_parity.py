@@ -384,3 +384,40 @@ def test_batched_persistent_graph_matches_per_call(ctx, P):
     ok = sets[0][1]
     assert np.array_equal(host(out)[:6], oracle.decrypt_chunks(host(x)[:6], ok))
     batch.destroy()
+
+
+@pytest.mark.parametrize("nbits,K,length", [(512, 3, 3000), (2048, 8, 61200)])
+def test_blinded_algorithm1_parity(ctx, nbits, K, length):
+    """Algorithm 1 with the random matrix R: GPU C*, C_R equal the oracle's bit
+    for bit; GPU decryption (c* c_r^-1)^d (full d and CRT) recovers every chunk,
+    and so does the oracle's literal r' = c_r^d, m* = c*^d, m* r'^-1."""
+    ks, ok = keys_for(ctx, K, nbits, seed=0x50444D4B0000D000 + nbits)
+    msg = np.random.default_rng(nbits).integers(0, 256, length, dtype=np.uint8)
+    m = oracle.split(msg, nbits)
+    r = W.blinding_values(len(m), nbits, seed=0x50444D4B0000D100 + nbits)
+    cstar_ref, cr_ref = oracle.blind_encrypt_chunks(m, r, ok, threads=8)
+    cstar, cr = ctx.encrypt_blinded(ks, dev(m), dev(r))
+    assert np.array_equal(host(cstar), cstar_ref)
+    assert np.array_equal(host(cr), cr_ref)
+    for use_crt in (False, True):
+        back = ctx.decrypt_blinded(ks, cstar, cr, use_crt=use_crt)
+        assert np.array_equal(host(back), m), use_crt
+    sample = slice(0, 10)
+    assert np.array_equal(oracle.blind_decrypt_chunks(cstar_ref[sample], cr_ref[sample], ok, threads=8), m[sample])
+    assert ctx.status() == 0
+
+
+def test_blinded_non_invertible_value_reported(ctx, P):
+    ks, ok = keys_for(ctx, 2, 256, seed=8)
+    k0 = ok.key(0)
+    m = np.stack([oracle.to_limbs(v, 8) for v in (5, 6, 7, 8)])
+    r = np.stack([oracle.to_limbs(v, 8) for v in (3, 4, 5, 6)])
+    cstar, cr = ctx.encrypt_blinded(ks, dev(m), dev(r))
+    assert ctx.status() == 0
+    bad = host(cr).copy()
+    bad[2] = oracle.to_limbs(k0["p"] * 11, 8)  # chunk 2 (key 0) shares the factor p with N_0
+    out = ctx.decrypt_blinded(ks, cstar, dev(bad))
+    assert ctx.status() == P.pmkrsa.PMK_ENOINV
+    got = host(out)
+    for t in (0, 1, 3):
+        assert oracle.from_limbs(got[t]) == oracle.from_limbs(m[t])
