@@ -553,6 +553,44 @@ def run_batched(args):
     return 0 if same else 1
 
 
+def run_serving(args):
+    """The serving workload: Poisson arrivals (--serve-rate per second) of
+    encrypt / decrypt requests (70% decrypt, CRT form), payloads log-uniform
+    over 1 KB - 25 MB times --serve-scale, key widths uniform over {2048, 3072,
+    4096} with resident key tables, admission by a 40 GB device budget.
+    Reports p50 / p99 latency and MB/s for continuous batching on streams and
+    for the plain one-request-at-a-time path on the same requests."""
+    import torch
+
+    import paper_2111_11924_gb300 as P
+    from paper_2111_11924_gb300 import serving as SV
+
+    ctx = P.Context(0)
+    widths = (2048, 3072, 4096)
+    keysets = {nb: ctx.keygen(8, nb, 65537, 0x50444D4B0000F000 + nb) for nb in widths}
+    for nb, ks in keysets.items():
+        for mode in ("encrypt", "crt"):
+            ctx.autotune(ks, 2000, mode, reps=1)
+    reqs = SV.poisson_requests(args.serve_rate, args.serve_requests, seed=5, widths=widths, scale=args.serve_scale)
+    SV.prepare_payloads(ctx, keysets, reqs)
+    server = SV.Server(ctx, keysets, budget_bytes=40 << 30, slots=args.serve_slots, use_crt=True)
+    server.serve(reqs[: min(16, len(reqs))])  # warm-up
+    for r in reqs:
+        r.result = None
+    cb = server.serve(reqs)
+    ok_cb = all(torch.equal(r.result, r.extra["message"]) for r in reqs if r.op == "decrypt")
+    for r in reqs:
+        r.result = None
+    plain = server.serve_one_at_a_time(reqs)
+    payload = sum(r.msg_len for r in reqs)
+    line = {"mode": "serving", "requests": len(reqs), "arrival_rate_per_s": args.serve_rate,
+            "payload_scale": args.serve_scale, "payload_MB": payload / 2**20,
+            "offered_MBps": payload / 2**20 / reqs[-1].arrival, "decrypt_form": "CRT",
+            "continuous_batching": cb, "one_at_a_time": plain, "decryptions_round_trip": ok_cb}
+    print(json.dumps(line))
+    return 0 if ok_cb else 1
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -566,6 +604,11 @@ def main(argv=None):
     ap.add_argument("--batched", action="store_true",
                     help="time the mixed-size 64-message batch (plain per-call vs persistent batch) and exit")
     ap.add_argument("--batch-scale", type=float, default=1.0, help="scale of the batch's message sizes")
+    ap.add_argument("--serve", action="store_true", help="run the serving workload and exit")
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--serve-scale", type=float, default=0.01, help="scale of the request payload sizes")
+    ap.add_argument("--serve-slots", type=int, default=32)
     ap.add_argument("--widths", action="store_true",
                     help="time the 100 KB / K=16 workload at each key length and exit")
     ap.add_argument("--width-list", type=int, nargs="*", default=[1024, 2048, 3072, 4096, 6144, 8192])
@@ -580,6 +623,8 @@ def main(argv=None):
         return run_widths(args)
     if args.batched:
         return run_batched(args)
+    if args.serve:
+        return run_serving(args)
     return run_reference(args) if args.impl == "reference" else run_ours(args)
 
 

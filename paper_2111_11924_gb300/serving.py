@@ -1,0 +1,203 @@
+"""Request serving over the PMKRSA kernels: continuous batching on streams.
+
+Requests (encrypt a message, or decrypt a ciphertext back to its message)
+arrive over time with uneven sizes and key widths.  The key tables of every
+width stay resident on the device.  A request is admitted as soon as it has
+arrived, an in-flight slot is free and its device memory fits the budget;
+its whole pipeline (host-to-device copy, split + encrypt or decrypt + join,
+device-to-host copy) is enqueued on the slot's own CUDA stream, so requests
+admitted while others are still running execute concurrently on the GPU.
+Completion is detected with CUDA events, which frees the slot and the memory
+for the next arrivals.  The host thread never blocks on the device while
+others are in flight.
+
+This is host orchestration only: every step of every request runs in the
+library's kernels through the C ABI.
+"""
+from __future__ import annotations
+
+import math
+import time
+from collections import deque
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .pmkrsa import Context, KeySet, num_chunks
+
+
+@dataclass
+class Request:
+    rid: int
+    op: str                 # "encrypt" (message -> ciphertext) or "decrypt" (ciphertext -> message)
+    nbits: int
+    arrival: float          # seconds after the start of serving
+    msg_len: int
+    payload: object         # pinned host tensor: uint8 message (encrypt) or int32 limb buffer (decrypt)
+    result: object = None   # pinned host tensor, filled when done
+    t_admit: float = math.nan
+    t_done: float = math.nan
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def latency(self) -> float:
+        return self.t_done - self.arrival
+
+    def device_bytes(self) -> int:
+        n = num_chunks(self.msg_len, self.nbits)
+        return self.msg_len + 2 * n * (self.nbits // 8)
+
+
+def _percentile(xs, q):
+    return float(np.percentile(np.asarray(xs), q)) if len(xs) else math.nan
+
+
+class Server:
+    """Admits requests by arrival time, in-flight slot and device-memory budget."""
+
+    def __init__(self, ctx: Context, keysets: dict, budget_bytes: int, slots: int = 16, use_crt: bool = True):
+        import torch
+
+        self.torch = torch
+        self.ctx = ctx
+        self.keysets = keysets          # nbits -> KeySet (resident on the device)
+        self.budget = int(budget_bytes)
+        self.slots = int(slots)
+        self.use_crt = use_crt
+        self.streams = [torch.cuda.Stream(device=ctx.device) for _ in range(self.slots)]
+
+    # ------------------------------------------------------------------ one request
+    def _enqueue(self, req: Request, stream) -> dict:
+        torch = self.torch
+        ks: KeySet = self.keysets[req.nbits]
+        n = num_chunks(req.msg_len, req.nbits)
+        with torch.cuda.stream(stream):
+            if req.op == "encrypt":
+                d_msg = req.payload.to(f"cuda:{self.ctx.device}", non_blocking=True)
+                chunks = self.ctx.split(req.nbits, d_msg, stream=stream)
+                self.ctx.encrypt_chunks(ks, chunks, out=chunks, stream=stream)
+                req.result.copy_(chunks, non_blocking=True)
+                bufs = (d_msg, chunks)
+            else:
+                d_c = req.payload.to(f"cuda:{self.ctx.device}", non_blocking=True)
+                plain = self.ctx.decrypt_chunks(ks, d_c, use_crt=self.use_crt, stream=stream)
+                d_msg = self.ctx.join(req.nbits, plain, req.msg_len, stream=stream)
+                req.result.copy_(d_msg, non_blocking=True)
+                bufs = (d_c, plain, d_msg)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+        return {"event": ev, "bufs": bufs, "n": n}
+
+    def _alloc_result(self, req: Request) -> None:
+        torch = self.torch
+        if req.result is None:
+            if req.op == "encrypt":
+                n = num_chunks(req.msg_len, req.nbits)
+                req.result = torch.empty((n, req.nbits // 32), dtype=torch.int32).pin_memory()
+            else:
+                req.result = torch.empty(req.msg_len, dtype=torch.uint8).pin_memory()
+
+    # ------------------------------------------------------------------ serving loops
+    def serve(self, requests: list) -> dict:
+        """Continuous batching: serve `requests` (sorted by arrival) as they arrive."""
+        for r in requests:
+            self._alloc_result(r)
+            if r.device_bytes() > self.budget:
+                raise ValueError(f"request {r.rid} needs more device memory than the whole budget")
+        pending = deque(sorted(requests, key=lambda r: r.arrival))
+        free_slots = list(range(self.slots))
+        inflight = {}  # slot -> (request, record)
+        used = 0
+        peak_used, peak_inflight = 0, 0
+        t0 = time.perf_counter()
+        while pending or inflight:
+            now = time.perf_counter() - t0
+            progressed = False
+            for slot in list(inflight):
+                req, rec = inflight[slot]
+                if rec["event"].query():
+                    req.t_done = time.perf_counter() - t0
+                    used -= req.device_bytes()
+                    del inflight[slot]
+                    free_slots.append(slot)
+                    progressed = True
+            # admit in arrival order while the head has arrived and fits
+            while pending and free_slots and pending[0].arrival <= now and used + pending[0].device_bytes() <= self.budget:
+                req = pending.popleft()
+                slot = free_slots.pop()
+                req.t_admit = time.perf_counter() - t0
+                inflight[slot] = (req, self._enqueue(req, self.streams[slot]))
+                used += req.device_bytes()
+                peak_used = max(peak_used, used)
+                peak_inflight = max(peak_inflight, len(inflight))
+                progressed = True
+            if not progressed:
+                if pending and not inflight and pending[0].arrival > now:
+                    time.sleep(min(pending[0].arrival - now, 1e-3))
+                else:
+                    time.sleep(20e-6)
+        self.torch.cuda.synchronize(self.ctx.device)
+        status = self.ctx.status()
+        return self._stats(requests, time.perf_counter() - t0, status,
+                           {"peak_device_bytes": peak_used, "peak_in_flight": peak_inflight})
+
+    def serve_one_at_a_time(self, requests: list) -> dict:
+        """The plain path: requests in arrival order, one at a time on one stream."""
+        for r in requests:
+            self._alloc_result(r)
+        stream = self.streams[0]
+        t0 = time.perf_counter()
+        for req in sorted(requests, key=lambda r: r.arrival):
+            now = time.perf_counter() - t0
+            if req.arrival > now:
+                time.sleep(req.arrival - now)
+            req.t_admit = time.perf_counter() - t0
+            rec = self._enqueue(req, stream)
+            rec["event"].synchronize()
+            req.t_done = time.perf_counter() - t0
+        status = self.ctx.status()
+        return self._stats(requests, time.perf_counter() - t0, status, {})
+
+    @staticmethod
+    def _stats(requests, wall, status, extra) -> dict:
+        lat = [r.latency for r in requests]
+        payload = sum(r.msg_len for r in requests)
+        return {"requests": len(requests), "wall_s": wall, "status": status,
+                "p50_ms": 1e3 * _percentile(lat, 50), "p99_ms": 1e3 * _percentile(lat, 99),
+                "max_ms": 1e3 * max(lat) if lat else math.nan,
+                "payload_MBps": payload / 2**20 / wall, "requests_per_s": len(requests) / wall} | extra
+
+
+def poisson_requests(rate_per_s: float, count: int, seed: int, widths=(2048, 3072, 4096), p_decrypt: float = 0.7,
+                     min_bytes: int = 1024, max_bytes: int = 25_000_000, scale: float = 1.0) -> list:
+    """Request shapes of the serving workload: Poisson arrivals, payloads
+    log-uniform over [min_bytes, max_bytes] times `scale`, widths uniform,
+    a fraction p_decrypt of decryptions.  Payloads are filled in by the caller
+    (decryptions need ciphertexts of their keys)."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate_per_s, count))
+    out = []
+    for i in range(count):
+        size = max(1, int(np.exp(rng.uniform(np.log(min_bytes), np.log(max_bytes))) * scale))
+        out.append(Request(rid=i, op="decrypt" if rng.random() < p_decrypt else "encrypt",
+                           nbits=int(rng.choice(widths)), arrival=float(t[i]), msg_len=size, payload=None,
+                           extra={"seed": seed * 1_000_003 + i}))
+    return out
+
+
+def prepare_payloads(ctx: Context, keysets: dict, requests: list) -> None:
+    """Fill each request's pinned payload: a seeded random message, or for a
+    decryption the ciphertext of one (made with the library, before serving).
+    The message is kept in request.extra["message"] for checking."""
+    import torch
+
+    for r in requests:
+        msg = torch.from_numpy(np.random.default_rng(r.extra["seed"]).integers(0, 256, r.msg_len, dtype=np.uint8))
+        r.extra["message"] = msg
+        if r.op == "encrypt":
+            r.payload = msg.pin_memory()
+        else:
+            ks = keysets[r.nbits]
+            cipher = ctx.encrypt_chunks(ks, ctx.split(r.nbits, msg.cuda(ctx.device)))
+            r.payload = cipher.cpu().pin_memory()
+    torch.cuda.synchronize(ctx.device)
