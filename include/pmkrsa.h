@@ -131,6 +131,16 @@ int pmk_decrypt_chunks(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_in,
                        size_t n_chunks, int use_crt, void *stream);
 
 /*
+ * The plain GPU formulation, kept as a measured baseline for the kernels
+ * above: one thread per chunk, single-thread Montgomery products and
+ * Algorithm 2's binary exponentiation, one launch per call.
+ * d_out[t] = d_in[t]^E mod N_{t mod K} with E = d (decrypt != 0) or e.
+ * Built for 1024- and 2048-bit keys only (PMK_EUNSUPPORTED otherwise).
+ */
+int pmk_modexp_chunks_baseline(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_in, uint32_t *d_out,
+                               size_t n_chunks, int decrypt, void *stream);
+
+/*
  * PMKRSA encryption with the random matrix R (Algorithm 1 "Encryption",
  * Section 3.1): for every chunk, with k = t mod K,
  *   c_t = m_t^e,  c*_t = c_t r_t^e,  c_r,t = r_t^e   (mod N_k).

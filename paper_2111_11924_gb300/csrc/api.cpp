@@ -65,7 +65,7 @@ size_t push(std::vector<uint32_t> &blob, const std::vector<uint32_t> &v) {
 int upload(pmk_keyset *ks) {
   std::vector<uint32_t> blob;
   struct Offs {
-    size_t N, R2, se, sd, P[2], R2h[2], R3h[2], sh[2], shi[2], qm;
+    size_t N, R2, se, sd, P[2], R2h[2], R3h[2], sh[2], shi[2], qm, el, dl;
   };
   std::vector<Offs> offs(ks->K);
   for (uint32_t k = 0; k < ks->K; k++) {
@@ -84,6 +84,8 @@ int upload(pmk_keyset *ks) {
       o.shi[i] = push(blob, h.sched_hinv[i].steps);
     }
     o.qm = push(blob, h.qinv_m);
+    o.el = push(blob, {(uint32_t)ks->e, (uint32_t)(ks->e >> 32)});
+    o.dl = push(blob, h.d);
   }
   if (cudaMalloc(&ks->d_blob, blob.size() * 4) != cudaSuccess) return PMK_ENOMEM;
   if (cudaMemcpy(ks->d_blob, blob.data(), blob.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) return PMK_ECUDA;
@@ -98,6 +100,8 @@ int upload(pmk_keyset *ks) {
     d.sched_e = b + o.se;
     d.sched_d = b + o.sd;
     d.qinv_m = b + o.qm;
+    d.e_limbs = b + o.el;
+    d.d_limbs = b + o.dl;
     d.n0 = h.n0;
     d.nsteps_e = (uint32_t)h.sched_e.steps.size();
     d.nsteps_d = (uint32_t)h.sched_d.steps.size();
@@ -399,6 +403,20 @@ int pmk_decrypt_blinded(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_cs
     rc = pmk::launch_modexp(pmk::ExpMode::kCrtHalf, H, cfg_for(ctx, H, true), ks->d_keys, ks->K, ctx->d_b, d_m,
                             n_chunks, st);
   if (rc == PMK_OK) rc = pmk::launch_garner(H, ks->d_keys, ks->K, d_m, n_chunks, st);
+  return rc;
+}
+
+int pmk_modexp_chunks_baseline(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_in, uint32_t *d_out,
+                               size_t n_chunks, int decrypt, void *stream) {
+  if (n_chunks == 0) return (ctx && ks) ? PMK_OK : PMK_EINVAL;
+  int rc = check_chunk_call(ctx, ks, d_in, d_out);
+  if (rc != PMK_OK) return rc;
+  DeviceGuard g(ctx->device);
+  if (!g.ok()) return PMK_ECUDA;
+  const uint32_t S = ks->nbits / 32;
+  rc = pmk::launch_range_check(ks->d_keys, ks->K, S, d_in, n_chunks, ctx->d_status, as_stream(stream));
+  if (rc == PMK_OK)
+    rc = pmk::launch_modexp_naive(!decrypt, S, ks->d_keys, ks->K, d_in, d_out, n_chunks, as_stream(stream));
   return rc;
 }
 

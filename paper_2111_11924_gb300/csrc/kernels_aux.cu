@@ -170,6 +170,73 @@ __global__ void __launch_bounds__(kAuxThreads) k_garner(const KeyDev *__restrict
   for (int i = 0; i < 2 * H; i++) o[i] = acc[i];
 }
 
+// The plain GPU formulation, kept as a measured baseline: one thread per
+// chunk, its S-limb values in local memory, single-thread CIOS Montgomery
+// products and Algorithm 2's binary exponentiation (right-to-left, as printed).
+// out[t] = in[t]^E mod N_{t mod K}, E = e (enc) or d.
+template <int S>
+__global__ void __launch_bounds__(128) k_modexp_naive(const KeyDev *__restrict__ keys, uint32_t K,
+                                                      const uint32_t *__restrict__ in, uint32_t *__restrict__ out,
+                                                      long long n, int enc) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const KeyDev &kd = keys[t % K];
+  const uint32_t *N = kd.N, n0 = kd.n0;
+  uint32_t x[S], y[S], acc[S + 2];
+  auto montmul = [&](uint32_t *a, const uint32_t *b) {  // a <- a b R^-1 mod N
+    for (int i = 0; i < S + 2; i++) acc[i] = 0;
+    for (int i = 0; i < S; i++) {
+      uint64_t c = 0;
+      for (int j = 0; j < S; j++) {
+        c += (uint64_t)a[j] * b[i] + acc[j];
+        acc[j] = (uint32_t)c;
+        c >>= 32;
+      }
+      c += acc[S];
+      acc[S] = (uint32_t)c;
+      acc[S + 1] = (uint32_t)(c >> 32);
+      const uint32_t q = acc[0] * n0;
+      c = ((uint64_t)q * N[0] + acc[0]) >> 32;
+      for (int j = 1; j < S; j++) {
+        c += (uint64_t)q * N[j] + acc[j];
+        acc[j - 1] = (uint32_t)c;
+        c >>= 32;
+      }
+      c += acc[S];
+      acc[S - 1] = (uint32_t)c;
+      acc[S] = acc[S + 1] + (uint32_t)(c >> 32);
+    }
+    uint32_t d[S], borrow = 0;
+    for (int i = 0; i < S; i++) {
+      const uint64_t v = (uint64_t)acc[i] - N[i] - borrow;
+      d[i] = (uint32_t)v;
+      borrow = (uint32_t)(v >> 63);
+    }
+    const bool ge = acc[S] || !borrow;
+    for (int i = 0; i < S; i++) a[i] = ge ? d[i] : acc[i];
+  };
+  const uint32_t *E = enc ? kd.e_limbs : kd.d_limbs;  // the exponent itself, bit by bit
+  const int ne = enc ? 2 : S;
+  for (int i = 0; i < S; i++) x[i] = in[t * S + i];
+  for (int i = 0; i < S; i++) y[i] = kd.R2[i];
+  montmul(x, y);                      // x R
+  for (int i = 0; i < S; i++) y[i] = (i == 0);
+  montmul(y, kd.R2);                  // y = R mod N (one)
+  int top = -1;
+  for (int i = 32 * ne - 1; i >= 0 && top < 0; i--)
+    if ((E[i / 32] >> (i % 32)) & 1) top = i;
+  for (int i = 0; i < top; i++) {     // Algorithm 2: bits e_0 .. e_{l-1}
+    if ((E[i / 32] >> (i % 32)) & 1) montmul(y, x);
+    uint32_t xc[S];
+    for (int j = 0; j < S; j++) xc[j] = x[j];
+    montmul(x, xc);
+  }
+  montmul(y, x);                      // the top bit
+  for (int i = 0; i < S; i++) x[i] = (i == 0);
+  montmul(y, x);                      // leave the Montgomery domain
+  for (int i = 0; i < S; i++) out[t * S + i] = y[i];
+}
+
 int grid_for(long long work, int threads) {
   long long b = (work + threads - 1) / threads;
   return (int)std::max(1LL, std::min(b, 152LL * 64));
@@ -260,6 +327,19 @@ int launch_mulmod(uint32_t limbs, const KeyDev *keys, uint32_t K, const uint32_t
   long long nl = (long long)n;
   void *args[] = {(void *)&keys, (void *)&K, (void *)&a, (void *)&b, (void *)&out, (void *)&nl};
   return cuda_rc(cudaLaunchKernel(e->fn, grid, dim3(dev::kThreads), args, e->smem, st));
+}
+
+int launch_modexp_naive(bool enc, uint32_t limbs, const KeyDev *keys, uint32_t K, const uint32_t *in, uint32_t *out,
+                        size_t n, cudaStream_t st) {
+  if (n == 0) return PMK_OK;
+  const unsigned blocks = (unsigned)((n + 127) / 128);
+  const int e = enc ? 1 : 0;
+  switch (limbs) {
+    case 32: k_modexp_naive<32><<<blocks, 128, 0, st>>>(keys, K, in, out, (long long)n, e); break;
+    case 64: k_modexp_naive<64><<<blocks, 128, 0, st>>>(keys, K, in, out, (long long)n, e); break;
+    default: return PMK_EUNSUPPORTED;
+  }
+  return cuda_rc(cudaGetLastError());
 }
 
 bool modexp_built(uint32_t limbs, KernelConfig cfg, bool crt) { return find_entry(limbs, cfg, crt) != nullptr; }

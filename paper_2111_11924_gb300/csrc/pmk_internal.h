@@ -49,6 +49,7 @@ struct KeyDev {
   const uint32_t *sched_h[2];
   const uint32_t *qinv_m;
   const uint32_t *sched_hinv[2];
+  const uint32_t *e_limbs, *d_limbs;  // e (2 limbs) and d (s limbs), for the thread-per-chunk baseline
   uint32_t n0, n0h[2];
   uint32_t nsteps_e, nsteps_d, nsteps_h[2], nsteps_hinv[2];
   uint32_t maxidx_e, maxidx_d, maxidx_h[2], maxidx_hinv[2];
@@ -89,6 +90,9 @@ int launch_garner(uint32_t half_limbs, const KeyDev *keys, uint32_t K, uint32_t 
 int launch_mulmod(uint32_t limbs, const KeyDev *keys, uint32_t K, const uint32_t *a, const uint32_t *b, uint32_t *out,
                   size_t n, cudaStream_t st);
 bool modexp_built(uint32_t limbs, KernelConfig cfg, bool crt);
+// The plain thread-per-chunk, binary-exponent kernel (a measured baseline; 32 or 64 limbs).
+int launch_modexp_naive(bool enc, uint32_t limbs, const KeyDev *keys, uint32_t K, const uint32_t *in, uint32_t *out,
+                        size_t n, cudaStream_t st);
 KernelConfig default_config(uint32_t limbs, bool crt);  // tpi == 0: limb count not built
 int list_configs(uint32_t limbs, bool crt, KernelConfig *out, int max);
 // Persistent batch kernel for (limbs, cfg, crt): `blocks` x 128 threads

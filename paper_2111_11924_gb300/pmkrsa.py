@@ -62,6 +62,7 @@ def load_library() -> ctypes.CDLL:
         "pmk_join": (i, [vp, u32, vp, sz, vp, sz, vp]),
         "pmk_encrypt_chunks": (i, [vp, vp, vp, vp, sz, vp]),
         "pmk_decrypt_chunks": (i, [vp, vp, vp, vp, sz, i, vp]),
+        "pmk_modexp_chunks_baseline": (i, [vp, vp, vp, vp, sz, i, vp]),
         "pmk_encrypt_blinded": (i, [vp, vp, vp, vp, vp, vp, sz, vp]),
         "pmk_decrypt_blinded": (i, [vp, vp, vp, vp, vp, sz, i, vp]),
         "pmk_encrypt_message_host": (i, [vp, vp, vp, sz, vp, sz, vp]),
@@ -262,6 +263,16 @@ class Context:
         _check(load_library().pmk_decrypt_chunks(self.handle, ks.handle, self._dev(chunks, torch.int32, "in"),
                                                  self._dev(out, torch.int32, "out"), chunks.shape[0], int(use_crt),
                                                  self.stream_handle(stream)), "pmk_decrypt_chunks")
+        return out
+
+    def modexp_chunks_baseline(self, ks: KeySet, chunks, decrypt: bool = True, out=None, stream=None):
+        """The plain thread-per-chunk, binary-exponent kernel (a measured baseline)."""
+        torch = _torch()
+        out = torch.empty_like(chunks) if out is None else out
+        _check(load_library().pmk_modexp_chunks_baseline(self.handle, ks.handle, self._dev(chunks, torch.int32, "in"),
+                                                         self._dev(out, torch.int32, "out"), chunks.shape[0],
+                                                         int(decrypt), self.stream_handle(stream)),
+               "pmk_modexp_chunks_baseline")
         return out
 
     def encrypt_blinded(self, ks: KeySet, chunks, rnd, out_cstar=None, out_cr=None, stream=None):

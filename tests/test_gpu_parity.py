@@ -421,3 +421,18 @@ def test_blinded_non_invertible_value_reported(ctx, P):
     got = host(out)
     for t in (0, 1, 3):
         assert oracle.from_limbs(got[t]) == oracle.from_limbs(m[t])
+
+
+@pytest.mark.parametrize("nbits", [1024, 2048])
+def test_thread_per_chunk_baseline_matches(ctx, nbits):
+    ks, ok = keys_for(ctx, 3, nbits, seed=321 + nbits)
+    rng = np.random.default_rng(nbits + 1)
+    Ns = ok.ints("N")
+    m = np.stack([oracle.to_limbs(W.random_below(rng, Ns[t % 3]), nbits // 32) for t in range(40)])
+    c_base = ctx.modexp_chunks_baseline(ks, dev(m), decrypt=False)
+    c = ctx.encrypt_chunks(ks, dev(m))
+    assert torch.equal(c_base, c)
+    assert np.array_equal(host(c)[:8], oracle.encrypt_chunks(m[:8], ok))
+    d_base = ctx.modexp_chunks_baseline(ks, c, decrypt=True)
+    assert np.array_equal(host(d_base), m)
+    assert ctx.status() == 0
