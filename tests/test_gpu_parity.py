@@ -436,3 +436,44 @@ def test_thread_per_chunk_baseline_matches(ctx, nbits):
     d_base = ctx.modexp_chunks_baseline(ks, c, decrypt=True)
     assert np.array_equal(host(d_base), m)
     assert ctx.status() == 0
+
+
+@pytest.mark.parametrize("e", [3, 17, 257])
+def test_other_public_exponents(ctx, e):
+    """Small public exponents change the encryption schedule (e = 3 and 17 use
+    the odd-power table) and d; results must still match the oracle."""
+    ks, ok = keys_for(ctx, 3, 1024, seed=2000 + e, e=e)
+    rng = np.random.default_rng(e)
+    Ns = ok.ints("N")
+    m = np.stack([oracle.to_limbs(W.random_below(rng, Ns[t % 3]), 32) for t in range(20)])
+    c = ctx.encrypt_chunks(ks, dev(m))
+    assert np.array_equal(host(c), oracle.encrypt_chunks(m, ok))
+    for use_crt in (False, True):
+        assert np.array_equal(host(ctx.decrypt_chunks(ks, c, use_crt=use_crt)), m)
+    assert np.array_equal(host(ctx.decrypt_chunks(ks, c))[:5], oracle.decrypt_chunks(host(c)[:5], ok))
+
+
+def test_100mib_roundtrip_and_oracle_sample(ctx):
+    """The 100 MiB / K=16 / 2048-bit file: the whole-file round trip on the
+    GPU (full d and CRT), and a seeded 4,096-chunk sample of the ciphertext
+    checked chunk by chunk against the oracle."""
+    w = W.FILE_100MIB_2048
+    ks, ok = keys_for(ctx, w.K, w.nbits, w.key_seed)
+    msg = w.message()
+    d_msg = torch.from_numpy(msg).cuda()
+    m = ctx.split(w.nbits, d_msg)
+    assert m.shape[0] == w.n_chunks == 411207
+    c = ctx.encrypt_chunks(ks, m)
+    back = ctx.join(w.nbits, ctx.decrypt_chunks(ks, c, use_crt=True), w.msg_bytes)
+    assert torch.equal(back, d_msg)
+    back_full = ctx.decrypt_chunks(ks, c)
+    assert torch.equal(back_full, m)
+    idx = np.sort(np.random.default_rng(0x50444D4B).choice(w.n_chunks, 4096, replace=False))
+    m_h, c_h = host(m)[idx], host(c)[idx]
+    # chunk t uses key t mod K: group the sample by key
+    for k in range(w.K):
+        sel = idx % w.K == k
+        sub_keys = oracle.OracleKeys(1, w.nbits, w.e, {f: ok.a[f][k:k + 1] for f in ok.a})
+        assert np.array_equal(oracle.encrypt_chunks(m_h[sel], sub_keys, threads=8), c_h[sel]), k
+    assert np.array_equal(m_h, oracle.split(msg, w.nbits)[idx])
+    assert ctx.status() == 0
