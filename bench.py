@@ -609,6 +609,50 @@ def run_serving(args):
     return 0 if ok_cb else 1
 
 
+def run_hbm(args):
+    """Split and join (the HBM-bound rows) on the 100 MiB / 2048-bit file:
+    GB/s of algorithmic bytes (message bytes + limb-buffer bytes) against the
+    measured copy bandwidth of this GPU."""
+    import torch
+
+    import paper_2111_11924_gb300 as P
+
+    w = W.FILE_100MIB_2048
+    ctx = P.Context(0)
+    d_msg = torch.from_numpy(w.message()).cuda()
+    n = w.n_chunks
+    chunks = torch.empty((n, w.limbs), dtype=torch.int32, device="cuda")
+    back = torch.empty_like(d_msg)
+    ctx.split(w.nbits, d_msg, out=chunks)
+    ctx.join(w.nbits, chunks, w.msg_bytes, out=back)
+    torch.cuda.synchronize()
+    assert torch.equal(back, d_msg)
+    bytes_moved = w.msg_bytes + n * w.limbs * 4
+    peak = _measured_peaks().get("hbm_gbs")
+    res = {}
+    for name, fn in (("split", lambda: ctx.split(w.nbits, d_msg, out=chunks)),
+                     ("join", lambda: ctx.join(w.nbits, chunks, w.msg_bytes, out=back))):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
+        for i in range(args.steps):
+            ev[2 * i].record()
+            fn()
+            ev[2 * i + 1].record()
+        torch.cuda.synchronize()
+        ms = statistics.median(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(args.steps))
+        gbs = bytes_moved / (ms / 1e3) / 1e9
+        res[name] = {"ms": ms, "GBps": gbs, "frac_of_measured_copy": gbs / peak if peak else None}
+    print(json.dumps({"mode": "hbm", "workload": w.name, "bytes_per_call": bytes_moved, "hbm_peak_GBps": peak,
+                      "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peak else None} | res))
+    return 0
+
+
+def _measured_peaks() -> dict:
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -622,6 +666,7 @@ def main(argv=None):
     ap.add_argument("--batched", action="store_true",
                     help="time the mixed-size 64-message batch (plain per-call vs persistent batch) and exit")
     ap.add_argument("--batch-scale", type=float, default=1.0, help="scale of the batch's message sizes")
+    ap.add_argument("--hbm", action="store_true", help="time split / join on the 100 MiB file and exit")
     ap.add_argument("--serve", action="store_true", help="run the serving workload and exit")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-requests", type=int, default=400)
@@ -643,6 +688,8 @@ def main(argv=None):
         return run_batched(args)
     if args.serve:
         return run_serving(args)
+    if args.hbm:
+        return run_hbm(args)
     return run_reference(args) if args.impl == "reference" else run_ours(args)
 
 

@@ -18,7 +18,7 @@
  *     the device (an input chunk >= its modulus) are recorded in the
  *     context and reported by pmk_status().
  *   - Chunk buffers hold n_chunks x nbits/32 little-endian uint32 limbs,
- *     chunk-major ("limb buffer").  Chunk t is bound to key t mod K, the
+ *     chunk-major ("limb buffer"), and must be 16-byte aligned (EINVAL).  Chunk t is bound to key t mod K, the
  *     row-per-key reshape of the i x j plaintext matrix (Section 3.1).
  *   - Calls on one context are not thread-safe; use one context per thread.
  */

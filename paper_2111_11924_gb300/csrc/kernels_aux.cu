@@ -13,39 +13,115 @@ namespace {
 
 constexpr int kAuxThreads = 256;
 
+// The 16 bytes starting at byte `off` (0..15) of the 32 bytes (lo, hi).
+__device__ __forceinline__ uint4 bytes_at(const uint4 lo, const uint4 hi, uint32_t off) {
+  const uint32_t x[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+  const uint32_t sh = (off & 3u) * 8u;
+  uint32_t w[4];
+  switch (off >> 2) {
+#define PMK_CASE(WO)                                                                 \
+  case WO:                                                                           \
+    for (int k = 0; k < 4; k++) w[k] = __funnelshift_r(x[k + WO], x[k + WO + 1], sh); \
+    break;
+    PMK_CASE(0)
+    PMK_CASE(1)
+    PMK_CASE(2)
+    default:
+      for (int k = 0; k < 4; k++) w[k] = __funnelshift_r(x[k + 3], x[k + 4], sh);
+      break;
+#undef PMK_CASE
+  }
+  return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// Bytes [0, n) of a, then bytes [0, 16 - n) of b (0 < n < 16).
+__device__ __forceinline__ uint4 concat_bytes(const uint4 a, const uint4 b, uint32_t n) {
+  const uint32_t A[4] = {a.x, a.y, a.z, a.w}, B[4] = {b.x, b.y, b.z, b.w};
+  const uint32_t sh = (n & 3u) * 8u, wo = n >> 2;
+  uint32_t w[4];
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    // b shifted up by n bytes: word k takes B[k - wo] high part and B[k - wo - 1] low part
+    const int i = k - (int)wo;
+    const uint32_t hi_w = (i >= 0 && i < 4) ? B[i] : 0u;
+    const uint32_t lo_w = (i - 1 >= 0 && i - 1 < 4) ? B[i - 1] : 0u;
+    const uint32_t bs = sh ? __funnelshift_l(lo_w, hi_w, sh) : hi_w;
+    const int keep = (int)n - 4 * k;  // bytes of a in word k
+    const uint32_t mask = keep >= 4 ? 0xffffffffu : keep <= 0 ? 0u : (1u << (8 * keep)) - 1u;
+    w[k] = (A[k] & mask) | (bs & ~mask);
+  }
+  return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
 // Split (Section 3.1): word j of chunk t holds message bytes t P + 4j .. +3
 // (little-endian), zero past the chunk payload P or the message end L.
-// One thread per output word; a warp reads a contiguous byte range.
-__global__ void __launch_bounds__(kAuxThreads) k_split(const uint8_t *__restrict__ msg, long long L, int P, int S,
-                                                       uint32_t *__restrict__ chunks, long long nwords) {
-  long long w = (long long)blockIdx.x * kAuxThreads + threadIdx.x;
-  const long long stride = (long long)gridDim.x * kAuxThreads;
-  for (; w < nwords; w += stride) {
-    const long long t = w / S;
-    const int b0 = (int)(w - t * S) * 4;
-    uint32_t v = 0;
+// One thread per 16 output bytes (4 limbs).  Consecutive threads read
+// consecutive message bytes: two aligned 16-byte loads cover the 16 needed
+// bytes, and a byte shift extracts them.  The message tail, and a message
+// that does not start on a 16-byte boundary, go byte by byte.
+template <typename I>
+__global__ void __launch_bounds__(kAuxThreads) k_split(const uint8_t *__restrict__ msg, I L, int P, int S,
+                                                       uint4 *__restrict__ out, I nvec, int msg_aligned) {
+  const I vpc = (I)(S / 4);  // vectors per chunk
+  const uint4 *msg16 = reinterpret_cast<const uint4 *>(msg);
+  for (I v = (I)blockIdx.x * kAuxThreads + threadIdx.x; v < nvec; v += (I)gridDim.x * kAuxThreads) {
+    const I t = v / vpc;
+    const int b0 = (int)(v - t * vpc) * 16;  // byte offset inside the chunk
+    uint4 r = make_uint4(0, 0, 0, 0);
     if (b0 < P) {
-      const long long o = t * P + b0;
-      const int cnt = (int)min((long long)min(4, P - b0), max(0LL, L - o));
-      for (int i = 0; i < cnt; i++) v |= (uint32_t)__ldg(msg + o + i) << (8 * i);
+      const I o = t * (I)P + (I)b0;
+      const I avail = L > o ? L - o : 0;
+      const int lim = (int)min((I)min(16, P - b0), avail);  // valid bytes of this vector
+      if (lim > 0) {
+        const I a = o >> 4;
+        if (msg_aligned && (a + 2) * 16 <= L) {
+          r = bytes_at(__ldg(msg16 + a), __ldg(msg16 + a + 1), (uint32_t)(o & 15));
+          if (lim < 16) {
+            const uint4 z = make_uint4(0, 0, 0, 0);
+            r = concat_bytes(r, z, (uint32_t)lim);
+          }
+        } else {
+          uint32_t w[4] = {0, 0, 0, 0};
+          for (int i = 0; i < lim; i++) w[i >> 2] |= (uint32_t)__ldg(msg + o + i) << (8 * (i & 3));
+          r = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+      }
     }
-    chunks[w] = v;
+    out[v] = r;
   }
 }
 
 // Join: byte b of the message is byte (b mod P) of chunk b / P.  One thread
-// per 4 output bytes.
+// per 16 message bytes: two aligned 16-byte loads of the chunk and a byte
+// shift give them, and a vector that runs past the chunk's payload takes its
+// remaining bytes from the start of the next chunk.  One 16-byte store writes
+// them; the message tail (or an unaligned output) is written byte by byte.
+template <typename I>
 __global__ void __launch_bounds__(kAuxThreads) k_join(const uint32_t *__restrict__ chunks, int P, int S,
-                                                      uint8_t *__restrict__ msg, long long L) {
-  long long q = (long long)blockIdx.x * kAuxThreads + threadIdx.x;
-  const long long stride = (long long)gridDim.x * kAuxThreads;
-  for (; 4 * q < L; q += stride) {
-    for (int i = 0; i < 4; i++) {
-      const long long b = 4 * q + i;
-      if (b >= L) break;
-      const long long t = b / P;
-      const int k = (int)(b - t * P);
-      msg[b] = (uint8_t)(__ldg(chunks + t * S + k / 4) >> (8 * (k % 4)));
+                                                      uint8_t *__restrict__ msg, I L, int out_aligned) {
+  const I nvec = (L + 15) / 16;
+  const uint4 *c16 = reinterpret_cast<const uint4 *>(chunks);
+  const int vpc = S / 4;
+  for (I u = (I)blockIdx.x * kAuxThreads + threadIdx.x; u < nvec; u += (I)gridDim.x * kAuxThreads) {
+    const I b0 = u * 16;
+    const I t = b0 / (I)P;
+    const int k0 = (int)(b0 - t * (I)P);
+    const int n1 = min(16, P - k0);  // bytes from chunk t
+    uint4 r;
+    {
+      const int a = k0 >> 4;  // aligned vector of chunk t holding byte k0
+      const uint4 lo = __ldg(c16 + t * vpc + a);
+      const uint4 hi = (a + 1 < vpc) ? __ldg(c16 + t * vpc + a + 1) : make_uint4(0, 0, 0, 0);
+      r = bytes_at(lo, hi, (uint32_t)(k0 & 15));
+    }
+    if (n1 < 16 && b0 + n1 < L) {  // continue in chunk t + 1 (it exists: its bytes are in the message)
+      r = concat_bytes(r, __ldg(c16 + (t + 1) * vpc), (uint32_t)n1);
+    }
+    const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+    if (out_aligned && b0 + 16 <= L) {
+      reinterpret_cast<uint4 *>(msg)[u] = r;
+    } else {
+      for (int i = 0; i < 16 && b0 + i < L; i++) msg[b0 + i] = (uint8_t)(w[i >> 2] >> (8 * (i & 3)));
     }
   }
 }
@@ -270,9 +346,17 @@ int configure_smem(const void *fn, size_t bytes);
 
 int launch_split(uint32_t nbits, const uint8_t *msg, size_t len, uint32_t *chunks, size_t n, cudaStream_t st) {
   const int P = (int)(nbits / 8 - 1), S = (int)(nbits / 32);
-  const long long nw = (long long)n * S;
-  if (nw == 0) return PMK_OK;
-  k_split<<<grid_for(nw, kAuxThreads), kAuxThreads, 0, st>>>(msg, (long long)len, P, S, chunks, nw);
+  const long long nvec = (long long)n * (S / 4);
+  if (nvec == 0) return PMK_OK;
+  if (reinterpret_cast<uintptr_t>(chunks) & 15u) return PMK_EINVAL;  // limb buffers are 16-byte aligned
+  const int msg_aligned = (reinterpret_cast<uintptr_t>(msg) & 15u) == 0;
+  const int g = grid_for(nvec, kAuxThreads);
+  uint4 *out = reinterpret_cast<uint4 *>(chunks);
+  if ((long long)len < (1LL << 31) && nvec < (1LL << 31))
+    k_split<uint32_t><<<g, kAuxThreads, 0, st>>>(msg, (uint32_t)len, P, S, out, (uint32_t)nvec, msg_aligned);
+  else
+    k_split<unsigned long long><<<g, kAuxThreads, 0, st>>>(msg, (unsigned long long)len, P, S, out,
+                                                            (unsigned long long)nvec, msg_aligned);
   return cuda_rc(cudaGetLastError());
 }
 
@@ -280,7 +364,13 @@ int launch_join(uint32_t nbits, const uint32_t *chunks, size_t n, uint8_t *msg, 
   (void)n;
   const int P = (int)(nbits / 8 - 1), S = (int)(nbits / 32);
   if (len == 0) return PMK_OK;
-  k_join<<<grid_for(((long long)len + 3) / 4, kAuxThreads), kAuxThreads, 0, st>>>(chunks, P, S, msg, (long long)len);
+  if (reinterpret_cast<uintptr_t>(chunks) & 15u) return PMK_EINVAL;
+  const int out_aligned = (reinterpret_cast<uintptr_t>(msg) & 15u) == 0;
+  const int g = grid_for(((long long)len + 15) / 16, kAuxThreads);
+  if ((long long)len < (1LL << 31))
+    k_join<uint32_t><<<g, kAuxThreads, 0, st>>>(chunks, P, S, msg, (uint32_t)len, out_aligned);
+  else
+    k_join<unsigned long long><<<g, kAuxThreads, 0, st>>>(chunks, P, S, msg, (unsigned long long)len, out_aligned);
   return cuda_rc(cudaGetLastError());
 }
 

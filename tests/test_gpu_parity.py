@@ -70,6 +70,25 @@ def test_split_join_parity(ctx, nbits):
         assert bytes(ctx.join(nbits, ch, L).cpu().numpy()) == msg.tobytes()
 
 
+@pytest.mark.parametrize("off", [1, 3, 4, 8, 15])
+def test_split_join_unaligned_message(ctx, off):
+    """A message (or join output) that starts off a 16-byte boundary takes the
+    byte-wise path and still gives the oracle's chunks."""
+    nbits = 1024
+    rng = np.random.default_rng(off)
+    for L in [5, 127, 128, 1000]:
+        msg = rng.integers(0, 256, L, dtype=np.uint8)
+        base = torch.zeros(L + 16, dtype=torch.uint8, device="cuda")
+        base[off:off + L] = torch.from_numpy(msg).cuda()
+        ch = ctx.split(nbits, base[off:off + L])
+        assert np.array_equal(host(ch), oracle.split(msg, nbits)), (off, L)
+        out = torch.zeros(L + 16, dtype=torch.uint8, device="cuda")
+        ctx.join(nbits, ch, L, out=out[off:off + L])
+        o = out.cpu().numpy()
+        assert bytes(o[off:off + L]) == msg.tobytes()
+        assert not o[:off].any() and not o[off + L:].any()  # nothing written outside the message
+
+
 def test_split_join_empty(ctx, P):
     d_msg = torch.empty(0, dtype=torch.uint8, device="cuda")
     ch = ctx.split(2048, d_msg)
