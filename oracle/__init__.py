@@ -9,8 +9,8 @@ package never does, and this module never imports the product.
 What lives where:
   * ``pmk_oracle.c`` -- schoolbook bignum (Knuth Algorithm D division),
     Algorithm 2 square-and-multiply, the Garner form of the Section 2.1 CRT
-    equations, extended Euclid, the seeded key initialisation of
-    Algorithm 1, and Algorithm 1's blinded encryption / decryption with the
+    equations and its multi-prime extension, extended Euclid, the seeded key
+    initialisation of Algorithm 1 (two primes or b primes), and Algorithm 1's blinded encryption / decryption with the
     random matrix R (see that file's header for the readings it fixes).
   * this file -- ctypes marshalling, plus ``split``/``join`` written
     directly from their definitions (Section 3.1: the message is cut into
@@ -66,6 +66,10 @@ def _load():
                                           P, P, P, P, P, P, P]
             lib.oracle_modexp_chunks.argtypes = [P, P, i, P, i, P, i, ctypes.c_long, ctypes.c_long]
             lib.oracle_crt_chunks.argtypes = [P, P, i, P, P, P, P, P, i, ctypes.c_long, ctypes.c_long]
+            lib.oracle_keygen_mp.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64,
+                                             ctypes.c_uint64, P, P, P, P, P]
+            lib.oracle_crt_mp.argtypes = [P, i, i, P, P, P, P]
+            lib.oracle_crt_mp_chunks.argtypes = [P, P, i, i, P, P, P, i, ctypes.c_long, ctypes.c_long]
             lib.oracle_blind_encrypt_chunks.argtypes = [P, P, P, P, i, P, i, P, i, ctypes.c_long, ctypes.c_long]
             lib.oracle_blind_decrypt_chunks.argtypes = [P, P, P, i, P, i, P, i, ctypes.c_long, ctypes.c_long]
             _lib = lib
@@ -148,15 +152,35 @@ def crt(c: int, dp: int, dq: int, p: int, q: int, qinv: int) -> int:
     return from_limbs(out)
 
 
+def crt_mp(c: int, primes: list, dexps: list, coefs: list) -> int:
+    """Multi-prime CRT decryption of one value (b primes of equal limb count)."""
+    b = len(primes)
+    h = _nlimbs(*primes)
+    cat = lambda vals: np.concatenate([to_limbs(v, h) for v in vals])
+    out = np.zeros(b * h, np.uint32)
+    R, D, C = cat(primes), cat(dexps), cat(coefs)
+    rc = _load().oracle_crt_mp(_ptr(to_limbs(c, b * h)), b, h, _ptr(R), _ptr(D), _ptr(C), _ptr(out))
+    if rc:
+        raise ValueError(f"oracle_crt_mp rc={rc}")
+    return from_limbs(out)
+
+
 # ---------------------------------------------------------------- keys
 
 class OracleKeys:
-    """K key pairs as limb arrays (key-major) and as Python ints."""
+    """K key pairs as limb arrays (key-major) and as Python ints.  Multi-prime
+    keys (b > 2) hold 'primes', 'dexp' and 'coef' as (K, b * nbits/(32 b))."""
 
-    def __init__(self, K: int, nbits: int, e: int, arrays: dict):
-        self.K, self.nbits, self.e = K, nbits, e
+    def __init__(self, K: int, nbits: int, e: int, arrays: dict, b: int = 2):
+        self.K, self.nbits, self.e, self.b = K, nbits, e, b
         self.s = nbits // 32
         self.a = arrays  # name -> (K, limbs) uint32
+
+    def prime_list(self, k: int, name: str = "primes") -> list[int]:
+        """The b values of `name` (primes, dexp or coef) of key k."""
+        h = self.s // self.b
+        row = self.a[name][k]
+        return [from_limbs(row[i * h:(i + 1) * h]) for i in range(self.b)]
 
     def ints(self, name: str) -> list[int]:
         return [from_limbs(row) for row in self.a[name]]
@@ -175,6 +199,17 @@ def keygen(K: int, nbits: int, e: int = 65537, seed: int = 0) -> OracleKeys:
     if rc:
         raise ValueError(f"oracle_keygen rc={rc}")
     return OracleKeys(K, nbits, e, arrs)
+
+
+def keygen_mp(K: int, nbits: int, b: int, e: int = 65537, seed: int = 0) -> OracleKeys:
+    """Multi-prime key initialisation (Section 2.1): b primes of nbits / b bits per key."""
+    s = nbits // 32
+    arrs = {n: np.zeros((K, s), np.uint32) for n in ("N", "d", "primes", "dexp", "coef")}
+    rc = _load().oracle_keygen_mp(K, nbits, b, e, seed & (2**64 - 1),
+                                  *[_ptr(arrs[n]) for n in ("N", "d", "primes", "dexp", "coef")])
+    if rc:
+        raise ValueError(f"oracle_keygen_mp rc={rc}")
+    return OracleKeys(K, nbits, e, arrs, b)
 
 
 # ---------------------------------------------------------------- split / join
@@ -254,6 +289,8 @@ def encrypt_chunks(chunks: np.ndarray, keys: OracleKeys, threads: int = 1) -> np
 def decrypt_chunks(chunks: np.ndarray, keys: OracleKeys, use_crt: bool = False, threads: int = 1) -> np.ndarray:
     if not use_crt:
         return modexp_chunks(chunks, keys.a["d"], keys.a["N"], threads)
+    if "primes" in keys.a:
+        return _decrypt_crt_mp(chunks, keys, threads)
     c = np.ascontiguousarray(chunks, dtype=np.uint32)
     n, s = c.shape
     out = np.zeros_like(c)
@@ -265,6 +302,23 @@ def decrypt_chunks(chunks: np.ndarray, keys: OracleKeys, use_crt: bool = False, 
                                    _ptr(A["qinv"]), keys.K, a, b)
         if rc:
             raise ValueError(f"oracle_crt_chunks rc={rc}")
+
+    _run(work, n, threads)
+    return out
+
+
+def _decrypt_crt_mp(chunks: np.ndarray, keys: OracleKeys, threads: int) -> np.ndarray:
+    c = np.ascontiguousarray(chunks, dtype=np.uint32)
+    n, s = c.shape
+    out = np.zeros_like(c)
+    lib = _load()
+    A = {k: np.ascontiguousarray(keys.a[k]) for k in ("primes", "dexp", "coef")}
+
+    def work(a, b):
+        rc = lib.oracle_crt_mp_chunks(_ptr(c), _ptr(out), s, keys.b, _ptr(A["primes"]), _ptr(A["dexp"]),
+                                      _ptr(A["coef"]), keys.K, a, b)
+        if rc:
+            raise ValueError(f"oracle_crt_mp_chunks rc={rc}")
 
     _run(work, n, threads)
     return out

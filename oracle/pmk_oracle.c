@@ -17,6 +17,11 @@
  *   oracle_keygen      Section 1.1 key initialisation and Algorithm 1
  *                      "Initialization": p != q of n/2 bits, N = pq,
  *                      phi = (p-1)(q-1), d = e^-1 mod phi (extended Euclid).
+ *   oracle_keygen_mp   Section 2.1, multi-prime RSA: b distinct primes of
+ *                      n/b bits, N their product, phi = prod (r_i - 1).
+ *   oracle_crt_mp      multi-prime CRT decryption: the CRT-RSA equation for
+ *                      the first two primes, extended one prime at a time
+ *                      (Garner's mixed-radix recombination).
  *   oracle_*_chunks    Algorithm 1 "Encryption"/"Decryption" loops: chunk t
  *                      is bound to key t mod K (row-per-key reshape, Sec. 3.1).
  *   oracle_blind_*     Algorithm 1 with the random matrix R (Sec. 3.1):
@@ -361,8 +366,11 @@ static int mr_round(const limb_t *n, int h, uint64_t base) {
   return pass;
 }
 
-/* draw a prime of exactly `bits` bits (bits a multiple of 64) into p[0..bits/32) */
-static void gen_prime(uint64_t *rng, int bits, uint64_t e, const int *small, int nsmall, limb_t *p) {
+/*
+ * draw a prime of exactly `bits` bits (bits a multiple of 64) into p[0..bits/32),
+ * whose top byte is at least min_top (>= 192: the top two bits are always set)
+ */
+static void gen_prime(uint64_t *rng, int bits, uint64_t e, const int *small, int nsmall, int min_top, limb_t *p) {
   int h = bits / 32;
   limb_t *em1 = calloc((size_t)h, 4), *one = calloc((size_t)h, 4);
   limb_t ev[2] = {(limb_t)e, (limb_t)(e >> 32)};
@@ -376,6 +384,7 @@ static void gen_prime(uint64_t *rng, int bits, uint64_t e, const int *small, int
     }
     p[h - 1] |= 0xC0000000u; /* exactly `bits` bits, top two set */
     p[0] |= 1u;
+    if ((int)(p[h - 1] >> 24) < min_top) continue;
     int composite = 0;
     for (int i = 0; i < nsmall && !composite; i++) {
       limb_t sp = (limb_t)small[i], r1[1];
@@ -396,6 +405,83 @@ static void gen_prime(uint64_t *rng, int bits, uint64_t e, const int *small, int
   }
   free(em1);
   free(one);
+}
+
+/* the odd primes below 2000, by trial division; returns their count */
+static int small_primes(int *small) {
+  int nsmall = 0;
+  for (int c = 3; c < 2000; c += 2) {
+    int pr = 1;
+    for (int f = 3; f * f <= c; f += 2)
+      if (c % f == 0) { pr = 0; break; }
+    if (pr) small[nsmall++] = c;
+  }
+  return nsmall;
+}
+
+/*
+ * The least top byte T (at least 192) with T^b >= 2^(8b - 1): b primes of k
+ * bits whose top bytes are all >= T have a product of at least
+ * (T / 256)^b 2^(bk) >= 2^(bk - 1), so the modulus has exactly bk bits.
+ */
+static int mp_top_floor(int b) {
+  const uint64_t need = 1ull << (8 * b - 1);
+  int t = 1;
+  for (;; t++) {
+    uint64_t v = 1;
+    for (int i = 0; i < b; i++) v *= (uint64_t)t;
+    if (v >= need) break;
+  }
+  return t < 192 ? 192 : t;
+}
+
+/*
+ * Multi-prime CRT decryption of one chunk (Section 2.1, multi-prime RSA),
+ * b primes r_0 .. r_{b-1} of h limbs each, c and out of b h limbs:
+ *   m_i = c^{d_i} mod r_i  (d_i = d mod (r_i - 1));
+ *   the first recombination is the CRT-RSA equation with p = r_0, q = r_1:
+ *     x = coef_0 (m_0 - m_1) mod r_0  (coef_0 = r_1^-1 mod r_0),  m = m_1 + x r_1;
+ *   each further prime r_i extends it the same way over the product
+ *   P_i = r_0 ... r_{i-1} of the primes already combined:
+ *     x = coef_i (m_i - m) mod r_i  (coef_i = P_i^-1 mod r_i),  m = m + x P_i.
+ * m stays below the product of the primes combined so far (Garner's
+ * mixed-radix form); after the last prime it is c^d mod N.
+ */
+static int crt_mp(const limb_t *c, int b, int h, const limb_t *r, const limb_t *dexp, const limb_t *coef,
+                  limb_t *out) {
+  const int s = b * h;
+  limb_t *mi = calloc((size_t)s, 4), *m = calloc((size_t)s, 4), *P = calloc((size_t)s, 4);
+  limb_t *x = calloc((size_t)h, 4), *diff = calloc((size_t)h, 4), *xr = calloc((size_t)(s + h), 4);
+  limb_t *tmp = calloc((size_t)(s + h), 4);
+  int rc = 0;
+  for (int i = 0; i < b && !rc; i++) rc = modexp(c, s, dexp + (size_t)i * h, h, r + (size_t)i * h, h, mi + (size_t)i * h);
+  if (!rc) {
+    /* the running value starts at m_1, its product at r_1; then r_0, r_2, r_3, ... */
+    bn_copy(m, s, mi + h, h);
+    bn_copy(P, s, r + h, h);
+    int len = h;
+    for (int step = 0; step < b - 1; step++) {
+      const int i = step == 0 ? 0 : step + 1;
+      const limb_t *ri = r + (size_t)i * h, *m_i = mi + (size_t)i * h;
+      bn_divmod(m, len, ri, h, NULL, 0, x, h);           /* m mod r_i */
+      if (bn_cmp(m_i, h, x, h) >= 0) {
+        bn_sub_n(diff, m_i, x, h);
+      } else {                                           /* m_i - m + r_i */
+        bn_sub_n(diff, ri, x, h);
+        bn_add_n(diff, diff, m_i, h);
+      }
+      bn_mulmod(diff, coef + (size_t)i * h, ri, h, x);   /* x = coef_i (m_i - m) mod r_i */
+      bn_mul(P, len, x, h, xr);                          /* x P_i */
+      bn_copy(tmp, len + h, m, len);
+      bn_add_n(m, tmp, xr, len + h);                     /* m + x P_i  (< P_i r_i, no carry) */
+      bn_mul(P, len, ri, h, tmp);                        /* P_{i+1} = P_i r_i */
+      bn_copy(P, s, tmp, len + h);
+      len += h;
+    }
+    bn_copy(out, s, m, s);
+  }
+  free(mi); free(m); free(P); free(x); free(diff); free(xr); free(tmp);
+  return rc;
 }
 
 /* ------------------------------------------------------------------ */
@@ -434,13 +520,8 @@ int oracle_keygen(uint32_t K, uint32_t nbits, uint64_t e, uint64_t seed, uint32_
                   uint32_t *p, uint32_t *q, uint32_t *dp, uint32_t *dq, uint32_t *qinv) {
   if (K == 0 || nbits < 128 || nbits % 128 != 0 || e < 3 || !(e & 1)) return -1;
   int s = (int)nbits / 32, h = s / 2;
-  int small[400], nsmall = 0;
-  for (int c = 3; c < 2000; c += 2) { /* odd primes below 2000 by trial division */
-    int pr = 1;
-    for (int f = 3; f * f <= c; f += 2)
-      if (c % f == 0) { pr = 0; break; }
-    if (pr) small[nsmall++] = c;
-  }
+  int small[400];
+  int nsmall = small_primes(small);
   uint64_t master = seed;
   limb_t *one = calloc((size_t)h, 4), *pm1 = calloc((size_t)h, 4), *qm1 = calloc((size_t)h, 4);
   limb_t *phi = calloc((size_t)s, 4), *ew = calloc((size_t)s, 4);
@@ -450,9 +531,9 @@ int oracle_keygen(uint32_t K, uint32_t nbits, uint64_t e, uint64_t seed, uint32_
   for (uint32_t k = 0; k < K; k++) {
     limb_t *pk = p + (size_t)k * h, *qk = q + (size_t)k * h;
     uint64_t rng = splitmix64(&master);   /* this key's own stream */
-    gen_prime(&rng, (int)nbits / 2, e, small, nsmall, pk);
+    gen_prime(&rng, (int)nbits / 2, e, small, nsmall, 192, pk);
     do {
-      gen_prime(&rng, (int)nbits / 2, e, small, nsmall, qk);
+      gen_prime(&rng, (int)nbits / 2, e, small, nsmall, 192, qk);
     } while (bn_cmp(pk, h, qk, h) == 0);
     bn_mul(pk, h, qk, h, N + (size_t)k * s);                 /* N = p q */
     bn_sub_n(pm1, pk, one, h);
@@ -488,6 +569,96 @@ int oracle_crt_chunks(const uint32_t *in, uint32_t *out, int s, const uint32_t *
   for (long t = t0; t < t1; t++) {
     size_t k = (size_t)(t % K);
     int rc = crt(in + (size_t)t * s, dp + k * h, dq + k * h, p + k * h, q + k * h, qinv + k * h, h, out + (size_t)t * s);
+    if (rc) return rc;
+  }
+  return 0;
+}
+
+/*
+ * Multi-prime key pairs (Section 2.1, multi-prime RSA): K keys of nbits with
+ * b in [2, 4] distinct primes of nbits / b bits each (nbits a multiple of 128
+ * and of 64 b).  Key k draws r_0, r_1, ... in order from its own stream as in
+ * oracle_keygen; every prime's top byte is at least mp_top_floor(b), so N
+ * has exactly nbits bits, and r_i is redrawn while it equals an earlier prime.
+ * For b = 2 this is oracle_keygen's key (p = r_0, q = r_1).  Outputs, key-major:
+ *   N, d: K x nbits/32 limbs;  primes, dexp, coef: K x b x nbits/(32 b) limbs,
+ *   dexp_i = d mod (r_i - 1), coef_0 = r_1^-1 mod r_0, coef_1 = 0,
+ *   coef_i = (r_0 ... r_{i-1})^-1 mod r_i for i >= 2.
+ */
+int oracle_keygen_mp(uint32_t K, uint32_t nbits, uint32_t b, uint64_t e, uint64_t seed, uint32_t *N, uint32_t *d,
+                     uint32_t *primes, uint32_t *dexp, uint32_t *coef) {
+  if (K == 0 || b < 2 || b > 4 || nbits < 128 || nbits % 128 || nbits % (64 * b) || e < 3 || !(e & 1)) return -1;
+  const int s = (int)nbits / 32, h = s / (int)b, top = mp_top_floor((int)b);
+  int small[400];
+  int nsmall = small_primes(small);
+  uint64_t master = seed;
+  limb_t *phi = calloc((size_t)s, 4), *ew = calloc((size_t)s, 4), *acc = calloc((size_t)s, 4);
+  limb_t *tmp = calloc((size_t)s, 4), *rm1 = calloc((size_t)h, 4), *one = calloc((size_t)h, 4);
+  limb_t *x = calloc((size_t)h, 4);
+  int rc = 0;
+  one[0] = 1;
+  ew[0] = (limb_t)e;
+  ew[1] = (limb_t)(e >> 32);
+  for (uint32_t k = 0; k < K && !rc; k++) {
+    limb_t *r = primes + (size_t)k * s, *Nk = N + (size_t)k * s, *dk = d + (size_t)k * s;
+    uint64_t rng = splitmix64(&master);
+    for (uint32_t i = 0; i < b; i++) {
+      int dup;
+      do {
+        gen_prime(&rng, (int)nbits / (int)b, e, small, nsmall, top, r + (size_t)i * h);
+        dup = 0;
+        for (uint32_t j = 0; j < i; j++)
+          if (bn_cmp(r + (size_t)j * h, h, r + (size_t)i * h, h) == 0) dup = 1;
+      } while (dup);
+    }
+    /* N = r_0 ... r_{b-1},  phi = (r_0 - 1) ... (r_{b-1} - 1) */
+    bn_copy(Nk, s, r, h);
+    bn_sub_n(rm1, r, one, h);
+    bn_copy(phi, s, rm1, h);
+    for (uint32_t i = 1; i < b; i++) {
+      bn_mul(Nk, (int)i * h, r + (size_t)i * h, h, tmp);
+      bn_copy(Nk, s, tmp, (int)(i + 1) * h);
+      bn_sub_n(rm1, r + (size_t)i * h, one, h);
+      bn_mul(phi, (int)i * h, rm1, h, tmp);
+      bn_copy(phi, s, tmp, (int)(i + 1) * h);
+    }
+    if (bn_modinv(ew, phi, s, dk)) { rc = -2; break; }           /* d = e^-1 mod phi */
+    for (uint32_t i = 0; i < b; i++) {
+      bn_sub_n(rm1, r + (size_t)i * h, one, h);
+      bn_divmod(dk, s, rm1, h, NULL, 0, dexp + (size_t)k * s + (size_t)i * h, h);  /* d mod (r_i - 1) */
+    }
+    limb_t *ck = coef + (size_t)k * s;
+    bn_zero(ck, s);
+    if (bn_modinv(r + h, r, h, ck)) { rc = -2; break; }          /* r_1^-1 mod r_0 */
+    bn_copy(acc, s, r, h);                                        /* acc = r_0 r_1 ... r_{i-1} */
+    for (uint32_t i = 1; i < b; i++) {
+      if (i >= 2) {
+        bn_divmod(acc, (int)i * h, r + (size_t)i * h, h, NULL, 0, x, h);
+        if (bn_modinv(x, r + (size_t)i * h, h, ck + (size_t)i * h)) { rc = -2; break; }
+      }
+      bn_mul(acc, (int)i * h, r + (size_t)i * h, h, tmp);
+      bn_copy(acc, s, tmp, (int)(i + 1) * h);
+    }
+  }
+  free(phi); free(ew); free(acc); free(tmp); free(rm1); free(one); free(x);
+  return rc;
+}
+
+/* multi-prime CRT decryption of one value: b primes of h limbs, c and out of b h limbs */
+int oracle_crt_mp(const uint32_t *c, int b, int h, const uint32_t *primes, const uint32_t *dexp, const uint32_t *coef,
+                  uint32_t *out) {
+  if (b < 2 || h <= 0) return -1;
+  return crt_mp(c, b, h, primes, dexp, coef, out);
+}
+
+/* multi-prime CRT decryption of chunks [t0, t1), key t mod K; key arrays K x b h limbs */
+int oracle_crt_mp_chunks(const uint32_t *in, uint32_t *out, int s, int b, const uint32_t *primes,
+                         const uint32_t *dexp, const uint32_t *coef, int K, long t0, long t1) {
+  if (b < 2 || s % b) return -1;
+  const int h = s / b;
+  for (long t = t0; t < t1; t++) {
+    size_t k = (size_t)(t % K);
+    int rc = crt_mp(in + (size_t)t * s, b, h, primes + k * s, dexp + k * s, coef + k * s, out + (size_t)t * s);
     if (rc) return rc;
   }
   return 0;

@@ -187,6 +187,79 @@ def test_crt_matches_full_exponent():
             assert oracle.crt(c, kd["dp"], kd["dq"], kd["p"], kd["q"], kd["qinv"]) == full
 
 
+# ---------------------------------------------------------------- multi-prime RSA (Section 2.1)
+
+def _mp_key_from_primes(primes, e):
+    """Key material of the multi-prime reading, computed with Python ints."""
+    N = math.prod(primes)
+    d = pow(e, -1, math.prod(r - 1 for r in primes))
+    dexp = [d % (r - 1) for r in primes]
+    coef = [pow(primes[1], -1, primes[0]), 0] + [pow(math.prod(primes[:i]), -1, primes[i]) for i in range(2, len(primes))]
+    return N, d, dexp, coef
+
+
+@pytest.mark.parametrize("primes,e", [((5, 7, 11), 7), ((11, 5, 7), 7), ((13, 3, 7, 11), 7), ((7, 11, 3, 5), 7),
+                                      ((61, 53), 17)])
+def test_crt_mp_bruteforce_tiny(primes, e):
+    """Every message of tiny 2-, 3- and 4-prime moduli: the CRT recombination
+    gives c^d mod N (Python pow) and inverts encryption (the RSA round trip)."""
+    N, d, dexp, coef = _mp_key_from_primes(list(primes), e)
+    for m in range(N):
+        c = pow(m, e, N)
+        assert oracle.crt_mp(c, list(primes), dexp, coef) == m
+        assert oracle.crt_mp(m, list(primes), dexp, coef) == pow(m, d, N)
+
+
+@pytest.mark.parametrize("nbits,b,K", [(384, 3, 3), (512, 4, 2), (768, 3, 2), (1024, 4, 1)])
+def test_keygen_mp_properties(nbits, b, K):
+    sympy = pytest.importorskip("sympy")
+    keys = oracle.keygen_mp(K, nbits, b, 65537, seed=4321 + nbits + b)
+    for k in range(K):
+        r = keys.prime_list(k)
+        N, d = oracle.from_limbs(keys.a["N"][k]), oracle.from_limbs(keys.a["d"][k])
+        assert len(set(r)) == b
+        for f in r:
+            assert sympy.isprime(f) and f.bit_length() == nbits // b and math.gcd(65537, f - 1) == 1
+        assert N == math.prod(r) and N.bit_length() == nbits
+        N2, d2, dexp, coef = _mp_key_from_primes(r, 65537)
+        assert d == d2
+        assert keys.prime_list(k, "dexp") == dexp
+        assert keys.prime_list(k, "coef") == coef
+    again = oracle.keygen_mp(K, nbits, b, 65537, seed=4321 + nbits + b)
+    assert all(np.array_equal(again.a[n], keys.a[n]) for n in keys.a)
+
+
+def test_keygen_mp_two_primes_is_the_two_prime_key():
+    two = oracle.keygen(3, 512, 65537, seed=31)
+    mp = oracle.keygen_mp(3, 512, 2, 65537, seed=31)
+    for k in range(3):
+        kd = two.key(k)
+        assert mp.prime_list(k) == [kd["p"], kd["q"]]
+        assert mp.prime_list(k, "dexp") == [kd["dp"], kd["dq"]]
+        assert mp.prime_list(k, "coef")[0] == kd["qinv"]
+        assert oracle.from_limbs(mp.a["N"][k]) == kd["N"] and oracle.from_limbs(mp.a["d"][k]) == kd["d"]
+
+
+def test_keygen_mp_argument_errors():
+    for args in [(1, 768, 5), (1, 768, 1), (1, 512, 3), (1, 640, 4), (0, 768, 3)]:
+        with pytest.raises(ValueError):
+            oracle.keygen_mp(*args)
+
+
+@pytest.mark.parametrize("nbits,b", [(768, 3), (1024, 4), (1536, 3)])
+def test_crt_mp_matches_full_exponent(nbits, b):
+    keys = oracle.keygen_mp(1, nbits, b, 65537, seed=17 + b)
+    r = keys.prime_list(0)
+    N, d = oracle.from_limbs(keys.a["N"][0]), oracle.from_limbs(keys.a["d"][0])
+    rnd = random.Random(b)
+    cs = [rnd.randrange(N) for _ in range(8)] + [0, 1, N - 1] + [f * 3 for f in r] + [N // r[0]]
+    for c in cs:
+        assert oracle.crt_mp(c, r, keys.prime_list(0, "dexp"), keys.prime_list(0, "coef")) == pow(c, d, N)
+    s = nbits // 32
+    m = np.stack([oracle.to_limbs(rnd.randrange(N), s) for _ in range(5)])
+    assert np.array_equal(oracle.decrypt_chunks(m, keys, use_crt=True), oracle.decrypt_chunks(m, keys))
+
+
 def test_chunk_loops_bind_key_t_mod_K():
     keys = oracle.keygen(3, 256, 65537, seed=5)
     r = random.Random(2)
