@@ -646,6 +646,63 @@ def run_hbm(args):
     return 0
 
 
+MULTIPRIME_CASES = [(2048, 2), (2048, 4), (3072, 2), (3072, 3), (4096, 2), (4096, 4), (6144, 2), (6144, 3),
+                    (6144, 4), (8192, 2), (8192, 4)]
+
+
+def run_multiprime(args):
+    """Multi-prime RSA (Section 2.1): CRT decryption of a 1 MiB random message
+    with K = 8 keys at each (key bits, primes) pair, next to two-prime CRT at
+    the same width.  The paper's cost model puts b primes at b^2 / 4 times
+    the speed of two.  One JSON line per pair; every output is checked equal
+    to the message's chunks."""
+    import torch
+
+    import paper_2111_11924_gb300 as P
+
+    ctx = P.Context(0)
+    msg = torch.from_numpy(W.FILE_1MIB_2048.message()).cuda()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # larger than L2
+    two_prime_ms = {}
+    for nbits, b in args.mp_list:
+        ks = ctx.keygen(8, nbits, 65537, W.KEY_SEED_BASE + 0x200 + nbits + b, nprimes=b)
+        chunks = ctx.split(nbits, msg)
+        n = chunks.shape[0]
+        cipher = ctx.encrypt_chunks(ks, chunks)
+        out = torch.empty_like(chunks)
+        tuned = ctx.autotune(ks, n, "crt", reps=2)
+        for _ in range(args.warmup):
+            ctx.decrypt_chunks(ks, cipher, use_crt=True, out=out)
+        torch.cuda.synchronize()
+        assert torch.equal(out, chunks)
+        ts = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ctx.decrypt_chunks(ks, cipher, use_crt=True, out=out)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        assert torch.equal(out, chunks)
+        ctx.check()
+        ms = statistics.median(ts)
+        if b == 2:
+            two_prime_ms[nbits] = ms
+        base = two_prime_ms.get(nbits)
+        print(json.dumps({"mode": "multiprime", "workload": f"pmkrsa-1MiB-K8-{nbits}bit-{b}primes", "key_bits": nbits,
+                          "primes": b, "chunks": n, "crt_decrypt_ms": round(ms, 4),
+                          "chunk_modexps_per_s": round(n / (ms / 1e3)),
+                          "speedup_vs_two_primes": round(base / ms, 3) if base else None,
+                          "model_b2_over_4": b * b / 4,
+                          "geometry": (tuned["tpi"], ["chain", "columns"][tuned["form"]]),
+                          "timing": "CUDA events around one pmk_decrypt_chunks call (range check, one "
+                                    "exponentiation per prime, recombination); L2 flushed between calls"}))
+        ctx.set_kernel_config(nbits // 32 // b, True, 0)
+        ks.free()
+    return 0
+
+
 def _measured_peaks() -> dict:
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -675,6 +732,10 @@ def main(argv=None):
     ap.add_argument("--widths", action="store_true",
                     help="time the 100 KB / K=16 workload at each key length and exit")
     ap.add_argument("--width-list", type=int, nargs="*", default=[1024, 2048, 3072, 4096, 6144, 8192])
+    ap.add_argument("--multiprime", action="store_true",
+                    help="time multi-prime CRT decryption (1 MiB, K = 8) against two primes and exit")
+    ap.add_argument("--mp-list", type=lambda v: tuple(int(x) for x in v.split(":")), nargs="*",
+                    default=MULTIPRIME_CASES, help="bits:primes pairs for --multiprime")
     ap.add_argument("--profile-mib", type=int, default=0,
                     help="with --profile: message size in MiB instead of the 1 MiB workload")
     args = ap.parse_args(argv)
@@ -690,6 +751,8 @@ def main(argv=None):
         return run_serving(args)
     if args.hbm:
         return run_hbm(args)
+    if args.multiprime:
+        return run_multiprime(args)
     return run_reference(args) if args.impl == "reference" else run_ours(args)
 
 

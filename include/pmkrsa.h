@@ -58,10 +58,37 @@ void pmk_ctx_destroy(pmk_ctx *ctx);
  * `seed`; candidates pass trial division by the odd primes below 2000,
  * gcd(e, p-1) = 1 and 40 Miller-Rabin rounds with bases (splitmix64()>>1)+2.
  * Runs on the host; then uploads the key tables to the context's device.
+ *   K: 1..16383 keys.
  *   nbits: 128..8192, a multiple of 128 (EUNSUPPORTED if not built).
  *   e: odd, 3 <= e < 2^32.
  */
 int pmk_keygen(pmk_ctx *ctx, uint32_t K, uint32_t nbits, uint64_t e, uint64_t seed, pmk_keyset **out);
+
+/*
+ * Multi-prime key initialisation (Section 2.1, multi-prime RSA): each key
+ * has nprimes distinct primes r_0 .. r_{b-1} of exactly nbits/nprimes bits,
+ * N = r_0 ... r_{b-1} of exactly nbits bits, d = e^-1 mod prod (r_i - 1).
+ * Key k draws r_0, r_1, ... in order from its own SplitMix64 stream exactly
+ * as pmk_keygen draws p and q; a candidate is also redrawn while its top
+ * byte is below the least T with T^b >= 2^(8b - 1), and a prime equal to an
+ * earlier one is redrawn.  nprimes = 2 gives pmk_keygen's keys.
+ * pmk_decrypt_chunks with use_crt then computes one residue per prime and
+ * recombines them (the CRT-RSA equation of Section 2.1 for r_0, r_1,
+ * extended one prime at a time); encryption and full-d decryption are
+ * unchanged.
+ *   nprimes: 2..4;  nbits: a multiple of 128 and of 64 nprimes, <= 8192
+ *   (EINVAL otherwise; EUNSUPPORTED if nbits/(32 nprimes) limbs are not built).
+ */
+int pmk_keygen_multiprime(pmk_ctx *ctx, uint32_t K, uint32_t nbits, uint32_t nprimes, uint64_t e, uint64_t seed,
+                          pmk_keyset **out);
+
+/*
+ * pmk_keygen_multiprime on the host only, with the output layout of
+ * pmk_keyset_export (N, d) and pmk_keyset_export_primes (primes, dexp,
+ * coef).  Any output pointer may be NULL.
+ */
+int pmk_keygen_host_multiprime(uint32_t K, uint32_t nbits, uint32_t nprimes, uint64_t e, uint64_t seed, uint32_t *N,
+                               uint32_t *d, uint32_t *primes, uint32_t *dexp, uint32_t *coef);
 
 /*
  * The same key initialisation as pmk_keygen, on the host only (no device,
@@ -81,9 +108,17 @@ int pmk_keyset_from_primes(pmk_ctx *ctx, uint32_t K, uint32_t nbits, uint64_t e,
                            const uint32_t *q, pmk_keyset **out);
 
 /* Copy the key material out (host arrays, key-major, little-endian limbs):
- * N, d: K x nbits/32;  p, q, dp, dq, qinv: K x nbits/64.  Any pointer may be NULL. */
+ * N, d: K x nbits/32;  p, q, dp, dq, qinv: K x nbits/64.  Any pointer may be
+ * NULL.  For a key set with more than two primes p .. qinv must be NULL
+ * (EINVAL): use pmk_keyset_export_primes. */
 int pmk_keyset_export(const pmk_keyset *ks, uint32_t *N, uint32_t *d, uint32_t *p, uint32_t *q, uint32_t *dp,
                       uint32_t *dq, uint32_t *qinv);
+/* The primes of every key and their CRT values, K x b x nbits/(32 b) limbs
+ * each (b = pmk_keyset_num_primes): primes r_i, dexp_i = d mod (r_i - 1),
+ * coef_0 = r_1^-1 mod r_0, coef_1 = 0, coef_i = (r_0 ... r_{i-1})^-1 mod r_i.
+ * Any pointer may be NULL. */
+int pmk_keyset_export_primes(const pmk_keyset *ks, uint32_t *primes, uint32_t *dexp, uint32_t *coef);
+uint32_t pmk_keyset_num_primes(const pmk_keyset *ks);
 uint32_t pmk_keyset_num_keys(const pmk_keyset *ks);
 uint32_t pmk_keyset_nbits(const pmk_keyset *ks);
 uint64_t pmk_keyset_e(const pmk_keyset *ks);
@@ -124,8 +159,9 @@ int pmk_encrypt_chunks(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_in,
  * Decryption (Algorithm 1 "Decryption", m = c^d mod N):
  * d_out[t] = d_in[t]^{d_k} mod N_k, k = t mod K.  use_crt = 0: one
  * full-width exponentiation; use_crt = 1: the CRT form of Section 2.1
- * (two half-width exponentiations and Garner's recombination), bit-identical.
- * With use_crt = 1, d_in and d_out must not overlap.
+ * (one exponentiation per prime over nbits/b bits -- two halves for an
+ * ordinary key, b for a multi-prime key -- and Garner's recombination),
+ * bit-identical.  With use_crt = 1, d_in and d_out must not overlap.
  */
 int pmk_decrypt_chunks(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_in, uint32_t *d_out,
                        size_t n_chunks, int use_crt, void *stream);

@@ -15,6 +15,7 @@ from .pmkrsa import (  # noqa: F401
     Context,
     KeySet,
     keygen_host,
+    keygen_host_multiprime,
     kernel_configs,
     load_library,
     num_chunks,
@@ -22,4 +23,4 @@ from .pmkrsa import (  # noqa: F401
     strerror,
 )
 
-__all__ = ["PMKError", "Context", "KeySet", "keygen_host", "kernel_configs", "load_library", "num_chunks", "payload_bytes", "strerror"]
+__all__ = ["PMKError", "Context", "KeySet", "keygen_host", "keygen_host_multiprime", "kernel_configs", "load_library", "num_chunks", "payload_bytes", "strerror"]

@@ -65,7 +65,8 @@ size_t push(std::vector<uint32_t> &blob, const std::vector<uint32_t> &v) {
 int upload(pmk_keyset *ks) {
   std::vector<uint32_t> blob;
   struct Offs {
-    size_t N, R2, se, sd, P[2], R2h[2], R3h[2], sh[2], shi[2], qm, el, dl;
+    size_t N, R2, se, sd, P[pmk::kMaxPrimes], R2h[pmk::kMaxPrimes], R3h[pmk::kMaxPrimes], sh[pmk::kMaxPrimes],
+        shi[pmk::kMaxPrimes], cf[pmk::kMaxPrimes], pf[pmk::kMaxPrimes], qm, el, dl;
   };
   std::vector<Offs> offs(ks->K);
   for (uint32_t k = 0; k < ks->K; k++) {
@@ -75,13 +76,14 @@ int upload(pmk_keyset *ks) {
     o.R2 = push(blob, h.R2);
     o.se = push(blob, h.sched_e.steps);
     o.sd = push(blob, h.sched_d.steps);
-    o.P[0] = push(blob, h.p);
-    o.P[1] = push(blob, h.q);
-    for (int i = 0; i < 2; i++) {
+    for (uint32_t i = 0; i < h.nprimes; i++) {
+      o.P[i] = push(blob, h.pr[i]);
       o.R2h[i] = push(blob, h.R2h[i]);
       o.R3h[i] = push(blob, h.R3h[i]);
       o.sh[i] = push(blob, h.sched_h[i].steps);
       o.shi[i] = push(blob, h.sched_hinv[i].steps);
+      o.cf[i] = push(blob, h.coef[i]);
+      o.pf[i] = push(blob, h.prefix[i]);
     }
     o.qm = push(blob, h.qinv_m);
     o.el = push(blob, {(uint32_t)ks->e, (uint32_t)(ks->e >> 32)});
@@ -107,7 +109,14 @@ int upload(pmk_keyset *ks) {
     d.nsteps_d = (uint32_t)h.sched_d.steps.size();
     d.maxidx_e = h.sched_e.maxidx;
     d.maxidx_d = h.sched_d.maxidx;
-    for (int i = 0; i < 2; i++) {
+    d.nprimes = h.nprimes;
+    for (int i = 0; i < pmk::kMaxPrimes; i++) {
+      d.P[i] = d.R2h[i] = d.R3h[i] = d.sched_h[i] = d.sched_hinv[i] = d.coef[i] = d.prefix[i] = nullptr;
+      d.n0h[i] = d.nsteps_h[i] = d.maxidx_h[i] = d.nsteps_hinv[i] = d.maxidx_hinv[i] = 0;
+    }
+    for (uint32_t i = 0; i < h.nprimes; i++) {
+      d.coef[i] = b + o.cf[i];
+      d.prefix[i] = b + o.pf[i];
       d.P[i] = b + o.P[i];
       d.R2h[i] = b + o.R2h[i];
       d.R3h[i] = b + o.R3h[i];
@@ -137,9 +146,12 @@ int finish_keyset(pmk_ctx *ctx, pmk_keyset *ks, pmk_keyset **out) {
   return PMK_OK;
 }
 
-bool width_built(uint32_t nbits) {
-  return pmk::default_config(nbits / 32, false).tpi != 0 && pmk::default_config(nbits / 64, true).tpi != 0;
+bool width_built(uint32_t nbits, uint32_t nprimes = 2) {
+  return pmk::default_config(nbits / 32, false).tpi != 0 && pmk::default_config(nbits / (32 * nprimes), true).tpi != 0;
 }
+
+// Most keys per key set: the CRT grid has one row per (key, prime) pair.
+constexpr uint32_t kMaxKeys = 65535 / pmk::kMaxPrimes;
 
 int check_chunk_call(const pmk_ctx *ctx, const pmk_keyset *ks, const void *in, const void *out) {
   if (!ctx || !ks) return PMK_EINVAL;
@@ -155,16 +167,24 @@ int enqueue_encrypt(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *in, uint
   return rc;
 }
 
+// One residue per prime of each chunk (exponent d mod (r_i - 1), or r_i - 2
+// for kCrtInverse) into out, then their recombination in place.
+int enqueue_crt(pmk_ctx *ctx, const pmk_keyset *ks, pmk::ExpMode mode, const uint32_t *in, uint32_t *out, size_t n,
+                cudaStream_t st, uint32_t *status_if_zero = nullptr) {
+  const uint32_t b = ks->nprimes, H = ks->nbits / 32 / b;
+  int rc = pmk::launch_modexp(mode, H, cfg_for(ctx, H, true), ks->d_keys, ks->K, in, out, n, st, b);
+  if (rc != PMK_OK) return rc;
+  if (b == 2) return pmk::launch_garner(H, ks->d_keys, ks->K, out, n, st, status_if_zero);
+  return pmk::launch_garner_mp(H, b, ks->d_keys, ks->K, out, n, st, status_if_zero);
+}
+
 int enqueue_decrypt(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *in, uint32_t *out, size_t n, int use_crt,
                     cudaStream_t st) {
   const uint32_t S = ks->nbits / 32;
   int rc = pmk::launch_range_check(ks->d_keys, ks->K, S, in, n, ctx->d_status, st);
   if (rc != PMK_OK) return rc;
   if (!use_crt) return pmk::launch_modexp(pmk::ExpMode::kDecrypt, S, cfg_for(ctx, S, false), ks->d_keys, ks->K, in, out, n, st);
-  const uint32_t H = S / 2;
-  rc = pmk::launch_modexp(pmk::ExpMode::kCrtHalf, H, cfg_for(ctx, H, true), ks->d_keys, ks->K, in, out, n, st);
-  if (rc == PMK_OK) rc = pmk::launch_garner(H, ks->d_keys, ks->K, out, n, st);
-  return rc;
+  return enqueue_crt(ctx, ks, pmk::ExpMode::kCrtHalf, in, out, n, st);
 }
 
 }  // namespace
@@ -204,16 +224,23 @@ void pmk_ctx_destroy(pmk_ctx *ctx) {
 }
 
 int pmk_keygen(pmk_ctx *ctx, uint32_t K, uint32_t nbits, uint64_t e, uint64_t seed, pmk_keyset **out) {
+  return pmk_keygen_multiprime(ctx, K, nbits, 2, e, seed, out);
+}
+
+int pmk_keygen_multiprime(pmk_ctx *ctx, uint32_t K, uint32_t nbits, uint32_t nprimes, uint64_t e, uint64_t seed,
+                          pmk_keyset **out) {
   if (!ctx || !out) return PMK_EINVAL;
-  if (K == 0 || nbits < 128 || nbits > 8192 || nbits % 128 || e < 3 || !(e & 1) || (e >> 32)) return PMK_EINVAL;
-  if (!width_built(nbits)) return PMK_EUNSUPPORTED;
+  if (K == 0 || K > kMaxKeys || !pmk::valid_multiprime(nbits, nprimes) || e < 3 || !(e & 1) || (e >> 32))
+    return PMK_EINVAL;
+  if (!width_built(nbits, nprimes)) return PMK_EUNSUPPORTED;
   try {
     pmk_keyset *ks = new pmk_keyset();
     ks->device = ctx->device;
     ks->K = K;
     ks->nbits = nbits;
     ks->e = e;
-    int rc = pmk::host_keygen(K, nbits, e, seed, ks->keys);
+    ks->nprimes = nprimes;
+    int rc = pmk::host_keygen_mp(K, nbits, nprimes, e, seed, ks->keys);
     if (rc != PMK_OK) {
       delete ks;
       return rc;
@@ -224,9 +251,29 @@ int pmk_keygen(pmk_ctx *ctx, uint32_t K, uint32_t nbits, uint64_t e, uint64_t se
   }
 }
 
+int pmk_keygen_host_multiprime(uint32_t K, uint32_t nbits, uint32_t nprimes, uint64_t e, uint64_t seed, uint32_t *N,
+                               uint32_t *d, uint32_t *primes, uint32_t *dexp, uint32_t *coef) {
+  if (K == 0 || K > kMaxKeys || !pmk::valid_multiprime(nbits, nprimes) || e < 3 || !(e & 1) || (e >> 32))
+    return PMK_EINVAL;
+  try {
+    pmk_keyset ks;
+    ks.K = K;
+    ks.nbits = nbits;
+    ks.e = e;
+    ks.nprimes = nprimes;
+    int rc = pmk::host_keygen_mp(K, nbits, nprimes, e, seed, ks.keys);
+    if (rc == PMK_OK) rc = pmk_keyset_export(&ks, N, d, nullptr, nullptr, nullptr, nullptr, nullptr);
+    if (rc == PMK_OK) rc = pmk_keyset_export_primes(&ks, primes, dexp, coef);
+    return rc;
+  } catch (const std::bad_alloc &) {
+    return PMK_ENOMEM;
+  }
+}
+
 int pmk_keygen_host(uint32_t K, uint32_t nbits, uint64_t e, uint64_t seed, uint32_t *N, uint32_t *d, uint32_t *p,
                     uint32_t *q, uint32_t *dp, uint32_t *dq, uint32_t *qinv) {
-  if (K == 0 || nbits < 128 || nbits > 8192 || nbits % 128 || e < 3 || !(e & 1) || (e >> 32)) return PMK_EINVAL;
+  if (K == 0 || K > kMaxKeys || nbits < 128 || nbits > 8192 || nbits % 128 || e < 3 || !(e & 1) || (e >> 32))
+    return PMK_EINVAL;
   try {
     pmk_keyset ks;
     ks.K = K;
@@ -242,7 +289,7 @@ int pmk_keygen_host(uint32_t K, uint32_t nbits, uint64_t e, uint64_t seed, uint3
 
 int pmk_keyset_from_primes(pmk_ctx *ctx, uint32_t K, uint32_t nbits, uint64_t e, const uint32_t *p,
                            const uint32_t *q, pmk_keyset **out) {
-  if (!ctx || !out || !p || !q || K == 0) return PMK_EINVAL;
+  if (!ctx || !out || !p || !q || K == 0 || K > kMaxKeys) return PMK_EINVAL;
   if (nbits < 128 || nbits > 8192 || nbits % 128 || e < 3 || !(e & 1) || (e >> 32)) return PMK_EINVAL;
   if (!width_built(nbits)) return PMK_EUNSUPPORTED;
   try {
@@ -269,6 +316,7 @@ int pmk_keyset_from_primes(pmk_ctx *ctx, uint32_t K, uint32_t nbits, uint64_t e,
 int pmk_keyset_export(const pmk_keyset *ks, uint32_t *N, uint32_t *d, uint32_t *p, uint32_t *q, uint32_t *dp,
                       uint32_t *dq, uint32_t *qinv) {
   if (!ks) return PMK_EINVAL;
+  if (ks->nprimes != 2 && (p || q || dp || dq || qinv)) return PMK_EINVAL;  // primes: pmk_keyset_export_primes
   const size_t s = ks->nbits / 32, h = s / 2;
   for (uint32_t k = 0; k < ks->K; k++) {
     const HostKey &x = ks->keys[k];
@@ -283,6 +331,24 @@ int pmk_keyset_export(const pmk_keyset *ks, uint32_t *N, uint32_t *d, uint32_t *
   return PMK_OK;
 }
 
+int pmk_keyset_export_primes(const pmk_keyset *ks, uint32_t *primes, uint32_t *dexp, uint32_t *coef) {
+  if (!ks) return PMK_EINVAL;
+  const size_t s = ks->nbits / 32, b = ks->nprimes, h = s / b;
+  for (uint32_t k = 0; k < ks->K; k++) {
+    const HostKey &x = ks->keys[k];
+    for (size_t i = 0; i < b; i++) {
+      if (primes) std::memcpy(primes + k * s + i * h, x.pr[i].data(), h * 4);
+      if (dexp) std::memcpy(dexp + k * s + i * h, x.dpr[i].data(), h * 4);
+      if (coef) {
+        if (i == 1) std::memset(coef + k * s + i * h, 0, h * 4);
+        else std::memcpy(coef + k * s + i * h, x.coef[i].data(), h * 4);
+      }
+    }
+  }
+  return PMK_OK;
+}
+
+uint32_t pmk_keyset_num_primes(const pmk_keyset *ks) { return ks ? ks->nprimes : 0; }
 uint32_t pmk_keyset_num_keys(const pmk_keyset *ks) { return ks ? ks->K : 0; }
 uint32_t pmk_keyset_nbits(const pmk_keyset *ks) { return ks ? ks->nbits : 0; }
 uint64_t pmk_keyset_e(const pmk_keyset *ks) { return ks ? ks->e : 0; }
@@ -381,14 +447,11 @@ int pmk_decrypt_blinded(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_cs
   DeviceGuard g(ctx->device);
   if (!g.ok()) return PMK_ECUDA;
   cudaStream_t st = as_stream(stream);
-  const uint32_t S = ks->nbits / 32, H = S / 2;
+  const uint32_t S = ks->nbits / 32;
   rc = pmk::launch_range_check(ks->d_keys, ks->K, S, d_cstar, n_chunks, ctx->d_status, st);
   if (rc == PMK_OK) rc = pmk::launch_range_check(ks->d_keys, ks->K, S, d_cr, n_chunks, ctx->d_status, st);
-  // c_r^-1 mod N: Fermat inverses mod p and q, recombined (into d_m)
-  if (rc == PMK_OK)
-    rc = pmk::launch_modexp(pmk::ExpMode::kCrtInverse, H, cfg_for(ctx, H, true), ks->d_keys, ks->K, d_cr, d_m,
-                            n_chunks, st);
-  if (rc == PMK_OK) rc = pmk::launch_garner(H, ks->d_keys, ks->K, d_m, n_chunks, st, ctx->d_status);
+  // c_r^-1 mod N: Fermat inverses mod each prime, recombined (into d_m)
+  if (rc == PMK_OK) rc = enqueue_crt(ctx, ks, pmk::ExpMode::kCrtInverse, d_cr, d_m, n_chunks, st, ctx->d_status);
   // x = c* c_r^-1, in place
   if (rc == PMK_OK) rc = pmk::launch_mulmod(S, ks->d_keys, ks->K, d_cstar, d_m, d_m, n_chunks, st);
   if (rc != PMK_OK) return rc;
@@ -399,10 +462,7 @@ int pmk_decrypt_blinded(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_cs
   rc = grow(reinterpret_cast<void **>(&ctx->d_b), &ctx->b_cap, n_chunks * S * 4);
   if (rc == PMK_OK && cudaMemcpyAsync(ctx->d_b, d_m, n_chunks * S * 4, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     rc = PMK_ECUDA;
-  if (rc == PMK_OK)
-    rc = pmk::launch_modexp(pmk::ExpMode::kCrtHalf, H, cfg_for(ctx, H, true), ks->d_keys, ks->K, ctx->d_b, d_m,
-                            n_chunks, st);
-  if (rc == PMK_OK) rc = pmk::launch_garner(H, ks->d_keys, ks->K, d_m, n_chunks, st);
+  if (rc == PMK_OK) rc = enqueue_crt(ctx, ks, pmk::ExpMode::kCrtHalf, ctx->d_b, d_m, n_chunks, st);
   return rc;
 }
 

@@ -1,7 +1,8 @@
 // Batched persistent execution: plan tasks for many jobs, group them by
 // exponentiation width and mode, and capture range checks, one persistent
 // kernel per group (on forked streams) and CRT recombination into a CUDA
-// graph that pmk_batch_launch replays.
+// graph that pmk_batch_launch replays.  A CRT job contributes one task per
+// (chunk group, prime) and one recombination launch.
 #include <algorithm>
 #include <new>
 #include <vector>
@@ -66,14 +67,14 @@ int plan_and_capture(pmk_ctx *ctx, const pmk_job *jobs, size_t n_jobs, pmk_batch
     if (jb.n_chunks == 0) continue;
     const pmk_keyset *ks = jb.ks;
     const bool crt = jb.op == PMK_OP_DECRYPT_CRT;
-    const uint32_t S = ks->nbits / 32, limbs = crt ? S / 2 : S;
+    const uint32_t S = ks->nbits / 32, limbs = crt ? S / ks->nprimes : S;
     Group *g = group_for(limbs, crt);
     if (!g) return PMK_EUNSUPPORTED;
     const uint32_t ipw = 32 / g->cfg.tpi;
     for (uint32_t k = 0; k < ks->K && k < jb.n_chunks; k++) {
       const long long count = ((long long)jb.n_chunks - k + ks->K - 1) / ks->K;
       for (long long i0 = 0; i0 < count; i0 += ipw)
-        for (int half = 0; half < (crt ? 2 : 1); half++) {
+        for (int half = 0; half < (crt ? (int)ks->nprimes : 1); half++) {
           pmk::BatchTask t;
           t.key = ks->d_keys + k;
           t.in = jb.d_in;
@@ -142,9 +143,12 @@ int plan_and_capture(pmk_ctx *ctx, const pmk_job *jobs, size_t n_jobs, pmk_batch
       rc = PMK_ECUDA;
   }
   for (size_t j = 0; j < n_jobs && rc == PMK_OK; j++)
-    if (jobs[j].n_chunks && jobs[j].op == PMK_OP_DECRYPT_CRT)
-      rc = pmk::launch_garner(jobs[j].ks->nbits / 64, jobs[j].ks->d_keys, jobs[j].ks->K, jobs[j].d_out,
-                              jobs[j].n_chunks, b->capture);
+    if (jobs[j].n_chunks && jobs[j].op == PMK_OP_DECRYPT_CRT) {
+      const pmk_keyset *ks = jobs[j].ks;
+      const uint32_t B = ks->nprimes, H = ks->nbits / 32 / B;
+      rc = B == 2 ? pmk::launch_garner(H, ks->d_keys, ks->K, jobs[j].d_out, jobs[j].n_chunks, b->capture)
+                  : pmk::launch_garner_mp(H, B, ks->d_keys, ks->K, jobs[j].d_out, jobs[j].n_chunks, b->capture);
+    }
   cudaGraph_t graph = nullptr;
   const cudaError_t end = cudaStreamEndCapture(b->capture, &graph);
   b->graph = graph;

@@ -391,6 +391,162 @@ int launch_garner(uint32_t half_limbs, const KeyDev *keys, uint32_t K, uint32_t 
   return cuda_rc(cudaGetLastError());
 }
 
+// ---------------------------------------------------------------- multi-prime recombination
+// Single-thread helpers over H limbs (H <= kGarnerMaxH) modulo an odd prime r.
+
+constexpr int kGarnerMaxH = 128, kGarnerMaxS = 256;
+
+// out = a b R_h^-1 mod r (CIOS, R_h = 2^(32 H)); a < R_h, b < r.  out may alias a.
+__device__ void mm_1t(uint32_t *out, const uint32_t *a, const uint32_t *b, const uint32_t *__restrict__ r, uint32_t n0,
+                      int H) {
+  uint32_t acc[kGarnerMaxH + 2];
+  for (int i = 0; i < H + 2; i++) acc[i] = 0;
+  for (int i = 0; i < H; i++) {
+    const uint32_t bi = b[i];
+    uint64_t c = 0;
+    for (int j = 0; j < H; j++) {
+      c += (uint64_t)a[j] * bi + acc[j];
+      acc[j] = (uint32_t)c;
+      c >>= 32;
+    }
+    c += acc[H];
+    acc[H] = (uint32_t)c;
+    acc[H + 1] = (uint32_t)(c >> 32);
+    const uint32_t m = acc[0] * n0;
+    c = ((uint64_t)m * __ldg(r) + acc[0]) >> 32;
+    for (int j = 1; j < H; j++) {
+      c += (uint64_t)m * __ldg(r + j) + acc[j];
+      acc[j - 1] = (uint32_t)c;
+      c >>= 32;
+    }
+    c += acc[H];
+    acc[H - 1] = (uint32_t)c;
+    acc[H] = acc[H + 1] + (uint32_t)(c >> 32);
+  }
+  // acc < 2 r: subtract r unless that borrows out of the H + 1 words
+  uint32_t borrow = 0;
+  for (int i = 0; i < H; i++) {
+    const uint64_t d = (uint64_t)acc[i] - __ldg(r + i) - borrow;
+    out[i] = (uint32_t)d;
+    borrow = (uint32_t)(d >> 63);
+  }
+  if (acc[H] == 0 && borrow)
+    for (int i = 0; i < H; i++) out[i] = acc[i];
+}
+
+// a = (a + b) mod r, or (a - b) mod r, for a, b < r.
+__device__ void addmod_1t(uint32_t *a, const uint32_t *b, const uint32_t *__restrict__ r, int H) {
+  uint64_t c = 0;
+  for (int i = 0; i < H; i++) {
+    c += (uint64_t)a[i] + b[i];
+    a[i] = (uint32_t)c;
+    c >>= 32;
+  }
+  uint32_t t[kGarnerMaxH], borrow = 0;
+  for (int i = 0; i < H; i++) {
+    const uint64_t d = (uint64_t)a[i] - __ldg(r + i) - borrow;
+    t[i] = (uint32_t)d;
+    borrow = (uint32_t)(d >> 63);
+  }
+  if (c || !borrow)
+    for (int i = 0; i < H; i++) a[i] = t[i];
+}
+__device__ void submod_1t(uint32_t *a, const uint32_t *b, const uint32_t *__restrict__ r, int H) {
+  uint32_t borrow = 0;
+  for (int i = 0; i < H; i++) {
+    const uint64_t d = (uint64_t)a[i] - b[i] - borrow;
+    a[i] = (uint32_t)d;
+    borrow = (uint32_t)(d >> 63);
+  }
+  if (borrow) {
+    uint64_t c = 0;
+    for (int i = 0; i < H; i++) {
+      c += (uint64_t)a[i] + __ldg(r + i);
+      a[i] = (uint32_t)c;
+      c >>= 32;
+    }
+  }
+}
+
+// Multi-prime CRT recombination (Section 2.1), one thread per chunk, in
+// place: out[t] holds the residues m_i = c^{d_i} mod r_i, i < B, H limbs
+// each, and receives m = c^d mod N (B H limbs).  The running value m starts
+// at m_1 and visits r_0, r_2, r_3, ...; visiting r_i adds
+//   x_i = coef_i (m_i - m) mod r_i  times  prefix_i = product of the primes visited so far,
+// the CRT-RSA equation for the first two primes and Garner's extension for
+// the rest.  m mod r_i comes from Montgomery products over m's H-limb
+// pieces (Horner: MontMul(v, R_h^2) is v R_h in Montgomery form), so the
+// kernel needs no division.  With `status`, a zero residue (c shares the
+// prime r_i: no inverse exists) sets kStatusNotInvertible.
+__global__ void __launch_bounds__(kAuxThreads) k_garner_mp(const KeyDev *__restrict__ keys, uint32_t K, int H, int B,
+                                                           uint32_t *__restrict__ out, long long n,
+                                                           uint32_t *__restrict__ status) {
+  const long long t = (long long)blockIdx.x * kAuxThreads + threadIdx.x;
+  if (t >= n) return;
+  const KeyDev &kd = keys[t % K];
+  uint32_t *o = out + t * (long long)(B * H);
+  if (status) {
+    bool zero = false;
+    for (int i = 0; i < B; i++) {
+      uint32_t any = 0;
+      for (int j = 0; j < H; j++) any |= o[i * H + j];
+      zero = zero || !any;
+    }
+    if (zero) atomicOr(status, kStatusNotInvertible);
+  }
+  uint32_t m[kGarnerMaxS];  // running value, `len` limbs
+  uint32_t acc[kGarnerMaxH], tmp[kGarnerMaxH], mi[kGarnerMaxH];
+  for (int j = 0; j < H; j++) m[j] = o[H + j];
+  int len = H;
+  for (int step = 0; step < B - 1; step++) {
+    const int i = step == 0 ? 0 : step + 1;
+    const uint32_t *ri = kd.P[i], *R2 = kd.R2h[i];
+    const uint32_t n0 = kd.n0h[i];
+    // acc = m R_h mod r_i (Montgomery form of m mod r_i), from m's top piece down
+    const int pieces = len / H;
+    mm_1t(acc, m + (pieces - 1) * H, R2, ri, n0, H);
+    for (int pc = pieces - 2; pc >= 0; pc--) {
+      mm_1t(acc, acc, R2, ri, n0, H);
+      mm_1t(tmp, m + pc * H, R2, ri, n0, H);
+      addmod_1t(acc, tmp, ri, H);
+    }
+    for (int j = 0; j < H; j++) mi[j] = o[i * H + j];
+    mm_1t(tmp, mi, R2, ri, n0, H);    // m_i R_h
+    submod_1t(tmp, acc, ri, H);       // (m_i - m) R_h mod r_i
+    mm_1t(tmp, tmp, kd.coef[i], ri, n0, H);  // x_i = coef_i (m_i - m) mod r_i
+    // m += prefix_i x_i  (prefix_i has len limbs; the sum stays below prefix_i r_i)
+    const uint32_t *pf = kd.prefix[i];
+    for (int j = len; j < len + H; j++) m[j] = 0;
+    for (int a = 0; a < H; a++) {
+      const uint32_t xa = tmp[a];
+      uint64_t c = 0;
+      for (int j = 0; j < len; j++) {
+        c += (uint64_t)__ldg(pf + j) * xa + m[a + j];
+        m[a + j] = (uint32_t)c;
+        c >>= 32;
+      }
+      for (int j = a + len; j < len + H && c; j++) {
+        c += m[j];
+        m[j] = (uint32_t)c;
+        c >>= 32;
+      }
+    }
+    len += H;
+  }
+  for (int j = 0; j < B * H; j++) o[j] = m[j];
+}
+
+int launch_garner_mp(uint32_t prime_limbs, uint32_t parts, const KeyDev *keys, uint32_t K, uint32_t *out, size_t n,
+                     cudaStream_t st, uint32_t *status_if_zero_residue) {
+  if (n == 0) return PMK_OK;
+  if (parts < 2 || parts > (uint32_t)kMaxPrimes || prime_limbs == 0 || prime_limbs > (uint32_t)kGarnerMaxH ||
+      prime_limbs * parts > (uint32_t)kGarnerMaxS)
+    return PMK_EINVAL;
+  k_garner_mp<<<(unsigned)((n + kAuxThreads - 1) / kAuxThreads), kAuxThreads, 0, st>>>(
+      keys, K, (int)prime_limbs, (int)parts, out, (long long)n, status_if_zero_residue);
+  return cuda_rc(cudaGetLastError());
+}
+
 const MulmodEntry *mulmod_entries(int *count) {
   static const MulmodEntry entries[] = {
       make_mulmod<4, 2>(),   make_mulmod<8, 2>(),    make_mulmod<16, 2>(),   make_mulmod<32, 4>(),
@@ -499,19 +655,22 @@ int launch_modexp_tasks(uint32_t limbs, KernelConfig cfg, bool crt, const BatchT
 }
 
 int launch_modexp(ExpMode mode, uint32_t limbs, KernelConfig cfg, const KeyDev *keys, uint32_t K, const uint32_t *in,
-                  uint32_t *out, size_t n, cudaStream_t st) {
+                  uint32_t *out, size_t n, cudaStream_t st, uint32_t parts) {
   if (n == 0) return PMK_OK;
   const bool crt = mode == ExpMode::kCrtHalf || mode == ExpMode::kCrtInverse;
+  if (crt && (parts < 2 || parts > (uint32_t)kMaxPrimes)) return PMK_EINVAL;
+  if ((unsigned long long)K * (crt ? parts : 1) > 65535ull) return PMK_EINVAL;  // grid.y
   const ModexpEntry *e = find_entry(limbs, cfg, crt);
   if (!e) return PMK_EUNSUPPORTED;
   const int rc = configure_smem(e->fn, e->smem);
   if (rc != PMK_OK) return rc;
   const long long per_key = ((long long)n + K - 1) / K;
   const int ipb = dev::kThreads / e->tpi;
-  dim3 grid((unsigned)((per_key + ipb - 1) / ipb), crt ? 2 * K : K);
+  dim3 grid((unsigned)((per_key + ipb - 1) / ipb), crt ? parts * K : K);
   long long nl = (long long)n;
   int sel = (mode == ExpMode::kEncrypt || mode == ExpMode::kCrtInverse) ? 1 : 0;
-  void *args[] = {(void *)&keys, (void *)&K, (void *)&in, (void *)&out, (void *)&nl, (void *)&sel};
+  int np = crt ? (int)parts : 1;
+  void *args[] = {(void *)&keys, (void *)&K, (void *)&in, (void *)&out, (void *)&nl, (void *)&sel, (void *)&np};
   return cuda_rc(cudaLaunchKernel(e->fn, grid, dim3(dev::kThreads), args, e->smem, st));
 }
 

@@ -15,6 +15,12 @@
 // two bits and bit 0 set; it is rejected if an odd prime below 2000 divides
 // it, then if gcd(e, cand - 1) != 1, then by 40 Miller-Rabin rounds with bases
 // (splitmix64() >> 1) + 2.  q is redrawn while q == p.
+//
+// Multi-prime keys (Section 2.1): b primes of nbits / b bits drawn in order
+// from the key's stream, each redrawn while it equals an earlier one; a
+// candidate is also redrawn while its top byte is below the least T with
+// T^b >= 2^(8b - 1), so that N has exactly nbits bits (T = 192 for b = 2:
+// the two-top-bits rule above, so b = 2 gives the same keys).
 #include <algorithm>
 #include <cstring>
 #include <thread>
@@ -177,13 +183,15 @@ const std::vector<u64> &small_primes() {
   return primes;
 }
 
-std::vector<u64> gen_prime(u64 &rng, int bits, u64 e) {
+// A prime of exactly `bits` bits whose top byte is at least min_top (>= 192).
+std::vector<u64> gen_prime(u64 &rng, int bits, u64 e, int min_top) {
   int n = bits / 64;
   std::vector<u64> p(n);
   for (;;) {
     for (int w = 0; w < n; w++) p[w] = splitmix64(rng);
     p[n - 1] |= 0xC000000000000000ull;
     p[0] |= 1;
+    if ((int)(p[n - 1] >> 56) < min_top) continue;
     bool composite = false;
     for (u64 sp : small_primes())
       if (mod_small(p.data(), n, sp) == 0) {
@@ -289,57 +297,96 @@ void pow2_mod(const std::vector<u64> &m, int bits_a, int bits_b, std::vector<u64
   }
 }
 
-void finish_key(uint32_t nbits, u64 e, const std::vector<u64> &p, const std::vector<u64> &q, HostKey &k) {
-  size_t s = nbits / 32, h = s / 2;
-  std::vector<u64> p1 = minus_one(p), q1 = minus_one(q);
-  std::vector<u64> N = mul_full(p, q), phi = mul_full(p1, q1);
-  std::vector<u64> d = inv_of_small(e, phi);
-  std::vector<u64> dp = inv_of_small(e, p1), dq = inv_of_small(e, q1);  // = d mod (p-1), d mod (q-1)
-  // qinv = q^(p-2) mod p (Fermat); q < 2p, so q mod p is one conditional subtraction
-  int n = (int)p.size();
-  std::vector<u64> qm(q), pm2(p), qinv(n);
-  if (cmp(qm.data(), p.data(), n) >= 0) sub(qm.data(), qm.data(), p.data(), n);
+// x mod m for x < 2 m (one conditional subtraction), n limbs
+std::vector<u64> reduce_once(std::vector<u64> x, const std::vector<u64> &m) {
+  const int n = (int)m.size();
+  if (cmp(x.data(), m.data(), n) >= 0) sub(x.data(), x.data(), m.data(), n);
+  return x;
+}
+
+// 2^(32 k) mod m as 32-bit limbs, for the Montgomery constants R^2, R^3.
+std::vector<uint32_t> pow2_32(const std::vector<u64> &m, int k, size_t limbs) {
+  std::vector<u64> a, unused;
+  pow2_mod(m, k, k, a, unused);
+  return to32(a, limbs);
+}
+
+// Key data for primes r_0 .. r_{b-1} of equal size (b >= 2).  Every prime's
+// top byte is >= 192, so r_j < 2 r_i for all i, j: a prime reduces modulo
+// another by one conditional subtraction.
+void finish_key(uint32_t nbits, u64 e, const std::vector<std::vector<u64>> &r, HostKey &k) {
+  const int b = (int)r.size(), n = (int)r[0].size();
+  const size_t s = nbits / 32, h = s / b;
+  std::vector<u64> N = r[0], phi = minus_one(r[0]);
+  for (int i = 1; i < b; i++) {
+    N = mul_full(N, r[i]);
+    phi = mul_full(phi, minus_one(r[i]));
+  }
+  N.resize(s / 2);
+  phi.resize(s / 2);
+  const std::vector<u64> d = inv_of_small(e, phi);
   std::vector<u64> two(n, 0);
   two[0] = 2;
-  sub(pm2.data(), p.data(), two.data(), n);
-  Mont mp(p);
-  mp.pow(qinv.data(), qm.data(), pm2.data(), n);
+  k.nprimes = (uint32_t)b;
   k.N = to32(N, s);
   k.d = to32(d, s);
-  k.p = to32(p, h);
-  k.q = to32(q, h);
-  k.dp = to32(dp, h);
-  k.dq = to32(dq, h);
-  k.qinv = to32(qinv, h);
-  // Montgomery constants (32-bit limb view)
   k.n0 = neg_inv32(k.N[0]);
-  k.n0h[0] = neg_inv32(k.p[0]);
-  k.n0h[1] = neg_inv32(k.q[0]);
-  std::vector<u64> r2, unused;
-  pow2_mod(N, (int)(64 * s), (int)(64 * s), r2, unused);
-  k.R2 = to32(r2, s);
-  const std::vector<u64> *pq[2] = {&p, &q};
-  for (int i = 0; i < 2; i++) {
-    std::vector<u64> a, b;
-    pow2_mod(*pq[i], (int)(64 * h), (int)(96 * h), a, b);
-    k.R2h[i] = to32(a, h);
-    k.R3h[i] = to32(b, h);
+  k.R2 = pow2_32(N, (int)(64 * s), s);
+  std::vector<u64> prefix = r[1];  // product of the primes visited so far (r_1, then r_0, r_2, ...)
+  for (int i = 0; i < b; i++) {
+    const Mont mt(r[i]);
+    std::vector<u64> rm2(r[i]);
+    sub(rm2.data(), r[i].data(), two.data(), n);
+    k.pr[i] = to32(r[i], h);
+    k.dpr[i] = to32(inv_of_small(e, minus_one(r[i])), h);  // = d mod (r_i - 1)
+    k.n0h[i] = neg_inv32(k.pr[i][0]);
+    k.R2h[i] = pow2_32(r[i], (int)(64 * h), h);
+    k.R3h[i] = pow2_32(r[i], (int)(96 * h), h);
+    k.sched_h[i] = make_schedule(k.dpr[i].data(), (int)h);
+    const std::vector<uint32_t> rm2_32 = to32(rm2, h);
+    k.sched_hinv[i] = make_schedule(rm2_32.data(), (int)h);
+    if (i == 1) continue;
+    // coef_i = (product of the primes visited before r_i)^-1 mod r_i, by Fermat
+    std::vector<u64> acc(n), t(n), x(n), coef(n);
+    bool first = true;
+    for (int j = 0; j < b; j++) {
+      const bool before = i == 0 ? j == 1 : j < i;
+      if (!before) continue;
+      mt.to_mont(t.data(), reduce_once(r[j], r[i]).data());
+      if (first) acc = t;
+      else mt.mul(acc.data(), acc.data(), t.data());
+      first = false;
+    }
+    mt.from_mont(x.data(), acc.data());
+    mt.pow(coef.data(), x.data(), rm2.data(), n);
+    k.coef[i] = to32(coef, h);
+    k.prefix[i] = to32(prefix, h * (i == 0 ? 1 : i));
+    prefix = mul_full(prefix, r[i]);
+    prefix.resize((size_t)n * (i == 0 ? 2 : i + 1));
   }
-  std::vector<u64> qm_r(qinv);  // qinv * R_h mod p
-  for (size_t i = 0; i < 32 * h; i++) dbl_mod(qm_r.data(), p.data(), n);
+  k.p = k.pr[0];
+  k.q = k.pr[1];
+  k.dp = k.dpr[0];
+  k.dq = k.dpr[1];
+  k.qinv = k.coef[0];
+  std::vector<u64> qm_r(to64(k.qinv.data(), h));  // qinv * R_h mod p
+  for (size_t i = 0; i < 32 * h; i++) dbl_mod(qm_r.data(), r[0].data(), n);
   k.qinv_m = to32(qm_r, h);
   uint32_t ev[2] = {(uint32_t)e, (uint32_t)(e >> 32)};
   k.sched_e = make_schedule(ev, 2);
   k.sched_d = make_schedule(k.d.data(), (int)s);
-  k.sched_h[0] = make_schedule(k.dp.data(), (int)h);
-  k.sched_h[1] = make_schedule(k.dq.data(), (int)h);
-  std::vector<u64> pm2x(p), qm2x(q), twox(n, 0);  // Fermat inverses mod p and q: exponents p - 2, q - 2
-  twox[0] = 2;
-  sub(pm2x.data(), p.data(), twox.data(), n);
-  sub(qm2x.data(), q.data(), twox.data(), n);
-  const std::vector<uint32_t> pm2_32 = to32(pm2x, h), qm2_32 = to32(qm2x, h);
-  k.sched_hinv[0] = make_schedule(pm2_32.data(), (int)h);
-  k.sched_hinv[1] = make_schedule(qm2_32.data(), (int)h);
+}
+
+// The least top byte T (at least 192) with T^b >= 2^(8 b - 1): b primes of
+// k bits whose top bytes are >= T multiply to at least 2^(b k - 1).
+int min_top_byte(int b) {
+  const u64 need = 1ull << (8 * b - 1);
+  int t = 192;
+  for (;; t++) {
+    u64 v = 1;
+    for (int i = 0; i < b; i++) v *= (u64)t;
+    if (v >= need) return t;
+  }
 }
 
 bool valid_width(uint32_t nbits) { return nbits >= 128 && nbits <= 8192 && nbits % 128 == 0; }
@@ -403,19 +450,32 @@ Schedule make_schedule(const uint32_t *exp, int nlimbs) {
   return best;
 }
 
-int host_keygen(uint32_t K, uint32_t nbits, uint64_t e, uint64_t seed, std::vector<HostKey> &out) {
-  if (K == 0 || !valid_width(nbits) || e < 3 || !(e & 1) || e >> 32) return PMK_EINVAL;
+bool valid_multiprime(uint32_t nbits, uint32_t nprimes) {
+  return nprimes >= 2 && nprimes <= (uint32_t)kMaxPrimes && valid_width(nbits) && nbits % (64 * nprimes) == 0;
+}
+
+int host_keygen_mp(uint32_t K, uint32_t nbits, uint32_t nprimes, uint64_t e, uint64_t seed,
+                   std::vector<HostKey> &out) {
+  if (K == 0 || !valid_multiprime(nbits, nprimes) || e < 3 || !(e & 1) || e >> 32) return PMK_EINVAL;
   std::vector<u64> seeds(K);
   u64 master = seed;
   for (uint32_t k = 0; k < K; k++) seeds[k] = splitmix64(master);
   out.assign(K, HostKey());
+  const int top = min_top_byte((int)nprimes), bits = (int)(nbits / nprimes);
   auto work = [&](uint32_t k) {
     u64 rng = seeds[k];
-    std::vector<u64> p = gen_prime(rng, (int)nbits / 2, e), q;
-    do {
-      q = gen_prime(rng, (int)nbits / 2, e);
-    } while (cmp(p.data(), q.data(), (int)p.size()) == 0);
-    finish_key(nbits, e, p, q, out[k]);
+    std::vector<std::vector<u64>> r;
+    for (uint32_t i = 0; i < nprimes; i++) {
+      std::vector<u64> c;
+      bool dup;
+      do {  // r_i is redrawn while it equals an earlier prime
+        c = gen_prime(rng, bits, e, top);
+        dup = false;
+        for (const auto &x : r) dup = dup || cmp(x.data(), c.data(), (int)c.size()) == 0;
+      } while (dup);
+      r.push_back(c);
+    }
+    finish_key(nbits, e, r, out[k]);
   };
   unsigned hw = std::max(1u, std::thread::hardware_concurrency());
   unsigned nt = std::min<unsigned>(hw, K);
@@ -426,6 +486,10 @@ int host_keygen(uint32_t K, uint32_t nbits, uint64_t e, uint64_t seed, std::vect
     });
   for (auto &th : pool) th.join();
   return PMK_OK;
+}
+
+int host_keygen(uint32_t K, uint32_t nbits, uint64_t e, uint64_t seed, std::vector<HostKey> &out) {
+  return host_keygen_mp(K, nbits, 2, e, seed, out);
 }
 
 int host_from_primes(uint32_t nbits, uint64_t e, const uint32_t *p32, const uint32_t *q32, HostKey &out) {
@@ -439,7 +503,7 @@ int host_from_primes(uint32_t nbits, uint64_t e, const uint32_t *p32, const uint
     if (gcd64(e, r) != 1) return PMK_EINVAL;
   }
   if (cmp(p.data(), q.data(), n) == 0) return PMK_EINVAL;
-  finish_key(nbits, e, p, q, out);
+  finish_key(nbits, e, {p, q}, out);
   return PMK_OK;
 }
 

@@ -7,34 +7,67 @@
 namespace pmk {
 namespace dev {
 
-// Grid: blockIdx.y selects the key (full width) or key * 2 + half (CRT);
-// blockIdx.x * IPB + instance slot selects the j-th chunk of that key, chunk
-// t = key + j K.  Every block therefore serves one key: schedules, modulus and
-// control flow are uniform across it.
+// The CRT input of one residue in Montgomery form: x = c R mod r for the
+// chunk c = sum_j c_j R^j of `parts` S-limb pieces (R = 2^(32 S)), by Horner
+// from the top piece: MontMul(c_top, R^3) = c_top R^2 is the Montgomery form
+// of c_top R, MontMul(c_j, R^2) that of c_j, and MontMul(x, R^2) multiplies
+// the value in Montgomery form by R.  Two pieces take two products.
+template <int S, int TPI, int FORM>
+__device__ __forceinline__ void crt_input(uint32_t (&a)[S / TPI], const uint32_t *c, bool active, int parts,
+                                          const uint32_t *sR2, const uint32_t *sR3, const uint32_t (&nn)[S / TPI],
+                                          uint32_t n0, uint32_t r) {
+  constexpr int L = S / TPI;
+  uint32_t lo[L];
+  if (active) {
+    load_slice_global<L>(a, c + (parts - 1) * S, r);
+    load_slice_global<L>(lo, c + (parts - 2) * S, r);
+  } else {
+#pragma unroll
+    for (int j = 0; j < L; j++) lo[j] = a[j] = 0;
+  }
+  mont<S, TPI, FORM>(a, sR3, nn, n0, r);   // c_top R^2
+  mont<S, TPI, FORM>(lo, sR2, nn, n0, r);  // c_next R
+  mod_add<L, TPI>(a, lo, nn, r);           // (c_top R + c_next) R
+  for (int piece = parts - 3; piece >= 0; piece--) {
+    mont<S, TPI, FORM>(a, sR2, nn, n0, r);  // value * R, still in Montgomery form
+    if (active) {
+      load_slice_global<L>(lo, c + piece * S, r);
+    } else {
+#pragma unroll
+      for (int j = 0; j < L; j++) lo[j] = 0;
+    }
+    mont<S, TPI, FORM>(lo, sR2, nn, n0, r);
+    mod_add<L, TPI>(a, lo, nn, r);
+  }
+}
+
+// Grid: blockIdx.y selects the key (full width) or key * parts + i (CRT,
+// residue mod prime r_i); blockIdx.x * IPB + instance slot selects the j-th
+// chunk of that key, chunk t = key + j K.  Every block therefore serves one
+// key: schedules, modulus and control flow are uniform across it.
 //
 // FULL: out[t] = in[t]^E mod N_key, E = e (sel != 0) or d, S = nbits / 32.
-// CRT:  out[t][half] = in[t]^E mod (p | q) over S = nbits / 64 limbs, with
-//       E = d_p | d_q (sel == 0), or p - 2 | q - 2 (sel != 0: inverses mod p,
-//       q by Fermat's little theorem), 
-//       input reduced via in mod p = hi R + lo -> MontMul(hi, R^3) +
-//       MontMul(lo, R^2) = in R mod p.  Garner combines the halves afterwards.
+// CRT:  out[t][i] = in[t]^E mod r_i over S = nbits / (32 parts) limbs, with
+//       E = d mod (r_i - 1) (sel == 0), or r_i - 2 (sel != 0: inverses mod
+//       r_i by Fermat's little theorem); the input is reduced by crt_input.
+//       The recombination kernel combines the residues afterwards.
 template <int S, int TPI, bool CRT, int FORM>
 __global__ void __launch_bounds__(kThreads) k_modexp(const KeyDev *__restrict__ keys, uint32_t K,
                                                      const uint32_t *__restrict__ in, uint32_t *__restrict__ out,
-                                                     long long n, int sel) {
+                                                     long long n, int sel, int parts) {
   constexpr int L = S / TPI;
   constexpr int IPB = kThreads / TPI;
   constexpr int ROW = Layout<S>::kRow;
   constexpr int INST = Layout<S>::kInst;
-  constexpr int W = CRT ? 2 * S : S;  // limbs per chunk in memory
+  const int W = CRT ? parts * S : S;  // limbs per chunk in memory
   extern __shared__ __align__(16) uint32_t smem[];
   uint32_t *sR2 = smem, *sOne = smem + ROW, *sR3 = smem + 2 * ROW;
   const uint32_t r = threadIdx.x % TPI, g = threadIdx.x / TPI;
   uint32_t *tbl = smem + Layout<S>::kConstRows * ROW + g * INST;
   uint32_t *ybuf = tbl + kTableMax * ROW;
 
-  const uint32_t key = CRT ? blockIdx.y >> 1 : blockIdx.y;
-  const uint32_t half = CRT ? blockIdx.y & 1 : 0;
+  const uint32_t key = CRT ? blockIdx.y / (uint32_t)parts : blockIdx.y;
+  const uint32_t half = CRT ? blockIdx.y % (uint32_t)parts : 0;
   const long long first = key + (long long)blockIdx.x * IPB * K;
   if (first >= n) return;  // block-uniform: no instance of this block has a chunk
   const KeyDev &kd = keys[key];
@@ -65,17 +98,7 @@ __global__ void __launch_bounds__(kThreads) k_modexp(const KeyDev *__restrict__ 
     }
     mont<S, TPI, FORM>(a, sR2, nn, n0, r);  // x R mod N
   } else {
-    uint32_t lo[L];
-    if (active) {
-      load_slice_global<L>(lo, in + t * W, r);
-      load_slice_global<L>(a, in + t * W + S, r);
-    } else {
-#pragma unroll
-      for (int j = 0; j < L; j++) lo[j] = a[j] = 0;
-    }
-    mont<S, TPI, FORM>(a, sR3, nn, n0, r);   // hi R^2 mod p
-    mont<S, TPI, FORM>(lo, sR2, nn, n0, r);  // lo R mod p
-    mod_add<L, TPI>(a, lo, nn, r);         // (hi R + lo) R mod p
+    crt_input<S, TPI, FORM>(a, in + t * W, active, parts, sR2, sR3, nn, n0, r);
   }
   exp_window<S, TPI, FORM>(a, tbl, ybuf, sched, nsteps, maxidx, nn, n0, r);
   mont<S, TPI, FORM>(a, sOne, nn, n0, r);  // leave the Montgomery domain
@@ -93,8 +116,9 @@ __global__ void __launch_bounds__(kThreads) k_modexp(const KeyDev *__restrict__ 
 
 // Persistent form for batches: each warp repeatedly takes the next task from
 // a device counter.  A task is up to 32 / TPI chunks of one key of one job
-// (chunk first + i * stride), in one mode.  Keys differ from warp to warp, so
-// the constant rows (R^2, 1, R^3) live in each warp's own shared-memory area.
+// (chunk first + i * stride), in one mode (CRT residue i of a key with
+// nprimes primes: mode 2 + i).  Keys differ from warp to warp, so the
+// constant rows (R^2, 1, R^3) live in each warp's own shared-memory area.
 template <int S, int TPI, bool CRT, int FORM>
 __global__ void __launch_bounds__(kThreads) k_modexp_tasks(const BatchTask *__restrict__ tasks, int ntasks,
                                                            int *__restrict__ counter) {
@@ -102,7 +126,6 @@ __global__ void __launch_bounds__(kThreads) k_modexp_tasks(const BatchTask *__re
   constexpr int IPW = 32 / TPI;
   constexpr int ROW = Layout<S>::kRow;
   constexpr int INST = Layout<S>::kInst;
-  constexpr int W = CRT ? 2 * S : S;
   constexpr int WAREA = Layout<S>::kConstRows * ROW + IPW * INST;
   extern __shared__ __align__(16) uint32_t smem[];
   const uint32_t lane = threadIdx.x & 31, r = lane % TPI, g = lane / TPI;
@@ -117,8 +140,10 @@ __global__ void __launch_bounds__(kThreads) k_modexp_tasks(const BatchTask *__re
     if (ti >= ntasks) break;
     const BatchTask tk = tasks[ti];
     const KeyDev &kd = *tk.key;
-    const int half = tk.mode == 3 ? 1 : 0;
+    const int half = tk.mode >= 2 ? tk.mode - 2 : 0;
     const bool enc = tk.mode == 0;
+    const int parts = CRT ? (int)kd.nprimes : 1;
+    const int W = parts * S;
     const uint32_t *M = CRT ? kd.P[half] : kd.N;
     const uint32_t *R2 = CRT ? kd.R2h[half] : kd.R2;
     const uint32_t *sched = CRT ? kd.sched_h[half] : (enc ? kd.sched_e : kd.sched_d);
@@ -145,17 +170,7 @@ __global__ void __launch_bounds__(kThreads) k_modexp_tasks(const BatchTask *__re
       }
       mont<S, TPI, FORM>(a, sR2, nn, n0, r);
     } else {
-      uint32_t lo[L];
-      if (active) {
-        load_slice_global<L>(lo, tk.in + t * W, r);
-        load_slice_global<L>(a, tk.in + t * W + S, r);
-      } else {
-#pragma unroll
-        for (int j = 0; j < L; j++) lo[j] = a[j] = 0;
-      }
-      mont<S, TPI, FORM>(a, sR3, nn, n0, r);
-      mont<S, TPI, FORM>(lo, sR2, nn, n0, r);
-      mod_add<L, TPI>(a, lo, nn, r);
+      crt_input<S, TPI, FORM>(a, tk.in + t * W, active, parts, sR2, sR3, nn, n0, r);
     }
     exp_window<S, TPI, FORM>(a, tbl, ybuf, sched, nsteps, maxidx, nn, n0, r);
     mont<S, TPI, FORM>(a, sOne, nn, n0, r);

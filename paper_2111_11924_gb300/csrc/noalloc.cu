@@ -76,7 +76,7 @@ extern "C" int pmk_decrypt_message_host_noalloc(const pmk_keyset *ks, const uint
     uint32_t *d_plain = reinterpret_cast<uint32_t *>(base + kStatusBytes + chunk_bytes);
     uint8_t *d_msg = base + kStatusBytes + 2 * chunk_bytes;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const uint32_t S = ks->nbits / 32, H = S / 2;
+    const uint32_t S = ks->nbits / 32, B = ks->nprimes, H = S / B;
     // The array keeps the previous call's contents: the status word must start at zero.
     if (cudaMemsetAsync(d_status, 0, sizeof(uint32_t), st) != cudaSuccess ||
         cudaMemcpyAsync(d_cipher, h_cipher, words * 4, cudaMemcpyHostToDevice, st) != cudaSuccess) {
@@ -87,8 +87,11 @@ extern "C" int pmk_decrypt_message_host_noalloc(const pmk_keyset *ks, const uint
     if (rc == PMK_OK && !use_crt)
       rc = launch_modexp(ExpMode::kDecrypt, S, default_config(S, false), ks->d_keys, ks->K, d_cipher, d_plain, n_chunks, st);
     if (rc == PMK_OK && use_crt) {
-      rc = launch_modexp(ExpMode::kCrtHalf, H, default_config(H, true), ks->d_keys, ks->K, d_cipher, d_plain, n_chunks, st);
-      if (rc == PMK_OK) rc = launch_garner(H, ks->d_keys, ks->K, d_plain, n_chunks, st);
+      rc = launch_modexp(ExpMode::kCrtHalf, H, default_config(H, true), ks->d_keys, ks->K, d_cipher, d_plain, n_chunks,
+                         st, B);
+      if (rc == PMK_OK)
+        rc = B == 2 ? launch_garner(H, ks->d_keys, ks->K, d_plain, n_chunks, st)
+                    : launch_garner_mp(H, B, ks->d_keys, ks->K, d_plain, n_chunks, st);
     }
     if (rc == PMK_OK) rc = launch_join(ks->nbits, d_plain, n_chunks, d_msg, msg_len, st);
     if (rc != PMK_OK) break;

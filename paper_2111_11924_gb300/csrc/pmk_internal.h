@@ -25,16 +25,28 @@ struct Schedule {
   uint32_t maxidx = 0;  // table entries 0..maxidx are needed
 };
 
-// One key pair on the host, 32-bit little-endian limbs.
+// Most primes of one modulus (multi-prime RSA, Section 2.1).
+constexpr int kMaxPrimes = 4;
+
+// One key pair on the host, 32-bit little-endian limbs.  A key has b >= 2
+// primes r_0 .. r_{b-1} of h = s / b limbs each; p = r_0, q = r_1.
 struct HostKey {
-  std::vector<uint32_t> N, d, p, q, dp, dq, qinv;  // N, d: s limbs; the rest s/2
-  // Montgomery data, R = 2^(32 s) for N and R_h = 2^(32 s/2) for p, q.
-  uint32_t n0 = 0, n0h[2] = {0, 0};                 // -M^-1 mod 2^32
-  std::vector<uint32_t> R2;                          // R^2 mod N
-  std::vector<uint32_t> R2h[2], R3h[2];              // R_h^2, R_h^3 mod p | q
-  std::vector<uint32_t> qinv_m;                      // qinv * R_h mod p
-  Schedule sched_e, sched_d, sched_h[2];             // e, d, dp, dq
-  Schedule sched_hinv[2];                            // p - 2, q - 2 (Fermat inverses mod p, q)
+  uint32_t nprimes = 2;
+  std::vector<uint32_t> N, d, p, q, dp, dq, qinv;  // N, d: s limbs; the rest h
+  std::vector<uint32_t> pr[kMaxPrimes], dpr[kMaxPrimes];  // r_i and d mod (r_i - 1)
+  // CRT recombination, visiting r_1, r_0, r_2, r_3, ...: the running value
+  // starts at m_1; visiting r_i adds coef_i (m_i - m) mod r_i times prefix_i,
+  // the product of the primes visited before r_i (coef_0 = qinv,
+  // prefix_0 = r_1; coef_i = (r_0 ... r_{i-1})^-1 mod r_i, prefix_i =
+  // r_0 ... r_{i-1} for i >= 2; entry 1 is unused).
+  std::vector<uint32_t> coef[kMaxPrimes], prefix[kMaxPrimes];
+  // Montgomery data, R = 2^(32 s) for N and R_h = 2^(32 h) for the primes.
+  uint32_t n0 = 0, n0h[kMaxPrimes] = {};               // -M^-1 mod 2^32
+  std::vector<uint32_t> R2;                            // R^2 mod N
+  std::vector<uint32_t> R2h[kMaxPrimes], R3h[kMaxPrimes];  // R_h^2, R_h^3 mod r_i
+  std::vector<uint32_t> qinv_m;                        // qinv * R_h mod p
+  Schedule sched_e, sched_d, sched_h[kMaxPrimes];      // e, d, d mod (r_i - 1)
+  Schedule sched_hinv[kMaxPrimes];                     // r_i - 2 (Fermat inverses mod r_i)
 };
 
 // Device view of one key (pointers into the key set's device blob).
@@ -43,16 +55,19 @@ struct KeyDev {
   const uint32_t *R2;
   const uint32_t *sched_e;
   const uint32_t *sched_d;
-  const uint32_t *P[2];
-  const uint32_t *R2h[2];
-  const uint32_t *R3h[2];
-  const uint32_t *sched_h[2];
+  const uint32_t *P[kMaxPrimes];
+  const uint32_t *R2h[kMaxPrimes];
+  const uint32_t *R3h[kMaxPrimes];
+  const uint32_t *sched_h[kMaxPrimes];
   const uint32_t *qinv_m;
-  const uint32_t *sched_hinv[2];
+  const uint32_t *sched_hinv[kMaxPrimes];
+  const uint32_t *coef[kMaxPrimes];
+  const uint32_t *prefix[kMaxPrimes];
   const uint32_t *e_limbs, *d_limbs;  // e (2 limbs) and d (s limbs), for the thread-per-chunk baseline
-  uint32_t n0, n0h[2];
-  uint32_t nsteps_e, nsteps_d, nsteps_h[2], nsteps_hinv[2];
-  uint32_t maxidx_e, maxidx_d, maxidx_h[2], maxidx_hinv[2];
+  uint32_t nprimes;
+  uint32_t n0, n0h[kMaxPrimes];
+  uint32_t nsteps_e, nsteps_d, nsteps_h[kMaxPrimes], nsteps_hinv[kMaxPrimes];
+  uint32_t maxidx_e, maxidx_d, maxidx_h[kMaxPrimes], maxidx_hinv[kMaxPrimes];
 };
 
 // One unit of work of the persistent batch kernels: up to 32 / TPI chunks
@@ -63,11 +78,13 @@ struct BatchTask {
   uint32_t *out;
   long long first, stride;
   int count;
-  int mode;  // 0 encrypt, 1 full-d decrypt, 2 / 3 CRT half p / q
+  int mode;  // 0 encrypt, 1 full-d decrypt, 2 + i: CRT residue mod prime r_i
 };
 
 // Host keygen (keygen.cpp).
 int host_keygen(uint32_t K, uint32_t nbits, uint64_t e, uint64_t seed, std::vector<HostKey> &out);
+int host_keygen_mp(uint32_t K, uint32_t nbits, uint32_t nprimes, uint64_t e, uint64_t seed, std::vector<HostKey> &out);
+bool valid_multiprime(uint32_t nbits, uint32_t nprimes);
 int host_from_primes(uint32_t nbits, uint64_t e, const uint32_t *p, const uint32_t *q, HostKey &out);
 Schedule make_schedule(const uint32_t *exp, int nlimbs);
 
@@ -82,10 +99,16 @@ int launch_range_check(const KeyDev *keys, uint32_t K, uint32_t s, const uint32_
 struct KernelConfig {
   uint32_t tpi = 0, form = 0;
 };
+// CRT modes run `parts` residues per chunk (the key's prime count) over
+// `limbs` = s / parts limbs each; residue i of chunk t goes to out[t][i * limbs].
 int launch_modexp(ExpMode mode, uint32_t limbs, KernelConfig cfg, const KeyDev *keys, uint32_t K, const uint32_t *in,
-                  uint32_t *out, size_t n, cudaStream_t st);
+                  uint32_t *out, size_t n, cudaStream_t st, uint32_t parts = 2);
 int launch_garner(uint32_t half_limbs, const KeyDev *keys, uint32_t K, uint32_t *out, size_t n, cudaStream_t st,
                   uint32_t *status_if_zero_half = nullptr);
+// Recombination of `parts` >= 2 residues of prime_limbs limbs each, in place
+// (out[t] holds the residues and receives m); the two-prime case may use either.
+int launch_garner_mp(uint32_t prime_limbs, uint32_t parts, const KeyDev *keys, uint32_t K, uint32_t *out, size_t n,
+                     cudaStream_t st, uint32_t *status_if_zero_residue = nullptr);
 // out[t] = a[t] * b[t] mod N_{t mod K} (full width; out may alias a or b)
 int launch_mulmod(uint32_t limbs, const KeyDev *keys, uint32_t K, const uint32_t *a, const uint32_t *b, uint32_t *out,
                   size_t n, cudaStream_t st);
@@ -109,6 +132,7 @@ int measure_int_peak(double *macs_per_clk_per_sm, double *sm_mhz, int *num_sms);
 struct pmk_keyset {
   int device = 0;
   uint32_t K = 0, nbits = 0;
+  uint32_t nprimes = 2;                    // primes per modulus
   uint64_t e = 0;
   std::vector<pmk::HostKey> keys;
   uint32_t *d_blob = nullptr;              // every key's limbs and schedules

@@ -16,7 +16,7 @@ extern "C" int pmk_autotune(pmk_ctx *ctx, const pmk_keyset *ks, size_t n_chunks,
   if (!ctx || !ks || n_chunks == 0 || mode < 0 || mode > 2) return PMK_EINVAL;
   const bool crt = mode == 2;
   const uint32_t S = ks->nbits / 32;
-  const uint32_t limbs = crt ? S / 2 : S;
+  const uint32_t limbs = crt ? S / ks->nprimes : S;
   const pmk::ExpMode em = mode == 0 ? pmk::ExpMode::kEncrypt : (crt ? pmk::ExpMode::kCrtHalf : pmk::ExpMode::kDecrypt);
   reps = std::max(1, std::min(reps, 20));
   std::vector<pmk::KernelConfig> cfgs(64);
@@ -43,7 +43,7 @@ extern "C" int pmk_autotune(pmk_ctx *ctx, const pmk_keyset *ks, size_t n_chunks,
     float t_min = 0;
     for (int r = 0; r <= reps && rc == PMK_OK; r++) {  // r = 0 warms up
       cudaEventRecord(e0, 0);
-      rc = pmk::launch_modexp(em, limbs, cfgs[c], ks->d_keys, ks->K, d_in, d_out, n_chunks, 0);
+      rc = pmk::launch_modexp(em, limbs, cfgs[c], ks->d_keys, ks->K, d_in, d_out, n_chunks, 0, ks->nprimes);
       cudaEventRecord(e1, 0);
       if (rc == PMK_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = PMK_ECUDA;
       float t = 0;

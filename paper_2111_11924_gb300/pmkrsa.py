@@ -52,6 +52,10 @@ def load_library() -> ctypes.CDLL:
         "pmk_keygen_host": (i, [u32, u32, u64, u64, P32, P32, P32, P32, P32, P32, P32]),
         "pmk_keyset_from_primes": (i, [vp, u32, u32, u64, P32, P32, ctypes.POINTER(vp)]),
         "pmk_keyset_export": (i, [vp, P32, P32, P32, P32, P32, P32, P32]),
+        "pmk_keygen_multiprime": (i, [vp, u32, u32, u32, u64, u64, ctypes.POINTER(vp)]),
+        "pmk_keygen_host_multiprime": (i, [u32, u32, u32, u64, u64, P32, P32, P32, P32, P32]),
+        "pmk_keyset_export_primes": (i, [vp, P32, P32, P32]),
+        "pmk_keyset_num_primes": (u32, [vp]),
         "pmk_keyset_num_keys": (u32, [vp]),
         "pmk_keyset_nbits": (u32, [vp]),
         "pmk_keyset_e": (u64, [vp]),
@@ -127,6 +131,20 @@ def keygen_host(K: int, nbits: int, e: int = 65537, seed: int = 0) -> dict:
     return arrs
 
 
+_MP_FIELDS = ("N", "d", "primes", "dexp", "coef")
+
+
+def keygen_host_multiprime(K: int, nbits: int, nprimes: int, e: int = 65537, seed: int = 0) -> dict:
+    """Multi-prime key initialisation on the host only: N, d, primes, dexp,
+    coef as (K, nbits/32) uint32 arrays (the prime fields hold b values of
+    nbits/(32 b) limbs each)."""
+    arrs = {f: np.zeros((K, nbits // 32), np.uint32) for f in _MP_FIELDS}
+    _check(load_library().pmk_keygen_host_multiprime(K, nbits, nprimes, e, seed & (2**64 - 1),
+                                                     *[_p32(arrs[f]) for f in _MP_FIELDS]),
+           "pmk_keygen_host_multiprime")
+    return arrs
+
+
 def _torch():
     import torch
 
@@ -143,6 +161,7 @@ class KeySet:
         self.K = int(lib.pmk_keyset_num_keys(handle))
         self.nbits = int(lib.pmk_keyset_nbits(handle))
         self.e = int(lib.pmk_keyset_e(handle))
+        self.nprimes = int(lib.pmk_keyset_num_primes(handle))
         self.limbs = self.nbits // 32
 
     @property
@@ -152,8 +171,18 @@ class KeySet:
         return self._h
 
     def export(self) -> dict:
+        """Key material as host arrays: N, d, p, q, dp, dq, qinv for a two-prime
+        key set; N, d, primes, dexp, coef for a multi-prime one."""
+        lib = load_library()
+        if self.nprimes != 2:
+            arrs = {f: np.zeros((self.K, self.limbs), np.uint32) for f in _MP_FIELDS}
+            _check(lib.pmk_keyset_export(self.handle, _p32(arrs["N"]), _p32(arrs["d"]), None, None, None, None, None),
+                   "export")
+            _check(lib.pmk_keyset_export_primes(self.handle, _p32(arrs["primes"]), _p32(arrs["dexp"]),
+                                                _p32(arrs["coef"])), "export_primes")
+            return arrs
         arrs = _key_arrays(self.K, self.nbits)
-        _check(load_library().pmk_keyset_export(self.handle, *[_p32(arrs[f]) for f in _KEY_FIELDS]), "export")
+        _check(lib.pmk_keyset_export(self.handle, *[_p32(arrs[f]) for f in _KEY_FIELDS]), "export")
         return arrs
 
     def free(self) -> None:
@@ -213,9 +242,15 @@ class Context:
         return ctypes.c_void_p(t.data_ptr())
 
     # ------------------------------------------------------------ keys
-    def keygen(self, K: int, nbits: int, e: int = 65537, seed: int = 0) -> KeySet:
+    def keygen(self, K: int, nbits: int, e: int = 65537, seed: int = 0, nprimes: int = 2) -> KeySet:
+        """K key pairs; nprimes > 2 gives multi-prime keys (Section 2.1)."""
         h = ctypes.c_void_p()
-        _check(load_library().pmk_keygen(self.handle, K, nbits, e, seed & (2**64 - 1), ctypes.byref(h)), "pmk_keygen")
+        if nprimes == 2:
+            _check(load_library().pmk_keygen(self.handle, K, nbits, e, seed & (2**64 - 1), ctypes.byref(h)),
+                   "pmk_keygen")
+        else:
+            _check(load_library().pmk_keygen_multiprime(self.handle, K, nbits, nprimes, e, seed & (2**64 - 1),
+                                                        ctypes.byref(h)), "pmk_keygen_multiprime")
         return KeySet(self, h)
 
     def keyset_from_primes(self, nbits: int, e: int, p: np.ndarray, q: np.ndarray) -> KeySet:

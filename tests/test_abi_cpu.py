@@ -75,6 +75,36 @@ def test_keygen_argument_errors(P):
             P.keygen_host(*bad, seed=1)
 
 
+@pytest.mark.parametrize("K,nbits,b,e,seed", [(3, 384, 3, 65537, 1), (2, 512, 4, 65537, 2), (2, 768, 3, 3, 3),
+                                              (2, 1536, 3, 65537, 4), (1, 2048, 4, 17, 5), (2, 512, 2, 65537, 6),
+                                              (1, 3072, 3, 65537, 7)])
+def test_library_multiprime_keygen_matches_oracle(P, K, nbits, b, e, seed):
+    """Multi-prime key initialisation (Section 2.1): the library's keys equal
+    the oracle's limb for limb (primes, N, d, d mod (r_i - 1), the
+    recombination coefficients)."""
+    lib_keys = P.keygen_host_multiprime(K, nbits, b, e, seed)
+    ok = oracle.keygen_mp(K, nbits, b, e, seed)
+    for f in ok.a:
+        assert np.array_equal(lib_keys[f], ok.a[f]), f
+
+
+def test_multiprime_two_primes_equal_keygen(P):
+    mp = P.keygen_host_multiprime(3, 1024, 2, 65537, 9)
+    two = P.keygen_host(3, 1024, 65537, 9)
+    h = 16
+    assert np.array_equal(mp["N"], two["N"]) and np.array_equal(mp["d"], two["d"])
+    assert np.array_equal(mp["primes"][:, :h], two["p"]) and np.array_equal(mp["primes"][:, h:], two["q"])
+    assert np.array_equal(mp["coef"][:, :h], two["qinv"])
+
+
+def test_multiprime_keygen_argument_errors(P):
+    for bad in [(1, 2048, 3), (1, 768, 5), (1, 768, 1), (1, 640, 4), (0, 768, 3), (16384, 768, 3), (1, 9216, 3)]:
+        with pytest.raises(P.PMKError):
+            P.keygen_host_multiprime(*bad, e=65537, seed=1)
+    with pytest.raises(P.PMKError):
+        P.keygen_host_multiprime(1, 768, 3, e=4, seed=1)
+
+
 def test_no_context_without_gpu(P):
     import torch
 

@@ -86,3 +86,19 @@ def test_noalloc_rejects_requests_beyond_its_capacity(setup):
                                                            ctypes.c_void_p(out.ctypes.data), length, 0, None)
     assert rc == P.pmkrsa.PMK_ETOOLARGE
     assert "capacity" in P.strerror(rc)
+
+
+def test_noalloc_multiprime_key_set(setup):
+    """The allocation-free call on a 3-prime key set (CRT over three primes)
+    equals the allocating call and recovers the message."""
+    P, ctx, _, _ = setup
+    ks = ctx.keygen(4, 3072, 65537, 0x50444D4B0000EA00, nprimes=3)
+    msg = torch.from_numpy(np.random.default_rng(8).integers(0, 256, 200_003, dtype=np.uint8)).pin_memory()
+    cipher = _cipher_of(ctx, ks, msg)
+    for use_crt in (False, True):
+        ref = torch.zeros_like(msg).pin_memory()
+        ctx.decrypt_message_host(ks, cipher, ref, use_crt=use_crt)
+        out = torch.full_like(msg, 0x5A).pin_memory()
+        assert P.pmkrsa.decrypt_message_host_noalloc(ks, cipher, out, use_crt=use_crt) == P.pmkrsa.PMK_OK
+        assert torch.equal(out, ref) and torch.equal(out, msg), use_crt
+    ks.free()
