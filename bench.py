@@ -41,8 +41,8 @@ KERNELS_PER_STEP = 6  # split, range check + modexp (encrypt), range check + mod
 
 # DRAM traffic of the full-d decryption kernel from one ncu capture, valid only
 # for the kernel sources it was measured on (see profiles/).
-TRAFFIC_SOURCES = ["paper_2111_11924_gb300/csrc/modexp_core.cuh", "paper_2111_11924_gb300/csrc/modexp_kernels.cuh"]
-TRAFFIC_MEASURED = {"6d95cf60cabb65f0": 1111296}  # source digest -> bytes per launch (profiles/)
+TRAFFIC_SOURCES = ["paper_2111_11924_gb300/csrc/modexp_core.cuh", "paper_2111_11924_gb300/csrc/modexp_grid.cuh"]
+TRAFFIC_MEASURED = {"d3366a023babd93b": 1112064}  # source digest -> bytes per launch (profiles/)
 
 
 def sources_digest() -> str:
@@ -395,9 +395,12 @@ def run_ours(args):
     if rank == 0 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
         r = oracle_sample(args.ref_sample, threads)
+        r1 = oracle_sample(max(8, args.ref_sample // 16), 1)
         line["cpu_baseline"] = {"value": r["value"], "unit": UNIT, "cores": threads, "kind": "oracle",
                                 "sample": f"first {r['chunks']} chunks of the workload (oracle split+encrypt+"
-                                          f"decrypt+join), {r['seconds']:.1f} s on {threads} threads"}
+                                          f"decrypt+join), {r['seconds']:.1f} s on {threads} threads",
+                                "single_thread": {"value": r1["value"], "unit": UNIT, "cores": 1,
+                                                  "sample": f"first {r1['chunks']} chunks, {r1['seconds']:.1f} s"}}
     if rank == 0:
         print(json.dumps(line))
     ks.free()
@@ -571,6 +574,68 @@ def run_batched(args):
     return 0 if same else 1
 
 
+def run_file100(args):
+    """The 100 MiB file with K = 16 2048-bit keys: full-d and CRT decryption
+    of all 411,207 chunks as one plain launch per call, and the same job
+    through the persistent graph-replayed batch path (pmk_batch), with the
+    full round trip (split, encrypt, decrypt, join) checked on both."""
+    import torch
+
+    import paper_2111_11924_gb300 as P
+    from paper_2111_11924_gb300 import pmkrsa as B
+
+    w = W.FILE_100MIB_2048
+    ctx = P.Context(0)
+    ks = ctx.keygen(w.K, w.nbits, w.e, w.key_seed)
+    d_msg = torch.from_numpy(w.message()).cuda()
+    n = w.n_chunks
+    chunks = ctx.split(w.nbits, d_msg)
+    cipher = ctx.encrypt_chunks(ks, chunks)
+    out = torch.empty_like(chunks)
+    tuned = {m: ctx.autotune(ks, n, m, reps=1) for m in ("decrypt", "crt")}
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    res = {}
+    for name, crt, op in (("full_d", False, B.OP_DECRYPT), ("crt", True, B.OP_DECRYPT_CRT)):
+        out.zero_()
+        t_plain = timed(lambda: ctx.decrypt_chunks(ks, cipher, use_crt=crt, out=out), args.steps)
+        ok_plain = bool(torch.equal(out, chunks))
+        back = ctx.join(w.nbits, out, w.msg_bytes)
+        roundtrip = bool(torch.equal(back, d_msg))
+        out.zero_()
+        batch = ctx.batch([(ks, cipher, out, op)])
+        t_batch = timed(batch.launch, args.steps)
+        ok_batch = bool(torch.equal(out, chunks))
+        res[name] = {"plain_ms": round(t_plain, 3), "batched_ms": round(t_batch, 3),
+                     "plain_chunk_modexps_per_s": round(n / (t_plain / 1e3)),
+                     "batched_chunk_modexps_per_s": round(n / (t_batch / 1e3)),
+                     "plain_MBps": round(w.msg_bytes / 2**20 / (t_plain / 1e3), 2),
+                     "batched_MBps": round(w.msg_bytes / 2**20 / (t_batch / 1e3), 2),
+                     "batched_over_plain": round(t_plain / t_batch, 3), "persistent_kernels": batch.n_kernels,
+                     "tasks": batch.n_tasks, "outputs_equal_message_chunks": ok_plain and ok_batch,
+                     "join_roundtrip": roundtrip,
+                     "geometry": [tuned["crt" if crt else "decrypt"]["tpi"],
+                                  ["chain", "columns"][tuned["crt" if crt else "decrypt"]["form"]]]}
+        batch.destroy()
+    ctx.check()
+    print(json.dumps({"mode": "file100", "workload": w.name, "chunks": n, "keys": w.K, "key_bits": w.nbits,
+                      "inputs": "resident in HBM (larger than L2)"} | res))
+    ok = all(r["outputs_equal_message_chunks"] and r["join_roundtrip"] for r in res.values())
+    return 0 if ok else 1
+
+
 def run_serving(args):
     """The serving workload: Poisson arrivals (--serve-rate per second) of
     encrypt / decrypt requests (70% decrypt, CRT form), payloads log-uniform
@@ -732,6 +797,8 @@ def main(argv=None):
     ap.add_argument("--widths", action="store_true",
                     help="time the 100 KB / K=16 workload at each key length and exit")
     ap.add_argument("--width-list", type=int, nargs="*", default=[1024, 2048, 3072, 4096, 6144, 8192])
+    ap.add_argument("--file100", action="store_true",
+                    help="100 MiB / K=16 decryption: one plain launch per call vs the persistent batch path, and exit")
     ap.add_argument("--multiprime", action="store_true",
                     help="time multi-prime CRT decryption (1 MiB, K = 8) against two primes and exit")
     ap.add_argument("--mp-list", type=lambda v: tuple(int(x) for x in v.split(":")), nargs="*",
@@ -753,6 +820,8 @@ def main(argv=None):
         return run_hbm(args)
     if args.multiprime:
         return run_multiprime(args)
+    if args.file100:
+        return run_file100(args)
     return run_reference(args) if args.impl == "reference" else run_ours(args)
 
 

@@ -73,9 +73,8 @@ int pmk_keygen(pmk_ctx *ctx, uint32_t K, uint32_t nbits, uint64_t e, uint64_t se
  * byte is below the least T with T^b >= 2^(8b - 1), and a prime equal to an
  * earlier one is redrawn.  nprimes = 2 gives pmk_keygen's keys.
  * pmk_decrypt_chunks with use_crt then computes one residue per prime and
- * recombines them (the CRT-RSA equation of Section 2.1 for r_0, r_1,
- * extended one prime at a time); encryption and full-d decryption are
- * unchanged.
+ * recombines them (the Chinese remainder theorem of Section 2.1);
+ * encryption and full-d decryption are unchanged.
  *   nprimes: 2..4;  nbits: a multiple of 128 and of 64 nprimes, <= 8192
  *   (EINVAL otherwise; EUNSUPPORTED if nbits/(32 nprimes) limbs are not built).
  */
@@ -160,8 +159,8 @@ int pmk_encrypt_chunks(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_in,
  * d_out[t] = d_in[t]^{d_k} mod N_k, k = t mod K.  use_crt = 0: one
  * full-width exponentiation; use_crt = 1: the CRT form of Section 2.1
  * (one exponentiation per prime over nbits/b bits -- two halves for an
- * ordinary key, b for a multi-prime key -- and Garner's recombination),
- * bit-identical.  With use_crt = 1, d_in and d_out must not overlap.
+ * ordinary key, b for a multi-prime key -- then the CRT recombination
+ * sum_i m_i c_i mod N, c_i = (N/r_i) ((N/r_i)^-1 mod r_i)), bit-identical.  With use_crt = 1, d_in and d_out must not overlap.
  */
 int pmk_decrypt_chunks(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_in, uint32_t *d_out,
                        size_t n_chunks, int use_crt, void *stream);
@@ -190,10 +189,10 @@ int pmk_encrypt_blinded(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_m,
 /*
  * PMKRSA decryption with R (Algorithm 1 "Decryption"): the paper computes
  * r' = c_r^d, m* = c*^d, m' = m* r'^-1 (mod N).  This library computes the
- * same residue as m' = (c* c_r^-1)^d: the inverse of c_r comes from two
- * half-width Fermat exponentiations (c_r^(p-2) mod p, c_r^(q-2) mod q) and
- * Garner's recombination, followed by one exponentiation by d (full width,
- * or the Section 2.1 CRT form with use_crt = 1).  A c_r sharing a factor
+ * same residue as m' = (c* c_r^-1)^d: the inverse of c_r comes from one
+ * Fermat exponentiation per prime (c_r^(r_i - 2) mod r_i: p and q for an
+ * ordinary key) and their CRT recombination, followed by one exponentiation
+ * by d (full width, or the Section 2.1 CRT form with use_crt = 1).  A c_r sharing a factor
  * with N reports PMK_ENOINV through pmk_status.  Buffers must not overlap.
  */
 int pmk_decrypt_blinded(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_cstar, const uint32_t *d_cr,

@@ -66,7 +66,7 @@ int upload(pmk_keyset *ks) {
   std::vector<uint32_t> blob;
   struct Offs {
     size_t N, R2, se, sd, P[pmk::kMaxPrimes], R2h[pmk::kMaxPrimes], R3h[pmk::kMaxPrimes], sh[pmk::kMaxPrimes],
-        shi[pmk::kMaxPrimes], cf[pmk::kMaxPrimes], pf[pmk::kMaxPrimes], qm, el, dl;
+        shi[pmk::kMaxPrimes], cs[pmk::kMaxPrimes], el, dl;
   };
   std::vector<Offs> offs(ks->K);
   for (uint32_t k = 0; k < ks->K; k++) {
@@ -82,10 +82,8 @@ int upload(pmk_keyset *ks) {
       o.R3h[i] = push(blob, h.R3h[i]);
       o.sh[i] = push(blob, h.sched_h[i].steps);
       o.shi[i] = push(blob, h.sched_hinv[i].steps);
-      o.cf[i] = push(blob, h.coef[i]);
-      o.pf[i] = push(blob, h.prefix[i]);
+      o.cs[i] = push(blob, h.crt_sum[i]);
     }
-    o.qm = push(blob, h.qinv_m);
     o.el = push(blob, {(uint32_t)ks->e, (uint32_t)(ks->e >> 32)});
     o.dl = push(blob, h.d);
   }
@@ -101,7 +99,6 @@ int upload(pmk_keyset *ks) {
     d.R2 = b + o.R2;
     d.sched_e = b + o.se;
     d.sched_d = b + o.sd;
-    d.qinv_m = b + o.qm;
     d.e_limbs = b + o.el;
     d.d_limbs = b + o.dl;
     d.n0 = h.n0;
@@ -111,12 +108,11 @@ int upload(pmk_keyset *ks) {
     d.maxidx_d = h.sched_d.maxidx;
     d.nprimes = h.nprimes;
     for (int i = 0; i < pmk::kMaxPrimes; i++) {
-      d.P[i] = d.R2h[i] = d.R3h[i] = d.sched_h[i] = d.sched_hinv[i] = d.coef[i] = d.prefix[i] = nullptr;
+      d.P[i] = d.R2h[i] = d.R3h[i] = d.sched_h[i] = d.sched_hinv[i] = d.crt_sum[i] = nullptr;
       d.n0h[i] = d.nsteps_h[i] = d.maxidx_h[i] = d.nsteps_hinv[i] = d.maxidx_hinv[i] = 0;
     }
     for (uint32_t i = 0; i < h.nprimes; i++) {
-      d.coef[i] = b + o.cf[i];
-      d.prefix[i] = b + o.pf[i];
+      d.crt_sum[i] = b + o.cs[i];
       d.P[i] = b + o.P[i];
       d.R2h[i] = b + o.R2h[i];
       d.R3h[i] = b + o.R3h[i];
@@ -174,8 +170,7 @@ int enqueue_crt(pmk_ctx *ctx, const pmk_keyset *ks, pmk::ExpMode mode, const uin
   const uint32_t b = ks->nprimes, H = ks->nbits / 32 / b;
   int rc = pmk::launch_modexp(mode, H, cfg_for(ctx, H, true), ks->d_keys, ks->K, in, out, n, st, b);
   if (rc != PMK_OK) return rc;
-  if (b == 2) return pmk::launch_garner(H, ks->d_keys, ks->K, out, n, st, status_if_zero);
-  return pmk::launch_garner_mp(H, b, ks->d_keys, ks->K, out, n, st, status_if_zero);
+  return pmk::launch_crt_sum(ks->nbits / 32, b, ks->d_keys, ks->K, out, n, st, status_if_zero);
 }
 
 int enqueue_decrypt(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *in, uint32_t *out, size_t n, int use_crt,

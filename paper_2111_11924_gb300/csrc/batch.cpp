@@ -145,9 +145,8 @@ int plan_and_capture(pmk_ctx *ctx, const pmk_job *jobs, size_t n_jobs, pmk_batch
   for (size_t j = 0; j < n_jobs && rc == PMK_OK; j++)
     if (jobs[j].n_chunks && jobs[j].op == PMK_OP_DECRYPT_CRT) {
       const pmk_keyset *ks = jobs[j].ks;
-      const uint32_t B = ks->nprimes, H = ks->nbits / 32 / B;
-      rc = B == 2 ? pmk::launch_garner(H, ks->d_keys, ks->K, jobs[j].d_out, jobs[j].n_chunks, b->capture)
-                  : pmk::launch_garner_mp(H, B, ks->d_keys, ks->K, jobs[j].d_out, jobs[j].n_chunks, b->capture);
+      rc = pmk::launch_crt_sum(ks->nbits / 32, ks->nprimes, ks->d_keys, ks->K, jobs[j].d_out, jobs[j].n_chunks,
+                               b->capture);
     }
   cudaGraph_t graph = nullptr;
   const cudaError_t end = cudaStreamEndCapture(b->capture, &graph);

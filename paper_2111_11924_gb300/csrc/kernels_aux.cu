@@ -1,5 +1,6 @@
-// Split / join (HBM-bound byte <-> limb repacking), the input range check and
-// Garner's CRT recombination, plus the launcher of the exponentiation kernels.
+// Split / join (HBM-bound byte <-> limb repacking), the input range check, the
+// thread-per-chunk baseline, and the launchers of the exponentiation,
+// modular-multiplication and CRT-recombination kernels.
 #include <algorithm>
 #include <mutex>
 #include <set>
@@ -145,107 +146,6 @@ __global__ void __launch_bounds__(kAuxThreads) k_range(const KeyDev *__restrict_
   if (ge) atomicOr(status, kStatusRange);
 }
 
-// Garner's recombination (Section 2.1 CRT equations): with m_p in the low half
-// of out[t] and m_q in the high half, out[t] <- m_q + q ((m_p - m_q) qinv mod p).
-// One thread per chunk; arrays sit in local memory (this kernel is a
-// negligible share of the CRT decryption).
-//
-// With `status` set, a zero half (the input was divisible by p or q, so it
-// has no inverse when the halves are Fermat inverses) is flagged as
-// kStatusNotInvertible.
-__global__ void __launch_bounds__(kAuxThreads) k_garner(const KeyDev *__restrict__ keys, uint32_t K, int H,
-                                                        uint32_t *__restrict__ out, long long n,
-                                                        uint32_t *__restrict__ status) {
-  const long long t = (long long)blockIdx.x * kAuxThreads + threadIdx.x;
-  if (t >= n) return;
-  const KeyDev &kd = keys[t % K];
-  const uint32_t *p = kd.P[0], *q = kd.P[1], *qm = kd.qinv_m;
-  const uint32_t n0 = kd.n0h[0];
-  uint32_t *o = out + t * 2 * H;
-  if (status) {
-    uint32_t any_p = 0, any_q = 0;
-    for (int i = 0; i < H; i++) {
-      any_p |= o[i];
-      any_q |= o[H + i];
-    }
-    if (!any_p || !any_q) atomicOr(status, kStatusNotInvertible);
-  }
-  uint32_t mq[128], d[128], acc[256];
-  // mq mod p: m_q < q < 2p, so at most one subtraction
-  uint32_t borrow = 0;
-  for (int i = 0; i < H; i++) {
-    const uint64_t s = (uint64_t)o[H + i] - p[i] - borrow;
-    d[i] = (uint32_t)s;
-    borrow = (uint32_t)(s >> 63);
-    mq[i] = o[H + i];
-  }
-  if (!borrow)
-    for (int i = 0; i < H; i++) mq[i] = d[i];
-  // d = (m_p - (m_q mod p)) mod p
-  borrow = 0;
-  for (int i = 0; i < H; i++) {
-    const uint64_t s = (uint64_t)o[i] - mq[i] - borrow;
-    d[i] = (uint32_t)s;
-    borrow = (uint32_t)(s >> 63);
-  }
-  if (borrow) {
-    uint64_t c = 0;
-    for (int i = 0; i < H; i++) {
-      c += (uint64_t)d[i] + p[i];
-      d[i] = (uint32_t)c;
-      c >>= 32;
-    }
-  }
-  // h = MontMul(d, qinv R mod p) = d qinv mod p  (CIOS, single thread)
-  for (int i = 0; i < H + 2; i++) acc[i] = 0;
-  for (int i = 0; i < H; i++) {
-    uint64_t c = 0;
-    for (int j = 0; j < H; j++) {
-      c += (uint64_t)d[j] * qm[i] + acc[j];
-      acc[j] = (uint32_t)c;
-      c >>= 32;
-    }
-    c += acc[H];
-    acc[H] = (uint32_t)c;
-    acc[H + 1] = (uint32_t)(c >> 32);
-    const uint32_t m = acc[0] * n0;
-    c = ((uint64_t)m * p[0] + acc[0]) >> 32;
-    for (int j = 1; j < H; j++) {
-      c += (uint64_t)m * p[j] + acc[j];
-      acc[j - 1] = (uint32_t)c;
-      c >>= 32;
-    }
-    c += acc[H];
-    acc[H - 1] = (uint32_t)c;
-    acc[H] = acc[H + 1] + (uint32_t)(c >> 32);
-  }
-  // conditional subtraction -> h < p, into d
-  borrow = 0;
-  for (int i = 0; i < H; i++) {
-    const uint64_t s = (uint64_t)acc[i] - p[i] - borrow;
-    d[i] = (uint32_t)s;
-    borrow = (uint32_t)(s >> 63);
-  }
-  if (acc[H] == 0 && borrow)
-    for (int i = 0; i < H; i++) d[i] = acc[i];
-  // out = m_q + h q  (m_q re-read: it is the original high half)
-  for (int i = 0; i < 2 * H; i++) acc[i] = i < H ? o[H + i] : 0;
-  for (int i = 0; i < H; i++) {
-    uint64_t c = 0;
-    for (int j = 0; j < H; j++) {
-      c += (uint64_t)d[i] * q[j] + acc[i + j];
-      acc[i + j] = (uint32_t)c;
-      c >>= 32;
-    }
-    for (int j = i + H; j < 2 * H && c; j++) {
-      c += acc[j];
-      acc[j] = (uint32_t)c;
-      c >>= 32;
-    }
-  }
-  for (int i = 0; i < 2 * H; i++) o[i] = acc[i];
-}
-
 // The plain GPU formulation, kept as a measured baseline: one thread per
 // chunk, its S-limb values in local memory, single-thread CIOS Montgomery
 // products and Algorithm 2's binary exponentiation (right-to-left, as printed).
@@ -382,171 +282,6 @@ int launch_range_check(const KeyDev *keys, uint32_t K, uint32_t s, const uint32_
   return cuda_rc(cudaGetLastError());
 }
 
-int launch_garner(uint32_t half_limbs, const KeyDev *keys, uint32_t K, uint32_t *out, size_t n, cudaStream_t st,
-                  uint32_t *status_if_zero_half) {
-  if (n == 0) return PMK_OK;
-  if (half_limbs > 128) return PMK_EUNSUPPORTED;
-  k_garner<<<(unsigned)((n + kAuxThreads - 1) / kAuxThreads), kAuxThreads, 0, st>>>(keys, K, (int)half_limbs, out,
-                                                                                    (long long)n, status_if_zero_half);
-  return cuda_rc(cudaGetLastError());
-}
-
-// ---------------------------------------------------------------- multi-prime recombination
-// Single-thread helpers over H limbs (H <= kGarnerMaxH) modulo an odd prime r.
-
-constexpr int kGarnerMaxH = 128, kGarnerMaxS = 256;
-
-// out = a b R_h^-1 mod r (CIOS, R_h = 2^(32 H)); a < R_h, b < r.  out may alias a.
-__device__ void mm_1t(uint32_t *out, const uint32_t *a, const uint32_t *b, const uint32_t *__restrict__ r, uint32_t n0,
-                      int H) {
-  uint32_t acc[kGarnerMaxH + 2];
-  for (int i = 0; i < H + 2; i++) acc[i] = 0;
-  for (int i = 0; i < H; i++) {
-    const uint32_t bi = b[i];
-    uint64_t c = 0;
-    for (int j = 0; j < H; j++) {
-      c += (uint64_t)a[j] * bi + acc[j];
-      acc[j] = (uint32_t)c;
-      c >>= 32;
-    }
-    c += acc[H];
-    acc[H] = (uint32_t)c;
-    acc[H + 1] = (uint32_t)(c >> 32);
-    const uint32_t m = acc[0] * n0;
-    c = ((uint64_t)m * __ldg(r) + acc[0]) >> 32;
-    for (int j = 1; j < H; j++) {
-      c += (uint64_t)m * __ldg(r + j) + acc[j];
-      acc[j - 1] = (uint32_t)c;
-      c >>= 32;
-    }
-    c += acc[H];
-    acc[H - 1] = (uint32_t)c;
-    acc[H] = acc[H + 1] + (uint32_t)(c >> 32);
-  }
-  // acc < 2 r: subtract r unless that borrows out of the H + 1 words
-  uint32_t borrow = 0;
-  for (int i = 0; i < H; i++) {
-    const uint64_t d = (uint64_t)acc[i] - __ldg(r + i) - borrow;
-    out[i] = (uint32_t)d;
-    borrow = (uint32_t)(d >> 63);
-  }
-  if (acc[H] == 0 && borrow)
-    for (int i = 0; i < H; i++) out[i] = acc[i];
-}
-
-// a = (a + b) mod r, or (a - b) mod r, for a, b < r.
-__device__ void addmod_1t(uint32_t *a, const uint32_t *b, const uint32_t *__restrict__ r, int H) {
-  uint64_t c = 0;
-  for (int i = 0; i < H; i++) {
-    c += (uint64_t)a[i] + b[i];
-    a[i] = (uint32_t)c;
-    c >>= 32;
-  }
-  uint32_t t[kGarnerMaxH], borrow = 0;
-  for (int i = 0; i < H; i++) {
-    const uint64_t d = (uint64_t)a[i] - __ldg(r + i) - borrow;
-    t[i] = (uint32_t)d;
-    borrow = (uint32_t)(d >> 63);
-  }
-  if (c || !borrow)
-    for (int i = 0; i < H; i++) a[i] = t[i];
-}
-__device__ void submod_1t(uint32_t *a, const uint32_t *b, const uint32_t *__restrict__ r, int H) {
-  uint32_t borrow = 0;
-  for (int i = 0; i < H; i++) {
-    const uint64_t d = (uint64_t)a[i] - b[i] - borrow;
-    a[i] = (uint32_t)d;
-    borrow = (uint32_t)(d >> 63);
-  }
-  if (borrow) {
-    uint64_t c = 0;
-    for (int i = 0; i < H; i++) {
-      c += (uint64_t)a[i] + __ldg(r + i);
-      a[i] = (uint32_t)c;
-      c >>= 32;
-    }
-  }
-}
-
-// Multi-prime CRT recombination (Section 2.1), one thread per chunk, in
-// place: out[t] holds the residues m_i = c^{d_i} mod r_i, i < B, H limbs
-// each, and receives m = c^d mod N (B H limbs).  The running value m starts
-// at m_1 and visits r_0, r_2, r_3, ...; visiting r_i adds
-//   x_i = coef_i (m_i - m) mod r_i  times  prefix_i = product of the primes visited so far,
-// the CRT-RSA equation for the first two primes and Garner's extension for
-// the rest.  m mod r_i comes from Montgomery products over m's H-limb
-// pieces (Horner: MontMul(v, R_h^2) is v R_h in Montgomery form), so the
-// kernel needs no division.  With `status`, a zero residue (c shares the
-// prime r_i: no inverse exists) sets kStatusNotInvertible.
-__global__ void __launch_bounds__(kAuxThreads) k_garner_mp(const KeyDev *__restrict__ keys, uint32_t K, int H, int B,
-                                                           uint32_t *__restrict__ out, long long n,
-                                                           uint32_t *__restrict__ status) {
-  const long long t = (long long)blockIdx.x * kAuxThreads + threadIdx.x;
-  if (t >= n) return;
-  const KeyDev &kd = keys[t % K];
-  uint32_t *o = out + t * (long long)(B * H);
-  if (status) {
-    bool zero = false;
-    for (int i = 0; i < B; i++) {
-      uint32_t any = 0;
-      for (int j = 0; j < H; j++) any |= o[i * H + j];
-      zero = zero || !any;
-    }
-    if (zero) atomicOr(status, kStatusNotInvertible);
-  }
-  uint32_t m[kGarnerMaxS];  // running value, `len` limbs
-  uint32_t acc[kGarnerMaxH], tmp[kGarnerMaxH], mi[kGarnerMaxH];
-  for (int j = 0; j < H; j++) m[j] = o[H + j];
-  int len = H;
-  for (int step = 0; step < B - 1; step++) {
-    const int i = step == 0 ? 0 : step + 1;
-    const uint32_t *ri = kd.P[i], *R2 = kd.R2h[i];
-    const uint32_t n0 = kd.n0h[i];
-    // acc = m R_h mod r_i (Montgomery form of m mod r_i), from m's top piece down
-    const int pieces = len / H;
-    mm_1t(acc, m + (pieces - 1) * H, R2, ri, n0, H);
-    for (int pc = pieces - 2; pc >= 0; pc--) {
-      mm_1t(acc, acc, R2, ri, n0, H);
-      mm_1t(tmp, m + pc * H, R2, ri, n0, H);
-      addmod_1t(acc, tmp, ri, H);
-    }
-    for (int j = 0; j < H; j++) mi[j] = o[i * H + j];
-    mm_1t(tmp, mi, R2, ri, n0, H);    // m_i R_h
-    submod_1t(tmp, acc, ri, H);       // (m_i - m) R_h mod r_i
-    mm_1t(tmp, tmp, kd.coef[i], ri, n0, H);  // x_i = coef_i (m_i - m) mod r_i
-    // m += prefix_i x_i  (prefix_i has len limbs; the sum stays below prefix_i r_i)
-    const uint32_t *pf = kd.prefix[i];
-    for (int j = len; j < len + H; j++) m[j] = 0;
-    for (int a = 0; a < H; a++) {
-      const uint32_t xa = tmp[a];
-      uint64_t c = 0;
-      for (int j = 0; j < len; j++) {
-        c += (uint64_t)__ldg(pf + j) * xa + m[a + j];
-        m[a + j] = (uint32_t)c;
-        c >>= 32;
-      }
-      for (int j = a + len; j < len + H && c; j++) {
-        c += m[j];
-        m[j] = (uint32_t)c;
-        c >>= 32;
-      }
-    }
-    len += H;
-  }
-  for (int j = 0; j < B * H; j++) o[j] = m[j];
-}
-
-int launch_garner_mp(uint32_t prime_limbs, uint32_t parts, const KeyDev *keys, uint32_t K, uint32_t *out, size_t n,
-                     cudaStream_t st, uint32_t *status_if_zero_residue) {
-  if (n == 0) return PMK_OK;
-  if (parts < 2 || parts > (uint32_t)kMaxPrimes || prime_limbs == 0 || prime_limbs > (uint32_t)kGarnerMaxH ||
-      prime_limbs * parts > (uint32_t)kGarnerMaxS)
-    return PMK_EINVAL;
-  k_garner_mp<<<(unsigned)((n + kAuxThreads - 1) / kAuxThreads), kAuxThreads, 0, st>>>(
-      keys, K, (int)prime_limbs, (int)parts, out, (long long)n, status_if_zero_residue);
-  return cuda_rc(cudaGetLastError());
-}
-
 const MulmodEntry *mulmod_entries(int *count) {
   static const MulmodEntry entries[] = {
       make_mulmod<4, 2>(),   make_mulmod<8, 2>(),    make_mulmod<16, 2>(),   make_mulmod<32, 4>(),
@@ -555,6 +290,37 @@ const MulmodEntry *mulmod_entries(int *count) {
   };
   *count = (int)(sizeof(entries) / sizeof(entries[0]));
   return entries;
+}
+
+const MulmodEntry *crt_sum_entries(int *count) {
+  static const MulmodEntry entries[] = {
+      make_crt_sum<4, 2>(),  make_crt_sum<8, 2>(),   make_crt_sum<16, 2>(),   make_crt_sum<32, 4>(),
+      make_crt_sum<64, 8>(), make_crt_sum<96, 8>(),  make_crt_sum<128, 16>(), make_crt_sum<192, 16>(),
+      make_crt_sum<256, 16>(),
+  };
+  *count = (int)(sizeof(entries) / sizeof(entries[0]));
+  return entries;
+}
+
+int launch_crt_sum(uint32_t limbs, uint32_t parts, const KeyDev *keys, uint32_t K, uint32_t *out, size_t n,
+                   cudaStream_t st, uint32_t *status_if_zero_residue) {
+  if (n == 0) return PMK_OK;
+  if (parts < 2 || parts > (uint32_t)kMaxPrimes || limbs % parts || K == 0 || K > 65535) return PMK_EINVAL;
+  int cnt = 0;
+  const MulmodEntry *list = crt_sum_entries(&cnt), *e = nullptr;
+  for (int i = 0; i < cnt; i++)
+    if (list[i].limbs == (int)limbs) e = &list[i];
+  if (!e) return PMK_EUNSUPPORTED;
+  int rc = configure_smem(e->fn, e->smem);
+  if (rc != PMK_OK) return rc;
+  const long long per_key = ((long long)n + K - 1) / K;
+  const int ipb = dev::kThreads / e->tpi;
+  dim3 grid((unsigned)((per_key + ipb - 1) / ipb), K);
+  long long nl = (long long)n;
+  int B = (int)parts;
+  uint32_t *status = status_if_zero_residue;
+  void *args[] = {(void *)&keys, (void *)&K, (void *)&out, (void *)&nl, (void *)&B, (void *)&status};
+  return cuda_rc(cudaLaunchKernel(e->fn, grid, dim3(dev::kThreads), args, e->smem, st));
 }
 
 int launch_mulmod(uint32_t limbs, const KeyDev *keys, uint32_t K, const uint32_t *a, const uint32_t *b, uint32_t *out,

@@ -332,7 +332,6 @@ void finish_key(uint32_t nbits, u64 e, const std::vector<std::vector<u64>> &r, H
   k.d = to32(d, s);
   k.n0 = neg_inv32(k.N[0]);
   k.R2 = pow2_32(N, (int)(64 * s), s);
-  std::vector<u64> prefix = r[1];  // product of the primes visited so far (r_1, then r_0, r_2, ...)
   for (int i = 0; i < b; i++) {
     const Mont mt(r[i]);
     std::vector<u64> rm2(r[i]);
@@ -346,7 +345,8 @@ void finish_key(uint32_t nbits, u64 e, const std::vector<std::vector<u64>> &r, H
     const std::vector<uint32_t> rm2_32 = to32(rm2, h);
     k.sched_hinv[i] = make_schedule(rm2_32.data(), (int)h);
     if (i == 1) continue;
-    // coef_i = (product of the primes visited before r_i)^-1 mod r_i, by Fermat
+    // Garner coefficients (exported): coef_0 = r_1^-1 mod r_0,
+    // coef_i = (r_0 ... r_{i-1})^-1 mod r_i, by Fermat
     std::vector<u64> acc(n), t(n), x(n), coef(n);
     bool first = true;
     for (int j = 0; j < b; j++) {
@@ -360,18 +360,34 @@ void finish_key(uint32_t nbits, u64 e, const std::vector<std::vector<u64>> &r, H
     mt.from_mont(x.data(), acc.data());
     mt.pow(coef.data(), x.data(), rm2.data(), n);
     k.coef[i] = to32(coef, h);
-    k.prefix[i] = to32(prefix, h * (i == 0 ? 1 : i));
-    prefix = mul_full(prefix, r[i]);
-    prefix.resize((size_t)n * (i == 0 ? 2 : i + 1));
+  }
+  // CRT recombination rows c_i R mod N, c_i = (N / r_i) ((N / r_i)^-1 mod r_i)
+  const Mont mN(N);
+  for (int i = 0; i < b; i++) {
+    const Mont mt(r[i]);
+    std::vector<u64> others, acc(n), t(n), x(n), inv(n), rm2(r[i]);
+    sub(rm2.data(), r[i].data(), two.data(), n);
+    bool first = true;
+    for (int j = 0; j < b; j++) {
+      if (j == i) continue;
+      others = others.empty() ? r[j] : mul_full(others, r[j]);
+      mt.to_mont(t.data(), reduce_once(r[j], r[i]).data());
+      if (first) acc = t;
+      else mt.mul(acc.data(), acc.data(), t.data());
+      first = false;
+    }
+    mt.from_mont(x.data(), acc.data());
+    mt.pow(inv.data(), x.data(), rm2.data(), n);     // (N / r_i)^-1 mod r_i (Fermat)
+    std::vector<u64> c = mul_full(others, inv), cR(s / 2);
+    c.resize(s / 2);                                   // c_i < N
+    mN.to_mont(cR.data(), c.data());
+    k.crt_sum[i] = to32(cR, s);
   }
   k.p = k.pr[0];
   k.q = k.pr[1];
   k.dp = k.dpr[0];
   k.dq = k.dpr[1];
   k.qinv = k.coef[0];
-  std::vector<u64> qm_r(to64(k.qinv.data(), h));  // qinv * R_h mod p
-  for (size_t i = 0; i < 32 * h; i++) dbl_mod(qm_r.data(), r[0].data(), n);
-  k.qinv_m = to32(qm_r, h);
   uint32_t ev[2] = {(uint32_t)e, (uint32_t)(e >> 32)};
   k.sched_e = make_schedule(ev, 2);
   k.sched_d = make_schedule(k.d.data(), (int)s);

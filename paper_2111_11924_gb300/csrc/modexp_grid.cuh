@@ -1,0 +1,118 @@
+// The one-launch-per-call exponentiation kernel (encryption, full-d
+// decryption, CRT residues) built on modexp_core.cuh.
+#pragma once
+
+#include "modexp_core.cuh"
+
+namespace pmk {
+namespace dev {
+
+// The CRT input of one residue in Montgomery form: x = c R mod r for the
+// chunk c = sum_j c_j R^j of `parts` S-limb pieces (R = 2^(32 S)), by Horner
+// from the top piece: MontMul(c_top, R^3) = c_top R^2 is the Montgomery form
+// of c_top R, MontMul(c_j, R^2) that of c_j, and MontMul(x, R^2) multiplies
+// the value in Montgomery form by R.  Two pieces take two products.
+template <int S, int TPI, int FORM>
+__device__ __forceinline__ void crt_input(uint32_t (&a)[S / TPI], const uint32_t *c, bool active, int parts,
+                                          const uint32_t *sR2, const uint32_t *sR3, const uint32_t (&nn)[S / TPI],
+                                          uint32_t n0, uint32_t r) {
+  constexpr int L = S / TPI;
+  uint32_t lo[L];
+  if (active) {
+    load_slice_global<L>(a, c + (parts - 1) * S, r);
+    load_slice_global<L>(lo, c + (parts - 2) * S, r);
+  } else {
+#pragma unroll
+    for (int j = 0; j < L; j++) lo[j] = a[j] = 0;
+  }
+  mont<S, TPI, FORM>(a, sR3, nn, n0, r);   // c_top R^2
+  mont<S, TPI, FORM>(lo, sR2, nn, n0, r);  // c_next R
+  mod_add<L, TPI>(a, lo, nn, r);           // (c_top R + c_next) R
+  for (int piece = parts - 3; piece >= 0; piece--) {
+    mont<S, TPI, FORM>(a, sR2, nn, n0, r);  // value * R, still in Montgomery form
+    if (active) {
+      load_slice_global<L>(lo, c + piece * S, r);
+    } else {
+#pragma unroll
+      for (int j = 0; j < L; j++) lo[j] = 0;
+    }
+    mont<S, TPI, FORM>(lo, sR2, nn, n0, r);
+    mod_add<L, TPI>(a, lo, nn, r);
+  }
+}
+
+// Grid: blockIdx.y selects the key (full width) or key * parts + i (CRT,
+// residue mod prime r_i); blockIdx.x * IPB + instance slot selects the j-th
+// chunk of that key, chunk t = key + j K.  Every block therefore serves one
+// key: schedules, modulus and control flow are uniform across it.
+//
+// FULL: out[t] = in[t]^E mod N_key, E = e (sel != 0) or d, S = nbits / 32.
+// CRT:  out[t][i] = in[t]^E mod r_i over S = nbits / (32 parts) limbs, with
+//       E = d mod (r_i - 1) (sel == 0), or r_i - 2 (sel != 0: inverses mod
+//       r_i by Fermat's little theorem); the input is reduced by crt_input.
+//       The recombination kernel combines the residues afterwards.
+template <int S, int TPI, bool CRT, int FORM>
+__global__ void __launch_bounds__(kThreads) k_modexp(const KeyDev *__restrict__ keys, uint32_t K,
+                                                     const uint32_t *__restrict__ in, uint32_t *__restrict__ out,
+                                                     long long n, int sel, int parts) {
+  constexpr int L = S / TPI;
+  constexpr int IPB = kThreads / TPI;
+  constexpr int ROW = Layout<S>::kRow;
+  constexpr int INST = Layout<S>::kInst;
+  const int W = CRT ? parts * S : S;  // limbs per chunk in memory
+  extern __shared__ __align__(16) uint32_t smem[];
+  uint32_t *sR2 = smem, *sOne = smem + ROW, *sR3 = smem + 2 * ROW;
+  const uint32_t r = threadIdx.x % TPI, g = threadIdx.x / TPI;
+  uint32_t *tbl = smem + Layout<S>::kConstRows * ROW + g * INST;
+  uint32_t *ybuf = tbl + kTableMax * ROW;
+
+  const uint32_t key = CRT ? blockIdx.y / (uint32_t)parts : blockIdx.y;
+  const uint32_t half = CRT ? blockIdx.y % (uint32_t)parts : 0;
+  const long long first = key + (long long)blockIdx.x * IPB * K;
+  if (first >= n) return;  // block-uniform: no instance of this block has a chunk
+  const KeyDev &kd = keys[key];
+  const uint32_t *M = CRT ? kd.P[half] : kd.N;
+  const uint32_t *R2 = CRT ? kd.R2h[half] : kd.R2;
+  const uint32_t *sched = CRT ? (sel ? kd.sched_hinv[half] : kd.sched_h[half]) : (sel ? kd.sched_e : kd.sched_d);
+  const uint32_t nsteps = CRT ? (sel ? kd.nsteps_hinv[half] : kd.nsteps_h[half]) : (sel ? kd.nsteps_e : kd.nsteps_d);
+  const uint32_t maxidx = CRT ? (sel ? kd.maxidx_hinv[half] : kd.maxidx_h[half]) : (sel ? kd.maxidx_e : kd.maxidx_d);
+  const uint32_t n0 = CRT ? kd.n0h[half] : kd.n0;
+
+  for (int i = threadIdx.x; i < S; i += kThreads) {
+    sR2[i] = __ldg(R2 + i);
+    sOne[i] = (i == 0);
+    if (CRT) sR3[i] = __ldg(kd.R3h[half] + i);
+  }
+  __syncthreads();
+
+  const long long t = first + (long long)g * K;
+  const bool active = t < n;
+  uint32_t nn[L], a[L];
+  load_slice_global<L>(nn, M, r);
+  if (!CRT) {
+    if (active) {
+      load_slice_global<L>(a, in + t * W, r);
+    } else {
+#pragma unroll
+      for (int j = 0; j < L; j++) a[j] = 0;
+    }
+    mont<S, TPI, FORM>(a, sR2, nn, n0, r);  // x R mod N
+  } else {
+    crt_input<S, TPI, FORM>(a, in + t * W, active, parts, sR2, sR3, nn, n0, r);
+  }
+  exp_window<S, TPI, FORM>(a, tbl, ybuf, sched, nsteps, maxidx, nn, n0, r);
+  mont<S, TPI, FORM>(a, sOne, nn, n0, r);  // leave the Montgomery domain
+  if (active) {
+    uint32_t *o = out + t * W + (CRT ? half * S : 0) + r * L;
+    if constexpr (L % 4 == 0) {
+#pragma unroll
+      for (int j = 0; j < L; j += 4) *reinterpret_cast<uint4 *>(o + j) = make_uint4(a[j], a[j + 1], a[j + 2], a[j + 3]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < L; j++) o[j] = a[j];
+    }
+  }
+}
+
+}  // namespace dev
+}  // namespace pmk

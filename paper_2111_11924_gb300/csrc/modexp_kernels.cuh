@@ -2,123 +2,22 @@
 // (mode, limb count, threads per instance) triple to an instantiation.
 #pragma once
 
-#include "modexp_core.cuh"
+#include "modexp_grid.cuh"
 
 namespace pmk {
 namespace dev {
 
-// The CRT input of one residue in Montgomery form: x = c R mod r for the
-// chunk c = sum_j c_j R^j of `parts` S-limb pieces (R = 2^(32 S)), by Horner
-// from the top piece: MontMul(c_top, R^3) = c_top R^2 is the Montgomery form
-// of c_top R, MontMul(c_j, R^2) that of c_j, and MontMul(x, R^2) multiplies
-// the value in Montgomery form by R.  Two pieces take two products.
-template <int S, int TPI, int FORM>
-__device__ __forceinline__ void crt_input(uint32_t (&a)[S / TPI], const uint32_t *c, bool active, int parts,
-                                          const uint32_t *sR2, const uint32_t *sR3, const uint32_t (&nn)[S / TPI],
-                                          uint32_t n0, uint32_t r) {
-  constexpr int L = S / TPI;
-  uint32_t lo[L];
-  if (active) {
-    load_slice_global<L>(a, c + (parts - 1) * S, r);
-    load_slice_global<L>(lo, c + (parts - 2) * S, r);
-  } else {
-#pragma unroll
-    for (int j = 0; j < L; j++) lo[j] = a[j] = 0;
-  }
-  mont<S, TPI, FORM>(a, sR3, nn, n0, r);   // c_top R^2
-  mont<S, TPI, FORM>(lo, sR2, nn, n0, r);  // c_next R
-  mod_add<L, TPI>(a, lo, nn, r);           // (c_top R + c_next) R
-  for (int piece = parts - 3; piece >= 0; piece--) {
-    mont<S, TPI, FORM>(a, sR2, nn, n0, r);  // value * R, still in Montgomery form
-    if (active) {
-      load_slice_global<L>(lo, c + piece * S, r);
-    } else {
-#pragma unroll
-      for (int j = 0; j < L; j++) lo[j] = 0;
-    }
-    mont<S, TPI, FORM>(lo, sR2, nn, n0, r);
-    mod_add<L, TPI>(a, lo, nn, r);
-  }
-}
-
-// Grid: blockIdx.y selects the key (full width) or key * parts + i (CRT,
-// residue mod prime r_i); blockIdx.x * IPB + instance slot selects the j-th
-// chunk of that key, chunk t = key + j K.  Every block therefore serves one
-// key: schedules, modulus and control flow are uniform across it.
-//
-// FULL: out[t] = in[t]^E mod N_key, E = e (sel != 0) or d, S = nbits / 32.
-// CRT:  out[t][i] = in[t]^E mod r_i over S = nbits / (32 parts) limbs, with
-//       E = d mod (r_i - 1) (sel == 0), or r_i - 2 (sel != 0: inverses mod
-//       r_i by Fermat's little theorem); the input is reduced by crt_input.
-//       The recombination kernel combines the residues afterwards.
-template <int S, int TPI, bool CRT, int FORM>
-__global__ void __launch_bounds__(kThreads) k_modexp(const KeyDev *__restrict__ keys, uint32_t K,
-                                                     const uint32_t *__restrict__ in, uint32_t *__restrict__ out,
-                                                     long long n, int sel, int parts) {
-  constexpr int L = S / TPI;
-  constexpr int IPB = kThreads / TPI;
-  constexpr int ROW = Layout<S>::kRow;
-  constexpr int INST = Layout<S>::kInst;
-  const int W = CRT ? parts * S : S;  // limbs per chunk in memory
-  extern __shared__ __align__(16) uint32_t smem[];
-  uint32_t *sR2 = smem, *sOne = smem + ROW, *sR3 = smem + 2 * ROW;
-  const uint32_t r = threadIdx.x % TPI, g = threadIdx.x / TPI;
-  uint32_t *tbl = smem + Layout<S>::kConstRows * ROW + g * INST;
-  uint32_t *ybuf = tbl + kTableMax * ROW;
-
-  const uint32_t key = CRT ? blockIdx.y / (uint32_t)parts : blockIdx.y;
-  const uint32_t half = CRT ? blockIdx.y % (uint32_t)parts : 0;
-  const long long first = key + (long long)blockIdx.x * IPB * K;
-  if (first >= n) return;  // block-uniform: no instance of this block has a chunk
-  const KeyDev &kd = keys[key];
-  const uint32_t *M = CRT ? kd.P[half] : kd.N;
-  const uint32_t *R2 = CRT ? kd.R2h[half] : kd.R2;
-  const uint32_t *sched = CRT ? (sel ? kd.sched_hinv[half] : kd.sched_h[half]) : (sel ? kd.sched_e : kd.sched_d);
-  const uint32_t nsteps = CRT ? (sel ? kd.nsteps_hinv[half] : kd.nsteps_h[half]) : (sel ? kd.nsteps_e : kd.nsteps_d);
-  const uint32_t maxidx = CRT ? (sel ? kd.maxidx_hinv[half] : kd.maxidx_h[half]) : (sel ? kd.maxidx_e : kd.maxidx_d);
-  const uint32_t n0 = CRT ? kd.n0h[half] : kd.n0;
-
-  for (int i = threadIdx.x; i < S; i += kThreads) {
-    sR2[i] = __ldg(R2 + i);
-    sOne[i] = (i == 0);
-    if (CRT) sR3[i] = __ldg(kd.R3h[half] + i);
-  }
-  __syncthreads();
-
-  const long long t = first + (long long)g * K;
-  const bool active = t < n;
-  uint32_t nn[L], a[L];
-  load_slice_global<L>(nn, M, r);
-  if (!CRT) {
-    if (active) {
-      load_slice_global<L>(a, in + t * W, r);
-    } else {
-#pragma unroll
-      for (int j = 0; j < L; j++) a[j] = 0;
-    }
-    mont<S, TPI, FORM>(a, sR2, nn, n0, r);  // x R mod N
-  } else {
-    crt_input<S, TPI, FORM>(a, in + t * W, active, parts, sR2, sR3, nn, n0, r);
-  }
-  exp_window<S, TPI, FORM>(a, tbl, ybuf, sched, nsteps, maxidx, nn, n0, r);
-  mont<S, TPI, FORM>(a, sOne, nn, n0, r);  // leave the Montgomery domain
-  if (active) {
-    uint32_t *o = out + t * W + (CRT ? half * S : 0) + r * L;
-    if constexpr (L % 4 == 0) {
-#pragma unroll
-      for (int j = 0; j < L; j += 4) *reinterpret_cast<uint4 *>(o + j) = make_uint4(a[j], a[j + 1], a[j + 2], a[j + 3]);
-    } else {
-#pragma unroll
-      for (int j = 0; j < L; j++) o[j] = a[j];
-    }
-  }
-}
+// The value 1 as a row of limbs, for leaving the Montgomery domain.
+static __device__ __align__(16) uint32_t g_one_row[256] = {1u};
 
 // Persistent form for batches: each warp repeatedly takes the next task from
 // a device counter.  A task is up to 32 / TPI chunks of one key of one job
 // (chunk first + i * stride), in one mode (CRT residue i of a key with
-// nprimes primes: mode 2 + i).  Keys differ from warp to warp, so the
-// constant rows (R^2, 1, R^3) live in each warp's own shared-memory area.
+// nprimes primes: mode 2 + i).  Keys differ from warp to warp, so the rows
+// used once or twice per exponentiation (R^2, R^3, 1) are read from global
+// memory (the key blob, L1-cached) instead of shared memory; a block then
+// needs only its instances' tables, as many blocks fit per SM as for
+// k_modexp.
 template <int S, int TPI, bool CRT, int FORM>
 __global__ void __launch_bounds__(kThreads) k_modexp_tasks(const BatchTask *__restrict__ tasks, int ntasks,
                                                            int *__restrict__ counter) {
@@ -126,12 +25,11 @@ __global__ void __launch_bounds__(kThreads) k_modexp_tasks(const BatchTask *__re
   constexpr int IPW = 32 / TPI;
   constexpr int ROW = Layout<S>::kRow;
   constexpr int INST = Layout<S>::kInst;
-  constexpr int WAREA = Layout<S>::kConstRows * ROW + IPW * INST;
+  constexpr int WAREA = IPW * INST;
   extern __shared__ __align__(16) uint32_t smem[];
   const uint32_t lane = threadIdx.x & 31, r = lane % TPI, g = lane / TPI;
   uint32_t *wbase = smem + (threadIdx.x / 32) * WAREA;
-  uint32_t *sR2 = wbase, *sOne = wbase + ROW, *sR3 = wbase + 2 * ROW;
-  uint32_t *tbl = wbase + Layout<S>::kConstRows * ROW + g * INST;
+  uint32_t *tbl = wbase + g * INST;
   uint32_t *ybuf = tbl + kTableMax * ROW;
   for (;;) {
     int ti = 0;
@@ -150,13 +48,7 @@ __global__ void __launch_bounds__(kThreads) k_modexp_tasks(const BatchTask *__re
     const uint32_t nsteps = CRT ? kd.nsteps_h[half] : (enc ? kd.nsteps_e : kd.nsteps_d);
     const uint32_t maxidx = CRT ? kd.maxidx_h[half] : (enc ? kd.maxidx_e : kd.maxidx_d);
     const uint32_t n0 = CRT ? kd.n0h[half] : kd.n0;
-    __syncwarp();  // the previous task's reads of the constant rows are done
-    for (int i = lane; i < S; i += 32) {
-      sR2[i] = __ldg(R2 + i);
-      sOne[i] = (i == 0);
-      if (CRT) sR3[i] = __ldg(kd.R3h[half] + i);
-    }
-    __syncwarp();
+    const uint32_t *sR2 = R2, *sR3 = CRT ? kd.R3h[half] : R2, *sOne = g_one_row;
     const bool active = (int)g < tk.count;
     const long long t = tk.first + (long long)g * tk.stride;
     uint32_t nn[L], a[L];
@@ -227,6 +119,64 @@ __global__ void __launch_bounds__(kThreads) k_mulmod(const KeyDev *__restrict__ 
   }
 }
 
+// CRT recombination at full width.  The congruences x = m_i mod r_i
+// (i < B) have one solution below N = r_0 ... r_{B-1} (the Chinese remainder
+// theorem, Section 2.1): x = sum_i m_i c_i mod N with c_i = (N / r_i) times
+// ((N / r_i)^-1 mod r_i), since c_i = 1 mod r_i and 0 mod every other prime.
+// Each term is one Montgomery product of the residue with the key's row
+// c_i R mod N, so the kernel is B products and B modular additions per
+// chunk.  In place: chunk t of `out` (S limbs) holds the B residues, S / B
+// limbs each, and receives x.  Every lane has consumed its loads of the last
+// residue before the group's shuffles inside that product, so the stores
+// cannot overtake another lane's loads.  With `status`, a residue equal to
+// zero (the input shares the prime r_i: no inverse exists) sets
+// kStatusNotInvertible.  Grid as k_mulmod.
+template <int S, int TPI>
+__global__ void __launch_bounds__(kThreads) k_crt_sum(const KeyDev *__restrict__ keys, uint32_t K,
+                                                      uint32_t *out, long long n, int B, uint32_t *status) {
+  constexpr int L = S / TPI;
+  constexpr int IPB = kThreads / TPI;
+  constexpr int ROW = Layout<S>::kRow;
+  extern __shared__ __align__(16) uint32_t smem[];  // B rows: c_i R mod N
+  const uint32_t r = threadIdx.x % TPI, g = threadIdx.x / TPI;
+  const uint32_t key = blockIdx.y;
+  const long long first = key + (long long)blockIdx.x * IPB * K;
+  if (first >= n) return;
+  const KeyDev &kd = keys[key];
+  for (int i = threadIdx.x; i < B * S; i += kThreads) smem[(i / S) * ROW + i % S] = __ldg(kd.crt_sum[i / S] + i % S);
+  __syncthreads();
+  const long long t = first + (long long)g * K;
+  const bool active = t < n;
+  const int H = S / B;
+  uint32_t nn[L], acc[L], a[L];
+  load_slice_global<L>(nn, kd.N, r);
+#pragma unroll
+  for (int j = 0; j < L; j++) acc[j] = 0;
+  bool zero = false;
+  for (int i = 0; i < B; i++) {
+    uint32_t any = 0;
+#pragma unroll
+    for (int j = 0; j < L; j++) {  // residue i, zero-extended to S limbs
+      const int limb = (int)r * L + j;
+      a[j] = (active && limb < H) ? out[t * S + i * H + limb] : 0u;
+      any |= a[j];
+    }
+    if constexpr (TPI > 1) {
+#pragma unroll
+      for (int o = 1; o < TPI; o <<= 1) any |= __shfl_xor_sync(kFull, any, o, TPI);
+    }
+    zero = zero || any == 0;
+    mont<S, TPI, kChain>(a, smem + i * ROW, nn, kd.n0, r);  // m_i c_i mod N
+    mod_add<L, TPI>(acc, a, nn, r);
+  }
+  if (active) {
+    if (status && zero && r == 0) atomicOr(status, kStatusNotInvertible);
+    uint32_t *o = out + t * S + r * L;
+#pragma unroll
+    for (int j = 0; j < L; j++) o[j] = acc[j];
+  }
+}
+
 template <int S>
 constexpr size_t modexp_smem_bytes(int tpi) {
   return sizeof(uint32_t) * ((size_t)Layout<S>::kConstRows * Layout<S>::kRow + (size_t)(kThreads / tpi) * Layout<S>::kInst);
@@ -249,8 +199,7 @@ struct ModexpEntry {
 
 template <int S, int TPI, bool CRT, int FORM>
 ModexpEntry make_entry() {
-  constexpr size_t warp_area = (size_t)dev::Layout<S>::kConstRows * dev::Layout<S>::kRow +
-                               (size_t)(32 / TPI) * dev::Layout<S>::kInst;
+  constexpr size_t warp_area = (size_t)(32 / TPI) * dev::Layout<S>::kInst;
   return ModexpEntry{S, TPI, CRT, FORM, reinterpret_cast<const void *>(&dev::k_modexp<S, TPI, CRT, FORM>),
                      dev::modexp_smem_bytes<S>(TPI),
                      reinterpret_cast<const void *>(&dev::k_modexp_tasks<S, TPI, CRT, FORM>),
@@ -274,5 +223,14 @@ MulmodEntry make_mulmod() {
                      sizeof(uint32_t) * (size_t)(1 + dev::kThreads / TPI) * dev::Layout<S>::kRow};
 }
 const MulmodEntry *mulmod_entries(int *count);
+
+// CRT recombination kernels, one per full-width limb count (same geometries
+// as the modular multiplication).
+template <int S, int TPI>
+MulmodEntry make_crt_sum() {
+  return MulmodEntry{S, TPI, reinterpret_cast<const void *>(&dev::k_crt_sum<S, TPI>),
+                     sizeof(uint32_t) * (size_t)kMaxPrimes * dev::Layout<S>::kRow};
+}
+const MulmodEntry *crt_sum_entries(int *count);
 
 }  // namespace pmk

@@ -90,8 +90,7 @@ extern "C" int pmk_decrypt_message_host_noalloc(const pmk_keyset *ks, const uint
       rc = launch_modexp(ExpMode::kCrtHalf, H, default_config(H, true), ks->d_keys, ks->K, d_cipher, d_plain, n_chunks,
                          st, B);
       if (rc == PMK_OK)
-        rc = B == 2 ? launch_garner(H, ks->d_keys, ks->K, d_plain, n_chunks, st)
-                    : launch_garner_mp(H, B, ks->d_keys, ks->K, d_plain, n_chunks, st);
+        rc = launch_crt_sum(S, B, ks->d_keys, ks->K, d_plain, n_chunks, st);
     }
     if (rc == PMK_OK) rc = launch_join(ks->nbits, d_plain, n_chunks, d_msg, msg_len, st);
     if (rc != PMK_OK) break;

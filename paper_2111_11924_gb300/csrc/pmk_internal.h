@@ -34,17 +34,16 @@ struct HostKey {
   uint32_t nprimes = 2;
   std::vector<uint32_t> N, d, p, q, dp, dq, qinv;  // N, d: s limbs; the rest h
   std::vector<uint32_t> pr[kMaxPrimes], dpr[kMaxPrimes];  // r_i and d mod (r_i - 1)
-  // CRT recombination, visiting r_1, r_0, r_2, r_3, ...: the running value
-  // starts at m_1; visiting r_i adds coef_i (m_i - m) mod r_i times prefix_i,
-  // the product of the primes visited before r_i (coef_0 = qinv,
-  // prefix_0 = r_1; coef_i = (r_0 ... r_{i-1})^-1 mod r_i, prefix_i =
-  // r_0 ... r_{i-1} for i >= 2; entry 1 is unused).
-  std::vector<uint32_t> coef[kMaxPrimes], prefix[kMaxPrimes];
+  // Garner coefficients (exported with the key): coef_0 = qinv = r_1^-1 mod
+  // r_0, coef_1 = 0, coef_i = (r_0 ... r_{i-1})^-1 mod r_i.
+  std::vector<uint32_t> coef[kMaxPrimes];
+  // CRT recombination rows, s limbs: c_i R mod N with
+  // c_i = (N / r_i) ((N / r_i)^-1 mod r_i).
+  std::vector<uint32_t> crt_sum[kMaxPrimes];
   // Montgomery data, R = 2^(32 s) for N and R_h = 2^(32 h) for the primes.
   uint32_t n0 = 0, n0h[kMaxPrimes] = {};               // -M^-1 mod 2^32
   std::vector<uint32_t> R2;                            // R^2 mod N
   std::vector<uint32_t> R2h[kMaxPrimes], R3h[kMaxPrimes];  // R_h^2, R_h^3 mod r_i
-  std::vector<uint32_t> qinv_m;                        // qinv * R_h mod p
   Schedule sched_e, sched_d, sched_h[kMaxPrimes];      // e, d, d mod (r_i - 1)
   Schedule sched_hinv[kMaxPrimes];                     // r_i - 2 (Fermat inverses mod r_i)
 };
@@ -59,10 +58,8 @@ struct KeyDev {
   const uint32_t *R2h[kMaxPrimes];
   const uint32_t *R3h[kMaxPrimes];
   const uint32_t *sched_h[kMaxPrimes];
-  const uint32_t *qinv_m;
   const uint32_t *sched_hinv[kMaxPrimes];
-  const uint32_t *coef[kMaxPrimes];
-  const uint32_t *prefix[kMaxPrimes];
+  const uint32_t *crt_sum[kMaxPrimes];  // c_i R mod N (s limbs)
   const uint32_t *e_limbs, *d_limbs;  // e (2 limbs) and d (s limbs), for the thread-per-chunk baseline
   uint32_t nprimes;
   uint32_t n0, n0h[kMaxPrimes];
@@ -103,12 +100,11 @@ struct KernelConfig {
 // `limbs` = s / parts limbs each; residue i of chunk t goes to out[t][i * limbs].
 int launch_modexp(ExpMode mode, uint32_t limbs, KernelConfig cfg, const KeyDev *keys, uint32_t K, const uint32_t *in,
                   uint32_t *out, size_t n, cudaStream_t st, uint32_t parts = 2);
-int launch_garner(uint32_t half_limbs, const KeyDev *keys, uint32_t K, uint32_t *out, size_t n, cudaStream_t st,
-                  uint32_t *status_if_zero_half = nullptr);
-// Recombination of `parts` >= 2 residues of prime_limbs limbs each, in place
-// (out[t] holds the residues and receives m); the two-prime case may use either.
-int launch_garner_mp(uint32_t prime_limbs, uint32_t parts, const KeyDev *keys, uint32_t K, uint32_t *out, size_t n,
-                     cudaStream_t st, uint32_t *status_if_zero_residue = nullptr);
+// CRT recombination of `parts` residues per chunk (limbs / parts limbs
+// each) in place at full width `limbs`: out[t] holds the residues and
+// receives the value mod N.
+int launch_crt_sum(uint32_t limbs, uint32_t parts, const KeyDev *keys, uint32_t K, uint32_t *out, size_t n,
+                   cudaStream_t st, uint32_t *status_if_zero_residue = nullptr);
 // out[t] = a[t] * b[t] mod N_{t mod K} (full width; out may alias a or b)
 int launch_mulmod(uint32_t limbs, const KeyDev *keys, uint32_t K, const uint32_t *a, const uint32_t *b, uint32_t *out,
                   size_t n, cudaStream_t st);
