@@ -42,7 +42,7 @@ KERNELS_PER_STEP = 6  # split, range check + modexp (encrypt), range check + mod
 # DRAM traffic of the full-d decryption kernel from one ncu capture, valid only
 # for the kernel sources it was measured on (see profiles/).
 TRAFFIC_SOURCES = ["paper_2111_11924_gb300/csrc/modexp_core.cuh", "paper_2111_11924_gb300/csrc/modexp_grid.cuh"]
-TRAFFIC_MEASURED = {"d3366a023babd93b": 1112064}  # source digest -> bytes per launch (profiles/)
+TRAFFIC_MEASURED = {"e0c7da38d1245e1b": 1178880}  # source digest -> bytes per launch (profiles/)
 
 
 def sources_digest() -> str:
@@ -414,7 +414,8 @@ def run_ours(args):
 
 def run_profile(args):
     """A short, fixed launch sequence for ncu captures: keygen, split,
-    encrypt, two full-d decryptions, one CRT decryption, join, checked."""
+    encrypt, two full-d decryptions, one CRT decryption, join, checked; with
+    --profile-batch, one more full-d decryption through pmk_batch."""
     import torch
 
     import paper_2111_11924_gb300 as P
@@ -433,6 +434,15 @@ def run_profile(args):
     back = ctx.join(w.nbits, plain, w.msg_bytes)
     ctx.check()
     assert torch.equal(plain, chunks) and torch.equal(plain_crt, chunks) and torch.equal(back, d_msg)
+    if args.profile_batch:  # the same full-d decryption through the persistent graph path
+        from paper_2111_11924_gb300 import pmkrsa as B
+
+        out = torch.zeros_like(cipher)
+        batch = ctx.batch([(ks, cipher, out, B.OP_DECRYPT)])
+        batch.launch()
+        ctx.check()
+        assert torch.equal(out, chunks)
+        batch.destroy()
     print("profile sequence ok")
     return 0
 
@@ -803,6 +813,8 @@ def main(argv=None):
                     help="time multi-prime CRT decryption (1 MiB, K = 8) against two primes and exit")
     ap.add_argument("--mp-list", type=lambda v: tuple(int(x) for x in v.split(":")), nargs="*",
                     default=MULTIPRIME_CASES, help="bits:primes pairs for --multiprime")
+    ap.add_argument("--profile-batch", action="store_true",
+                    help="with --profile: also run the full-d decryption through the persistent batch path")
     ap.add_argument("--profile-mib", type=int, default=0,
                     help="with --profile: message size in MiB instead of the 1 MiB workload")
     args = ap.parse_args(argv)

@@ -201,13 +201,37 @@ __device__ __forceinline__ void finalize(uint32_t (&t)[L], uint32_t c0, const ui
   }
 }
 
+// Rows of a product processed per unrolled group (y limbs fetched as 16-byte
+// broadcasts).  In the carry-chain form with 8 limbs per lane, a group of 8
+// rows brings the per-row shift of the lane's words back to the starting
+// registers (measured 3% faster than groups of 4; the column form measured
+// no gain and keeps 4).
+template <int S, int L, bool kChainForm>
+__host__ __device__ constexpr int row_group() {
+  return (kChainForm && L == 8 && S % 8 == 0) ? 8 : (S % 4 == 0) ? 4 : 2;
+}
+
+template <int K>
+__device__ __forceinline__ void load_y(uint32_t (&yv)[K], const uint32_t *ys) {
+  if constexpr (K % 4 == 0) {
+#pragma unroll
+    for (int q = 0; q < K; q += 4) {
+      const uint4 v = *reinterpret_cast<const uint4 *>(ys + q);
+      yv[q] = v.x; yv[q + 1] = v.y; yv[q + 2] = v.z; yv[q + 3] = v.w;
+    }
+  } else {
+    const uint2 v = *reinterpret_cast<const uint2 *>(ys);
+    yv[0] = v.x; yv[1] = v.y;
+  }
+}
+
 // a <- MontMul(a, y) = a y R^-1 mod N.  a: this lane's limbs (any value < R);
 // ys: y's S limbs in shared memory (y < N), read as 16-byte broadcasts.
 template <int S, int TPI>
 __device__ __forceinline__ void mont_mul(uint32_t (&a)[S / TPI], const uint32_t *ys, const uint32_t (&nn)[S / TPI],
                                          uint32_t n0, uint32_t r) {
   constexpr int L = S / TPI;
-  constexpr int kStep = (S % 4 == 0) ? 4 : 2;
+  constexpr int kStep = row_group<S, L, true>();
   uint32_t t[L];
 #pragma unroll
   for (int j = 0; j < L; j++) t[j] = 0;
@@ -215,13 +239,7 @@ __device__ __forceinline__ void mont_mul(uint32_t (&a)[S / TPI], const uint32_t 
 #pragma unroll 1
   for (int i0 = 0; i0 < S; i0 += kStep) {
     uint32_t yv[kStep];
-    if constexpr (kStep == 4) {
-      const uint4 v = *reinterpret_cast<const uint4 *>(ys + i0);
-      yv[0] = v.x; yv[1] = v.y; yv[2] = v.z; yv[3] = v.w;
-    } else {
-      const uint2 v = *reinterpret_cast<const uint2 *>(ys + i0);
-      yv[0] = v.x; yv[1] = v.y;
-    }
+    load_y<kStep>(yv, ys + i0);
 #pragma unroll
     for (int u = 0; u < kStep; u++) {
       row_mac<L, kFormA>(t, c0, c1, a, yv[u]);
@@ -258,20 +276,14 @@ template <int S, int TPI>
 __device__ __forceinline__ void mont_mul_cols(uint32_t (&a)[S / TPI], const uint32_t *ys, const uint32_t (&nn)[S / TPI],
                                               uint32_t n0, uint32_t r) {
   constexpr int L = S / TPI;
-  constexpr int kStep = (S % 4 == 0) ? 4 : 2;
+  constexpr int kStep = row_group<S, L, false>();
   uint64_t acc[L];
 #pragma unroll
   for (int j = 0; j < L; j++) acc[j] = 0;
 #pragma unroll 1
   for (int i0 = 0; i0 < S; i0 += kStep) {
     uint32_t yv[kStep];
-    if constexpr (kStep == 4) {
-      const uint4 v = *reinterpret_cast<const uint4 *>(ys + i0);
-      yv[0] = v.x; yv[1] = v.y; yv[2] = v.z; yv[3] = v.w;
-    } else {
-      const uint2 v = *reinterpret_cast<const uint2 *>(ys + i0);
-      yv[0] = v.x; yv[1] = v.y;
-    }
+    load_y<kStep>(yv, ys + i0);
 #pragma unroll
     for (int u = 0; u < kStep; u++) {
       uint32_t hprev = 0;
