@@ -375,7 +375,8 @@ def run_ours(args):
         "default_geometry": {"value": world * n / (float(ph_default.sum(axis=1).mean()) / 1e3), "unit": UNIT,
                              "decrypt_ms": float(ph_default[:, 2].mean())},
         "split_join_GBps": {"split": (w.msg_bytes + cipher_bytes) / (split_ms / 1e3) / 1e9,
-                            "join": (w.msg_bytes + cipher_bytes) / (join_ms / 1e3) / 1e9},
+                            "join": (w.msg_bytes + cipher_bytes) / (join_ms / 1e3) / 1e9,
+                            "note": "1 MiB step: launch-latency bound; see split_join_hbm for bandwidth"},
         "int32_ops": {"achieved_tops": 2 * achieved, "mad_lo_peak_tops": 64 * sms * max_mhz * 1e6 / 1e12,
                       "frac": 2 * achieved / (64 * sms * max_mhz * 1e6 / 1e12),
                       "note": "2 INT32 multiply-add halves per MAC against the measured 64 mad.lo/clk/SM"},
@@ -392,6 +393,8 @@ def run_ours(args):
         "gpu_launches": KERNELS_PER_STEP * args.steps,
         "source_digest": digest,
     }
+    if rank == 0:  # outside the timed region: split / join bandwidth on the 100 MiB file
+        line["split_join_hbm"] = hbm_split_join(ctx, 10)
     if rank == 0 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
         r = oracle_sample(args.ref_sample, threads)
@@ -684,16 +687,13 @@ def run_serving(args):
     return 0 if ok_cb else 1
 
 
-def run_hbm(args):
+def hbm_split_join(ctx, steps: int) -> dict:
     """Split and join (the HBM-bound rows) on the 100 MiB / 2048-bit file:
     GB/s of algorithmic bytes (message bytes + limb-buffer bytes) against the
-    measured copy bandwidth of this GPU."""
+    measured copy bandwidth of this GPU; both buffers are larger than L2."""
     import torch
 
-    import paper_2111_11924_gb300 as P
-
     w = W.FILE_100MIB_2048
-    ctx = P.Context(0)
     d_msg = torch.from_numpy(w.message()).cuda()
     n = w.n_chunks
     chunks = torch.empty((n, w.limbs), dtype=torch.int32, device="cuda")
@@ -704,20 +704,29 @@ def run_hbm(args):
     assert torch.equal(back, d_msg)
     bytes_moved = w.msg_bytes + n * w.limbs * 4
     peak = _measured_peaks().get("hbm_gbs")
-    res = {}
+    res = {"workload": w.name, "bytes_per_call": bytes_moved, "hbm_peak_GBps": peak,
+           "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peak else None}
     for name, fn in (("split", lambda: ctx.split(w.nbits, d_msg, out=chunks)),
                      ("join", lambda: ctx.join(w.nbits, chunks, w.msg_bytes, out=back))):
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
-        for i in range(args.steps):
+        fn()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * steps)]
+        for i in range(steps):
             ev[2 * i].record()
             fn()
             ev[2 * i + 1].record()
         torch.cuda.synchronize()
-        ms = statistics.median(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(args.steps))
+        ms = statistics.median(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(steps))
         gbs = bytes_moved / (ms / 1e3) / 1e9
         res[name] = {"ms": ms, "GBps": gbs, "frac_of_measured_copy": gbs / peak if peak else None}
-    print(json.dumps({"mode": "hbm", "workload": w.name, "bytes_per_call": bytes_moved, "hbm_peak_GBps": peak,
-                      "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peak else None} | res))
+    assert torch.equal(back, d_msg)
+    return res
+
+
+def run_hbm(args):
+    """Split and join on the 100 MiB file, one JSON line."""
+    import paper_2111_11924_gb300 as P
+
+    print(json.dumps({"mode": "hbm"} | hbm_split_join(P.Context(0), args.steps)))
     return 0
 
 
