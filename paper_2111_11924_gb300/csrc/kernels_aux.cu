@@ -14,7 +14,34 @@ namespace {
 
 constexpr int kAuxThreads = 256;
 
-// The 16 bytes starting at byte `off` (0..15) of the 32 bytes (lo, hi).
+// Division of numerators below 2^31 by a run-time constant d (Granlund and
+// Montgomery, PLDI 1994): q = floor(x M / 2^(31 + s)) with s = ceil(log2 d)
+// and M = ceil(2^(31 + s) / d) < 2^32.  Exact: writing M d = 2^(31+s) + e
+// with 0 <= e < d, the excess x e / (d 2^(31+s)) is below 2^-s <= 1/d.
+struct DivMagic {
+  uint32_t M;
+  int sh;  // s - 1; -1 for d = 1
+};
+
+DivMagic div_magic(uint32_t d) {
+  if (d <= 1) return DivMagic{1u, -1};
+  int s = 0;
+  while ((1ull << s) < d) s++;
+  const unsigned long long M = ((1ull << (31 + s)) + d - 1) / d;
+  return DivMagic{(uint32_t)M, s - 1};
+}
+
+// x / d: the magic multiply for 32-bit indices (x < 2^31), plain division otherwise.
+template <typename I>
+__device__ __forceinline__ I quot(I x, uint32_t d, DivMagic m) {
+  if constexpr (sizeof(I) == 4) {
+    return m.sh < 0 ? x : (__umulhi(x, m.M) >> m.sh);
+  } else {
+    return x / d;
+  }
+}
+
+// The 16 bytes starting at byte `off` (0..16) of the 32 bytes (lo, hi).
 __device__ __forceinline__ uint4 bytes_at(const uint4 lo, const uint4 hi, uint32_t off) {
   const uint32_t x[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
   const uint32_t sh = (off & 3u) * 8u;
@@ -27,101 +54,93 @@ __device__ __forceinline__ uint4 bytes_at(const uint4 lo, const uint4 hi, uint32
     PMK_CASE(0)
     PMK_CASE(1)
     PMK_CASE(2)
-    default:
+    case 3:
       for (int k = 0; k < 4; k++) w[k] = __funnelshift_r(x[k + 3], x[k + 4], sh);
       break;
+    default:
+      return hi;
 #undef PMK_CASE
   }
   return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
-// Bytes [0, n) of a, then bytes [0, 16 - n) of b (0 < n < 16).
-__device__ __forceinline__ uint4 concat_bytes(const uint4 a, const uint4 b, uint32_t n) {
-  const uint32_t A[4] = {a.x, a.y, a.z, a.w}, B[4] = {b.x, b.y, b.z, b.w};
-  const uint32_t sh = (n & 3u) * 8u, wo = n >> 2;
-  uint32_t w[4];
-#pragma unroll
-  for (int k = 0; k < 4; k++) {
-    // b shifted up by n bytes: word k takes B[k - wo] high part and B[k - wo - 1] low part
-    const int i = k - (int)wo;
-    const uint32_t hi_w = (i >= 0 && i < 4) ? B[i] : 0u;
-    const uint32_t lo_w = (i - 1 >= 0 && i - 1 < 4) ? B[i - 1] : 0u;
-    const uint32_t bs = sh ? __funnelshift_l(lo_w, hi_w, sh) : hi_w;
-    const int keep = (int)n - 4 * k;  // bytes of a in word k
-    const uint32_t mask = keep >= 4 ? 0xffffffffu : keep <= 0 ? 0u : (1u << (8 * keep)) - 1u;
-    w[k] = (A[k] & mask) | (bs & ~mask);
-  }
-  return make_uint4(w[0], w[1], w[2], w[3]);
+// Word k of the mask of bytes [0, n) of a 16-byte vector.
+__device__ __forceinline__ uint32_t keep_mask(int n, int k) {
+  const int c = n - 4 * k;
+  return c >= 4 ? 0xffffffffu : c <= 0 ? 0u : (0xffffffffu >> (32 - 8 * c));
 }
+
+// A chunk holds nbits/8 = P + 1 bytes, so the limb buffer is the message
+// with one zero byte (the "pad") after every P message bytes: chunk byte j
+// of chunk t is message byte t P + j for j < P, and zero for j = P.
 
 // Split (Section 3.1): word j of chunk t holds message bytes t P + 4j .. +3
 // (little-endian), zero past the chunk payload P or the message end L.
-// One thread per 16 output bytes (4 limbs).  Consecutive threads read
-// consecutive message bytes: two aligned 16-byte loads cover the 16 needed
-// bytes, and a byte shift extracts them.  The message tail, and a message
+// One thread per 16 output bytes: limb vector v of the buffer starts at
+// message byte 16 v - t (t = v / (S/4), its chunk), so it is the 16-byte
+// window there -- two aligned 16-byte loads and a byte shift -- with the pad
+// byte cleared in a chunk's last vector.  The message tail, and a message
 // that does not start on a 16-byte boundary, go byte by byte.
 template <typename I>
 __global__ void __launch_bounds__(kAuxThreads) k_split(const uint8_t *__restrict__ msg, I L, int P, int S,
-                                                       uint4 *__restrict__ out, I nvec, int msg_aligned) {
+                                                       uint4 *__restrict__ out, I nvec, int msg_aligned,
+                                                       DivMagic mvpc) {
   const I vpc = (I)(S / 4);  // vectors per chunk
   const uint4 *msg16 = reinterpret_cast<const uint4 *>(msg);
+  (void)P;
   for (I v = (I)blockIdx.x * kAuxThreads + threadIdx.x; v < nvec; v += (I)gridDim.x * kAuxThreads) {
-    const I t = v / vpc;
-    const int b0 = (int)(v - t * vpc) * 16;  // byte offset inside the chunk
+    const I t = quot<I>(v, (uint32_t)vpc, mvpc);
+    const I m0 = v * 16 - t;
     uint4 r = make_uint4(0, 0, 0, 0);
-    if (b0 < P) {
-      const I o = t * (I)P + (I)b0;
-      const I avail = L > o ? L - o : 0;
-      const int lim = (int)min((I)min(16, P - b0), avail);  // valid bytes of this vector
-      if (lim > 0) {
-        const I a = o >> 4;
-        if (msg_aligned && (a + 2) * 16 <= L) {
-          r = bytes_at(__ldg(msg16 + a), __ldg(msg16 + a + 1), (uint32_t)(o & 15));
-          if (lim < 16) {
-            const uint4 z = make_uint4(0, 0, 0, 0);
-            r = concat_bytes(r, z, (uint32_t)lim);
-          }
-        } else {
-          uint32_t w[4] = {0, 0, 0, 0};
-          for (int i = 0; i < lim; i++) w[i >> 2] |= (uint32_t)__ldg(msg + o + i) << (8 * (i & 3));
-          r = make_uint4(w[0], w[1], w[2], w[3]);
-        }
+    if (m0 < L) {
+      const I a = m0 >> 4;
+      if (msg_aligned && (a + 2) * 16 <= L) {
+        r = bytes_at(__ldg(msg16 + a), __ldg(msg16 + a + 1), (uint32_t)(m0 & 15));
+      } else {
+        uint32_t w[4] = {0, 0, 0, 0};
+        for (int i = 0; i < 16 && m0 + i < L; i++) w[i >> 2] |= (uint32_t)__ldg(msg + m0 + i) << (8 * (i & 3));
+        r = make_uint4(w[0], w[1], w[2], w[3]);
       }
+      if (v - t * vpc == vpc - 1) r.w &= 0x00ffffffu;  // chunk byte P: the pad
     }
     out[v] = r;
   }
 }
 
-// Join: byte b of the message is byte (b mod P) of chunk b / P.  One thread
-// per 16 message bytes: two aligned 16-byte loads of the chunk and a byte
-// shift give them, and a vector that runs past the chunk's payload takes its
-// remaining bytes from the start of the next chunk.  One 16-byte store writes
-// them; the message tail (or an unaligned output) is written byte by byte.
+// Join: byte b of the message is byte (b mod P) of chunk b / P, i.e. byte
+// b + b / P of the limb buffer.  One thread per 16 message bytes: the 17
+// buffer bytes from b0 + t (t = b0 / P) hold them, with the pad inside when
+// the vector crosses into chunk t + 1 after n1 = P - (b0 mod P) < 16 bytes;
+// then bytes [0, n1) come from the window at b0 + t and the rest from the
+// window one byte later.  One 16-byte store writes the vector; the message
+// tail (or an unaligned output) is written byte by byte.
 template <typename I>
 __global__ void __launch_bounds__(kAuxThreads) k_join(const uint32_t *__restrict__ chunks, int P, int S,
-                                                      uint8_t *__restrict__ msg, I L, int out_aligned) {
+                                                      uint8_t *__restrict__ msg, I L, int out_aligned,
+                                                      DivMagic mP, I nbuf16) {
   const I nvec = (L + 15) / 16;
   const uint4 *c16 = reinterpret_cast<const uint4 *>(chunks);
-  const int vpc = S / 4;
+  (void)S;
   for (I u = (I)blockIdx.x * kAuxThreads + threadIdx.x; u < nvec; u += (I)gridDim.x * kAuxThreads) {
     const I b0 = u * 16;
-    const I t = b0 / (I)P;
-    const int k0 = (int)(b0 - t * (I)P);
-    const int n1 = min(16, P - k0);  // bytes from chunk t
-    uint4 r;
-    {
-      const int a = k0 >> 4;  // aligned vector of chunk t holding byte k0
-      const uint4 lo = __ldg(c16 + t * vpc + a);
-      const uint4 hi = (a + 1 < vpc) ? __ldg(c16 + t * vpc + a + 1) : make_uint4(0, 0, 0, 0);
-      r = bytes_at(lo, hi, (uint32_t)(k0 & 15));
+    const I t = quot<I>(b0, (uint32_t)P, mP);
+    const int n1 = P - (int)(b0 - t * (I)P);  // bytes left in chunk t (>= 1)
+    const I src0 = b0 + t;
+    const I a = src0 >> 4;
+    const uint32_t off = (uint32_t)(src0 & 15);
+    const uint4 lo = __ldg(c16 + a);
+    const uint4 hi = (a + 1 < nbuf16) ? __ldg(c16 + a + 1) : make_uint4(0, 0, 0, 0);
+    uint4 r = bytes_at(lo, hi, off);
+    if (n1 < 16) {  // skip the pad byte at position n1
+      const uint4 r1 = bytes_at(lo, hi, off + 1);
+      const uint32_t m0 = keep_mask(n1, 0), m1 = keep_mask(n1, 1), m2 = keep_mask(n1, 2), m3 = keep_mask(n1, 3);
+      r = make_uint4((r.x & m0) | (r1.x & ~m0), (r.y & m1) | (r1.y & ~m1), (r.z & m2) | (r1.z & ~m2),
+                     (r.w & m3) | (r1.w & ~m3));
     }
-    if (n1 < 16 && b0 + n1 < L) {  // continue in chunk t + 1 (it exists: its bytes are in the message)
-      r = concat_bytes(r, __ldg(c16 + (t + 1) * vpc), (uint32_t)n1);
-    }
-    const uint32_t w[4] = {r.x, r.y, r.z, r.w};
     if (out_aligned && b0 + 16 <= L) {
       reinterpret_cast<uint4 *>(msg)[u] = r;
     } else {
+      const uint32_t w[4] = {r.x, r.y, r.z, r.w};
       for (int i = 0; i < 16 && b0 + i < L; i++) msg[b0 + i] = (uint8_t)(w[i >> 2] >> (8 * (i & 3)));
     }
   }
@@ -253,24 +272,27 @@ int launch_split(uint32_t nbits, const uint8_t *msg, size_t len, uint32_t *chunk
   const int g = grid_for(nvec, kAuxThreads);
   uint4 *out = reinterpret_cast<uint4 *>(chunks);
   if ((long long)len < (1LL << 31) && nvec < (1LL << 31))
-    k_split<uint32_t><<<g, kAuxThreads, 0, st>>>(msg, (uint32_t)len, P, S, out, (uint32_t)nvec, msg_aligned);
+    k_split<uint32_t><<<g, kAuxThreads, 0, st>>>(msg, (uint32_t)len, P, S, out, (uint32_t)nvec, msg_aligned,
+                                                  div_magic((uint32_t)(S / 4)));
   else
     k_split<unsigned long long><<<g, kAuxThreads, 0, st>>>(msg, (unsigned long long)len, P, S, out,
-                                                            (unsigned long long)nvec, msg_aligned);
+                                                            (unsigned long long)nvec, msg_aligned, DivMagic{});
   return cuda_rc(cudaGetLastError());
 }
 
 int launch_join(uint32_t nbits, const uint32_t *chunks, size_t n, uint8_t *msg, size_t len, cudaStream_t st) {
-  (void)n;
   const int P = (int)(nbits / 8 - 1), S = (int)(nbits / 32);
   if (len == 0) return PMK_OK;
   if (reinterpret_cast<uintptr_t>(chunks) & 15u) return PMK_EINVAL;
   const int out_aligned = (reinterpret_cast<uintptr_t>(msg) & 15u) == 0;
   const int g = grid_for(((long long)len + 15) / 16, kAuxThreads);
-  if ((long long)len < (1LL << 31))
-    k_join<uint32_t><<<g, kAuxThreads, 0, st>>>(chunks, P, S, msg, (uint32_t)len, out_aligned);
+  const long long nbuf16 = (long long)n * (S / 4);  // 16-byte vectors of the limb buffer
+  if ((long long)len < (1LL << 31) - 16 && nbuf16 < (1LL << 31))  // 16 u stays below 2^31 (exact division)
+    k_join<uint32_t><<<g, kAuxThreads, 0, st>>>(chunks, P, S, msg, (uint32_t)len, out_aligned,
+                                                 div_magic((uint32_t)P), (uint32_t)nbuf16);
   else
-    k_join<unsigned long long><<<g, kAuxThreads, 0, st>>>(chunks, P, S, msg, (unsigned long long)len, out_aligned);
+    k_join<unsigned long long><<<g, kAuxThreads, 0, st>>>(chunks, P, S, msg, (unsigned long long)len, out_aligned,
+                                                           DivMagic{}, (unsigned long long)nbuf16);
   return cuda_rc(cudaGetLastError());
 }
 
