@@ -287,8 +287,9 @@ int pmk_measure_int_peak(pmk_ctx *ctx, double *macs_per_clk_per_sm, double *sm_m
 
 /*
  * Launch geometry of the exponentiation kernels for one limb count and mode.
- *   limbs: nbits/32 for the full-width kernels (crt = 0), nbits/64 for the
- *          CRT half-width kernels (crt = 1).
+ *   limbs: nbits/32 for the full-width kernels (crt = 0); for the CRT
+ *          kernels (crt = 1) the limbs of one prime, nbits/(32 b) for a key
+ *          with b primes (nbits/64 for an ordinary key).
  *   tpi:   lanes of a warp that hold one exponentiation (a power of two
  *          dividing 32 and the limb count); 0 restores the built-in default.
  *   form:  Montgomery product form, 0 = one add-with-carry chain per lane and

@@ -74,7 +74,7 @@ int plan_and_capture(pmk_ctx *ctx, const pmk_job *jobs, size_t n_jobs, pmk_batch
     for (uint32_t k = 0; k < ks->K && k < jb.n_chunks; k++) {
       const long long count = ((long long)jb.n_chunks - k + ks->K - 1) / ks->K;
       for (long long i0 = 0; i0 < count; i0 += ipw)
-        for (int half = 0; half < (crt ? (int)ks->nprimes : 1); half++) {
+        for (int prime = 0; prime < (crt ? (int)ks->nprimes : 1); prime++) {
           pmk::BatchTask t;
           t.key = ks->d_keys + k;
           t.in = jb.d_in;
@@ -82,7 +82,7 @@ int plan_and_capture(pmk_ctx *ctx, const pmk_job *jobs, size_t n_jobs, pmk_batch
           t.first = k + i0 * ks->K;
           t.stride = ks->K;
           t.count = (int)std::min<long long>(ipw, count - i0);
-          t.mode = crt ? 2 + half : (jb.op == PMK_OP_ENCRYPT ? 0 : 1);
+          t.mode = crt ? 2 + prime : (jb.op == PMK_OP_ENCRYPT ? 0 : 1);
           g->tasks.push_back(t);
         }
     }

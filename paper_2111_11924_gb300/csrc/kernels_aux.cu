@@ -251,8 +251,8 @@ std::vector<ModexpEntry> entries(bool crt) {
 }
 
 const ModexpEntry *find_entry(uint32_t limbs, KernelConfig cfg, bool crt) {
-  static const std::vector<ModexpEntry> full = entries(false), half = entries(true);
-  for (const ModexpEntry &e : crt ? half : full)
+  static const std::vector<ModexpEntry> full = entries(false), residue = entries(true);
+  for (const ModexpEntry &e : crt ? residue : full)
     if (e.limbs == (int)limbs && e.tpi == (int)cfg.tpi && e.form == (int)cfg.form) return &e;
   return nullptr;
 }
@@ -379,7 +379,7 @@ int launch_modexp_naive(bool enc, uint32_t limbs, const KeyDev *keys, uint32_t K
 bool modexp_built(uint32_t limbs, KernelConfig cfg, bool crt) { return find_entry(limbs, cfg, crt) != nullptr; }
 
 // Defaults measured on GB300 (1 MiB and 100 MiB workloads at 2048 bits):
-// 64-limb full-width and 32-limb CRT halves run fastest with independent
+// 64-limb full-width and 32-limb CRT residues run fastest with independent
 // columns at 8 and 4 lanes; other widths use the carry-chain form.
 KernelConfig default_config(uint32_t limbs, bool crt) {
   KernelConfig c;

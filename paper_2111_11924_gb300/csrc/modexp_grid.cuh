@@ -67,21 +67,21 @@ __global__ void __launch_bounds__(kThreads) k_modexp(const KeyDev *__restrict__ 
   uint32_t *ybuf = tbl + kTableMax * ROW;
 
   const uint32_t key = CRT ? blockIdx.y / (uint32_t)parts : blockIdx.y;
-  const uint32_t half = CRT ? blockIdx.y % (uint32_t)parts : 0;
+  const uint32_t prime = CRT ? blockIdx.y % (uint32_t)parts : 0;
   const long long first = key + (long long)blockIdx.x * IPB * K;
   if (first >= n) return;  // block-uniform: no instance of this block has a chunk
   const KeyDev &kd = keys[key];
-  const uint32_t *M = CRT ? kd.P[half] : kd.N;
-  const uint32_t *R2 = CRT ? kd.R2h[half] : kd.R2;
-  const uint32_t *sched = CRT ? (sel ? kd.sched_hinv[half] : kd.sched_h[half]) : (sel ? kd.sched_e : kd.sched_d);
-  const uint32_t nsteps = CRT ? (sel ? kd.nsteps_hinv[half] : kd.nsteps_h[half]) : (sel ? kd.nsteps_e : kd.nsteps_d);
-  const uint32_t maxidx = CRT ? (sel ? kd.maxidx_hinv[half] : kd.maxidx_h[half]) : (sel ? kd.maxidx_e : kd.maxidx_d);
-  const uint32_t n0 = CRT ? kd.n0h[half] : kd.n0;
+  const uint32_t *M = CRT ? kd.P[prime] : kd.N;
+  const uint32_t *R2 = CRT ? kd.R2h[prime] : kd.R2;
+  const uint32_t *sched = CRT ? (sel ? kd.sched_hinv[prime] : kd.sched_h[prime]) : (sel ? kd.sched_e : kd.sched_d);
+  const uint32_t nsteps = CRT ? (sel ? kd.nsteps_hinv[prime] : kd.nsteps_h[prime]) : (sel ? kd.nsteps_e : kd.nsteps_d);
+  const uint32_t maxidx = CRT ? (sel ? kd.maxidx_hinv[prime] : kd.maxidx_h[prime]) : (sel ? kd.maxidx_e : kd.maxidx_d);
+  const uint32_t n0 = CRT ? kd.n0h[prime] : kd.n0;
 
   for (int i = threadIdx.x; i < S; i += kThreads) {
     sR2[i] = __ldg(R2 + i);
     sOne[i] = (i == 0);
-    if (CRT) sR3[i] = __ldg(kd.R3h[half] + i);
+    if (CRT) sR3[i] = __ldg(kd.R3h[prime] + i);
   }
   __syncthreads();
 
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(kThreads) k_modexp(const KeyDev *__restrict__ 
   exp_window<S, TPI, FORM>(a, tbl, ybuf, sched, nsteps, maxidx, nn, n0, r);
   mont<S, TPI, FORM>(a, sOne, nn, n0, r);  // leave the Montgomery domain
   if (active) {
-    uint32_t *o = out + t * W + (CRT ? half * S : 0) + r * L;
+    uint32_t *o = out + t * W + (CRT ? prime * S : 0) + r * L;
     if constexpr (L % 4 == 0) {
 #pragma unroll
       for (int j = 0; j < L; j += 4) *reinterpret_cast<uint4 *>(o + j) = make_uint4(a[j], a[j + 1], a[j + 2], a[j + 3]);

@@ -38,17 +38,17 @@ __global__ void __launch_bounds__(kThreads) k_modexp_tasks(const BatchTask *__re
     if (ti >= ntasks) break;
     const BatchTask tk = tasks[ti];
     const KeyDev &kd = *tk.key;
-    const int half = tk.mode >= 2 ? tk.mode - 2 : 0;
+    const int prime = tk.mode >= 2 ? tk.mode - 2 : 0;
     const bool enc = tk.mode == 0;
     const int parts = CRT ? (int)kd.nprimes : 1;
     const int W = parts * S;
-    const uint32_t *M = CRT ? kd.P[half] : kd.N;
-    const uint32_t *R2 = CRT ? kd.R2h[half] : kd.R2;
-    const uint32_t *sched = CRT ? kd.sched_h[half] : (enc ? kd.sched_e : kd.sched_d);
-    const uint32_t nsteps = CRT ? kd.nsteps_h[half] : (enc ? kd.nsteps_e : kd.nsteps_d);
-    const uint32_t maxidx = CRT ? kd.maxidx_h[half] : (enc ? kd.maxidx_e : kd.maxidx_d);
-    const uint32_t n0 = CRT ? kd.n0h[half] : kd.n0;
-    const uint32_t *sR2 = R2, *sR3 = CRT ? kd.R3h[half] : R2, *sOne = g_one_row;
+    const uint32_t *M = CRT ? kd.P[prime] : kd.N;
+    const uint32_t *R2 = CRT ? kd.R2h[prime] : kd.R2;
+    const uint32_t *sched = CRT ? kd.sched_h[prime] : (enc ? kd.sched_e : kd.sched_d);
+    const uint32_t nsteps = CRT ? kd.nsteps_h[prime] : (enc ? kd.nsteps_e : kd.nsteps_d);
+    const uint32_t maxidx = CRT ? kd.maxidx_h[prime] : (enc ? kd.maxidx_e : kd.maxidx_d);
+    const uint32_t n0 = CRT ? kd.n0h[prime] : kd.n0;
+    const uint32_t *sR2 = R2, *sR3 = CRT ? kd.R3h[prime] : R2, *sOne = g_one_row;
     const bool active = (int)g < tk.count;
     const long long t = tk.first + (long long)g * tk.stride;
     uint32_t nn[L], a[L];
@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(kThreads) k_modexp_tasks(const BatchTask *__re
     exp_window<S, TPI, FORM>(a, tbl, ybuf, sched, nsteps, maxidx, nn, n0, r);
     mont<S, TPI, FORM>(a, sOne, nn, n0, r);
     if (active) {
-      uint32_t *o = tk.out + t * W + (CRT ? half * S : 0) + r * L;
+      uint32_t *o = tk.out + t * W + (CRT ? prime * S : 0) + r * L;
       if constexpr (L % 4 == 0) {
 #pragma unroll
         for (int j = 0; j < L; j += 4) *reinterpret_cast<uint4 *>(o + j) = make_uint4(a[j], a[j + 1], a[j + 2], a[j + 3]);

@@ -1,5 +1,5 @@
 // Wide-key instantiations: 6144- and 8192-bit full width (192 / 256 limbs),
-// the CRT halves of 6144- and 8192-bit keys (96 / 128 limbs), and geometries
+// the CRT residues of two-prime 6144- and 8192-bit keys (96 / 128 limbs), and geometries
 // with more lanes per instance for latency-bound small batches.
 #include "modexp_kernels.cuh"
 
