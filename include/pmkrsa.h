@@ -286,6 +286,15 @@ const char *pmk_strerror(int code);
 int pmk_measure_int_peak(pmk_ctx *ctx, double *macs_per_clk_per_sm, double *sm_mhz, int *num_sms);
 
 /*
+ * INT32 multiply-add issue rate of this GPU, measured the same way with a
+ * loop of plain 32-bit multiply-adds (mad.lo, sixteen independent chains per
+ * thread): mad.lo per clock per SM, the SM clock seen (MHz) and the SM count.
+ * One 32x32->64 MAC is two such operations (low and high halves); this is
+ * the denominator of the kernels' "% of INT32 peak".
+ */
+int pmk_measure_imad_peak(pmk_ctx *ctx, double *mad_lo_per_clk_per_sm, double *sm_mhz, int *num_sms);
+
+/*
  * Launch geometry of the exponentiation kernels for one limb count and mode.
  *   limbs: nbits/32 for the full-width kernels (crt = 0); for the CRT
  *          kernels (crt = 1) the limbs of one prime, nbits/(32 b) for a key

@@ -552,6 +552,13 @@ int pmk_measure_int_peak(pmk_ctx *ctx, double *macs_per_clk_per_sm, double *sm_m
   return pmk::measure_int_peak(macs_per_clk_per_sm, sm_mhz, num_sms);
 }
 
+int pmk_measure_imad_peak(pmk_ctx *ctx, double *mad_lo_per_clk_per_sm, double *sm_mhz, int *num_sms) {
+  if (!ctx || !mad_lo_per_clk_per_sm || !sm_mhz || !num_sms) return PMK_EINVAL;
+  DeviceGuard g(ctx->device);
+  if (!g.ok()) return PMK_ECUDA;
+  return pmk::measure_imad_peak(mad_lo_per_clk_per_sm, sm_mhz, num_sms);
+}
+
 int pmk_set_kernel_config(pmk_ctx *ctx, uint32_t limbs, int crt, uint32_t tpi, uint32_t form) {
   if (!ctx) return PMK_EINVAL;
   const uint32_t key = limbs << 1 | (crt ? 1u : 0u);

@@ -7,7 +7,9 @@
 //   wide:  p = lo32(p >> 32) * m          (one wide IMAD per MAC)
 //   pair:  lo = x * m + c; hi = mulhi(x, m) + d   (mad.lo + mad.hi per MAC)
 // The larger of the two rates (MACs per clock per SM) is the roofline
-// denominator for the exponentiation kernels.
+// denominator for the exponentiation kernels.  A third loop of plain 32-bit
+// multiply-adds (mad.lo only, sixteen chains) gives the INT32 multiply-add
+// issue rate, the denominator of the "% of INT32 peak" figure.
 #include "pmk_internal.h"
 
 namespace pmk {
@@ -17,11 +19,35 @@ constexpr int kPeakThreads = 256;
 constexpr int kPeakBlocksPerSm = 4;
 constexpr int kPeakIters = 1024;
 
-template <bool kWide>
+enum PeakLoop : int { kPair = 0, kWide = 1, kLoOnly = 2 };
+
+template <int kLoop>
 __global__ void __launch_bounds__(kPeakThreads, kPeakBlocksPerSm) k_peak(uint64_t *out, long long *cycles, uint32_t m0) {
   uint64_t r = 0;
   long long t0, t1;
-  if constexpr (kWide) {
+  if constexpr (kLoop == kLoOnly) {
+    uint32_t x[16], m[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+      x[k] = threadIdx.x * 0x9E3779B9u + 7 * k;
+      m[k] = m0 + 2 * k;
+    }
+    __syncthreads();
+    t0 = clock64();
+#pragma unroll 1
+    for (int it = 0; it < kPeakIters; it++) {
+#pragma unroll
+      for (int k = 0; k < 16; k++) {
+        uint32_t a;
+        asm volatile("mad.lo.u32 %0, %1, %2, %3;" : "=r"(a) : "r"(x[k]), "r"(m[k]), "r"(x[(k + 5) & 15]));
+        x[k] = a;
+      }
+    }
+    __syncthreads();
+    t1 = clock64();
+#pragma unroll
+    for (int k = 0; k < 16; k++) r ^= x[k];
+  } else if constexpr (kLoop == kWide) {
     uint64_t p[16];
     uint32_t m[16];
 #pragma unroll
@@ -70,8 +96,9 @@ __global__ void __launch_bounds__(kPeakThreads, kPeakBlocksPerSm) k_peak(uint64_
   if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
 }
 
-// MACs per clock per SM of one variant, best of a few launches.
-template <bool kWide>
+// Operations per clock per SM of one loop (MACs, or mad.lo for kLoOnly),
+// best of a few launches.
+template <int kLoop>
 int measure(int sms, uint64_t *out, long long *cyc, double *rate, double *mhz) {
   const int blocks = sms * kPeakBlocksPerSm;
   std::vector<long long> hc(blocks);
@@ -81,7 +108,7 @@ int measure(int sms, uint64_t *out, long long *cyc, double *rate, double *mhz) {
   *rate = 0;
   for (int rep = 0; rep < 4; rep++) {
     cudaEventRecord(e0);
-    k_peak<kWide><<<blocks, kPeakThreads>>>(out, cyc, 0x9E3779B1u + 2 * rep);
+    k_peak<kLoop><<<blocks, kPeakThreads>>>(out, cyc, 0x9E3779B1u + 2 * rep);
     cudaEventRecord(e1);
     if (cudaEventSynchronize(e1) != cudaSuccess) return PMK_ECUDA;
     float ms = 0;
@@ -89,7 +116,7 @@ int measure(int sms, uint64_t *out, long long *cyc, double *rate, double *mhz) {
     if (cudaMemcpy(hc.data(), cyc, sizeof(long long) * blocks, cudaMemcpyDeviceToHost) != cudaSuccess) return PMK_ECUDA;
     long long mx = 1;
     for (long long c : hc) mx = c > mx ? c : mx;
-    const double macs = (double)kPeakBlocksPerSm * kPeakThreads * kPeakIters * (kWide ? 16 : 8);
+    const double macs = (double)kPeakBlocksPerSm * kPeakThreads * kPeakIters * (kLoop == kPair ? 8 : 16);
     if (rep > 0 && macs / mx > *rate) {  // the first launch warms up
       *rate = macs / mx;
       *mhz = mx / (ms * 1e3);
@@ -100,18 +127,17 @@ int measure(int sms, uint64_t *out, long long *cyc, double *rate, double *mhz) {
   return cudaGetLastError() == cudaSuccess ? PMK_OK : PMK_ECUDA;
 }
 
-}  // namespace
-
-int measure_int_peak(double *macs_per_clk_per_sm, double *sm_mhz, int *num_sms) {
+// Runs loop kLoop on every SM (kPeakBlocksPerSm resident blocks each).
+template <int kLoop>
+int run_peak(double *rate, double *mhz, int *num_sms) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return PMK_ECUDA;
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PMK_ECUDA;
   int occ = 0;  // all blocks must be resident at once for the per-block clock to hold
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_peak<true>, kPeakThreads, 0);
-  int occ2 = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_peak<false>, kPeakThreads, 0);
-  if (occ < kPeakBlocksPerSm || occ2 < kPeakBlocksPerSm) return PMK_ECUDA;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_peak<kLoop>, kPeakThreads, 0) != cudaSuccess ||
+      occ < kPeakBlocksPerSm)
+    return PMK_ECUDA;
   const int blocks = sms * kPeakBlocksPerSm;
   uint64_t *out = nullptr;
   long long *cyc = nullptr;
@@ -120,16 +146,27 @@ int measure_int_peak(double *macs_per_clk_per_sm, double *sm_mhz, int *num_sms) 
     cudaFree(out);
     return PMK_ENOMEM;
   }
-  double wide = 0, pair = 0, mhz_w = 0, mhz_p = 0;
-  int rc = measure<true>(sms, out, cyc, &wide, &mhz_w);
-  if (rc == PMK_OK) rc = measure<false>(sms, out, cyc, &pair, &mhz_p);
+  const int rc = measure<kLoop>(sms, out, cyc, rate, mhz);
   cudaFree(out);
   cudaFree(cyc);
+  *num_sms = sms;
+  return rc;
+}
+
+}  // namespace
+
+int measure_int_peak(double *macs_per_clk_per_sm, double *sm_mhz, int *num_sms) {
+  double wide = 0, pair = 0, mhz_w = 0, mhz_p = 0;
+  int rc = run_peak<kWide>(&wide, &mhz_w, num_sms);
+  if (rc == PMK_OK) rc = run_peak<kPair>(&pair, &mhz_p, num_sms);
   if (rc != PMK_OK) return rc;
   *macs_per_clk_per_sm = wide > pair ? wide : pair;
   *sm_mhz = wide > pair ? mhz_w : mhz_p;
-  *num_sms = sms;
   return PMK_OK;
+}
+
+int measure_imad_peak(double *mad_lo_per_clk_per_sm, double *sm_mhz, int *num_sms) {
+  return run_peak<kLoOnly>(mad_lo_per_clk_per_sm, sm_mhz, num_sms);
 }
 
 }  // namespace pmk

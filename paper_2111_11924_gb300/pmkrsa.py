@@ -80,6 +80,8 @@ def load_library() -> ctypes.CDLL:
         "pmk_strerror": (ctypes.c_char_p, [i]),
         "pmk_measure_int_peak": (i, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(i)]),
+        "pmk_measure_imad_peak": (i, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(i)]),
         "pmk_set_kernel_config": (i, [vp, u32, i, u32, u32]),
         "pmk_get_kernel_config": (i, [vp, u32, i, P32, P32]),
         "pmk_list_kernel_configs": (i, [u32, i, P32, P32, i]),
@@ -370,6 +372,13 @@ class Context:
         _check(load_library().pmk_measure_int_peak(self.handle, ctypes.byref(m), ctypes.byref(mhz), ctypes.byref(sms)),
                "pmk_measure_int_peak")
         return {"macs_per_clk_per_sm": m.value, "sm_mhz": mhz.value, "num_sms": sms.value}
+
+    def measure_imad_peak(self) -> dict:
+        """The INT32 multiply-add (mad.lo) issue rate per clock per SM, measured on this GPU."""
+        m, mhz, sms = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+        _check(load_library().pmk_measure_imad_peak(self.handle, ctypes.byref(m), ctypes.byref(mhz),
+                                                    ctypes.byref(sms)), "pmk_measure_imad_peak")
+        return {"mad_lo_per_clk_per_sm": m.value, "sm_mhz": mhz.value, "num_sms": sms.value}
 
     def set_kernel_config(self, limbs: int, crt: bool, tpi: int, form: int = 0) -> None:
         """Lanes per instance and Montgomery form for (limbs, crt); tpi = 0 restores the default."""

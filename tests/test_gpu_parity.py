@@ -496,3 +496,17 @@ def test_100mib_roundtrip_and_oracle_sample(ctx):
         assert np.array_equal(oracle.encrypt_chunks(m_h[sel], sub_keys, threads=8), c_h[sel]), k
     assert np.array_equal(m_h, oracle.split(msg, w.nbits)[idx])
     assert ctx.status() == 0
+
+
+def test_integer_peak_measurements_are_sane(ctx):
+    """The roofline denominators come from the library's own loops: the MAC
+    rate and the mad.lo rate per clock per SM must be positive, below the
+    architectural issue limit of 128 lanes per clock per SM, and consistent
+    with each other (a MAC costs at least one mad.lo-equivalent issue)."""
+    mac = ctx.measure_int_peak()
+    lo = ctx.measure_imad_peak()
+    assert mac["num_sms"] == lo["num_sms"] > 0
+    assert 1.0 < mac["macs_per_clk_per_sm"] <= 128.0
+    assert 1.0 < lo["mad_lo_per_clk_per_sm"] <= 128.0
+    assert mac["macs_per_clk_per_sm"] <= lo["mad_lo_per_clk_per_sm"] * 1.05
+    assert mac["sm_mhz"] > 100 and lo["sm_mhz"] > 100
