@@ -106,6 +106,17 @@ int pmk_keygen_host(uint32_t K, uint32_t nbits, uint64_t e, uint64_t seed, uint3
 int pmk_keyset_from_primes(pmk_ctx *ctx, uint32_t K, uint32_t nbits, uint64_t e, const uint32_t *p,
                            const uint32_t *q, pmk_keyset **out);
 
+/*
+ * Build a multi-prime key set from given primes: K x nprimes x
+ * nbits/(32 nprimes) limbs, key-major (the layout of
+ * pmk_keyset_export_primes).  Derives N, d, the CRT values and the device
+ * tables.  The caller guarantees the primes are prime; EINVAL if a cheap
+ * check fails: each odd with exactly nbits/nprimes bits and its top two bits
+ * set, gcd(e, r_i - 1) = 1, pairwise distinct, N of exactly nbits bits.
+ */
+int pmk_keyset_from_primes_multi(pmk_ctx *ctx, uint32_t K, uint32_t nbits, uint32_t nprimes, uint64_t e,
+                                 const uint32_t *primes, pmk_keyset **out);
+
 /* Copy the key material out (host arrays, key-major, little-endian limbs):
  * N, d: K x nbits/32;  p, q, dp, dq, qinv: K x nbits/64.  Any pointer may be
  * NULL.  For a key set with more than two primes p .. qinv must be NULL

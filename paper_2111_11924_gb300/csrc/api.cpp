@@ -308,6 +308,33 @@ int pmk_keyset_from_primes(pmk_ctx *ctx, uint32_t K, uint32_t nbits, uint64_t e,
   }
 }
 
+int pmk_keyset_from_primes_multi(pmk_ctx *ctx, uint32_t K, uint32_t nbits, uint32_t nprimes, uint64_t e,
+                                 const uint32_t *primes, pmk_keyset **out) {
+  if (!ctx || !out || !primes || K == 0 || K > kMaxKeys) return PMK_EINVAL;
+  if (!pmk::valid_multiprime(nbits, nprimes) || e < 3 || !(e & 1) || (e >> 32)) return PMK_EINVAL;
+  if (!width_built(nbits, nprimes)) return PMK_EUNSUPPORTED;
+  try {
+    pmk_keyset *ks = new pmk_keyset();
+    ks->device = ctx->device;
+    ks->K = K;
+    ks->nbits = nbits;
+    ks->e = e;
+    ks->nprimes = nprimes;
+    ks->keys.resize(K);
+    const size_t s = nbits / 32;
+    for (uint32_t k = 0; k < K; k++) {
+      int rc = pmk::host_from_primes_mp(nbits, nprimes, e, primes + k * s, ks->keys[k]);
+      if (rc != PMK_OK) {
+        delete ks;
+        return rc;
+      }
+    }
+    return finish_keyset(ctx, ks, out);
+  } catch (const std::bad_alloc &) {
+    return PMK_ENOMEM;
+  }
+}
+
 int pmk_keyset_export(const pmk_keyset *ks, uint32_t *N, uint32_t *d, uint32_t *p, uint32_t *q, uint32_t *dp,
                       uint32_t *dq, uint32_t *qinv) {
   if (!ks) return PMK_EINVAL;

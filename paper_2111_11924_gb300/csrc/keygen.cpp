@@ -523,4 +523,25 @@ int host_from_primes(uint32_t nbits, uint64_t e, const uint32_t *p32, const uint
   return PMK_OK;
 }
 
+int host_from_primes_mp(uint32_t nbits, uint32_t nprimes, uint64_t e, const uint32_t *primes32, HostKey &out) {
+  if (!valid_multiprime(nbits, nprimes) || e < 3 || !(e & 1) || e >> 32) return PMK_EINVAL;
+  const size_t h = nbits / 32 / nprimes;
+  std::vector<std::vector<u64>> r;
+  for (uint32_t i = 0; i < nprimes; i++) {
+    std::vector<u64> f = to64(primes32 + i * h, h);
+    const int n = (int)f.size();
+    if (!(f[0] & 1) || (f[n - 1] >> 62) != 3) return PMK_EINVAL;  // odd, exactly nbits/b bits, top two set
+    const u64 rm = (mod_small(f.data(), n, e) + e - 1) % e;
+    if (gcd64(e, rm) != 1) return PMK_EINVAL;
+    for (const auto &x : r)
+      if (cmp(x.data(), f.data(), n) == 0) return PMK_EINVAL;
+    r.push_back(f);
+  }
+  std::vector<u64> N = r[0];
+  for (uint32_t i = 1; i < nprimes; i++) N = mul_full(N, r[i]);
+  if (!(N[N.size() - 1] >> 63)) return PMK_EINVAL;  // the modulus must have exactly nbits bits
+  finish_key(nbits, e, r, out);
+  return PMK_OK;
+}
+
 }  // namespace pmk

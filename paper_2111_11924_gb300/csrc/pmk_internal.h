@@ -83,6 +83,7 @@ int host_keygen(uint32_t K, uint32_t nbits, uint64_t e, uint64_t seed, std::vect
 int host_keygen_mp(uint32_t K, uint32_t nbits, uint32_t nprimes, uint64_t e, uint64_t seed, std::vector<HostKey> &out);
 bool valid_multiprime(uint32_t nbits, uint32_t nprimes);
 int host_from_primes(uint32_t nbits, uint64_t e, const uint32_t *p, const uint32_t *q, HostKey &out);
+int host_from_primes_mp(uint32_t nbits, uint32_t nprimes, uint64_t e, const uint32_t *primes, HostKey &out);
 Schedule make_schedule(const uint32_t *exp, int nlimbs);
 
 // Kernel launchers (kernels_*.cu).  All return PMK_* codes.

@@ -55,6 +55,7 @@ def load_library() -> ctypes.CDLL:
         "pmk_keygen_multiprime": (i, [vp, u32, u32, u32, u64, u64, ctypes.POINTER(vp)]),
         "pmk_keygen_host_multiprime": (i, [u32, u32, u32, u64, u64, P32, P32, P32, P32, P32]),
         "pmk_keyset_export_primes": (i, [vp, P32, P32, P32]),
+        "pmk_keyset_from_primes_multi": (i, [vp, u32, u32, u32, u64, P32, ctypes.POINTER(vp)]),
         "pmk_keyset_num_primes": (u32, [vp]),
         "pmk_keyset_num_keys": (u32, [vp]),
         "pmk_keyset_nbits": (u32, [vp]),
@@ -262,6 +263,15 @@ class Context:
         h = ctypes.c_void_p()
         _check(load_library().pmk_keyset_from_primes(self.handle, K, nbits, e, _p32(p), _p32(q), ctypes.byref(h)),
                "pmk_keyset_from_primes")
+        return KeySet(self, h)
+
+    def keyset_from_primes_multi(self, nbits: int, nprimes: int, e: int, primes: np.ndarray) -> KeySet:
+        """Multi-prime key set from (K, nbits/32) limbs holding each key's nprimes primes."""
+        primes = np.ascontiguousarray(primes, np.uint32)
+        h = ctypes.c_void_p()
+        _check(load_library().pmk_keyset_from_primes_multi(self.handle, primes.shape[0], nbits, nprimes, e,
+                                                           _p32(primes), ctypes.byref(h)),
+               "pmk_keyset_from_primes_multi")
         return KeySet(self, h)
 
     # ------------------------------------------------------------ hot path

@@ -256,3 +256,27 @@ def test_multiprime_autotune_and_errors(ctx, P):
     buf = np.zeros(2 * 2048 // 32, np.uint32)
     p32 = buf.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
     assert lib.pmk_keyset_export(ks.handle, None, None, p32, None, None, None, None) == P.pmkrsa.PMK_EINVAL
+
+
+def test_multiprime_keyset_from_oracle_primes(ctx, P):
+    """Importing the oracle's primes gives the oracle's key material, and the
+    imported set decrypts like the generated one; malformed primes are rejected."""
+    ok = oracle.keygen_mp(3, 3072, 3, 65537, 0x50444D4B0000EB00)
+    ks = ctx.keyset_from_primes_multi(3072, 3, 65537, ok.a["primes"])
+    ex = ks.export()
+    for f in ok.a:
+        assert np.array_equal(ex[f], ok.a[f]), f
+    rng = np.random.default_rng(4)
+    m = np.stack([oracle.to_limbs(W.random_below(rng, N), 96) for N in ok.ints("N") * 4])
+    c = ctx.encrypt_chunks(ks, dev(m))
+    assert np.array_equal(host(c), oracle.encrypt_chunks(m, ok))
+    assert np.array_equal(host(ctx.decrypt_chunks(ks, c, use_crt=True)), m)
+    bad = ok.a["primes"].copy()
+    bad[0, 32:64] = bad[0, 0:32]  # r_1 = r_0
+    with pytest.raises(P.PMKError):
+        ctx.keyset_from_primes_multi(3072, 3, 65537, bad)
+    bad = ok.a["primes"].copy()
+    bad[1, 0] &= ~np.uint32(1)  # an even "prime"
+    with pytest.raises(P.PMKError):
+        ctx.keyset_from_primes_multi(3072, 3, 65537, bad)
+    ks.free()
