@@ -2,7 +2,9 @@
 // exponentiation width and mode, and capture range checks, one persistent
 // kernel per group (on forked streams) and CRT recombination into a CUDA
 // graph that pmk_batch_launch replays.  A CRT job contributes one task per
-// (chunk group, prime) and one recombination launch.
+// (chunk group, prime) and one recombination launch.  Jobs that fill the GPU
+// several times over skip the queue and get their own grid launch in the
+// same graph.
 #include <algorithm>
 #include <new>
 #include <vector>
@@ -23,6 +25,12 @@ struct pmk_batch {
 };
 
 namespace {
+
+// A job with at least this many GPU-fulls of exponentiations runs as one
+// plain grid launch inside the graph: it fills the GPU alone, and the grid
+// kernel is a few percent faster than the persistent one on a single large
+// job (measured on 100 MiB).  Smaller jobs share the persistent queues.
+constexpr long long kDirectWaves = 4;
 
 struct Group {
   uint32_t limbs = 0;
@@ -62,6 +70,14 @@ int plan_and_capture(pmk_ctx *ctx, const pmk_job *jobs, size_t n_jobs, pmk_batch
     groups.push_back(g);
     return &groups.back();
   };
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess) return PMK_ECUDA;
+  struct Direct {
+    size_t job;
+    uint32_t limbs;
+    pmk::KernelConfig cfg;
+  };
+  std::vector<Direct> direct;  // jobs large enough to fill the GPU alone: one plain grid launch each
   for (size_t j = 0; j < n_jobs; j++) {
     const pmk_job &jb = jobs[j];
     if (jb.n_chunks == 0) continue;
@@ -70,6 +86,13 @@ int plan_and_capture(pmk_ctx *ctx, const pmk_job *jobs, size_t n_jobs, pmk_batch
     const uint32_t S = ks->nbits / 32, limbs = crt ? S / ks->nprimes : S;
     Group *g = group_for(limbs, crt);
     if (!g) return PMK_EUNSUPPORTED;
+    const long long wave = pmk::modexp_resident_instances(limbs, g->cfg, crt);  // one GPU-full
+    if (wave <= 0) return PMK_EUNSUPPORTED;
+    const long long instances = (long long)jb.n_chunks * (crt ? ks->nprimes : 1);
+    if (instances >= kDirectWaves * wave) {
+      direct.push_back(Direct{j, limbs, g->cfg});
+      continue;
+    }
     const uint32_t ipw = 32 / g->cfg.tpi;
     for (uint32_t k = 0; k < ks->K && k < jb.n_chunks; k++) {
       const long long count = ((long long)jb.n_chunks - k + ks->K - 1) / ks->K;
@@ -94,9 +117,9 @@ int plan_and_capture(pmk_ctx *ctx, const pmk_job *jobs, size_t n_jobs, pmk_batch
                      [](const pmk::BatchTask &x, const pmk::BatchTask &y) { return (x.mode != 0) > (y.mode != 0); });
   std::stable_sort(groups.begin(), groups.end(),
                    [](const Group &x, const Group &y) { return x.limbs * (x.crt ? 1 : 2) > y.limbs * (y.crt ? 1 : 2); });
+  groups.erase(std::remove_if(groups.begin(), groups.end(), [](const Group &g) { return g.tasks.empty(); }),
+               groups.end());
   std::vector<pmk::BatchTask> all;
-  int sms = 0;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess) return PMK_ECUDA;
   for (Group &g : groups) {
     g.offset = all.size();
     all.insert(all.end(), g.tasks.begin(), g.tasks.end());
@@ -106,7 +129,8 @@ int plan_and_capture(pmk_ctx *ctx, const pmk_job *jobs, size_t n_jobs, pmk_batch
     g.blocks = (int)std::max<long long>(1, std::min<long long>(need, (long long)per_sm * sms));
   }
   b->n_tasks = all.size();
-  b->n_kernels = (int)groups.size();
+  b->n_kernels = (int)(groups.size() + direct.size());
+  const size_t units = groups.size() + direct.size();  // one side stream per kernel
   if (!all.empty()) {
     if (cudaMalloc(&b->d_tasks, sizeof(pmk::BatchTask) * all.size()) != cudaSuccess) return PMK_ENOMEM;
     if (cudaMemcpy(b->d_tasks, all.data(), sizeof(pmk::BatchTask) * all.size(), cudaMemcpyHostToDevice) != cudaSuccess)
@@ -114,8 +138,8 @@ int plan_and_capture(pmk_ctx *ctx, const pmk_job *jobs, size_t n_jobs, pmk_batch
   }
   if (cudaMalloc(&b->d_counters, sizeof(int) * std::max<size_t>(1, groups.size())) != cudaSuccess) return PMK_ENOMEM;
   if (cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking) != cudaSuccess) return PMK_ECUDA;
-  b->side.resize(groups.size(), nullptr);
-  b->events.resize(groups.size() + 1, nullptr);
+  b->side.resize(units, nullptr);
+  b->events.resize(units + 1, nullptr);
   for (auto &s : b->side)
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return PMK_ECUDA;
   for (auto &e : b->events)
@@ -140,6 +164,22 @@ int plan_and_capture(pmk_ctx *ctx, const pmk_job *jobs, size_t n_jobs, pmk_batch
                                   b->d_counters + gi, g.blocks, b->side[gi]);
     if (rc == PMK_OK && (cudaEventRecord(b->events[gi], b->side[gi]) != cudaSuccess ||
                          cudaStreamWaitEvent(b->capture, b->events[gi], 0) != cudaSuccess))
+      rc = PMK_ECUDA;
+  }
+  for (size_t di = 0; di < direct.size() && rc == PMK_OK; di++) {
+    const size_t u = groups.size() + di;
+    const pmk_job &jb = jobs[direct[di].job];
+    const pmk::ExpMode mode = jb.op == PMK_OP_ENCRYPT   ? pmk::ExpMode::kEncrypt
+                              : jb.op == PMK_OP_DECRYPT ? pmk::ExpMode::kDecrypt
+                                                        : pmk::ExpMode::kCrtHalf;
+    if (cudaStreamWaitEvent(b->side[u], b->events.back(), 0) != cudaSuccess) {
+      rc = PMK_ECUDA;
+      break;
+    }
+    rc = pmk::launch_modexp(mode, direct[di].limbs, direct[di].cfg, jb.ks->d_keys, jb.ks->K, jb.d_in, jb.d_out,
+                            jb.n_chunks, b->side[u], jb.ks->nprimes);
+    if (rc == PMK_OK && (cudaEventRecord(b->events[u], b->side[u]) != cudaSuccess ||
+                         cudaStreamWaitEvent(b->capture, b->events[u], 0) != cudaSuccess))
       rc = PMK_ECUDA;
   }
   for (size_t j = 0; j < n_jobs && rc == PMK_OK; j++)

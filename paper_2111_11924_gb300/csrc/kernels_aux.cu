@@ -431,6 +431,15 @@ int modexp_tasks_blocks_per_sm(uint32_t limbs, KernelConfig cfg, bool crt) {
   return blocks;
 }
 
+long long modexp_resident_instances(uint32_t limbs, KernelConfig cfg, bool crt) {
+  const int per_sm = modexp_tasks_blocks_per_sm(limbs, cfg, crt);
+  int dev = 0, sms = 0;
+  if (per_sm <= 0 || cfg.tpi == 0 || cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 0;
+  return (long long)per_sm * sms * (dev::kThreads / (int)cfg.tpi);
+}
+
 int launch_modexp_tasks(uint32_t limbs, KernelConfig cfg, bool crt, const BatchTask *tasks, int ntasks, int *counter,
                         int blocks, cudaStream_t st) {
   if (ntasks == 0) return PMK_OK;

@@ -121,6 +121,8 @@ int launch_modexp_tasks(uint32_t limbs, KernelConfig cfg, bool crt, const BatchT
                         int blocks, cudaStream_t st);
 // Resident blocks per SM of that kernel (0 if not built).
 int modexp_tasks_blocks_per_sm(uint32_t limbs, KernelConfig cfg, bool crt);
+// Exponentiations the whole GPU holds at once in that geometry (0 if not built).
+long long modexp_resident_instances(uint32_t limbs, KernelConfig cfg, bool crt);
 int measure_int_peak(double *macs_per_clk_per_sm, double *sm_mhz, int *num_sms);
 int measure_imad_peak(double *mad_lo_per_clk_per_sm, double *sm_mhz, int *num_sms);
 

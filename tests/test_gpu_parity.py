@@ -510,3 +510,34 @@ def test_integer_peak_measurements_are_sane(ctx):
     assert 1.0 < lo["mad_lo_per_clk_per_sm"] <= 128.0
     assert mac["macs_per_clk_per_sm"] <= lo["mad_lo_per_clk_per_sm"] * 1.05
     assert mac["sm_mhz"] > 100 and lo["sm_mhz"] > 100
+
+
+def test_batch_large_jobs_take_a_grid_launch(ctx, P):
+    """Jobs that fill the GPU several times over run as plain grid launches
+    inside the batch graph, next to queued small jobs; every output equals the
+    per-call result, and a batch of one large job holds no queued tasks."""
+    from paper_2111_11924_gb300 import pmkrsa as B
+
+    ks = ctx.keygen(8, 2048, 65537, 0x50444D4B0000EC00)
+    msg = torch.from_numpy(np.random.default_rng(12).integers(0, 256, 30000 * 255, dtype=np.uint8)).cuda()
+    big = ctx.encrypt_chunks(ks, ctx.split(2048, msg))            # 30,000 chunks
+    small = big[:37].clone()
+    jobs = [(ks, big[:20000], torch.zeros_like(big[:20000]), B.OP_DECRYPT_CRT),
+            (ks, big, torch.zeros_like(big), B.OP_DECRYPT),
+            (ks, small, torch.zeros_like(small), B.OP_DECRYPT_CRT)]
+    batch = ctx.batch(jobs)
+    assert batch.n_kernels >= 3 and batch.n_tasks > 0
+    batch.launch()
+    ctx.check()
+    for k, x, out, op in jobs:
+        assert torch.equal(out, ctx.decrypt_chunks(k, x, use_crt=op == B.OP_DECRYPT_CRT)), (x.shape[0], op)
+    assert torch.equal(jobs[1][2], ctx.split(2048, msg))
+    batch.destroy()
+    out = torch.zeros_like(big)
+    one = ctx.batch([(ks, big, out, B.OP_DECRYPT_CRT)])
+    assert one.n_tasks == 0 and one.n_kernels == 1
+    one.launch()
+    ctx.check()
+    assert torch.equal(out, ctx.split(2048, msg))
+    one.destroy()
+    ks.free()
