@@ -280,3 +280,24 @@ def test_multiprime_keyset_from_oracle_primes(ctx, P):
     with pytest.raises(P.PMKError):
         ctx.keyset_from_primes_multi(3072, 3, 65537, bad)
     ks.free()
+
+
+@pytest.mark.parametrize("nbits,b,K,n,e", [(1024, 4, 1, 9, 65537), (3072, 3, 5, 3, 65537), (2048, 4, 2, 11, 3),
+                                           (512, 4, 3, 1, 17)])
+def test_multiprime_degenerate_counts_and_exponents(ctx, nbits, b, K, n, e):
+    """One key, fewer chunks than keys, small public exponents; encryption in
+    place; CRT and full d against the oracle."""
+    ks = ctx.keygen(K, nbits, e, 0x50444D4B0000ED00 + nbits + K, nprimes=b)
+    ok = oracle.keygen_mp(K, nbits, b, e, 0x50444D4B0000ED00 + nbits + K)
+    ex = ks.export()
+    assert all(np.array_equal(ex[f], ok.a[f]) for f in ok.a)
+    rng = np.random.default_rng(n)
+    Ns = ok.ints("N")
+    m = np.stack([oracle.to_limbs(W.random_below(rng, Ns[t % K]), nbits // 32) for t in range(n)])
+    x = dev(m)
+    ctx.encrypt_chunks(ks, x, out=x)  # in place
+    assert np.array_equal(host(x), oracle.encrypt_chunks(m, ok))
+    for use_crt in (True, False):
+        assert np.array_equal(host(ctx.decrypt_chunks(ks, x, use_crt=use_crt)), m), use_crt
+    assert ctx.status() == 0
+    ks.free()
