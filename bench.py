@@ -395,6 +395,7 @@ def run_ours(args):
         "e2e": {"value": world * n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": w.msg_bytes + cipher_bytes,
                 "d2h_bytes_per_step": cipher_bytes + w.msg_bytes},
         "gpu_launches": KERNELS_PER_STEP * args.steps,
+        "gpu": {"name": torch.cuda.get_device_name(local), "sms": sms, "host_cores": os.cpu_count()},
         "source_digest": digest,
     }
     if rank == 0:  # outside the timed region: split / join bandwidth on the 100 MiB file

@@ -18,8 +18,10 @@
  *     the device (an input chunk >= its modulus) are recorded in the
  *     context and reported by pmk_status().
  *   - Chunk buffers hold n_chunks x nbits/32 little-endian uint32 limbs,
- *     chunk-major ("limb buffer"), and must be 16-byte aligned (EINVAL).  Chunk t is bound to key t mod K, the
- *     row-per-key reshape of the i x j plaintext matrix (Section 3.1).
+ *     chunk-major ("limb buffer"), and must be 16-byte aligned (EINVAL).
+ *     Chunk t is bound to key t mod K, the row-per-key reshape of the i x j
+ *     plaintext matrix (Section 3.1).  A call takes fewer than 2^32 chunks
+ *     (EINVAL otherwise).
  *   - Calls on one context are not thread-safe; use one context per thread.
  */
 #ifndef PMKRSA_H

@@ -16,6 +16,7 @@ from .pmkrsa import (  # noqa: F401
     KeySet,
     keygen_host,
     keygen_host_multiprime,
+    TuneCache,
     kernel_configs,
     load_library,
     num_chunks,
@@ -23,4 +24,4 @@ from .pmkrsa import (  # noqa: F401
     strerror,
 )
 
-__all__ = ["PMKError", "Context", "KeySet", "keygen_host", "keygen_host_multiprime", "kernel_configs", "load_library", "num_chunks", "payload_bytes", "strerror"]
+__all__ = ["PMKError", "Context", "KeySet", "keygen_host", "keygen_host_multiprime", "TuneCache", "kernel_configs", "load_library", "num_chunks", "payload_bytes", "strerror"]

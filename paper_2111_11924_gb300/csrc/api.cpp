@@ -149,8 +149,12 @@ bool width_built(uint32_t nbits, uint32_t nprimes = 2) {
 // Most keys per key set: the CRT grid has one row per (key, prime) pair.
 constexpr uint32_t kMaxKeys = 65535 / pmk::kMaxPrimes;
 
-int check_chunk_call(const pmk_ctx *ctx, const pmk_keyset *ks, const void *in, const void *out) {
-  if (!ctx || !ks) return PMK_EINVAL;
+// Most chunks per call: keeps byte counts and grid sizes far from overflow
+// (2^32 chunks of 2048 bits are 1 TiB, beyond any device's memory).
+constexpr size_t kMaxChunks = (size_t)1 << 32;
+
+int check_chunk_call(const pmk_ctx *ctx, const pmk_keyset *ks, const void *in, const void *out, size_t n_chunks) {
+  if (!ctx || !ks || n_chunks >= kMaxChunks) return PMK_EINVAL;
   if (ks->device != ctx->device) return PMK_EINVAL;
   if (!in || !out || !aligned16(in) || !aligned16(out)) return PMK_EINVAL;
   return PMK_OK;
@@ -224,6 +228,7 @@ int pmk_keygen(pmk_ctx *ctx, uint32_t K, uint32_t nbits, uint64_t e, uint64_t se
 
 int pmk_keygen_multiprime(pmk_ctx *ctx, uint32_t K, uint32_t nbits, uint32_t nprimes, uint64_t e, uint64_t seed,
                           pmk_keyset **out) {
+  pmk::TraceRange trace("pmk_keygen_multiprime");
   if (!ctx || !out) return PMK_EINVAL;
   if (K == 0 || K > kMaxKeys || !pmk::valid_multiprime(nbits, nprimes) || e < 3 || !(e & 1) || (e >> 32))
     return PMK_EINVAL;
@@ -284,6 +289,7 @@ int pmk_keygen_host(uint32_t K, uint32_t nbits, uint64_t e, uint64_t seed, uint3
 
 int pmk_keyset_from_primes(pmk_ctx *ctx, uint32_t K, uint32_t nbits, uint64_t e, const uint32_t *p,
                            const uint32_t *q, pmk_keyset **out) {
+  pmk::TraceRange trace("pmk_keyset_from_primes");
   if (!ctx || !out || !p || !q || K == 0 || K > kMaxKeys) return PMK_EINVAL;
   if (nbits < 128 || nbits > 8192 || nbits % 128 || e < 3 || !(e & 1) || (e >> 32)) return PMK_EINVAL;
   if (!width_built(nbits)) return PMK_EUNSUPPORTED;
@@ -310,6 +316,7 @@ int pmk_keyset_from_primes(pmk_ctx *ctx, uint32_t K, uint32_t nbits, uint64_t e,
 
 int pmk_keyset_from_primes_multi(pmk_ctx *ctx, uint32_t K, uint32_t nbits, uint32_t nprimes, uint64_t e,
                                  const uint32_t *primes, pmk_keyset **out) {
+  pmk::TraceRange trace("pmk_keyset_from_primes_multi");
   if (!ctx || !out || !primes || K == 0 || K > kMaxKeys) return PMK_EINVAL;
   if (!pmk::valid_multiprime(nbits, nprimes) || e < 3 || !(e & 1) || (e >> 32)) return PMK_EINVAL;
   if (!width_built(nbits, nprimes)) return PMK_EUNSUPPORTED;
@@ -394,8 +401,9 @@ size_t pmk_num_chunks(size_t msg_len, uint32_t nbits) {
 
 int pmk_split(pmk_ctx *ctx, uint32_t nbits, const uint8_t *d_msg, size_t msg_len, uint32_t *d_chunks, size_t n_chunks,
               void *stream) {
+  pmk::TraceRange trace("pmk_split");
   if (!ctx || nbits < 128 || nbits % 128 || nbits > 8192) return PMK_EINVAL;
-  if (n_chunks != pmk_num_chunks(msg_len, nbits)) return PMK_EINVAL;
+  if (n_chunks != pmk_num_chunks(msg_len, nbits) || n_chunks >= kMaxChunks) return PMK_EINVAL;
   if (n_chunks == 0) return PMK_OK;
   if (!d_msg || !d_chunks) return PMK_EINVAL;
   DeviceGuard g(ctx->device);
@@ -405,8 +413,9 @@ int pmk_split(pmk_ctx *ctx, uint32_t nbits, const uint8_t *d_msg, size_t msg_len
 
 int pmk_join(pmk_ctx *ctx, uint32_t nbits, const uint32_t *d_chunks, size_t n_chunks, uint8_t *d_msg, size_t msg_len,
              void *stream) {
+  pmk::TraceRange trace("pmk_join");
   if (!ctx || nbits < 128 || nbits % 128 || nbits > 8192) return PMK_EINVAL;
-  if (n_chunks != pmk_num_chunks(msg_len, nbits)) return PMK_EINVAL;
+  if (n_chunks != pmk_num_chunks(msg_len, nbits) || n_chunks >= kMaxChunks) return PMK_EINVAL;
   if (msg_len == 0) return PMK_OK;
   if (!d_msg || !d_chunks) return PMK_EINVAL;
   DeviceGuard g(ctx->device);
@@ -416,8 +425,9 @@ int pmk_join(pmk_ctx *ctx, uint32_t nbits, const uint32_t *d_chunks, size_t n_ch
 
 int pmk_encrypt_chunks(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_in, uint32_t *d_out, size_t n_chunks,
                        void *stream) {
+  pmk::TraceRange trace("pmk_encrypt_chunks");
   if (n_chunks == 0) return (ctx && ks) ? PMK_OK : PMK_EINVAL;
-  int rc = check_chunk_call(ctx, ks, d_in, d_out);
+  int rc = check_chunk_call(ctx, ks, d_in, d_out, n_chunks);
   if (rc != PMK_OK) return rc;
   DeviceGuard g(ctx->device);
   if (!g.ok()) return PMK_ECUDA;
@@ -426,8 +436,9 @@ int pmk_encrypt_chunks(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_in,
 
 int pmk_decrypt_chunks(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_in, uint32_t *d_out, size_t n_chunks,
                        int use_crt, void *stream) {
+  pmk::TraceRange trace("pmk_decrypt_chunks");
   if (n_chunks == 0) return (ctx && ks) ? PMK_OK : PMK_EINVAL;
-  int rc = check_chunk_call(ctx, ks, d_in, d_out);
+  int rc = check_chunk_call(ctx, ks, d_in, d_out, n_chunks);
   if (rc != PMK_OK) return rc;
   const size_t bytes = n_chunks * (ks->nbits / 8);
   if (use_crt && overlap(d_in, bytes, d_out, bytes)) return PMK_EINVAL;
@@ -438,9 +449,10 @@ int pmk_decrypt_chunks(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_in,
 
 int pmk_encrypt_blinded(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_m, const uint32_t *d_r,
                         uint32_t *d_cstar, uint32_t *d_cr, size_t n_chunks, void *stream) {
+  pmk::TraceRange trace("pmk_encrypt_blinded");
   if (n_chunks == 0) return (ctx && ks) ? PMK_OK : PMK_EINVAL;
-  int rc = check_chunk_call(ctx, ks, d_m, d_cstar);
-  if (rc == PMK_OK) rc = check_chunk_call(ctx, ks, d_r, d_cr);
+  int rc = check_chunk_call(ctx, ks, d_m, d_cstar, n_chunks);
+  if (rc == PMK_OK) rc = check_chunk_call(ctx, ks, d_r, d_cr, n_chunks);
   if (rc != PMK_OK) return rc;
   const size_t bytes = n_chunks * (ks->nbits / 8);
   const void *bufs[4] = {d_m, d_r, d_cstar, d_cr};
@@ -459,9 +471,10 @@ int pmk_encrypt_blinded(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_m,
 
 int pmk_decrypt_blinded(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_cstar, const uint32_t *d_cr,
                         uint32_t *d_m, size_t n_chunks, int use_crt, void *stream) {
+  pmk::TraceRange trace("pmk_decrypt_blinded");
   if (n_chunks == 0) return (ctx && ks) ? PMK_OK : PMK_EINVAL;
-  int rc = check_chunk_call(ctx, ks, d_cstar, d_m);
-  if (rc == PMK_OK) rc = check_chunk_call(ctx, ks, d_cr, d_m);
+  int rc = check_chunk_call(ctx, ks, d_cstar, d_m, n_chunks);
+  if (rc == PMK_OK) rc = check_chunk_call(ctx, ks, d_cr, d_m, n_chunks);
   if (rc != PMK_OK) return rc;
   const size_t bytes = n_chunks * (ks->nbits / 8);
   if (overlap(d_cstar, bytes, d_m, bytes) || overlap(d_cr, bytes, d_m, bytes) || overlap(d_cstar, bytes, d_cr, bytes))
@@ -490,8 +503,9 @@ int pmk_decrypt_blinded(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_cs
 
 int pmk_modexp_chunks_baseline(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_in, uint32_t *d_out,
                                size_t n_chunks, int decrypt, void *stream) {
+  pmk::TraceRange trace("pmk_modexp_chunks_baseline");
   if (n_chunks == 0) return (ctx && ks) ? PMK_OK : PMK_EINVAL;
-  int rc = check_chunk_call(ctx, ks, d_in, d_out);
+  int rc = check_chunk_call(ctx, ks, d_in, d_out, n_chunks);
   if (rc != PMK_OK) return rc;
   DeviceGuard g(ctx->device);
   if (!g.ok()) return PMK_ECUDA;
@@ -503,6 +517,7 @@ int pmk_modexp_chunks_baseline(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_
 }
 
 int pmk_status(pmk_ctx *ctx, void *stream) {
+  pmk::TraceRange trace("pmk_status");
   if (!ctx) return PMK_EINVAL;
   DeviceGuard g(ctx->device);
   if (!g.ok()) return PMK_ECUDA;
@@ -517,8 +532,9 @@ int pmk_status(pmk_ctx *ctx, void *stream) {
 
 int pmk_encrypt_message_host(pmk_ctx *ctx, const pmk_keyset *ks, const uint8_t *h_msg, size_t msg_len,
                              uint32_t *h_cipher, size_t n_chunks, void *stream) {
+  pmk::TraceRange trace("pmk_encrypt_message_host");
   if (!ctx || !ks || ks->device != ctx->device) return PMK_EINVAL;
-  if (n_chunks != pmk_num_chunks(msg_len, ks->nbits)) return PMK_EINVAL;
+  if (n_chunks != pmk_num_chunks(msg_len, ks->nbits) || n_chunks >= kMaxChunks) return PMK_EINVAL;
   if (n_chunks == 0) return PMK_OK;
   if (!h_msg || !h_cipher) return PMK_EINVAL;
   DeviceGuard g(ctx->device);
@@ -538,8 +554,9 @@ int pmk_encrypt_message_host(pmk_ctx *ctx, const pmk_keyset *ks, const uint8_t *
 
 int pmk_decrypt_message_host(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *h_cipher, size_t n_chunks,
                              uint8_t *h_msg, size_t msg_len, int use_crt, void *stream) {
+  pmk::TraceRange trace("pmk_decrypt_message_host");
   if (!ctx || !ks || ks->device != ctx->device) return PMK_EINVAL;
-  if (n_chunks != pmk_num_chunks(msg_len, ks->nbits)) return PMK_EINVAL;
+  if (n_chunks != pmk_num_chunks(msg_len, ks->nbits) || n_chunks >= kMaxChunks) return PMK_EINVAL;
   if (n_chunks == 0) return PMK_OK;
   if (!h_msg || !h_cipher) return PMK_EINVAL;
   DeviceGuard g(ctx->device);

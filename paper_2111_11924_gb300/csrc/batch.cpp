@@ -202,10 +202,12 @@ int plan_and_capture(pmk_ctx *ctx, const pmk_job *jobs, size_t n_jobs, pmk_batch
 extern "C" {
 
 int pmk_batch_create(pmk_ctx *ctx, const pmk_job *jobs, size_t n_jobs, pmk_batch **out) {
+  pmk::TraceRange trace("pmk_batch_create");
   if (!ctx || !out || (n_jobs && !jobs)) return PMK_EINVAL;
   for (size_t j = 0; j < n_jobs; j++) {
     const pmk_job &jb = jobs[j];
     if (!jb.ks || jb.ks->device != ctx->device || jb.op < 0 || jb.op > 2) return PMK_EINVAL;
+    if (jb.n_chunks >= ((size_t)1 << 32)) return PMK_EINVAL;  // the per-call limit of the chunk calls
     if (jb.n_chunks == 0) continue;
     if (!jb.d_in || !jb.d_out || !aligned16(jb.d_in) || !aligned16(jb.d_out)) return PMK_EINVAL;
     const size_t bytes = jb.n_chunks * (jb.ks->nbits / 8);
@@ -236,6 +238,7 @@ int pmk_batch_create(pmk_ctx *ctx, const pmk_job *jobs, size_t n_jobs, pmk_batch
 }
 
 int pmk_batch_launch(pmk_batch *b, void *stream) {
+  pmk::TraceRange trace("pmk_batch_launch");
   if (!b || !b->exec) return PMK_EINVAL;
   int prev = 0;
   if (cudaGetDevice(&prev) != cudaSuccess) return PMK_ECUDA;

@@ -53,6 +53,7 @@ size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 extern "C" int pmk_decrypt_message_host_noalloc(const pmk_keyset *ks, const uint32_t *h_cipher, size_t n_chunks,
                                                 uint8_t *h_msg, size_t msg_len, int use_crt, void *stream) {
+  pmk::TraceRange trace("pmk_decrypt_message_host_noalloc");
   using namespace pmk;
   if (!ks) return PMK_EINVAL;
   if (n_chunks != pmk_num_chunks(msg_len, ks->nbits)) return PMK_EINVAL;

@@ -8,10 +8,22 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "pmkrsa.h"
 
 namespace pmk {
+
+// An NVTX range named after a C ABI entry point, open for the call's host
+// duration: profilers (ncu --nvtx, nsys) attribute the call's launches to it.
+// Without a profiler attached the push / pop are no-ops.
+class TraceRange {
+ public:
+  explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange &) = delete;
+  TraceRange &operator=(const TraceRange &) = delete;
+};
 
 // Error bits written by kernels into the context's device status word.
 enum : uint32_t { kStatusRange = 1u, kStatusNotInvertible = 2u };

@@ -394,20 +394,68 @@ class Context:
         """Lanes per instance and Montgomery form for (limbs, crt); tpi = 0 restores the default."""
         _check(load_library().pmk_set_kernel_config(self.handle, limbs, int(crt), tpi, form), "pmk_set_kernel_config")
 
-    def autotune(self, ks: KeySet, n_chunks: int, mode: str = "decrypt", reps: int = 3) -> dict:
+    def autotune(self, ks: KeySet, n_chunks: int, mode: str = "decrypt", reps: int = 3,
+                 cache: "TuneCache | None" = None) -> dict:
         """Time every compiled geometry for this key set and batch size; keep the fastest.
-        mode: "encrypt", "decrypt" (full d) or "crt"."""
+        mode: "encrypt", "decrypt" (full d) or "crt".  With a TuneCache, a
+        result stored for this GPU, width, prime count, mode and batch-size
+        bucket is applied without timing, and a new result is stored."""
         m = {"encrypt": 0, "decrypt": 1, "crt": 2}[mode]
+        key = None
+        if cache is not None:
+            key = cache.key(_torch().cuda.get_device_name(self.device), ks.nbits, ks.nprimes, mode, n_chunks)
+            hit = cache.get(key)
+            if hit is not None:
+                limbs = ks.nbits // 32 // (ks.nprimes if mode == "crt" else 1)
+                self.set_kernel_config(limbs, mode == "crt", hit["tpi"], hit["form"])
+                return dict(hit) | {"cached": True}
         tpi, form, ms = np.zeros(1, np.uint32), np.zeros(1, np.uint32), ctypes.c_float()
         _check(load_library().pmk_autotune(self.handle, ks.handle, n_chunks, m, reps, _p32(tpi), _p32(form),
                                            ctypes.byref(ms)), "pmk_autotune")
-        return {"tpi": int(tpi[0]), "form": int(form[0]), "ms": ms.value}
+        res = {"tpi": int(tpi[0]), "form": int(form[0]), "ms": ms.value}
+        if cache is not None:
+            cache.put(key, res)
+        return res
 
     def get_kernel_config(self, limbs: int, crt: bool) -> tuple:
         tpi, form = np.zeros(1, np.uint32), np.zeros(1, np.uint32)
         _check(load_library().pmk_get_kernel_config(self.handle, limbs, int(crt), _p32(tpi), _p32(form)),
                "pmk_get_kernel_config")
         return int(tpi[0]), int(form[0])
+
+
+class TuneCache:
+    """Autotuner results persisted as JSON, keyed by GPU name, key width,
+    prime count, mode and batch size rounded up to a power of two (the best
+    geometry depends on how many exponentiations fill the GPU)."""
+
+    def __init__(self, path: str):
+        import json
+        import os
+
+        self.path = path
+        self._json, self._os = json, os
+        try:
+            with open(path) as f:
+                self.entries = json.load(f)
+        except (OSError, ValueError):
+            self.entries = {}
+
+    @staticmethod
+    def key(gpu: str, nbits: int, nprimes: int, mode: str, n_chunks: int) -> str:
+        bucket = 1 << max(0, (int(n_chunks) - 1).bit_length())
+        return f"{gpu}|{nbits}|{nprimes}|{mode}|{bucket}"
+
+    def get(self, key: str):
+        e = self.entries.get(key)
+        return None if e is None else {"tpi": int(e["tpi"]), "form": int(e["form"]), "ms": float(e["ms"])}
+
+    def put(self, key: str, res: dict) -> None:
+        self.entries[key] = {"tpi": int(res["tpi"]), "form": int(res["form"]), "ms": float(res["ms"])}
+        tmp = f"{self.path}.tmp{self._os.getpid()}"
+        with open(tmp, "w") as f:
+            self._json.dump(self.entries, f, indent=1, sort_keys=True)
+        self._os.replace(tmp, self.path)
 
 
 def kernel_configs(limbs: int, crt: bool) -> list:

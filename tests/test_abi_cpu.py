@@ -112,3 +112,20 @@ def test_no_context_without_gpu(P):
         pytest.skip("a GPU is present")
     with pytest.raises(P.PMKError):
         P.Context(0)  # no silent CPU path
+
+
+def test_tune_cache_keys_and_persistence(P, tmp_path):
+    """The autotuner cache keys results by GPU, width, prime count, mode and
+    power-of-two batch bucket, and survives a reload from disk."""
+    path = str(tmp_path / "tune.json")
+    c = P.TuneCache(path)
+    k1 = c.key("GB300", 2048, 2, "crt", 4113)
+    assert k1 == c.key("GB300", 2048, 2, "crt", 8192) != c.key("GB300", 2048, 2, "crt", 8193)
+    assert k1 != c.key("GB300", 2048, 3, "crt", 4113) != c.key("B200", 2048, 2, "crt", 4113)
+    assert c.key("GB300", 2048, 2, "decrypt", 1) == "GB300|2048|2|decrypt|1"
+    assert c.get(k1) is None
+    c.put(k1, {"tpi": 4, "form": 1, "ms": 4.8})
+    again = P.TuneCache(path)
+    assert again.get(k1) == {"tpi": 4, "form": 1, "ms": 4.8}
+    (tmp_path / "bad.json").write_text("not json")
+    assert P.TuneCache(str(tmp_path / "bad.json")).entries == {}

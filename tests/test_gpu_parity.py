@@ -4,6 +4,8 @@ Integer results are compared bit-exactly: a modular exponentiation has one
 correct residue.  Key material on the oracle side comes from the oracle's own
 keygen and is checked equal to the library's.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -541,3 +543,89 @@ def test_batch_large_jobs_take_a_grid_launch(ctx, P):
     assert torch.equal(out, ctx.split(2048, msg))
     one.destroy()
     ks.free()
+
+
+def _guarded(n_words, fill=0x5A5A5A5A):
+    """A device int32 buffer of n_words with 1024-word guard zones on both
+    sides filled with `fill`; returns (whole buffer, interior slice)."""
+    g = 1024
+    buf = torch.full((n_words + 2 * g,), fill - (1 << 32) if fill >= (1 << 31) else fill, dtype=torch.int32,
+                     device="cuda")
+    return buf, buf[g:g + n_words]
+
+
+def _guards_intact(buf, n_words, fill=0x5A5A5A5A):
+    g = 1024
+    torch.cuda.synchronize()
+    h = buf.cpu().numpy().view(np.uint32)
+    return bool((h[:g] == fill).all() and (h[g + n_words:] == fill).all())
+
+
+def test_canary_words_around_every_output(ctx, P):
+    """Every kernel writes only inside its output: guard zones around the
+    device buffers (a stand-in for a sanitizer, which this pool does not run)
+    keep their pattern through split, encrypt, full-d and CRT decrypt (2 and
+    3 primes), blinded encrypt / decrypt, the batch graph and join."""
+    from paper_2111_11924_gb300 import pmkrsa as B
+
+    for nbits, b in ((2048, 2), (3072, 3)):
+        ks = ctx.keygen(3, nbits, 65537, 0x50444D4B0000EE00 + nbits, nprimes=b)
+        s = nbits // 32
+        L = 12345
+        msg = np.random.default_rng(nbits).integers(0, 256, L, dtype=np.uint8)
+        n = oracle.num_chunks(L, nbits)
+        mbuf = torch.full((L + 8192,), 0x5A, dtype=torch.uint8, device="cuda")
+        d_msg = mbuf[4096:4096 + L]
+        d_msg.copy_(torch.from_numpy(msg).cuda())
+        cb, chunks = _guarded(n * s)
+        ctx.split(nbits, d_msg, out=chunks.view(n, s))
+        xb, cipher = _guarded(n * s)
+        ctx.encrypt_chunks(ks, chunks.view(n, s), out=cipher.view(n, s))
+        for use_crt in (False, True):
+            pb, plain = _guarded(n * s)
+            ctx.decrypt_chunks(ks, cipher.view(n, s), use_crt=use_crt, out=plain.view(n, s))
+            assert _guards_intact(pb, n * s), (nbits, use_crt)
+            assert torch.equal(plain, chunks)
+        r = torch.from_numpy(W.blinding_values(n, nbits, 9).view(np.int32)).cuda()
+        sb, cstar = _guarded(n * s)
+        rb, cr = _guarded(n * s)
+        ctx.encrypt_blinded(ks, chunks.view(n, s), r, out_cstar=cstar.view(n, s), out_cr=cr.view(n, s))
+        assert _guards_intact(sb, n * s) and _guards_intact(rb, n * s)
+        bb, bl = _guarded(n * s)
+        ctx.decrypt_blinded(ks, cstar.view(n, s), cr.view(n, s), use_crt=True, out=bl.view(n, s))
+        assert _guards_intact(bb, n * s) and torch.equal(bl, chunks)
+        qb, qout = _guarded(n * s)
+        batch = ctx.batch([(ks, cipher.view(n, s), qout.view(n, s), B.OP_DECRYPT_CRT)])
+        batch.launch()
+        ctx.check()
+        assert _guards_intact(qb, n * s) and torch.equal(qout, chunks)
+        batch.destroy()
+        obuf = torch.full((L + 8192,), 0x5A, dtype=torch.uint8, device="cuda")
+        ctx.join(nbits, chunks.view(n, s), L, out=obuf[4096:4096 + L])
+        o = obuf.cpu().numpy()
+        assert (o[:4096] == 0x5A).all() and (o[4096 + L:] == 0x5A).all()
+        assert bytes(o[4096:4096 + L]) == msg.tobytes()
+        for buf in (cb, xb):
+            assert _guards_intact(buf, n * s)
+        assert ctx.status() == 0
+        ks.free()
+
+
+def test_chunk_count_bound(ctx, P):
+    ks, _ = keys_for(ctx, 2, 512, seed=3)
+    x = torch.zeros((4, 16), dtype=torch.int32, device="cuda")
+    rc = P.load_library().pmk_encrypt_chunks(ctx.handle, ks.handle, ctypes.c_void_p(x.data_ptr()),
+                                             ctypes.c_void_p(x.data_ptr()), 1 << 32, None)
+    assert rc == P.pmkrsa.PMK_EINVAL
+
+
+def test_autotune_cache_applies_stored_geometry(ctx, P, tmp_path):
+    ks, ok = keys_for(ctx, 2, 1024, seed=556)
+    cache = P.TuneCache(str(tmp_path / "tune.json"))
+    first = ctx.autotune(ks, 300, "decrypt", reps=1, cache=cache)
+    assert "cached" not in first
+    ctx.set_kernel_config(32, False, 0)
+    second = ctx.autotune(ks, 300, "decrypt", reps=1, cache=P.TuneCache(str(tmp_path / "tune.json")))
+    assert second["cached"] and (second["tpi"], second["form"]) == (first["tpi"], first["form"])
+    assert ctx.get_kernel_config(32, False) == (first["tpi"], first["form"])
+    ctx.set_kernel_config(32, False, 0)
