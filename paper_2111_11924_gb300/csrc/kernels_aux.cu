@@ -462,13 +462,13 @@ int launch_modexp(ExpMode mode, uint32_t limbs, KernelConfig cfg, const KeyDev *
   const int rc = configure_smem(e->fn, e->smem);
   if (rc != PMK_OK) return rc;
   const long long per_key = ((long long)n + K - 1) / K;
-  const int ipb = dev::kThreads / e->tpi;
+  const int ipb = e->threads / e->tpi;
   dim3 grid((unsigned)((per_key + ipb - 1) / ipb), crt ? parts * K : K);
   long long nl = (long long)n;
   int sel = (mode == ExpMode::kEncrypt || mode == ExpMode::kCrtInverse) ? 1 : 0;
   int np = crt ? (int)parts : 1;
   void *args[] = {(void *)&keys, (void *)&K, (void *)&in, (void *)&out, (void *)&nl, (void *)&sel, (void *)&np};
-  return cuda_rc(cudaLaunchKernel(e->fn, grid, dim3(dev::kThreads), args, e->smem, st));
+  return cuda_rc(cudaLaunchKernel(e->fn, grid, dim3(e->threads), args, e->smem, st));
 }
 
 }  // namespace pmk

@@ -9,8 +9,8 @@ using dev::kCols;
 const ModexpEntry *modexp_entries_full(int *count) {
   static const ModexpEntry entries[] = {
       make_entry<4, 2, false, kChain>(),    make_entry<8, 2, false, kChain>(),
-      make_entry<16, 2, false, kChain>(),   make_entry<32, 4, false, kChain>(),
-      make_entry<32, 8, false, kChain>(),   make_entry<32, 4, false, kCols>(),
+      make_entry<16, 2, false, kChain>(),   make_entry<32, 4, false, kChain, 64>(),
+      make_entry<32, 8, false, kChain>(),   make_entry<32, 4, false, kCols, 64>(),
       make_entry<32, 8, false, kCols>(),    make_entry<64, 4, false, kChain>(),
       make_entry<64, 8, false, kChain>(),   make_entry<64, 16, false, kChain>(),
       make_entry<64, 8, false, kCols>(),    make_entry<64, 16, false, kCols>(),

@@ -51,12 +51,14 @@ __device__ __forceinline__ void crt_input(uint32_t (&a)[S / TPI], const uint32_t
 //       E = d mod (r_i - 1) (sel == 0), or r_i - 2 (sel != 0: inverses mod
 //       r_i by Fermat's little theorem); the input is reduced by crt_input.
 //       The recombination kernel combines the residues afterwards.
-template <int S, int TPI, bool CRT, int FORM>
-__global__ void __launch_bounds__(kThreads) k_modexp(const KeyDev *__restrict__ keys, uint32_t K,
-                                                     const uint32_t *__restrict__ in, uint32_t *__restrict__ out,
-                                                     long long n, int sel, int parts) {
+// NT threads per block (128, or 64 where smaller blocks fit more
+// instances in an SM's shared memory).
+template <int S, int TPI, bool CRT, int FORM, int NT = kThreads>
+__global__ void __launch_bounds__(NT) k_modexp(const KeyDev *__restrict__ keys, uint32_t K,
+                                               const uint32_t *__restrict__ in, uint32_t *__restrict__ out,
+                                               long long n, int sel, int parts) {
   constexpr int L = S / TPI;
-  constexpr int IPB = kThreads / TPI;
+  constexpr int IPB = NT / TPI;
   constexpr int ROW = Layout<S>::kRow;
   constexpr int INST = Layout<S>::kInst;
   const int W = CRT ? parts * S : S;  // limbs per chunk in memory
@@ -78,7 +80,7 @@ __global__ void __launch_bounds__(kThreads) k_modexp(const KeyDev *__restrict__ 
   const uint32_t maxidx = CRT ? (sel ? kd.maxidx_hinv[prime] : kd.maxidx_h[prime]) : (sel ? kd.maxidx_e : kd.maxidx_d);
   const uint32_t n0 = CRT ? kd.n0h[prime] : kd.n0;
 
-  for (int i = threadIdx.x; i < S; i += kThreads) {
+  for (int i = threadIdx.x; i < S; i += NT) {
     sR2[i] = __ldg(R2 + i);
     sOne[i] = (i == 0);
     if (CRT) sR3[i] = __ldg(kd.R3h[prime] + i);
