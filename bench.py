@@ -64,6 +64,16 @@ def macs_per_montmul(nbits: int) -> int:
     return 2 * s * s + s  # CIOS: s rows of (s + s) MACs plus the q products
 
 
+def algorithmic_crt_macs(nbits: int, primes: int = 2) -> float:
+    """MACs of one CRT decryption at the same fixed w = 5 count: per prime,
+    an (n/b)-bit exponentiation over n/b-bit operands plus the 2b - 1
+    products that reduce the chunk mod the prime; then b full-width products
+    that recombine the residues."""
+    h = nbits // primes
+    per_prime = (algorithmic_montmuls(h) + 2 * primes - 1) * macs_per_montmul(h)
+    return primes * per_prime + primes * macs_per_montmul(nbits)
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle sampling while the timed region runs."""
 
@@ -364,6 +374,10 @@ def run_ours(args):
                             "round_trip": mb / (t_step / 1e3)},
         "crt": {"value": world * n / (crt_step / 1e3), "unit": UNIT, "ms_per_step": crt_step,
                 "decrypt_ms": crt_dec, "decrypt_only": n / (crt_dec / 1e3),
+                "roofline": {"bound": "alu", "unit": "TMAC/s", "peak": peak_tmacs,
+                             "achieved": n * algorithmic_crt_macs(w.nbits) / (crt_dec / 1e3) / 1e12,
+                             "frac": n * algorithmic_crt_macs(w.nbits) / (crt_dec / 1e3) / 1e12 / peak_tmacs,
+                             "macs_per_chunk": algorithmic_crt_macs(w.nbits)},
                 "geometry": {"lanes_per_instance": tuned_crt["tpi"], "form": ["chain", "columns"][tuned_crt["form"]]}},
         "blinded": {"value": world * n / (float(ph_bl.sum(axis=1).mean()) / 1e3), "unit": UNIT,
                     "ms_per_step": float(ph_bl.sum(axis=1).mean()), "encrypt_ms": float(ph_bl[:, 1].mean()),
