@@ -38,3 +38,30 @@ def test_each_result_same_alone_and_in_the_mix():
             back = ctx.join(r.nbits, ctx.decrypt_chunks(ks, m.cuda()), r.msg_len)
             assert torch.equal(back.cpu(), r.extra["message"]), r.rid
     ctx.close()
+
+
+def test_budget_admission_serialises_and_rejects():
+    """A budget that fits one request at a time admits them one by one
+    (never two in flight) and still produces every result; a request larger
+    than the whole budget is refused before anything runs."""
+    import paper_2111_11924_gb300 as P
+    from paper_2111_11924_gb300 import serving as SV
+
+    ctx = P.Context(0)
+    keysets = {1024: ctx.keygen(2, 1024, 65537, 0x50444D4B0000EF00)}
+    reqs = SV.poisson_requests(rate_per_s=50000, count=12, seed=5, widths=(1024,), min_bytes=20_000,
+                               max_bytes=30_000)
+    SV.prepare_payloads(ctx, keysets, reqs)
+    biggest = max(r.device_bytes() for r in reqs)
+    server = SV.Server(ctx, keysets, budget_bytes=biggest + 1, slots=8, use_crt=False)
+    stats = server.serve(reqs)
+    assert stats["status"] == 0 and stats["peak_in_flight"] == 1 and stats["peak_device_bytes"] <= biggest + 1
+    for r in reqs:
+        if r.op == "decrypt":
+            assert torch.equal(r.result, r.extra["message"]), r.rid
+    small = SV.Server(ctx, keysets, budget_bytes=biggest - 1, slots=8)
+    for r in reqs:
+        r.result = None
+    with pytest.raises(ValueError):
+        small.serve(reqs)
+    ctx.close()
