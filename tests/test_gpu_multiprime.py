@@ -301,3 +301,27 @@ def test_multiprime_degenerate_counts_and_exponents(ctx, nbits, b, K, n, e):
         assert np.array_equal(host(ctx.decrypt_chunks(ks, x, use_crt=use_crt)), m), use_crt
     assert ctx.status() == 0
     ks.free()
+
+
+def test_maximum_key_count(ctx, P):
+    """16,383 keys, the most a key set takes: with 4 primes the CRT grid has
+    65,532 rows (the CUDA limit is 65,535).  Every key's chunks round-trip
+    and a sample matches Python pow."""
+    K = 16383
+    for nbits, b in ((512, 4), (128, 2)):
+        ks = ctx.keygen(K, nbits, 65537, 0x50444D4B0000F000 + nbits, nprimes=b)
+        ex = ks.export()
+        s = nbits // 32
+        n = K + 17
+        rng = np.random.default_rng(nbits)
+        m = rng.integers(0, 2**32, (n, s), dtype=np.uint64).astype(np.uint32)
+        m[:, -1] = 0  # below every modulus
+        c = ctx.encrypt_chunks(ks, dev(m))
+        for use_crt in (True, False):
+            assert np.array_equal(host(ctx.decrypt_chunks(ks, c, use_crt=use_crt)), m), (nbits, use_crt)
+        ch = host(c)
+        for t in (0, 1, K - 1, K, n - 1):
+            N = oracle.from_limbs(ex["N"][t % K])
+            assert oracle.from_limbs(ch[t]) == pow(oracle.from_limbs(m[t]), 65537, N), (nbits, t)
+        assert ctx.status() == 0
+        ks.free()
