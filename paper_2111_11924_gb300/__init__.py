@@ -23,5 +23,6 @@ from .pmkrsa import (  # noqa: F401
     payload_bytes,
     strerror,
 )
+from . import sharding  # noqa: F401
 
-__all__ = ["PMKError", "Context", "KeySet", "keygen_host", "keygen_host_multiprime", "TuneCache", "kernel_configs", "load_library", "num_chunks", "payload_bytes", "strerror"]
+__all__ = ["PMKError", "Context", "KeySet", "keygen_host", "keygen_host_multiprime", "TuneCache", "kernel_configs", "load_library", "num_chunks", "payload_bytes", "strerror", "sharding"]

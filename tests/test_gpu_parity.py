@@ -629,3 +629,23 @@ def test_autotune_cache_applies_stored_geometry(ctx, P, tmp_path):
     assert second["cached"] and (second["tpi"], second["form"]) == (first["tpi"], first["form"])
     assert ctx.get_kernel_config(32, False) == (first["tpi"], first["form"])
     ctx.set_kernel_config(32, False, 0)
+
+
+def test_sharded_message_through_the_library(ctx):
+    """The shards of one message, each split / encrypted / decrypted / joined
+    on its own (as one rank per GPU would, here one after another on one
+    GPU), give the whole message's ciphertext chunks and plaintext."""
+    from paper_2111_11924_gb300 import sharding as SH
+
+    w = W.FILE_1MIB_2048
+    ks, ok = keys_for(ctx, w.K, w.nbits, w.key_seed)
+    msg = torch.from_numpy(w.message()).cuda()
+    whole = ctx.encrypt_chunks(ks, ctx.split(w.nbits, msg))
+    parts, back = [], []
+    for sh in SH.shards(w.msg_bytes, w.nbits, w.K, 5):
+        piece = msg[sh.byte_lo:sh.byte_hi]
+        c = ctx.encrypt_chunks(ks, ctx.split(w.nbits, piece))
+        parts.append(c)
+        back.append(ctx.join(w.nbits, ctx.decrypt_chunks(ks, c, use_crt=True), sh.n_bytes))
+    assert torch.equal(torch.cat(parts), whole)
+    assert torch.equal(torch.cat(back), msg)
