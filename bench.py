@@ -530,6 +530,71 @@ def run_widths(args):
     return 0
 
 
+# Section 4, Table 3, configuration D (P100, 16 keys, blinded, 2048 bits):
+# encryption / decryption seconds per file size (MB = 2^20 B), quoted as context.
+PAPER_TABLE3 = {1: (0.0009, 0.0617), 10: (0.0009, 0.0618), 25: (0.0009, 0.0612), 50: (0.0009, 0.0623),
+                100: (0.0009, 0.0622)}
+
+
+def run_table3(args):
+    """The paper's Table 3 workload: random files of 1, 10, 25, 50 and 100 MB,
+    K = 16 key pairs of 2048 bits.  Per size: split + encrypt and decrypt +
+    join, plain (full d and CRT) and blinded with R (the scheme the paper
+    times), CUDA events around each phase sequence, every round trip checked.
+    One JSON line per size."""
+    import torch
+
+    import paper_2111_11924_gb300 as P
+
+    ctx = P.Context(0)
+    ks = ctx.keygen(16, 2048, 65537, W.KEY_SEED_BASE + 0x300)
+    for mb in args.table3_sizes:
+        L = mb << 20
+        msg = torch.from_numpy(np.random.default_rng(mb).integers(0, 256, L, dtype=np.uint8)).cuda()
+        n = P.num_chunks(L, 2048)
+        chunks = ctx.split(2048, msg)
+        cipher = ctx.encrypt_chunks(ks, chunks)
+        rnd = torch.from_numpy(W.blinding_values(n, 2048, 0x5000 + mb).view(np.int32)).cuda()
+        cstar, cr = ctx.encrypt_blinded(ks, chunks, rnd)
+        out = torch.empty_like(chunks)
+        back = torch.empty_like(msg)
+
+        def timed(fn, reps):
+            fn()
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                fn()
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            return statistics.median(ts)
+
+        reps = max(1, min(args.steps, 3 if mb >= 25 else args.steps))
+        res = {
+            "encrypt": timed(lambda: (ctx.split(2048, msg, out=out), ctx.encrypt_chunks(ks, out, out=cipher)), reps),
+            "decrypt_full_d": timed(lambda: (ctx.decrypt_chunks(ks, cipher, out=out),
+                                             ctx.join(2048, out, L, out=back)), reps),
+            "decrypt_crt": timed(lambda: (ctx.decrypt_chunks(ks, cipher, use_crt=True, out=out),
+                                          ctx.join(2048, out, L, out=back)), reps),
+            "encrypt_blinded": timed(lambda: (ctx.split(2048, msg, out=out),
+                                              ctx.encrypt_blinded(ks, out, rnd, out_cstar=cstar, out_cr=cr)), reps),
+            "decrypt_blinded_crt": timed(lambda: (ctx.decrypt_blinded(ks, cstar, cr, use_crt=True, out=out),
+                                                  ctx.join(2048, out, L, out=back)), reps),
+        }
+        assert torch.equal(back, msg)
+        ctx.check()
+        paper = PAPER_TABLE3.get(mb)
+        print(json.dumps({"mode": "table3", "file_MB": mb, "chunks": n, "keys": 16, "key_bits": 2048,
+                          "ms": {k: round(v, 3) for k, v in res.items()},
+                          "MBps": {k: round(mb / (v / 1e3), 1) for k, v in res.items()},
+                          "paper_table3_P100_config_D_s": {"encrypt": paper[0], "decrypt": paper[1]} if paper else None,
+                          "timing": "CUDA events around split+encrypt / decrypt+join on device-resident data"}))
+    return 0
+
+
 def run_batched(args):
     """Many messages of mixed sizes and key widths in one batch: 64 messages,
     sizes log-uniform over 4 KB - 25 MB (times --batch-scale), each with its
@@ -837,6 +902,9 @@ def main(argv=None):
     ap.add_argument("--width-list", type=int, nargs="*", default=[1024, 2048, 3072, 4096, 6144, 8192])
     ap.add_argument("--file100", action="store_true",
                     help="100 MiB / K=16 decryption: one plain launch per call vs the persistent batch path, and exit")
+    ap.add_argument("--table3", action="store_true",
+                    help="the paper's Table 3 file sizes (1-100 MB, K=16, 2048 bits), plain and blinded, and exit")
+    ap.add_argument("--table3-sizes", type=int, nargs="*", default=[1, 10, 25, 50, 100])
     ap.add_argument("--multiprime", action="store_true",
                     help="time multi-prime CRT decryption (1 MiB, K = 8) against two primes and exit")
     ap.add_argument("--mp-list", type=lambda v: tuple(int(x) for x in v.split(":")), nargs="*",
@@ -860,6 +928,8 @@ def main(argv=None):
         return run_hbm(args)
     if args.multiprime:
         return run_multiprime(args)
+    if args.table3:
+        return run_table3(args)
     if args.file100:
         return run_file100(args)
     return run_reference(args) if args.impl == "reference" else run_ours(args)
