@@ -256,7 +256,10 @@ int pmk_decrypt_message_host_noalloc(const pmk_keyset *ks, const uint32_t *h_cip
  *   - jobs are grouped by exponentiation width and mode; each group runs as
  *     one persistent kernel whose warps take tasks (up to 32/TPI chunks of
  *     one key) from a device queue, longest tasks first;
- *   - groups run concurrently on internal streams, widest first;
+ *   - a job with at least four GPU-fulls of exponentiations instead gets
+ *     its own grid launch (the kernel of pmk_*_chunks);
+ *   - groups and such jobs run concurrently on internal streams, widest
+ *     first;
  *   - range checks, the kernels and CRT recombination are captured once into
  *     a CUDA graph (geometry: the context's current kernel configs).
  * pmk_batch_launch replays that graph on `stream` (asynchronous; errors via
@@ -278,7 +281,8 @@ typedef struct pmk_batch pmk_batch;
 
 int pmk_batch_create(pmk_ctx *ctx, const pmk_job *jobs, size_t n_jobs, pmk_batch **out);
 int pmk_batch_launch(pmk_batch *batch, void *stream);
-/* Tasks planned and persistent kernels per launch. */
+/* Tasks queued for the persistent kernels, and exponentiation kernels per
+ * launch (persistent kernels plus grid launches of large jobs). */
 int pmk_batch_info(const pmk_batch *batch, size_t *n_tasks, int *n_kernels);
 void pmk_batch_destroy(pmk_batch *batch);
 
