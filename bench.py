@@ -664,7 +664,7 @@ def run_batched(args):
             "per_call_chunk_modexps_per_s": n_total / (t_plain / 1e3),
             "batched_chunk_modexps_per_s": n_total / (t_batch / 1e3), "speedup": t_plain / t_batch,
             "payload_MBps_batched": payload / 2**20 / (t_batch / 1e3), "identical_outputs": same,
-            "persistent_kernels": batch.n_kernels, "tasks": batch.n_tasks,
+            "kernels_in_graph": batch.n_kernels, "queued_tasks": batch.n_tasks,
             "geometry": {f"{nb}-{m}": [t["tpi"], ["chain", "columns"][t["form"]]] for (nb, m), t in tuned.items()}}
     print(json.dumps(line))
     batch.destroy()
@@ -720,8 +720,8 @@ def run_file100(args):
                      "batched_chunk_modexps_per_s": round(n / (t_batch / 1e3)),
                      "plain_MBps": round(w.msg_bytes / 2**20 / (t_plain / 1e3), 2),
                      "batched_MBps": round(w.msg_bytes / 2**20 / (t_batch / 1e3), 2),
-                     "batched_over_plain": round(t_plain / t_batch, 3), "persistent_kernels": batch.n_kernels,
-                     "tasks": batch.n_tasks, "outputs_equal_message_chunks": ok_plain and ok_batch,
+                     "batched_over_plain": round(t_plain / t_batch, 3), "kernels_in_graph": batch.n_kernels,
+                     "queued_tasks": batch.n_tasks, "outputs_equal_message_chunks": ok_plain and ok_batch,
                      "join_roundtrip": roundtrip,
                      "geometry": [tuned["crt" if crt else "decrypt"]["tpi"],
                                   ["chain", "columns"][tuned["crt" if crt else "decrypt"]["form"]]]}
