@@ -65,3 +65,28 @@ def test_budget_admission_serialises_and_rejects():
     with pytest.raises(ValueError):
         small.serve(reqs)
     ctx.close()
+
+
+def test_corrupted_request_is_reported_and_isolated():
+    """Fault injection from the host: one decryption request carries a chunk
+    equal to its modulus.  The run reports PMK_ERANGE through the context's
+    status, and every other request still gets its exact result."""
+    import paper_2111_11924_gb300 as P
+    from paper_2111_11924_gb300 import serving as SV
+
+    ctx = P.Context(0)
+    keysets = {1024: ctx.keygen(3, 1024, 65537, 0x50444D4B0000F100)}
+    reqs = SV.poisson_requests(rate_per_s=20000, count=16, seed=9, widths=(1024,), p_decrypt=1.0, min_bytes=500,
+                               max_bytes=20_000)
+    SV.prepare_payloads(ctx, keysets, reqs)
+    bad = reqs[5]
+    N0 = keysets[1024].export()["N"][0]
+    bad.payload[0] = torch.from_numpy(N0.view(np.int32).copy())  # chunk 0 (key 0) := N_0, out of range
+    server = SV.Server(ctx, keysets, budget_bytes=10_000_000, slots=4, use_crt=True)
+    stats = server.serve(reqs)
+    assert stats["status"] == P.pmkrsa.PMK_ERANGE
+    for r in reqs:
+        if r is not bad:
+            assert torch.equal(r.result, r.extra["message"]), r.rid
+    assert ctx.status() == 0  # the status was read and cleared by the run
+    ctx.close()
