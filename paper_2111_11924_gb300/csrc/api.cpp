@@ -66,7 +66,7 @@ int upload(pmk_keyset *ks) {
   std::vector<uint32_t> blob;
   struct Offs {
     size_t N, R2, se, sd, P[pmk::kMaxPrimes], R2h[pmk::kMaxPrimes], R3h[pmk::kMaxPrimes], sh[pmk::kMaxPrimes],
-        shi[pmk::kMaxPrimes], cs[pmk::kMaxPrimes], el, dl;
+        shi[pmk::kMaxPrimes], cs[pmk::kMaxPrimes], sb[pmk::kMaxPrimes], el, dl;
   };
   std::vector<Offs> offs(ks->K);
   for (uint32_t k = 0; k < ks->K; k++) {
@@ -83,6 +83,7 @@ int upload(pmk_keyset *ks) {
       o.sh[i] = push(blob, h.sched_h[i].steps);
       o.shi[i] = push(blob, h.sched_hinv[i].steps);
       o.cs[i] = push(blob, h.crt_sum[i]);
+      o.sb[i] = push(blob, h.sched_blind[i].steps);
     }
     o.el = push(blob, {(uint32_t)ks->e, (uint32_t)(ks->e >> 32)});
     o.dl = push(blob, h.d);
@@ -108,11 +109,16 @@ int upload(pmk_keyset *ks) {
     d.maxidx_d = h.sched_d.maxidx;
     d.nprimes = h.nprimes;
     for (int i = 0; i < pmk::kMaxPrimes; i++) {
-      d.P[i] = d.R2h[i] = d.R3h[i] = d.sched_h[i] = d.sched_hinv[i] = d.crt_sum[i] = nullptr;
+      d.P[i] = d.R2h[i] = d.R3h[i] = d.sched_h[i] = d.sched_hinv[i] = d.crt_sum[i] = d.sched_blind[i] = nullptr;
       d.n0h[i] = d.nsteps_h[i] = d.maxidx_h[i] = d.nsteps_hinv[i] = d.maxidx_hinv[i] = 0;
+      d.nsteps_blind[i] = d.maxa_blind[i] = d.maxb_blind[i] = 0;
     }
     for (uint32_t i = 0; i < h.nprimes; i++) {
       d.crt_sum[i] = b + o.cs[i];
+      d.sched_blind[i] = b + o.sb[i];
+      d.nsteps_blind[i] = (uint32_t)h.sched_blind[i].steps.size();
+      d.maxa_blind[i] = h.sched_blind[i].maxa;
+      d.maxb_blind[i] = h.sched_blind[i].maxb;
       d.P[i] = b + o.P[i];
       d.R2h[i] = b + o.R2h[i];
       d.R3h[i] = b + o.R3h[i];
@@ -482,11 +488,19 @@ int pmk_decrypt_blinded(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_cs
   DeviceGuard g(ctx->device);
   if (!g.ok()) return PMK_ECUDA;
   cudaStream_t st = as_stream(stream);
-  const uint32_t S = ks->nbits / 32;
+  const uint32_t S = ks->nbits / 32, H = S / ks->nprimes;
   rc = pmk::launch_range_check(ks->d_keys, ks->K, S, d_cstar, n_chunks, ctx->d_status, st);
   if (rc == PMK_OK) rc = pmk::launch_range_check(ks->d_keys, ks->K, S, d_cr, n_chunks, ctx->d_status, st);
+  if (rc != PMK_OK) return rc;
+  if (use_crt && pmk::blind_crt_built(H)) {
+    // per prime: c*^(d_i) c_r^(r_i - 1 - d_i) = (c* c_r^-1)^d mod r_i in one
+    // joint exponentiation, then the recombination
+    rc = pmk::launch_blind_crt(H, ks->nprimes, ks->d_keys, ks->K, d_cstar, d_cr, d_m, n_chunks, st, ctx->d_status);
+    if (rc == PMK_OK) rc = pmk::launch_crt_sum(S, ks->nprimes, ks->d_keys, ks->K, d_m, n_chunks, st);
+    return rc;
+  }
   // c_r^-1 mod N: Fermat inverses mod each prime, recombined (into d_m)
-  if (rc == PMK_OK) rc = enqueue_crt(ctx, ks, pmk::ExpMode::kCrtInverse, d_cr, d_m, n_chunks, st, ctx->d_status);
+  rc = enqueue_crt(ctx, ks, pmk::ExpMode::kCrtInverse, d_cr, d_m, n_chunks, st, ctx->d_status);
   // x = c* c_r^-1, in place
   if (rc == PMK_OK) rc = pmk::launch_mulmod(S, ks->d_keys, ks->K, d_cstar, d_m, d_m, n_chunks, st);
   if (rc != PMK_OK) return rc;

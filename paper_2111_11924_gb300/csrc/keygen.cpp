@@ -344,6 +344,12 @@ void finish_key(uint32_t nbits, u64 e, const std::vector<std::vector<u64>> &r, H
     k.sched_h[i] = make_schedule(k.dpr[i].data(), (int)h);
     const std::vector<uint32_t> rm2_32 = to32(rm2, h);
     k.sched_hinv[i] = make_schedule(rm2_32.data(), (int)h);
+    {  // blinded CRT: exponents d_i and r_i - 1 - d_i
+      std::vector<u64> eb = minus_one(r[i]), di = to64(k.dpr[i].data(), h);
+      sub(eb.data(), eb.data(), di.data(), n);
+      const std::vector<uint32_t> eb32 = to32(eb, h);
+      k.sched_blind[i] = make_schedule2(k.dpr[i].data(), eb32.data(), (int)h);
+    }
     if (i == 1) continue;
     // Garner coefficients (exported): coef_0 = r_1^-1 mod r_0,
     // coef_i = (r_0 ... r_{i-1})^-1 mod r_i, by Fermat
@@ -468,6 +474,74 @@ Schedule make_schedule(const uint32_t *exp, int nlimbs) {
 
 bool valid_multiprime(uint32_t nbits, uint32_t nprimes) {
   return nprimes >= 2 && nprimes <= (uint32_t)kMaxPrimes && valid_width(nbits) && nbits % (64 * nprimes) == 0;
+}
+
+namespace {
+
+// Left-to-right sliding windows of width <= w over exp: (lowest bit, odd-power index).
+std::vector<std::pair<int, uint32_t>> sliding_windows(const uint32_t *exp, int nlimbs, int w) {
+  std::vector<std::pair<int, uint32_t>> out;
+  auto bit = [&](int i) { return (exp[i / 32] >> (i % 32)) & 1; };
+  int i = 32 * nlimbs - 1;
+  while (i >= 0) {
+    if (!bit(i)) {
+      i--;
+      continue;
+    }
+    int j = std::max(i - w + 1, 0);
+    while (!bit(j)) j++;
+    uint32_t v = 0;
+    for (int b = i; b >= j; b--) v = (v << 1) | bit(b);
+    out.push_back({j, (v - 1) / 2});
+    i = j - 1;
+  }
+  return out;
+}
+
+// Windows of width <= 4 (8 odd powers) that minimise windows + table products.
+std::vector<std::pair<int, uint32_t>> best_windows(const uint32_t *exp, int nlimbs, uint32_t *maxidx) {
+  std::vector<std::pair<int, uint32_t>> best;
+  size_t best_cost = ~(size_t)0;
+  for (int w = 1; w <= 4; w++) {
+    auto ws = sliding_windows(exp, nlimbs, w);
+    uint32_t mx = 0;
+    for (auto &x : ws) mx = std::max(mx, x.second);
+    const size_t cost = ws.size() + mx + (mx ? 1 : 0);
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = ws;
+      *maxidx = mx;
+    }
+  }
+  return best;
+}
+
+}  // namespace
+
+Schedule2 make_schedule2(const uint32_t *expa, const uint32_t *expb, int nlimbs) {
+  Schedule2 sc;
+  auto wa = best_windows(expa, nlimbs, &sc.maxa);
+  auto wb = best_windows(expb, nlimbs, &sc.maxb);
+  if (wa.empty() || wb.empty()) return Schedule2();  // a zero exponent: callers reject it
+  struct Ev {
+    int pos, which;
+    uint32_t idx;
+  };
+  std::vector<Ev> ev;
+  for (auto &x : wa) ev.push_back({x.first, 0, x.second});
+  for (auto &x : wb) ev.push_back({x.first, 1, x.second});
+  std::stable_sort(ev.begin(), ev.end(), [](const Ev &x, const Ev &y) { return x.pos > y.pos; });
+  int prev = -1;
+  for (size_t k = 0; k < ev.size();) {
+    const int p = ev[k].pos;
+    uint32_t ia = 0xFF, ib = 0xFF;
+    for (; k < ev.size() && ev[k].pos == p; k++) (ev[k].which == 0 ? ia : ib) = ev[k].idx;
+    const uint32_t nsq = prev < 0 ? 0u : (uint32_t)(prev - p);
+    sc.steps.push_back((nsq << 16) | (ia << 8) | ib);
+    prev = p;
+  }
+  if (prev > 0) sc.steps.push_back(((uint32_t)prev << 16) | 0xFFFFu);
+  return sc;
 }
 
 int host_keygen_mp(uint32_t K, uint32_t nbits, uint32_t nprimes, uint64_t e, uint64_t seed,

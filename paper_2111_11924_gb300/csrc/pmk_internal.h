@@ -40,6 +40,17 @@ struct Schedule {
 // Most primes of one modulus (multi-prime RSA, Section 2.1).
 constexpr int kMaxPrimes = 4;
 
+// Joint schedule of two exponents (Straus / Shamir simultaneous
+// exponentiation with interleaved sliding windows of width <= 4), for
+// A^eA B^eB in one squaring chain.  steps[i] = (nsq << 16) | (ia << 8) | ib:
+// nsq squarings, then multiplies by A's odd power ia and B's odd power ib
+// (0xFF: none); steps[0] has nsq = 0 and loads instead of multiplying.
+// Odd powers: A^(2 ia + 1), ia <= maxa <= 7, and likewise for B.
+struct Schedule2 {
+  std::vector<uint32_t> steps;
+  uint32_t maxa = 0, maxb = 0;
+};
+
 // One key pair on the host, 32-bit little-endian limbs.  A key has b >= 2
 // primes r_0 .. r_{b-1} of h = s / b limbs each; p = r_0, q = r_1.
 struct HostKey {
@@ -58,6 +69,9 @@ struct HostKey {
   std::vector<uint32_t> R2h[kMaxPrimes], R3h[kMaxPrimes];  // R_h^2, R_h^3 mod r_i
   Schedule sched_e, sched_d, sched_h[kMaxPrimes];      // e, d, d mod (r_i - 1)
   Schedule sched_hinv[kMaxPrimes];                     // r_i - 2 (Fermat inverses mod r_i)
+  // Blinded CRT decryption: c*^(d_i) c_r^(r_i - 1 - d_i) mod r_i
+  // = (c* c_r^-1)^d mod r_i, jointly.
+  Schedule2 sched_blind[kMaxPrimes];
 };
 
 // Device view of one key (pointers into the key set's device blob).
@@ -72,11 +86,13 @@ struct KeyDev {
   const uint32_t *sched_h[kMaxPrimes];
   const uint32_t *sched_hinv[kMaxPrimes];
   const uint32_t *crt_sum[kMaxPrimes];  // c_i R mod N (s limbs)
+  const uint32_t *sched_blind[kMaxPrimes];
   const uint32_t *e_limbs, *d_limbs;  // e (2 limbs) and d (s limbs), for the thread-per-chunk baseline
   uint32_t nprimes;
   uint32_t n0, n0h[kMaxPrimes];
   uint32_t nsteps_e, nsteps_d, nsteps_h[kMaxPrimes], nsteps_hinv[kMaxPrimes];
   uint32_t maxidx_e, maxidx_d, maxidx_h[kMaxPrimes], maxidx_hinv[kMaxPrimes];
+  uint32_t nsteps_blind[kMaxPrimes], maxa_blind[kMaxPrimes], maxb_blind[kMaxPrimes];
 };
 
 // One unit of work of the persistent batch kernels: up to 32 / TPI chunks
@@ -97,6 +113,7 @@ bool valid_multiprime(uint32_t nbits, uint32_t nprimes);
 int host_from_primes(uint32_t nbits, uint64_t e, const uint32_t *p, const uint32_t *q, HostKey &out);
 int host_from_primes_mp(uint32_t nbits, uint32_t nprimes, uint64_t e, const uint32_t *primes, HostKey &out);
 Schedule make_schedule(const uint32_t *exp, int nlimbs);
+Schedule2 make_schedule2(const uint32_t *expa, const uint32_t *expb, int nlimbs);
 
 // Kernel launchers (kernels_*.cu).  All return PMK_* codes.
 enum class ExpMode : int { kEncrypt = 0, kDecrypt = 1, kCrtHalf = 2, kCrtInverse = 3 };
@@ -118,6 +135,13 @@ int launch_modexp(ExpMode mode, uint32_t limbs, KernelConfig cfg, const KeyDev *
 // receives the value mod N.
 int launch_crt_sum(uint32_t limbs, uint32_t parts, const KeyDev *keys, uint32_t K, uint32_t *out, size_t n,
                    cudaStream_t st, uint32_t *status_if_zero_residue = nullptr);
+// Fused blinded CRT decryption: out[t][i] = c*[t]^(d_i) c_r[t]^(r_i - 1 - d_i)
+// mod r_i for each of the key's `parts` primes (prime_limbs limbs each); the
+// residues of (c* c_r^-1)^d, to be recombined by launch_crt_sum.  A c_r
+// divisible by a prime sets kStatusNotInvertible in *status.
+int launch_blind_crt(uint32_t prime_limbs, uint32_t parts, const KeyDev *keys, uint32_t K, const uint32_t *cstar,
+                     const uint32_t *cr, uint32_t *out, size_t n, cudaStream_t st, uint32_t *status);
+bool blind_crt_built(uint32_t prime_limbs);
 // out[t] = a[t] * b[t] mod N_{t mod K} (full width; out may alias a or b)
 int launch_mulmod(uint32_t limbs, const KeyDev *keys, uint32_t K, const uint32_t *a, const uint32_t *b, uint32_t *out,
                   size_t n, cudaStream_t st);
