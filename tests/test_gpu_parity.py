@@ -437,11 +437,12 @@ def test_blinded_non_invertible_value_reported(ctx, P):
     assert ctx.status() == 0
     bad = host(cr).copy()
     bad[2] = oracle.to_limbs(k0["p"] * 11, 8)  # chunk 2 (key 0) shares the factor p with N_0
-    out = ctx.decrypt_blinded(ks, cstar, dev(bad))
-    assert ctx.status() == P.pmkrsa.PMK_ENOINV
-    got = host(out)
-    for t in (0, 1, 3):
-        assert oracle.from_limbs(got[t]) == oracle.from_limbs(m[t])
+    for use_crt in (False, True):  # the inverse-then-power path and the fused joint exponentiation
+        out = ctx.decrypt_blinded(ks, cstar, dev(bad), use_crt=use_crt)
+        assert ctx.status() == P.pmkrsa.PMK_ENOINV, use_crt
+        got = host(out)
+        for t in (0, 1, 3):
+            assert oracle.from_limbs(got[t]) == oracle.from_limbs(m[t]), (use_crt, t)
 
 
 @pytest.mark.parametrize("nbits", [1024, 2048])
