@@ -247,6 +247,9 @@ std::vector<ModexpEntry> entries(bool crt) {
   std::vector<ModexpEntry> v(list, list + n);
   for (int i = 0; i < m; i++)
     if (wide[i].crt == crt) v.push_back(wide[i]);
+  const ModexpEntry *lat = modexp_entries_latency(&m);
+  for (int i = 0; i < m; i++)
+    if (lat[i].crt == crt) v.push_back(lat[i]);
   return v;
 }
 

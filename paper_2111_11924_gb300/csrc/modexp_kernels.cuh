@@ -216,7 +216,8 @@ ModexpEntry make_entry() {
 // Instantiation lists live in separate translation units (compiled in parallel).
 const ModexpEntry *modexp_entries_full(int *count);
 const ModexpEntry *modexp_entries_crt(int *count);
-const ModexpEntry *modexp_entries_wide(int *count);  // 6144/8192-bit full width, 3072/4096-bit CRT halves
+const ModexpEntry *modexp_entries_wide(int *count);  // 6144/8192-bit full width, their CRT residues
+const ModexpEntry *modexp_entries_latency(int *count);  // more lanes per instance for small batches
 
 // Modular multiplication kernels, one per full-width limb count.
 struct MulmodEntry {

@@ -407,7 +407,7 @@ def test_batched_persistent_graph_matches_per_call(ctx, P):
     batch.destroy()
 
 
-@pytest.mark.parametrize("nbits,K,length", [(512, 3, 3000), (2048, 8, 61200)])
+@pytest.mark.parametrize("nbits,K,length", [(512, 3, 3000), (2048, 8, 61200), (2048, 8, 400000)])
 def test_blinded_algorithm1_parity(ctx, nbits, K, length):
     """Algorithm 1 with the random matrix R: GPU C*, C_R equal the oracle's bit
     for bit; GPU decryption (c* c_r^-1)^d (full d and CRT) recovers every chunk,
