@@ -1,8 +1,5 @@
 // Instantiations and launcher of the fused blinded CRT decryption
 // (modexp_blind.cuh): one geometry per prime limb count, the CRT default.
-#include <mutex>
-#include <set>
-
 #include "modexp_blind.cuh"
 #include "modexp_kernels.cuh"
 
@@ -45,20 +42,6 @@ const BlindEntry *blind_entries_latency(int *count) {
   return entries;
 }
 
-int set_smem_once(const void *fn, size_t bytes) {
-  static std::mutex mu;
-  static std::set<std::pair<const void *, int>> done;
-  std::lock_guard<std::mutex> lock(mu);
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return PMK_ECUDA;
-  if (!done.count({fn, dev})) {
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
-      return PMK_ECUDA;
-    done.insert({fn, dev});
-  }
-  return PMK_OK;
-}
-
 }  // namespace
 
 bool blind_crt_built(uint32_t prime_limbs) {
@@ -85,7 +68,7 @@ int launch_blind_crt(uint32_t prime_limbs, uint32_t parts, const KeyDev *keys, u
     for (int i = 0; i < cnt; i++)
       if (lat[i].limbs == (int)prime_limbs) e = &lat[i];
   }
-  int rc = set_smem_once(e->fn, e->smem);
+  int rc = configure_smem(e->fn, e->smem);
   if (rc != PMK_OK) return rc;
   const long long per_key = ((long long)n + K - 1) / K;
   const int ipb = e->threads / e->tpi;

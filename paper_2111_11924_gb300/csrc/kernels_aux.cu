@@ -262,10 +262,6 @@ const ModexpEntry *find_entry(uint32_t limbs, KernelConfig cfg, bool crt) {
 
 }  // namespace
 
-namespace {
-int configure_smem(const void *fn, size_t bytes);
-}  // namespace
-
 int launch_split(uint32_t nbits, const uint8_t *msg, size_t len, uint32_t *chunks, size_t n, cudaStream_t st) {
   const int P = (int)(nbits / 8 - 1), S = (int)(nbits / 32);
   const long long nvec = (long long)n * (S / 4);
@@ -408,7 +404,6 @@ int list_configs(uint32_t limbs, bool crt, KernelConfig *out, int max) {
   return k;
 }
 
-namespace {
 // Raise a kernel's dynamic shared-memory limit once per device.
 int configure_smem(const void *fn, size_t bytes) {
   static std::mutex mu;
@@ -423,7 +418,6 @@ int configure_smem(const void *fn, size_t bytes) {
   }
   return PMK_OK;
 }
-}  // namespace
 
 int modexp_tasks_blocks_per_sm(uint32_t limbs, KernelConfig cfg, bool crt) {
   const ModexpEntry *e = find_entry(limbs, cfg, crt);

@@ -160,6 +160,8 @@ int modexp_tasks_blocks_per_sm(uint32_t limbs, KernelConfig cfg, bool crt);
 // Exponentiations the whole GPU holds at once in that geometry (0 if not built).
 long long modexp_resident_instances(uint32_t limbs, KernelConfig cfg, bool crt);
 int measure_int_peak(double *macs_per_clk_per_sm, double *sm_mhz, int *num_sms);
+// Raise a kernel's dynamic shared-memory limit to `bytes`, once per (kernel, device).
+int configure_smem(const void *fn, size_t bytes);
 int measure_imad_peak(double *mad_lo_per_clk_per_sm, double *sm_mhz, int *num_sms);
 
 }  // namespace pmk
