@@ -129,3 +129,27 @@ def test_tune_cache_keys_and_persistence(P, tmp_path):
     assert again.get(k1) == {"tpi": 4, "form": 1, "ms": 4.8}
     (tmp_path / "bad.json").write_text("not json")
     assert P.TuneCache(str(tmp_path / "bad.json")).entries == {}
+
+
+def test_header_is_plain_c_and_links_from_c(P, tmp_path):
+    """A C99 program includes include/pmkrsa.h (no C++), links libpmkrsa.so
+    and runs the host-only entry points; its key equals the oracle's."""
+    import shutil
+    import subprocess
+
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    from paper_2111_11924_gb300 import _native_build as NB
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    lib = NB.LIB
+    exe = str(tmp_path / "abi_host_calls")
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-o", exe,
+                           os.path.join(root, "tests", "c", "abi_host_calls.c"), "-I", os.path.join(root, "include"),
+                           lib, "-Wl,-rpath," + os.path.dirname(lib)])
+    out = subprocess.run([exe, "0x1234"], capture_output=True, text=True, check=True).stdout.split("\n")
+    assert out[0] == "payload 255 chunks 4113"
+    assert "modulus" in out[1] and out[2] == "keygen 0" and out[4] == f"bad_width {P.pmkrsa.PMK_EINVAL}"
+    limbs = [int(x, 16) for x in out[3].split()[1:]]
+    ok = oracle.keygen(2, 512, 65537, 0x1234)
+    assert limbs == [int(v) for v in ok.a["N"][0]]
