@@ -42,7 +42,7 @@ KERNELS_PER_STEP = 6  # split, range check + modexp (encrypt), range check + mod
 # DRAM traffic of the full-d decryption kernel from one ncu capture, valid only
 # for the kernel sources it was measured on (see profiles/).
 TRAFFIC_SOURCES = ["paper_2111_11924_gb300/csrc/modexp_core.cuh", "paper_2111_11924_gb300/csrc/modexp_grid.cuh"]
-TRAFFIC_MEASURED = {"b6280fe88332f5fa": 1457920}  # source digest -> bytes per launch (profiles/)
+TRAFFIC_MEASURED = {"021fac76db846f4a": 1474304}  # source digest -> bytes per launch (profiles/)
 
 
 def sources_digest() -> str:

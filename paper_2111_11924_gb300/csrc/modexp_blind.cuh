@@ -105,6 +105,9 @@ __global__ void __launch_bounds__(NT) k_blind_crt(const KeyDev *__restrict__ key
     sR3[i] = __ldg(kd.R3h[prime] + i);
   }
   __syncthreads();
+  // After the barrier the warps are independent: a warp whose instances all
+  // lie past the last chunk (the tail block of a key) leaves.
+  if (first + (long long)((threadIdx.x / 32) * (32 / TPI)) * K >= n) return;
 
   const long long t = first + (long long)g * K;
   const bool active = t < n;
