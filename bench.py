@@ -437,7 +437,8 @@ def run_ours(args):
 def run_profile(args):
     """A short, fixed launch sequence for ncu captures: keygen, split,
     encrypt, two full-d decryptions, one CRT decryption, join, checked; with
-    --profile-batch, one more full-d decryption through pmk_batch."""
+    --profile-batch, one more full-d decryption through pmk_batch; with
+    --profile-blinded, a blinded encryption and blinded CRT decryption."""
     import torch
 
     import paper_2111_11924_gb300 as P
@@ -465,6 +466,12 @@ def run_profile(args):
         ctx.check()
         assert torch.equal(out, chunks)
         batch.destroy()
+    if args.profile_blinded:  # Algorithm 1 with R: blinded encryption, fused blinded CRT decryption
+        rnd = torch.from_numpy(W.blinding_values(cipher.shape[0], w.nbits, w.msg_seed + 77).view(np.int32)).cuda()
+        cstar, cr = ctx.encrypt_blinded(ks, chunks, rnd)
+        plain_bl = ctx.decrypt_blinded(ks, cstar, cr, use_crt=True)
+        ctx.check()
+        assert torch.equal(plain_bl, chunks)
     print("profile sequence ok")
     return 0
 
@@ -911,6 +918,8 @@ def main(argv=None):
                     default=MULTIPRIME_CASES, help="bits:primes pairs for --multiprime")
     ap.add_argument("--profile-batch", action="store_true",
                     help="with --profile: also run the full-d decryption through the persistent batch path")
+    ap.add_argument("--profile-blinded", action="store_true",
+                    help="with --profile: also run a blinded encryption and a blinded CRT decryption")
     ap.add_argument("--profile-mib", type=int, default=0,
                     help="with --profile: message size in MiB instead of the 1 MiB workload")
     args = ap.parse_args(argv)
