@@ -42,7 +42,7 @@ KERNELS_PER_STEP = 6  # split, range check + modexp (encrypt), range check + mod
 # DRAM traffic of the full-d decryption kernel from one ncu capture, valid only
 # for the kernel sources it was measured on (see profiles/).
 TRAFFIC_SOURCES = ["paper_2111_11924_gb300/csrc/modexp_core.cuh", "paper_2111_11924_gb300/csrc/modexp_grid.cuh"]
-TRAFFIC_MEASURED = {"021fac76db846f4a": 1474304}  # source digest -> bytes per launch (profiles/)
+TRAFFIC_MEASURED = {"f92603a7b5fae024": 1680896}  # source digest -> bytes per launch (profiles/)
 
 
 def sources_digest() -> str:
@@ -378,13 +378,15 @@ def run_ours(args):
                              "achieved": n * algorithmic_crt_macs(w.nbits) / (crt_dec / 1e3) / 1e12,
                              "frac": n * algorithmic_crt_macs(w.nbits) / (crt_dec / 1e3) / 1e12 / peak_tmacs,
                              "macs_per_chunk": algorithmic_crt_macs(w.nbits)},
-                "geometry": {"lanes_per_instance": tuned_crt["tpi"], "form": ["chain", "columns"][tuned_crt["form"]]}},
+                "geometry": {"lanes_per_instance": tuned_crt["tpi"], "form": ["chain", "columns"][tuned_crt["form"]],
+                             "max_window": tuned_crt["window"]}},
         "blinded": {"value": world * n / (float(ph_bl.sum(axis=1).mean()) / 1e3), "unit": UNIT,
                     "ms_per_step": float(ph_bl.sum(axis=1).mean()), "encrypt_ms": float(ph_bl[:, 1].mean()),
                     "decrypt_ms": float(ph_bl[:, 2].mean()),
                     "step": "split + Algorithm 1 encryption with R + decryption as (c* c_r^-1)^d + join"},
         "geometry": {"lanes_per_instance": tuned["tpi"], "form": ["chain", "columns"][tuned["form"]],
-                     "chosen_by": "pmk_autotune over every compiled geometry"},
+                     "max_window": tuned["window"],
+                     "chosen_by": "pmk_autotune over every compiled geometry and window bound"},
         "thread_per_chunk_baseline": {"decrypt_only": n / (base_ms / 1e3), "unit": UNIT, "decrypt_ms": base_ms,
                                       "kernel": "one thread per chunk, binary exponent, local-memory limbs"},
         "default_geometry": {"value": world * n / (float(ph_default.sum(axis=1).mean()) / 1e3), "unit": UNIT,
@@ -532,7 +534,8 @@ def run_widths(args):
                           "ms": {k: round(v, 4) for k, v in res.items()},
                           "paper_table2_P100_config_D_ms": paper,
                           "chunk_modexps_per_s": {k: round(n / (v / 1e3)) for k, v in res.items()},
-                          "geometry": {m: (t["tpi"], ["chain", "columns"][t["form"]]) for m, t in tuned.items()}}))
+                          "geometry": {m: (t["tpi"], ["chain", "columns"][t["form"]], t["window"])
+                                       for m, t in tuned.items()}}))
         ks.free()
     return 0
 
@@ -672,7 +675,8 @@ def run_batched(args):
             "batched_chunk_modexps_per_s": n_total / (t_batch / 1e3), "speedup": t_plain / t_batch,
             "payload_MBps_batched": payload / 2**20 / (t_batch / 1e3), "identical_outputs": same,
             "kernels_in_graph": batch.n_kernels, "queued_tasks": batch.n_tasks,
-            "geometry": {f"{nb}-{m}": [t["tpi"], ["chain", "columns"][t["form"]]] for (nb, m), t in tuned.items()}}
+            "geometry": {f"{nb}-{m}": [t["tpi"], ["chain", "columns"][t["form"]], t["window"]]
+                         for (nb, m), t in tuned.items()}}
     print(json.dumps(line))
     batch.destroy()
     return 0 if same else 1
@@ -731,7 +735,8 @@ def run_file100(args):
                      "queued_tasks": batch.n_tasks, "outputs_equal_message_chunks": ok_plain and ok_batch,
                      "join_roundtrip": roundtrip,
                      "geometry": [tuned["crt" if crt else "decrypt"]["tpi"],
-                                  ["chain", "columns"][tuned["crt" if crt else "decrypt"]["form"]]]}
+                                  ["chain", "columns"][tuned["crt" if crt else "decrypt"]["form"]],
+                                  tuned["crt" if crt else "decrypt"]["window"]]}
         batch.destroy()
     ctx.check()
     print(json.dumps({"mode": "file100", "workload": w.name, "chunks": n, "keys": w.K, "key_bits": w.nbits,
@@ -870,7 +875,7 @@ def run_multiprime(args):
                           "chunk_modexps_per_s": round(n / (ms / 1e3)),
                           "speedup_vs_two_primes": round(base / ms, 3) if base else None,
                           "model_b2_over_4": b * b / 4,
-                          "geometry": (tuned["tpi"], ["chain", "columns"][tuned["form"]]),
+                          "geometry": (tuned["tpi"], ["chain", "columns"][tuned["form"]], tuned["window"]),
                           "timing": "CUDA events around one pmk_decrypt_chunks call (range check, one "
                                     "exponentiation per prime, recombination); L2 flushed between calls"}))
         ctx.set_kernel_config(nbits // 32 // b, True, 0)

@@ -331,12 +331,36 @@ int pmk_get_kernel_config(const pmk_ctx *ctx, uint32_t limbs, int crt, uint32_t 
 int pmk_list_kernel_configs(uint32_t limbs, int crt, uint32_t *tpi, uint32_t *form, int max);
 
 /*
- * Autotuner: time every compiled geometry of one exponentiation on
- * `n_chunks` synthetic chunks of this key set (mode 0 = encrypt, 1 = full-d
- * decrypt, 2 = CRT decrypt), `reps` timed launches each after one warm-up,
- * and make the fastest the context's geometry for that limb count and mode
- * (as pmk_set_kernel_config would).  Writes the choice and its best launch
- * time in ms (any output pointer may be NULL).  Allocates and frees two
+ * Widest sliding window of the exponentiation kernels for (limbs, crt) (the
+ * left-to-right windowed form of Algorithm 2's square-and-multiply).  Each
+ * exponentiation keeps a table of odd powers x, x^3, ... in shared memory:
+ *   max_window = 5: 16 odd powers (the default);
+ *   max_window = 4: 8 odd powers, half the shared memory, so more
+ *                   exponentiations are resident per SM.
+ * Every key holds a schedule for each; within the bound the host picks, per
+ * exponent, the width with the fewest products.  0 restores the default.
+ * The small table is compiled for the CRT residue kernels (crt = 1) of the
+ * throughput geometries; a geometry without it runs with the full table,
+ * and pmk_get_kernel_window reports the bound in effect for the current
+ * geometry.  Returns EINVAL for any other width or a NULL context,
+ * EUNSUPPORTED if no kernel for (limbs, crt) is compiled with that bound.
+ * Results are bit-identical either way; pmk_autotune chooses the bound
+ * together with the geometry.
+ */
+int pmk_set_kernel_window(pmk_ctx *ctx, uint32_t limbs, int crt, uint32_t max_window);
+/* The widest window the context currently uses for (limbs, crt). */
+int pmk_get_kernel_window(const pmk_ctx *ctx, uint32_t limbs, int crt, uint32_t *max_window);
+
+/*
+ * Autotuner: time every compiled geometry of one exponentiation, with each
+ * window bound it is compiled for (5, and 4 for the CRT residue kernels), on
+ * `n_chunks` synthetic chunks of this key set
+ * (mode 0 = encrypt, 1 = full-d decrypt, 2 = CRT decrypt), `reps` timed
+ * launches each after one warm-up, and make the fastest the context's
+ * geometry and window for that limb count and mode (as
+ * pmk_set_kernel_config and pmk_set_kernel_window would).  Writes the
+ * geometry and its best launch time in ms (any output pointer may be NULL);
+ * pmk_get_kernel_window reads the window chosen.  Allocates and frees two
  * temporary device buffers and synchronises the device's legacy stream.
  */
 int pmk_autotune(pmk_ctx *ctx, const pmk_keyset *ks, size_t n_chunks, int mode, int reps, uint32_t *tpi,

@@ -1,5 +1,6 @@
 // C ABI of the PMKRSA library (include/pmkrsa.h): argument checks, key-set
 // upload, and the order of kernel launches for each call.
+#include <algorithm>
 #include <cstring>
 #include <map>
 #include <new>
@@ -50,9 +51,24 @@ int grow(void **buf, size_t *cap, size_t bytes) {
 // Kernel geometry for an exponentiation over `limbs` limbs: the context's
 // override for this mode, else the built-in default.
 pmk::KernelConfig cfg_for(const pmk_ctx *ctx, uint32_t limbs, bool crt) {
-  auto it = ctx->cfg.find(limbs << 1 | (crt ? 1u : 0u));
-  if (it != ctx->cfg.end()) return it->second;
-  return pmk::default_config(limbs, crt);
+  const uint32_t key = limbs << 1 | (crt ? 1u : 0u);
+  auto it = ctx->cfg.find(key);
+  pmk::KernelConfig c = it != ctx->cfg.end() ? it->second : pmk::default_config(limbs, crt);
+  // The small table applies where this geometry is compiled with it.
+  auto t = ctx->table.find(key);
+  const bool small = t != ctx->table.end() && t->second == pmk::kTableSmall &&
+                     pmk::modexp_small_table_built(limbs, c, crt);
+  c.table = small ? pmk::kTableSmall : pmk::kTableFull;
+  return c;
+}
+
+// Whether any geometry for (limbs, crt) is compiled with the small table.
+bool small_table_available(uint32_t limbs, bool crt) {
+  pmk::KernelConfig v[64];
+  const int n = std::min(pmk::list_configs(limbs, crt, v, 64), 64);
+  for (int i = 0; i < n; i++)
+    if (pmk::modexp_small_table_built(limbs, v[i], crt)) return true;
+  return false;
 }
 
 size_t push(std::vector<uint32_t> &blob, const std::vector<uint32_t> &v) {
@@ -65,8 +81,8 @@ size_t push(std::vector<uint32_t> &blob, const std::vector<uint32_t> &v) {
 int upload(pmk_keyset *ks) {
   std::vector<uint32_t> blob;
   struct Offs {
-    size_t N, R2, se, sd, P[pmk::kMaxPrimes], R2h[pmk::kMaxPrimes], R3h[pmk::kMaxPrimes], sh[pmk::kMaxPrimes],
-        shi[pmk::kMaxPrimes], cs[pmk::kMaxPrimes], sb[pmk::kMaxPrimes], el, dl;
+    size_t N, R2, se[2], sd[2], P[pmk::kMaxPrimes], R2h[pmk::kMaxPrimes], R3h[pmk::kMaxPrimes],
+        sh[2][pmk::kMaxPrimes], shi[2][pmk::kMaxPrimes], cs[pmk::kMaxPrimes], sb[pmk::kMaxPrimes], el, dl;
   };
   std::vector<Offs> offs(ks->K);
   for (uint32_t k = 0; k < ks->K; k++) {
@@ -74,14 +90,18 @@ int upload(pmk_keyset *ks) {
     Offs &o = offs[k];
     o.N = push(blob, h.N);
     o.R2 = push(blob, h.R2);
-    o.se = push(blob, h.sched_e.steps);
-    o.sd = push(blob, h.sched_d.steps);
+    for (int t = 0; t < 2; t++) {
+      o.se[t] = push(blob, h.sched_e[t].steps);
+      o.sd[t] = push(blob, h.sched_d[t].steps);
+    }
     for (uint32_t i = 0; i < h.nprimes; i++) {
       o.P[i] = push(blob, h.pr[i]);
       o.R2h[i] = push(blob, h.R2h[i]);
       o.R3h[i] = push(blob, h.R3h[i]);
-      o.sh[i] = push(blob, h.sched_h[i].steps);
-      o.shi[i] = push(blob, h.sched_hinv[i].steps);
+      for (int t = 0; t < 2; t++) {
+        o.sh[t][i] = push(blob, h.sched_h[t][i].steps);
+        o.shi[t][i] = push(blob, h.sched_hinv[t][i].steps);
+      }
       o.cs[i] = push(blob, h.crt_sum[i]);
       o.sb[i] = push(blob, h.sched_blind[i].steps);
     }
@@ -90,28 +110,28 @@ int upload(pmk_keyset *ks) {
   }
   if (cudaMalloc(&ks->d_blob, blob.size() * 4) != cudaSuccess) return PMK_ENOMEM;
   if (cudaMemcpy(ks->d_blob, blob.data(), blob.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) return PMK_ECUDA;
+  const uint32_t *b = ks->d_blob;
+  // A schedule's device pointer, step count and highest table entry.
+  auto view = [b](size_t off, const pmk::Schedule &sc, const uint32_t *&steps, uint32_t &nsteps, uint32_t &maxidx) {
+    steps = b + off;
+    nsteps = (uint32_t)sc.steps.size();
+    maxidx = sc.maxidx;
+  };
   std::vector<KeyDev> kd(ks->K);
   for (uint32_t k = 0; k < ks->K; k++) {
     const HostKey &h = ks->keys[k];
     const Offs &o = offs[k];
     KeyDev &d = kd[k];
-    const uint32_t *b = ks->d_blob;
+    d = KeyDev{};
     d.N = b + o.N;
     d.R2 = b + o.R2;
-    d.sched_e = b + o.se;
-    d.sched_d = b + o.sd;
     d.e_limbs = b + o.el;
     d.d_limbs = b + o.dl;
     d.n0 = h.n0;
-    d.nsteps_e = (uint32_t)h.sched_e.steps.size();
-    d.nsteps_d = (uint32_t)h.sched_d.steps.size();
-    d.maxidx_e = h.sched_e.maxidx;
-    d.maxidx_d = h.sched_d.maxidx;
     d.nprimes = h.nprimes;
-    for (int i = 0; i < pmk::kMaxPrimes; i++) {
-      d.P[i] = d.R2h[i] = d.R3h[i] = d.sched_h[i] = d.sched_hinv[i] = d.crt_sum[i] = d.sched_blind[i] = nullptr;
-      d.n0h[i] = d.nsteps_h[i] = d.maxidx_h[i] = d.nsteps_hinv[i] = d.maxidx_hinv[i] = 0;
-      d.nsteps_blind[i] = d.maxa_blind[i] = d.maxb_blind[i] = 0;
+    for (int t = 0; t < 2; t++) {
+      view(o.se[t], h.sched_e[t], d.sched_e[t], d.nsteps_e[t], d.maxidx_e[t]);
+      view(o.sd[t], h.sched_d[t], d.sched_d[t], d.nsteps_d[t], d.maxidx_d[t]);
     }
     for (uint32_t i = 0; i < h.nprimes; i++) {
       d.crt_sum[i] = b + o.cs[i];
@@ -122,13 +142,11 @@ int upload(pmk_keyset *ks) {
       d.P[i] = b + o.P[i];
       d.R2h[i] = b + o.R2h[i];
       d.R3h[i] = b + o.R3h[i];
-      d.sched_h[i] = b + o.sh[i];
       d.n0h[i] = h.n0h[i];
-      d.nsteps_h[i] = (uint32_t)h.sched_h[i].steps.size();
-      d.maxidx_h[i] = h.sched_h[i].maxidx;
-      d.sched_hinv[i] = b + o.shi[i];
-      d.nsteps_hinv[i] = (uint32_t)h.sched_hinv[i].steps.size();
-      d.maxidx_hinv[i] = h.sched_hinv[i].maxidx;
+      for (int t = 0; t < 2; t++) {
+        view(o.sh[t][i], h.sched_h[t][i], d.sched_h[t][i], d.nsteps_h[t][i], d.maxidx_h[t][i]);
+        view(o.shi[t][i], h.sched_hinv[t][i], d.sched_hinv[t][i], d.nsteps_hinv[t][i], d.maxidx_hinv[t][i]);
+      }
     }
   }
   if (cudaMalloc(&ks->d_keys, sizeof(KeyDev) * ks->K) != cudaSuccess) return PMK_ENOMEM;
@@ -636,6 +654,26 @@ int pmk_get_kernel_config(const pmk_ctx *ctx, uint32_t limbs, int crt, uint32_t 
   if (c.tpi == 0) return PMK_EUNSUPPORTED;
   *tpi = c.tpi;
   *form = c.form;
+  return PMK_OK;
+}
+
+int pmk_set_kernel_window(pmk_ctx *ctx, uint32_t limbs, int crt, uint32_t max_window) {
+  if (!ctx || (max_window != 0 && max_window != pmk::kWindowFull && max_window != pmk::kWindowSmall))
+    return PMK_EINVAL;
+  if (pmk::list_configs(limbs, crt != 0, nullptr, 0) <= 0) return PMK_EUNSUPPORTED;
+  if (max_window == pmk::kWindowSmall && !small_table_available(limbs, crt != 0)) return PMK_EUNSUPPORTED;
+  const uint32_t key = limbs << 1 | (crt ? 1u : 0u);
+  if (max_window == pmk::kWindowSmall)
+    ctx->table[key] = pmk::kTableSmall;
+  else
+    ctx->table.erase(key);
+  return PMK_OK;
+}
+
+int pmk_get_kernel_window(const pmk_ctx *ctx, uint32_t limbs, int crt, uint32_t *max_window) {
+  if (!ctx || !max_window) return PMK_EINVAL;
+  if (pmk::list_configs(limbs, crt != 0, nullptr, 0) <= 0) return PMK_EUNSUPPORTED;
+  *max_window = pmk::window_of(cfg_for(ctx, limbs, crt != 0).table);
   return PMK_OK;
 }
 

@@ -66,7 +66,11 @@ int plan_and_capture(pmk_ctx *ctx, const pmk_job *jobs, size_t n_jobs, pmk_batch
     Group g;
     g.limbs = limbs;
     g.crt = crt;
-    if (pmk_get_kernel_config(ctx, limbs, crt ? 1 : 0, &g.cfg.tpi, &g.cfg.form) != PMK_OK) return nullptr;
+    uint32_t window = 0;
+    if (pmk_get_kernel_config(ctx, limbs, crt ? 1 : 0, &g.cfg.tpi, &g.cfg.form) != PMK_OK ||
+        pmk_get_kernel_window(ctx, limbs, crt ? 1 : 0, &window) != PMK_OK)
+      return nullptr;
+    g.cfg.table = window == pmk::kWindowSmall ? pmk::kTableSmall : pmk::kTableFull;
     groups.push_back(g);
     return &groups.back();
   };

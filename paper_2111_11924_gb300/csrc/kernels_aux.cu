@@ -250,14 +250,26 @@ std::vector<ModexpEntry> entries(bool crt) {
   const ModexpEntry *lat = modexp_entries_latency(&m);
   for (int i = 0; i < m; i++)
     if (lat[i].crt == crt) v.push_back(lat[i]);
+  const ModexpEntry *small = modexp_entries_small(&m);
+  for (int i = 0; i < m; i++)
+    if (small[i].crt == crt) v.push_back(small[i]);
   return v;
 }
 
-const ModexpEntry *find_entry(uint32_t limbs, KernelConfig cfg, bool crt) {
+const ModexpEntry *find_exact(uint32_t limbs, KernelConfig cfg, bool crt) {
   static const std::vector<ModexpEntry> full = entries(false), residue = entries(true);
   for (const ModexpEntry &e : crt ? residue : full)
-    if (e.limbs == (int)limbs && e.tpi == (int)cfg.tpi && e.form == (int)cfg.form) return &e;
+    if (e.limbs == (int)limbs && e.tpi == (int)cfg.tpi && e.form == (int)cfg.form && e.table == cfg.table) return &e;
   return nullptr;
+}
+
+// The instantiation for cfg; a geometry not built with the small table runs
+// with the full one (same results, only the speed differs).
+const ModexpEntry *find_entry(uint32_t limbs, KernelConfig cfg, bool crt) {
+  const ModexpEntry *e = find_exact(limbs, cfg, crt);
+  if (e || cfg.table == kTableFull) return e;
+  cfg.table = kTableFull;
+  return find_exact(limbs, cfg, crt);
 }
 
 }  // namespace
@@ -397,7 +409,7 @@ KernelConfig default_config(uint32_t limbs, bool crt) {
 int list_configs(uint32_t limbs, bool crt, KernelConfig *out, int max) {
   int k = 0;
   for (const ModexpEntry &e : entries(crt))
-    if (e.limbs == (int)limbs) {
+    if (e.limbs == (int)limbs && e.table == kTableFull) {  // geometries; the small-table twins are not listed
       if (k < max && out) out[k] = KernelConfig{(uint32_t)e.tpi, (uint32_t)e.form};
       k++;
     }
@@ -426,6 +438,11 @@ int modexp_tasks_blocks_per_sm(uint32_t limbs, KernelConfig cfg, bool crt) {
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, e->fn_tasks, dev::kThreads, e->smem_tasks) != cudaSuccess)
     return 0;
   return blocks;
+}
+
+bool modexp_small_table_built(uint32_t limbs, KernelConfig cfg, bool crt) {
+  cfg.table = kTableSmall;
+  return find_exact(limbs, cfg, crt) != nullptr;
 }
 
 long long modexp_resident_instances(uint32_t limbs, KernelConfig cfg, bool crt) {

@@ -341,9 +341,11 @@ void finish_key(uint32_t nbits, u64 e, const std::vector<std::vector<u64>> &r, H
     k.n0h[i] = neg_inv32(k.pr[i][0]);
     k.R2h[i] = pow2_32(r[i], (int)(64 * h), h);
     k.R3h[i] = pow2_32(r[i], (int)(96 * h), h);
-    k.sched_h[i] = make_schedule(k.dpr[i].data(), (int)h);
     const std::vector<uint32_t> rm2_32 = to32(rm2, h);
-    k.sched_hinv[i] = make_schedule(rm2_32.data(), (int)h);
+    for (int t = 0; t < 2; t++) {
+      k.sched_h[t][i] = make_schedule(k.dpr[i].data(), (int)h, window_of(t));
+      k.sched_hinv[t][i] = make_schedule(rm2_32.data(), (int)h, window_of(t));
+    }
     {  // blinded CRT: exponents d_i and r_i - 1 - d_i
       std::vector<u64> eb = minus_one(r[i]), di = to64(k.dpr[i].data(), h);
       sub(eb.data(), eb.data(), di.data(), n);
@@ -395,8 +397,10 @@ void finish_key(uint32_t nbits, u64 e, const std::vector<std::vector<u64>> &r, H
   k.dq = k.dpr[1];
   k.qinv = k.coef[0];
   uint32_t ev[2] = {(uint32_t)e, (uint32_t)(e >> 32)};
-  k.sched_e = make_schedule(ev, 2);
-  k.sched_d = make_schedule(k.d.data(), (int)s);
+  for (int t = 0; t < 2; t++) {
+    k.sched_e[t] = make_schedule(ev, 2, window_of(t));
+    k.sched_d[t] = make_schedule(k.d.data(), (int)s, window_of(t));
+  }
 }
 
 // The least top byte T (at least 192) with T^b >= 2^(8 b - 1): b primes of
@@ -415,16 +419,10 @@ bool valid_width(uint32_t nbits) { return nbits >= 128 && nbits <= 8192 && nbits
 
 }  // namespace
 
-#ifndef PMK_TABLE_MAX
-#define PMK_TABLE_MAX 16
-#endif
-// Widest window whose odd powers fit the kernels' table (2^(w-1) entries).
-constexpr int kMaxWindow = PMK_TABLE_MAX >= 16 ? 5 : PMK_TABLE_MAX >= 8 ? 4 : PMK_TABLE_MAX >= 4 ? 3 : 2;
-
 // Sliding-window recoding of an exponent, scanned from its top bit.  The
-// window width w <= kMaxWindow (at most PMK_TABLE_MAX odd powers) minimises
-// the product count (table entries + multiplies) for this exponent.
-Schedule make_schedule(const uint32_t *exp, int nlimbs) {
+// window width w <= max_window (a table of 2^(max_window - 1) odd powers)
+// minimises the product count (table entries + multiplies) for this exponent.
+Schedule make_schedule(const uint32_t *exp, int nlimbs, uint32_t max_window) {
   int top = -1;
   for (int i = 32 * nlimbs - 1; i >= 0; i--)
     if ((exp[i / 32] >> (i % 32)) & 1) {
@@ -435,7 +433,7 @@ Schedule make_schedule(const uint32_t *exp, int nlimbs) {
   size_t best_cost = ~(size_t)0;
   if (top < 0) return best;  // exponent 0: empty schedule (callers reject it)
   auto bit = [&](int i) { return (exp[i / 32] >> (i % 32)) & 1; };
-  for (int w = 1; w <= kMaxWindow; w++) {
+  for (int w = 1; w <= (int)max_window; w++) {
     Schedule sc;
     int i = top, pending = 0;
     bool first = true;

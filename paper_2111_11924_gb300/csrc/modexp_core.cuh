@@ -28,10 +28,9 @@ namespace pmk {
 namespace dev {
 
 constexpr int kThreads = 128;   // threads per block (4 warps)
-#ifndef PMK_TABLE_MAX
-#define PMK_TABLE_MAX 16
-#endif
-constexpr int kTableMax = PMK_TABLE_MAX;  // odd powers x^1 .. x^(2 kTableMax - 1)
+constexpr int kTableMax = 1 << (kWindowFull - 1);  // odd powers x^1 .. x^(2 kTableMax - 1)
+// Rows of the odd-power table of each size (kTableFull, kTableSmall).
+__host__ __device__ constexpr int table_rows(int table) { return table == kTableSmall ? kTableMax / 2 : kTableMax; }
 constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ void add_cc(uint32_t &r, uint32_t a, uint32_t b) {
@@ -57,10 +56,13 @@ __device__ __forceinline__ void subc(uint32_t &r, uint32_t a, uint32_t b) {
 template <int S>
 struct Layout {
   static constexpr int kRow = S + 4;
-  // Per-instance block (table + one operand buffer), padded to 4 mod 32 words
-  // so the 32/TPI instances of a warp read distinct 16-byte bank groups.
-  static constexpr int kRaw = (kTableMax + 1) * kRow;
-  static constexpr int kInst = kRaw + ((4 - kRaw % 32) + 32) % 32;
+  // Per-instance block (a table of `rows` rows + one operand buffer), padded
+  // to 4 mod 32 words so the 32/TPI instances of a warp read distinct
+  // 16-byte bank groups.
+  static __host__ __device__ constexpr int inst(int rows) {
+    return (rows + 1) * kRow + ((4 - ((rows + 1) * kRow) % 32) + 32) % 32;
+  }
+  static constexpr int kInst = inst(kTableMax);
   static constexpr int kConstRows = 3;  // R^2, one, R^3
 };
 

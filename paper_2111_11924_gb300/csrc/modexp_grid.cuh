@@ -52,21 +52,24 @@ __device__ __forceinline__ void crt_input(uint32_t (&a)[S / TPI], const uint32_t
 //       r_i by Fermat's little theorem); the input is reduced by crt_input.
 //       The recombination kernel combines the residues afterwards.
 // NT threads per block (128, or 64 where smaller blocks fit more
-// instances in an SM's shared memory).
-template <int S, int TPI, bool CRT, int FORM, int NT = kThreads>
+// instances in an SM's shared memory).  TABLE (kTableFull or kTableSmall)
+// sizes the odd-power tables in shared memory and selects the key's
+// schedules built for it.
+template <int S, int TPI, bool CRT, int FORM, int NT = kThreads, int TABLE = kTableFull>
 __global__ void __launch_bounds__(NT) k_modexp(const KeyDev *__restrict__ keys, uint32_t K,
                                                const uint32_t *__restrict__ in, uint32_t *__restrict__ out,
                                                long long n, int sel, int parts) {
   constexpr int L = S / TPI;
   constexpr int IPB = NT / TPI;
   constexpr int ROW = Layout<S>::kRow;
-  constexpr int INST = Layout<S>::kInst;
+  constexpr int ROWS = table_rows(TABLE);
+  constexpr int INST = Layout<S>::inst(ROWS);
   const int W = CRT ? parts * S : S;  // limbs per chunk in memory
   extern __shared__ __align__(16) uint32_t smem[];
   uint32_t *sR2 = smem, *sOne = smem + ROW, *sR3 = smem + 2 * ROW;
   const uint32_t r = threadIdx.x % TPI, g = threadIdx.x / TPI;
   uint32_t *tbl = smem + Layout<S>::kConstRows * ROW + g * INST;
-  uint32_t *ybuf = tbl + kTableMax * ROW;
+  uint32_t *ybuf = tbl + ROWS * ROW;
 
   const uint32_t key = CRT ? blockIdx.y / (uint32_t)parts : blockIdx.y;
   const uint32_t prime = CRT ? blockIdx.y % (uint32_t)parts : 0;
@@ -75,9 +78,12 @@ __global__ void __launch_bounds__(NT) k_modexp(const KeyDev *__restrict__ keys, 
   const KeyDev &kd = keys[key];
   const uint32_t *M = CRT ? kd.P[prime] : kd.N;
   const uint32_t *R2 = CRT ? kd.R2h[prime] : kd.R2;
-  const uint32_t *sched = CRT ? (sel ? kd.sched_hinv[prime] : kd.sched_h[prime]) : (sel ? kd.sched_e : kd.sched_d);
-  const uint32_t nsteps = CRT ? (sel ? kd.nsteps_hinv[prime] : kd.nsteps_h[prime]) : (sel ? kd.nsteps_e : kd.nsteps_d);
-  const uint32_t maxidx = CRT ? (sel ? kd.maxidx_hinv[prime] : kd.maxidx_h[prime]) : (sel ? kd.maxidx_e : kd.maxidx_d);
+  const uint32_t *sched = CRT ? (sel ? kd.sched_hinv[TABLE][prime] : kd.sched_h[TABLE][prime])
+                              : (sel ? kd.sched_e[TABLE] : kd.sched_d[TABLE]);
+  const uint32_t nsteps = CRT ? (sel ? kd.nsteps_hinv[TABLE][prime] : kd.nsteps_h[TABLE][prime])
+                              : (sel ? kd.nsteps_e[TABLE] : kd.nsteps_d[TABLE]);
+  const uint32_t maxidx = CRT ? (sel ? kd.maxidx_hinv[TABLE][prime] : kd.maxidx_h[TABLE][prime])
+                              : (sel ? kd.maxidx_e[TABLE] : kd.maxidx_d[TABLE]);
   const uint32_t n0 = CRT ? kd.n0h[prime] : kd.n0;
 
   for (int i = threadIdx.x; i < S; i += NT) {

@@ -18,19 +18,20 @@ static __device__ __align__(16) uint32_t g_one_row[256] = {1u};
 // memory (the key blob, L1-cached) instead of shared memory; a block then
 // needs only its instances' tables, as many blocks fit per SM as for
 // k_modexp.
-template <int S, int TPI, bool CRT, int FORM>
+template <int S, int TPI, bool CRT, int FORM, int TABLE = kTableFull>
 __global__ void __launch_bounds__(kThreads) k_modexp_tasks(const BatchTask *__restrict__ tasks, int ntasks,
                                                            int *__restrict__ counter) {
   constexpr int L = S / TPI;
   constexpr int IPW = 32 / TPI;
   constexpr int ROW = Layout<S>::kRow;
-  constexpr int INST = Layout<S>::kInst;
+  constexpr int ROWS = table_rows(TABLE);
+  constexpr int INST = Layout<S>::inst(ROWS);
   constexpr int WAREA = IPW * INST;
   extern __shared__ __align__(16) uint32_t smem[];
   const uint32_t lane = threadIdx.x & 31, r = lane % TPI, g = lane / TPI;
   uint32_t *wbase = smem + (threadIdx.x / 32) * WAREA;
   uint32_t *tbl = wbase + g * INST;
-  uint32_t *ybuf = tbl + kTableMax * ROW;
+  uint32_t *ybuf = tbl + ROWS * ROW;
   for (;;) {
     int ti = 0;
     if (lane == 0) ti = atomicAdd(counter, 1);
@@ -44,9 +45,9 @@ __global__ void __launch_bounds__(kThreads) k_modexp_tasks(const BatchTask *__re
     const int W = parts * S;
     const uint32_t *M = CRT ? kd.P[prime] : kd.N;
     const uint32_t *R2 = CRT ? kd.R2h[prime] : kd.R2;
-    const uint32_t *sched = CRT ? kd.sched_h[prime] : (enc ? kd.sched_e : kd.sched_d);
-    const uint32_t nsteps = CRT ? kd.nsteps_h[prime] : (enc ? kd.nsteps_e : kd.nsteps_d);
-    const uint32_t maxidx = CRT ? kd.maxidx_h[prime] : (enc ? kd.maxidx_e : kd.maxidx_d);
+    const uint32_t *sched = CRT ? kd.sched_h[TABLE][prime] : (enc ? kd.sched_e[TABLE] : kd.sched_d[TABLE]);
+    const uint32_t nsteps = CRT ? kd.nsteps_h[TABLE][prime] : (enc ? kd.nsteps_e[TABLE] : kd.nsteps_d[TABLE]);
+    const uint32_t maxidx = CRT ? kd.maxidx_h[TABLE][prime] : (enc ? kd.maxidx_e[TABLE] : kd.maxidx_d[TABLE]);
     const uint32_t n0 = CRT ? kd.n0h[prime] : kd.n0;
     const uint32_t *sR2 = R2, *sR3 = CRT ? kd.R3h[prime] : R2, *sOne = g_one_row;
     const bool active = (int)g < tk.count;
@@ -178,15 +179,17 @@ __global__ void __launch_bounds__(kThreads) k_crt_sum(const KeyDev *__restrict__
 }
 
 template <int S>
-constexpr size_t modexp_smem_bytes(int tpi, int threads = kThreads) {
-  return sizeof(uint32_t) * ((size_t)Layout<S>::kConstRows * Layout<S>::kRow + (size_t)(threads / tpi) * Layout<S>::kInst);
+constexpr size_t modexp_smem_bytes(int tpi, int threads = kThreads, int table = kTableFull) {
+  return sizeof(uint32_t) * ((size_t)Layout<S>::kConstRows * Layout<S>::kRow +
+                             (size_t)(threads / tpi) * Layout<S>::inst(table_rows(table)));
 }
 
 }  // namespace dev
 
 // One compiled instantiation: limb count, lanes per instance, CRT or full
-// width, Montgomery form (dev::kChain / dev::kCols); the one-launch-per-call
-// kernel and the persistent batch kernel with their shared-memory sizes.
+// width, Montgomery form (dev::kChain / dev::kCols), odd-power table size
+// (kTableFull / kTableSmall); the one-launch-per-call kernel and the
+// persistent batch kernel with their shared-memory sizes.
 struct ModexpEntry {
   int limbs, tpi;
   bool crt;
@@ -196,6 +199,7 @@ struct ModexpEntry {
   const void *fn_tasks;
   size_t smem_tasks;
   int threads;  // block size of fn (fn_tasks always uses dev::kThreads)
+  int table;
 };
 
 // NT: block size of the one-launch-per-call kernel.  64 for 32 limbs at 4
@@ -204,13 +208,19 @@ struct ModexpEntry {
 // instances per SM): 3.4% faster CRT decryption at 2048 bits and 100 MiB.
 // Other geometries measured no gain or a loss (64 limbs at 4 lanes: 12%
 // slower at 1 MiB) and keep 128.
-template <int S, int TPI, bool CRT, int FORM, int NT = dev::kThreads>
+template <int S, int TPI, bool CRT, int FORM, int NT = dev::kThreads, int TABLE = kTableFull>
 ModexpEntry make_entry() {
-  constexpr size_t warp_area = (size_t)(32 / TPI) * dev::Layout<S>::kInst;
-  return ModexpEntry{S, TPI, CRT, FORM, reinterpret_cast<const void *>(&dev::k_modexp<S, TPI, CRT, FORM, NT>),
-                     dev::modexp_smem_bytes<S>(TPI, NT),
-                     reinterpret_cast<const void *>(&dev::k_modexp_tasks<S, TPI, CRT, FORM>),
-                     sizeof(uint32_t) * warp_area * (dev::kThreads / 32), NT};
+  constexpr size_t warp_area = (size_t)(32 / TPI) * dev::Layout<S>::inst(dev::table_rows(TABLE));
+  return ModexpEntry{S,
+                     TPI,
+                     CRT,
+                     FORM,
+                     reinterpret_cast<const void *>(&dev::k_modexp<S, TPI, CRT, FORM, NT, TABLE>),
+                     dev::modexp_smem_bytes<S>(TPI, NT, TABLE),
+                     reinterpret_cast<const void *>(&dev::k_modexp_tasks<S, TPI, CRT, FORM, TABLE>),
+                     sizeof(uint32_t) * warp_area * (dev::kThreads / 32),
+                     NT,
+                     TABLE};
 }
 
 // Instantiation lists live in separate translation units (compiled in parallel).
@@ -218,6 +228,7 @@ const ModexpEntry *modexp_entries_full(int *count);
 const ModexpEntry *modexp_entries_crt(int *count);
 const ModexpEntry *modexp_entries_wide(int *count);  // 6144/8192-bit full width, their CRT residues
 const ModexpEntry *modexp_entries_latency(int *count);  // more lanes per instance for small batches
+const ModexpEntry *modexp_entries_small(int *count);    // CRT residue kernels with the small table
 
 // Modular multiplication kernels, one per full-width limb count.
 struct MulmodEntry {

@@ -37,6 +37,16 @@ struct Schedule {
   uint32_t maxidx = 0;  // table entries 0..maxidx are needed
 };
 
+// Odd-power tables of the exponentiation kernels: the full table holds 16
+// odd powers (windows up to 5 bits), the small one 8 (windows up to 4 bits)
+// and takes half the shared memory, so more instances fit on an SM.  Every
+// key carries one schedule set per table size, index kTableFull or
+// kTableSmall.
+enum : int { kTableFull = 0, kTableSmall = 1 };
+constexpr uint32_t kWindowFull = 5, kWindowSmall = 4;
+constexpr uint32_t window_of(int table) { return table == kTableSmall ? kWindowSmall : kWindowFull; }
+
+
 // Most primes of one modulus (multi-prime RSA, Section 2.1).
 constexpr int kMaxPrimes = 4;
 
@@ -67,8 +77,9 @@ struct HostKey {
   uint32_t n0 = 0, n0h[kMaxPrimes] = {};               // -M^-1 mod 2^32
   std::vector<uint32_t> R2;                            // R^2 mod N
   std::vector<uint32_t> R2h[kMaxPrimes], R3h[kMaxPrimes];  // R_h^2, R_h^3 mod r_i
-  Schedule sched_e, sched_d, sched_h[kMaxPrimes];      // e, d, d mod (r_i - 1)
-  Schedule sched_hinv[kMaxPrimes];                     // r_i - 2 (Fermat inverses mod r_i)
+  // Exponent schedules per table size (kTableFull, kTableSmall): e, d,
+  // d mod (r_i - 1) and r_i - 2 (Fermat inverses mod r_i).
+  Schedule sched_e[2], sched_d[2], sched_h[2][kMaxPrimes], sched_hinv[2][kMaxPrimes];
   // Blinded CRT decryption: c*^(d_i) c_r^(r_i - 1 - d_i) mod r_i
   // = (c* c_r^-1)^d mod r_i, jointly.
   Schedule2 sched_blind[kMaxPrimes];
@@ -76,22 +87,22 @@ struct HostKey {
 
 // Device view of one key (pointers into the key set's device blob).
 struct KeyDev {
+  // Schedules (steps, step count, highest table entry) per table size,
+  // [kTableFull] or [kTableSmall].
   const uint32_t *N;
   const uint32_t *R2;
-  const uint32_t *sched_e;
-  const uint32_t *sched_d;
+  const uint32_t *sched_e[2], *sched_d[2];
   const uint32_t *P[kMaxPrimes];
   const uint32_t *R2h[kMaxPrimes];
   const uint32_t *R3h[kMaxPrimes];
-  const uint32_t *sched_h[kMaxPrimes];
-  const uint32_t *sched_hinv[kMaxPrimes];
+  const uint32_t *sched_h[2][kMaxPrimes], *sched_hinv[2][kMaxPrimes];
   const uint32_t *crt_sum[kMaxPrimes];  // c_i R mod N (s limbs)
   const uint32_t *sched_blind[kMaxPrimes];
   const uint32_t *e_limbs, *d_limbs;  // e (2 limbs) and d (s limbs), for the thread-per-chunk baseline
   uint32_t nprimes;
   uint32_t n0, n0h[kMaxPrimes];
-  uint32_t nsteps_e, nsteps_d, nsteps_h[kMaxPrimes], nsteps_hinv[kMaxPrimes];
-  uint32_t maxidx_e, maxidx_d, maxidx_h[kMaxPrimes], maxidx_hinv[kMaxPrimes];
+  uint32_t nsteps_e[2], nsteps_d[2], nsteps_h[2][kMaxPrimes], nsteps_hinv[2][kMaxPrimes];
+  uint32_t maxidx_e[2], maxidx_d[2], maxidx_h[2][kMaxPrimes], maxidx_hinv[2][kMaxPrimes];
   uint32_t nsteps_blind[kMaxPrimes], maxa_blind[kMaxPrimes], maxb_blind[kMaxPrimes];
 };
 
@@ -112,7 +123,7 @@ int host_keygen_mp(uint32_t K, uint32_t nbits, uint32_t nprimes, uint64_t e, uin
 bool valid_multiprime(uint32_t nbits, uint32_t nprimes);
 int host_from_primes(uint32_t nbits, uint64_t e, const uint32_t *p, const uint32_t *q, HostKey &out);
 int host_from_primes_mp(uint32_t nbits, uint32_t nprimes, uint64_t e, const uint32_t *primes, HostKey &out);
-Schedule make_schedule(const uint32_t *exp, int nlimbs);
+Schedule make_schedule(const uint32_t *exp, int nlimbs, uint32_t max_window = kWindowFull);
 Schedule2 make_schedule2(const uint32_t *expa, const uint32_t *expb, int nlimbs);
 
 // Kernel launchers (kernels_*.cu).  All return PMK_* codes.
@@ -121,10 +132,13 @@ int launch_split(uint32_t nbits, const uint8_t *msg, size_t len, uint32_t *chunk
 int launch_join(uint32_t nbits, const uint32_t *chunks, size_t n, uint8_t *msg, size_t len, cudaStream_t st);
 int launch_range_check(const KeyDev *keys, uint32_t K, uint32_t s, const uint32_t *in, size_t n,
                        uint32_t *status, cudaStream_t st);
-// Launch geometry of an exponentiation kernel: lanes per instance and
-// Montgomery form (0 = one carry chain per lane, 1 = independent columns).
+// Launch geometry of an exponentiation kernel: lanes per instance, Montgomery
+// form (0 = one carry chain per lane, 1 = independent columns) and the
+// odd-power table size (kTableFull or kTableSmall; a geometry compiled only
+// with the full table runs with it).
 struct KernelConfig {
   uint32_t tpi = 0, form = 0;
+  int table = kTableFull;
 };
 // CRT modes run `parts` residues per chunk (the key's prime count) over
 // `limbs` = s / parts limbs each; residue i of chunk t goes to out[t][i * limbs].
@@ -146,6 +160,8 @@ bool blind_crt_built(uint32_t prime_limbs);
 int launch_mulmod(uint32_t limbs, const KeyDev *keys, uint32_t K, const uint32_t *a, const uint32_t *b, uint32_t *out,
                   size_t n, cudaStream_t st);
 bool modexp_built(uint32_t limbs, KernelConfig cfg, bool crt);
+// Whether that geometry is also compiled with the small odd-power table.
+bool modexp_small_table_built(uint32_t limbs, KernelConfig cfg, bool crt);
 // The plain thread-per-chunk, binary-exponent kernel (a measured baseline; 32 or 64 limbs).
 int launch_modexp_naive(bool enc, uint32_t limbs, const KeyDev *keys, uint32_t K, const uint32_t *in, uint32_t *out,
                         size_t n, cudaStream_t st);
@@ -186,4 +202,5 @@ struct pmk_ctx {
   uint32_t *d_a = nullptr, *d_b = nullptr;
   size_t a_cap = 0, b_cap = 0;             // in words
   std::map<uint32_t, pmk::KernelConfig> cfg;  // (limbs << 1 | crt) -> kernel geometry override
+  std::map<uint32_t, int> table;              // (limbs << 1 | crt) -> odd-power table size override
 };

@@ -1,6 +1,11 @@
 // Autotuner: for one key set and batch size, time every compiled kernel
 // geometry (lanes per instance x Montgomery form) of the exponentiation that
-// the caller will run, and keep the fastest in the context.
+// the caller will run, with the full odd-power table (window bound 5) and,
+// where compiled, the small one (bound 4), and keep the fastest in the
+// context.  The window
+// width within the bound is chosen per exponent on the host (fewest
+// products); the table size trades a few more products for more resident
+// instances, which only a measurement can settle.
 //
 // Inputs are synthetic chunks below every modulus (top limb zero), so the
 // timing covers the same schedule lengths as real ciphertexts; results of
@@ -20,9 +25,17 @@ extern "C" int pmk_autotune(pmk_ctx *ctx, const pmk_keyset *ks, size_t n_chunks,
   const uint32_t limbs = crt ? S / ks->nprimes : S;
   const pmk::ExpMode em = mode == 0 ? pmk::ExpMode::kEncrypt : (crt ? pmk::ExpMode::kCrtHalf : pmk::ExpMode::kDecrypt);
   reps = std::max(1, std::min(reps, 20));
-  std::vector<pmk::KernelConfig> cfgs(64);
-  const int ncfg = std::min(pmk::list_configs(limbs, crt, cfgs.data(), 64), 64);
-  if (ncfg <= 0) return PMK_EUNSUPPORTED;
+  std::vector<pmk::KernelConfig> geoms(64);
+  const int ngeom = std::min(pmk::list_configs(limbs, crt, geoms.data(), 64), 64);
+  if (ngeom <= 0) return PMK_EUNSUPPORTED;
+  std::vector<pmk::KernelConfig> cfgs;
+  for (int table : {pmk::kTableFull, pmk::kTableSmall})
+    for (int c = 0; c < ngeom; c++) {
+      pmk::KernelConfig k = geoms[c];
+      k.table = table;
+      if (table == pmk::kTableFull || pmk::modexp_small_table_built(limbs, k, crt)) cfgs.push_back(k);
+    }
+  const int ncfg = (int)cfgs.size();
 
   int prev = 0;
   if (cudaGetDevice(&prev) != cudaSuccess) return PMK_ECUDA;
@@ -62,6 +75,7 @@ extern "C" int pmk_autotune(pmk_ctx *ctx, const pmk_keyset *ks, size_t n_chunks,
   cudaFree(d_out);
   if (rc == PMK_OK) {
     rc = pmk_set_kernel_config(ctx, limbs, crt ? 1 : 0, best.tpi, best.form);
+    if (rc == PMK_OK) rc = pmk_set_kernel_window(ctx, limbs, crt ? 1 : 0, pmk::window_of(best.table));
     if (tpi) *tpi = best.tpi;
     if (form) *form = best.form;
     if (ms) *ms = best_ms;

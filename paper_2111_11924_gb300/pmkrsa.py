@@ -86,6 +86,8 @@ def load_library() -> ctypes.CDLL:
         "pmk_set_kernel_config": (i, [vp, u32, i, u32, u32]),
         "pmk_get_kernel_config": (i, [vp, u32, i, P32, P32]),
         "pmk_list_kernel_configs": (i, [u32, i, P32, P32, i]),
+        "pmk_set_kernel_window": (i, [vp, u32, i, u32]),
+        "pmk_get_kernel_window": (i, [vp, u32, i, P32]),
         "pmk_autotune": (i, [vp, vp, sz, i, i, P32, P32, ctypes.POINTER(ctypes.c_float)]),
     }
     for name, (res, args) in sig.items():
@@ -394,25 +396,40 @@ class Context:
         """Lanes per instance and Montgomery form for (limbs, crt); tpi = 0 restores the default."""
         _check(load_library().pmk_set_kernel_config(self.handle, limbs, int(crt), tpi, form), "pmk_set_kernel_config")
 
+    def set_kernel_window(self, limbs: int, crt: bool, max_window: int) -> None:
+        """Widest exponent window for (limbs, crt): 5 (16 odd powers per
+        exponentiation in shared memory), 4 (8 odd powers, more resident
+        exponentiations per SM) or 0 for the default (5)."""
+        _check(load_library().pmk_set_kernel_window(self.handle, limbs, int(crt), max_window),
+               "pmk_set_kernel_window")
+
+    def get_kernel_window(self, limbs: int, crt: bool) -> int:
+        w = np.zeros(1, np.uint32)
+        _check(load_library().pmk_get_kernel_window(self.handle, limbs, int(crt), _p32(w)), "pmk_get_kernel_window")
+        return int(w[0])
+
     def autotune(self, ks: KeySet, n_chunks: int, mode: str = "decrypt", reps: int = 3,
                  cache: "TuneCache | None" = None) -> dict:
-        """Time every compiled geometry for this key set and batch size; keep the fastest.
-        mode: "encrypt", "decrypt" (full d) or "crt".  With a TuneCache, a
-        result stored for this GPU, width, prime count, mode and batch-size
-        bucket is applied without timing, and a new result is stored."""
+        """Time every compiled geometry, with each window bound (5 and 4), for
+        this key set and batch size; keep the fastest.  mode: "encrypt",
+        "decrypt" (full d) or "crt".  With a TuneCache, a result stored for
+        this GPU, width, prime count, mode and batch-size bucket is applied
+        without timing, and a new result is stored."""
         m = {"encrypt": 0, "decrypt": 1, "crt": 2}[mode]
+        limbs = ks.nbits // 32 // (ks.nprimes if mode == "crt" else 1)
         key = None
         if cache is not None:
             key = cache.key(_torch().cuda.get_device_name(self.device), ks.nbits, ks.nprimes, mode, n_chunks)
             hit = cache.get(key)
             if hit is not None:
-                limbs = ks.nbits // 32 // (ks.nprimes if mode == "crt" else 1)
                 self.set_kernel_config(limbs, mode == "crt", hit["tpi"], hit["form"])
+                self.set_kernel_window(limbs, mode == "crt", hit["window"])
                 return dict(hit) | {"cached": True}
         tpi, form, ms = np.zeros(1, np.uint32), np.zeros(1, np.uint32), ctypes.c_float()
         _check(load_library().pmk_autotune(self.handle, ks.handle, n_chunks, m, reps, _p32(tpi), _p32(form),
                                            ctypes.byref(ms)), "pmk_autotune")
-        res = {"tpi": int(tpi[0]), "form": int(form[0]), "ms": ms.value}
+        res = {"tpi": int(tpi[0]), "form": int(form[0]), "window": self.get_kernel_window(limbs, mode == "crt"),
+               "ms": ms.value}
         if cache is not None:
             cache.put(key, res)
         return res
@@ -448,10 +465,13 @@ class TuneCache:
 
     def get(self, key: str):
         e = self.entries.get(key)
-        return None if e is None else {"tpi": int(e["tpi"]), "form": int(e["form"]), "ms": float(e["ms"])}
+        if e is None:
+            return None
+        return {"tpi": int(e["tpi"]), "form": int(e["form"]), "window": int(e.get("window", 5)), "ms": float(e["ms"])}
 
     def put(self, key: str, res: dict) -> None:
-        self.entries[key] = {"tpi": int(res["tpi"]), "form": int(res["form"]), "ms": float(res["ms"])}
+        self.entries[key] = {"tpi": int(res["tpi"]), "form": int(res["form"]), "window": int(res.get("window", 5)),
+                             "ms": float(res["ms"])}
         tmp = f"{self.path}.tmp{self._os.getpid()}"
         with open(tmp, "w") as f:
             self._json.dump(self.entries, f, indent=1, sort_keys=True)

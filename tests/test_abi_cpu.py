@@ -124,9 +124,12 @@ def test_tune_cache_keys_and_persistence(P, tmp_path):
     assert k1 != c.key("GB300", 2048, 3, "crt", 4113) != c.key("B200", 2048, 2, "crt", 4113)
     assert c.key("GB300", 2048, 2, "decrypt", 1) == "GB300|2048|2|decrypt|1"
     assert c.get(k1) is None
-    c.put(k1, {"tpi": 4, "form": 1, "ms": 4.8})
+    c.put(k1, {"tpi": 4, "form": 1, "window": 4, "ms": 4.8})
+    k2 = c.key("GB300", 4096, 2, "decrypt", 100)
+    c.put(k2, {"tpi": 16, "form": 0, "ms": 9.5})  # no window given: the default bound, 5
     again = P.TuneCache(path)
-    assert again.get(k1) == {"tpi": 4, "form": 1, "ms": 4.8}
+    assert again.get(k1) == {"tpi": 4, "form": 1, "window": 4, "ms": 4.8}
+    assert again.get(k2) == {"tpi": 16, "form": 0, "window": 5, "ms": 9.5}
     (tmp_path / "bad.json").write_text("not json")
     assert P.TuneCache(str(tmp_path / "bad.json")).entries == {}
 

@@ -189,7 +189,8 @@ def test_1mib_2048_encrypt_all_decrypt_sampled(ctx):
 @pytest.mark.parametrize("nbits,crt", [(2048, False), (2048, True), (1024, False), (1024, True), (4096, False),
                                        (3072, True)])
 def test_every_kernel_geometry(ctx, P, nbits, crt):
-    """Every compiled (lanes, form) geometry gives the same bit-exact result."""
+    """Every compiled (lanes, form) geometry gives the same bit-exact result;
+    for the CRT residues also with the small odd-power table (window <= 4)."""
     K = 3
     ks, ok = keys_for(ctx, K, nbits, seed=4242 + nbits)
     rng = np.random.default_rng(1)
@@ -200,17 +201,71 @@ def test_every_kernel_geometry(ctx, P, nbits, crt):
     limbs = nbits // 64 if crt else nbits // 32
     configs = P.kernel_configs(limbs, crt)
     assert len(configs) >= 1
-    outs = []
-    for tpi, form in configs:
-        ctx.set_kernel_config(limbs, crt, tpi, form)
-        try:
-            outs.append(host(ctx.decrypt_chunks(ks, dev(c), use_crt=crt)))
-        finally:
-            ctx.set_kernel_config(limbs, crt, 0)
-    for o, cfg in zip(outs, configs):
+    outs, tried = [], []
+    for window in ((5, 4) if crt else (5,)):
+        for tpi, form in configs:
+            ctx.set_kernel_config(limbs, crt, tpi, form)
+            ctx.set_kernel_window(limbs, crt, window)
+            try:
+                outs.append(host(ctx.decrypt_chunks(ks, dev(c), use_crt=crt)))
+                tried.append((tpi, form, window))
+            finally:
+                ctx.set_kernel_config(limbs, crt, 0)
+                ctx.set_kernel_window(limbs, crt, 0)
+    for o, cfg in zip(outs, tried):
         assert np.array_equal(o[:6], ref), cfg
         assert np.array_equal(o, outs[0]), cfg
     assert ctx.get_kernel_config(limbs, crt)[0] in {t for t, _ in configs}
+    assert ctx.get_kernel_window(limbs, crt) == 5
+
+
+def test_window_bound_api_batch_and_autotune(ctx, P):
+    """The window bound is validated and read back; the per-call kernels, the
+    persistent batch kernels and the autotuner honour it; no result changes."""
+    from paper_2111_11924_gb300 import pmkrsa as B
+
+    for bad in (1, 3, 6):
+        with pytest.raises(B.PMKError) as ei:
+            ctx.set_kernel_window(32, True, bad)
+        assert ei.value.code == B.PMK_EINVAL
+    for limbs, crt in ((40, True), (64, False)):  # no kernel / no small-table kernel
+        with pytest.raises(B.PMKError) as ei:
+            ctx.set_kernel_window(limbs, crt, 4)
+        assert ei.value.code == B.PMK_EUNSUPPORTED
+    assert ctx.get_kernel_window(64, False) == 5 and ctx.get_kernel_window(32, True) == 5
+    ks, ok = keys_for(ctx, 3, 2048, seed=4242 + 2048)
+    rng = np.random.default_rng(5)
+    Ns = ok.ints("N")
+    n = 70
+    c = dev(np.stack([oracle.to_limbs(W.random_below(rng, Ns[t % 3]), 64) for t in range(n)]))
+    full5, crt5 = ctx.decrypt_chunks(ks, c), ctx.decrypt_chunks(ks, c, use_crt=True)
+    assert torch.equal(full5, crt5)
+    assert np.array_equal(host(full5)[:4], oracle.decrypt_chunks(host(c)[:4], ok))
+    try:
+        ctx.set_kernel_window(32, True, 4)
+        assert ctx.get_kernel_window(32, True) == 4
+        assert torch.equal(ctx.decrypt_chunks(ks, c, use_crt=True), full5)
+        for tpi, form in P.kernel_configs(32, True):  # every geometry; those without a small build use the full table
+            ctx.set_kernel_config(32, True, tpi, form)
+            assert torch.equal(ctx.decrypt_chunks(ks, c, use_crt=True), full5), (tpi, form)
+        ctx.set_kernel_config(32, True, 0)
+        outs = [torch.zeros_like(c) for _ in range(3)]
+        batch = ctx.batch([(ks, c, outs[0], B.OP_DECRYPT), (ks, c, outs[1], B.OP_DECRYPT_CRT),
+                           (ks, full5, outs[2], B.OP_ENCRYPT)])
+        batch.launch()
+        ctx.check()
+        assert torch.equal(outs[0], full5) and torch.equal(outs[1], full5) and torch.equal(outs[2], c)
+        batch.destroy()
+        for mode in ("decrypt", "crt"):
+            res = ctx.autotune(ks, n, mode, reps=1)
+            limbs = 32 if mode == "crt" else 64
+            assert res["window"] in ((4, 5) if mode == "crt" else (5,))
+            assert ctx.get_kernel_window(limbs, mode == "crt") == res["window"]
+            assert torch.equal(ctx.decrypt_chunks(ks, c, use_crt=(mode == "crt")), full5)
+    finally:
+        for limbs, crt in ((64, False), (32, True)):
+            ctx.set_kernel_window(limbs, crt, 0)
+            ctx.set_kernel_config(limbs, crt, 0)
 
 
 @pytest.mark.parametrize("nbits", [3072, 4096])
@@ -473,6 +528,11 @@ def test_other_public_exponents(ctx, e):
     for use_crt in (False, True):
         assert np.array_equal(host(ctx.decrypt_chunks(ks, c, use_crt=use_crt)), m)
     assert np.array_equal(host(ctx.decrypt_chunks(ks, c))[:5], oracle.decrypt_chunks(host(c)[:5], ok))
+    ctx.set_kernel_window(16, True, 4)  # CRT schedules within 4-bit windows
+    try:
+        assert np.array_equal(host(ctx.decrypt_chunks(ks, c, use_crt=True)), m)
+    finally:
+        ctx.set_kernel_window(16, True, 0)
 
 
 def test_100mib_roundtrip_and_oracle_sample(ctx):
