@@ -132,13 +132,16 @@ def test_multiprime_every_geometry(ctx, P, nbits, b):
     assert np.array_equal(ref, m[:4])
     configs = P.kernel_configs(h, True)
     assert configs
-    for tpi, form in configs:
-        ctx.set_kernel_config(h, True, tpi, form)
-        try:
-            got = host(ctx.decrypt_chunks(ks, c, use_crt=True))
-        finally:
-            ctx.set_kernel_config(h, True, 0)
-        assert np.array_equal(got, m), (tpi, form)
+    for window in (5, 4):  # the full and the small odd-power table
+        for tpi, form in configs:
+            ctx.set_kernel_config(h, True, tpi, form)
+            ctx.set_kernel_window(h, True, window)
+            try:
+                got = host(ctx.decrypt_chunks(ks, c, use_crt=True))
+            finally:
+                ctx.set_kernel_config(h, True, 0)
+                ctx.set_kernel_window(h, True, 0)
+            assert np.array_equal(got, m), (tpi, form, window)
 
 
 @pytest.mark.parametrize("nbits,b", [(6144, 3), (6144, 4), (8192, 4)])
