@@ -440,7 +440,8 @@ def run_profile(args):
     """A short, fixed launch sequence for ncu captures: keygen, split,
     encrypt, two full-d decryptions, one CRT decryption, join, checked; with
     --profile-batch, one more full-d decryption through pmk_batch; with
-    --profile-blinded, a blinded encryption and blinded CRT decryption."""
+    --profile-blinded, a blinded encryption and blinded CRT decryption; with
+    --profile-crt-window W, the CRT decryption once more with window bound W."""
     import torch
 
     import paper_2111_11924_gb300 as P
@@ -456,6 +457,12 @@ def run_profile(args):
     for _ in range(2):
         plain = ctx.decrypt_chunks(ks, cipher)
     plain_crt = ctx.decrypt_chunks(ks, cipher, use_crt=True)
+    if args.profile_crt_window:  # the same CRT decryption again with another window bound
+        limbs = w.nbits // 64
+        ctx.set_kernel_window(limbs, True, args.profile_crt_window)
+        again = ctx.decrypt_chunks(ks, cipher, use_crt=True)
+        ctx.set_kernel_window(limbs, True, 0)
+        assert torch.equal(again, chunks)
     back = ctx.join(w.nbits, plain, w.msg_bytes)
     ctx.check()
     assert torch.equal(plain, chunks) and torch.equal(plain_crt, chunks) and torch.equal(back, d_msg)
@@ -925,6 +932,8 @@ def main(argv=None):
                     help="with --profile: also run the full-d decryption through the persistent batch path")
     ap.add_argument("--profile-blinded", action="store_true",
                     help="with --profile: also run a blinded encryption and a blinded CRT decryption")
+    ap.add_argument("--profile-crt-window", type=int, default=0,
+                    help="with --profile: run the CRT decryption a second time with this window bound (4 or 5)")
     ap.add_argument("--profile-mib", type=int, default=0,
                     help="with --profile: message size in MiB instead of the 1 MiB workload")
     args = ap.parse_args(argv)
