@@ -156,3 +156,23 @@ def test_header_is_plain_c_and_links_from_c(P, tmp_path):
     limbs = [int(x, 16) for x in out[3].split()[1:]]
     ok = oracle.keygen(2, 512, 65537, 0x1234)
     assert limbs == [int(v) for v in ok.a["N"][0]]
+
+
+def test_geometry_calls_host_only(P):
+    """The geometry and window-bound calls reject a NULL context and bad
+    arguments on the host; the compiled geometry list needs no GPU."""
+    import ctypes
+
+    import paper_2111_11924_gb300.pmkrsa as B
+
+    lib = P.load_library()
+    w = (ctypes.c_uint32 * 1)()
+    assert lib.pmk_set_kernel_window(None, 32, 1, 4) == B.PMK_EINVAL
+    assert lib.pmk_get_kernel_window(None, 32, 1, w) == B.PMK_EINVAL
+    assert lib.pmk_set_kernel_config(None, 64, 0, 8, 1) == B.PMK_EINVAL
+    assert lib.pmk_list_kernel_configs(64, 0, None, None, -1) == B.PMK_EINVAL
+    full64 = P.kernel_configs(64, False)
+    assert (8, 1) in full64 and len(full64) == len(set(full64))  # one entry per geometry, whatever the tables
+    crt32 = P.kernel_configs(32, True)
+    assert (4, 1) in crt32 and len(crt32) == len(set(crt32))  # small-table twins are not listed twice
+    assert P.kernel_configs(40, True) == []
