@@ -410,8 +410,10 @@ __device__ __forceinline__ void load_slice_global(uint32_t (&a)[L], const uint32
 }
 
 // Table of odd powers and the exponent walk.  On entry a = x in Montgomery
-// form; on exit a = x^E in Montgomery form.  tbl: kTableMax rows, ybuf: one
-// row, all of this instance.  sched: steps of make_schedule() (block-uniform).
+// form; on exit a = x^E in Montgomery form.  tbl: the instance's odd-power
+// table (at least maxidx + 1 rows: the table size the schedule was built
+// for), ybuf: one row of this instance.  sched: steps of make_schedule()
+// (block-uniform).
 template <int S, int TPI, int FORM>
 __device__ __forceinline__ void exp_window(uint32_t (&a)[S / TPI], uint32_t *tbl, uint32_t *ybuf,
                                            const uint32_t *__restrict__ sched, uint32_t nsteps, uint32_t maxidx,
