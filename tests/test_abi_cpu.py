@@ -176,3 +176,28 @@ def test_geometry_calls_host_only(P):
     crt32 = P.kernel_configs(32, True)
     assert (4, 1) in crt32 and len(crt32) == len(set(crt32))  # small-table twins are not listed twice
     assert P.kernel_configs(40, True) == []
+
+
+def test_exponent_schedules_replay_to_their_exponents(tmp_path):
+    """The host's window schedules (tests/c/schedule_check.cpp, built against
+    keygen.cpp with g++): replayed on plain integers, every single-exponent
+    schedule (window bounds 1-5) and every joint schedule of the blinded CRT
+    decryption gives back its exponents, with each odd-power index inside
+    the table bound, over 1-256-limb exponents (random, sparse, dense and
+    special values)."""
+    import shutil
+    import subprocess
+
+    if shutil.which("g++") is None:
+        pytest.skip("g++ not available")
+    from paper_2111_11924_gb300 import _native_build as NB
+
+    cuda_inc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
+    exe = str(tmp_path / "schedule_check")
+    subprocess.check_call(["g++", "-std=c++17", "-O2", "-Wall", "-Wextra", "-Werror", "-o", exe,
+                           os.path.join(ROOT, "tests", "c", "schedule_check.cpp"),
+                           os.path.join(NB.CSRC, "keygen.cpp"), "-I", os.path.join(ROOT, "include"), "-I", NB.CSRC,
+                           "-I", cuda_inc, "-lpthread"])
+    res = subprocess.run([exe], capture_output=True, text=True)
+    assert res.returncode == 0, res.stdout
+    assert res.stdout.strip().endswith("0 failures") and int(res.stdout.split()[0]) >= 1000
