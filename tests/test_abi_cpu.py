@@ -201,3 +201,27 @@ def test_exponent_schedules_replay_to_their_exponents(tmp_path):
     res = subprocess.run([exe], capture_output=True, text=True)
     assert res.returncode == 0, res.stdout
     assert res.stdout.strip().endswith("0 failures") and int(res.stdout.split()[0]) >= 1000
+
+
+def test_unexported_key_constants_from_their_definitions(tmp_path):
+    """The per-key constants the kernels use but the C ABI does not export
+    (Montgomery constants, R^2 / R_h^2 / R_h^3, the CRT recombination rows,
+    d mod (r_i - 1), the Garner coefficients), recomputed from their
+    definitions with 128-bit integers on keys whose primes fit in 64 bits
+    (tests/c/keyconst_check.cpp, built against keygen.cpp with g++)."""
+    import shutil
+    import subprocess
+
+    if shutil.which("g++") is None:
+        pytest.skip("g++ not available")
+    from paper_2111_11924_gb300 import _native_build as NB
+
+    cuda_inc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
+    exe = str(tmp_path / "keyconst_check")
+    subprocess.check_call(["g++", "-std=c++17", "-O2", "-Wall", "-Wextra", "-Werror", "-o", exe,
+                           os.path.join(ROOT, "tests", "c", "keyconst_check.cpp"),
+                           os.path.join(NB.CSRC, "keygen.cpp"), "-I", os.path.join(ROOT, "include"), "-I", NB.CSRC,
+                           "-I", cuda_inc, "-lpthread"])
+    res = subprocess.run([exe], capture_output=True, text=True)
+    assert res.returncode == 0, res.stdout
+    assert res.stdout.strip().endswith("0 failures") and int(res.stdout.split()[0]) >= 500
