@@ -52,6 +52,51 @@ def _percentile(xs, q):
     return float(np.percentile(np.asarray(xs), q)) if len(xs) else math.nan
 
 
+class Admission:
+    """The admission policy of the serving loop, free of any device call.
+
+    Requests are admitted in arrival order: the head of the queue is admitted
+    once it has arrived, an in-flight slot is free and its device bytes fit
+    in what the budget has left.  A head that does not fit blocks the ones
+    behind it (no overtaking), so admission order equals arrival order."""
+
+    def __init__(self, requests: list, budget_bytes: int, slots: int):
+        self.budget = int(budget_bytes)
+        for r in requests:
+            if r.device_bytes() > self.budget:
+                raise ValueError(f"request {r.rid} needs more device memory than the whole budget")
+        self.pending = deque(sorted(requests, key=lambda r: r.arrival))
+        self.free_slots = list(range(int(slots)))
+        self.inflight = {}  # slot -> request
+        self.used = 0
+        self.peak_used, self.peak_inflight = 0, 0
+
+    def done(self) -> bool:
+        return not self.pending and not self.inflight
+
+    def next_arrival(self) -> float:
+        return self.pending[0].arrival if self.pending else math.inf
+
+    def complete(self, slot: int) -> None:
+        req = self.inflight.pop(slot)
+        self.used -= req.device_bytes()
+        self.free_slots.append(slot)
+
+    def admit(self, now: float) -> list:
+        """(request, slot) pairs admitted at time `now`, in arrival order."""
+        out = []
+        while (self.pending and self.free_slots and self.pending[0].arrival <= now
+               and self.used + self.pending[0].device_bytes() <= self.budget):
+            req = self.pending.popleft()
+            slot = self.free_slots.pop()
+            self.inflight[slot] = req
+            self.used += req.device_bytes()
+            self.peak_used = max(self.peak_used, self.used)
+            self.peak_inflight = max(self.peak_inflight, len(self.inflight))
+            out.append((req, slot))
+        return out
+
+
 class Server:
     """Admits requests by arrival time, in-flight slot and device-memory budget."""
 
@@ -102,44 +147,31 @@ class Server:
         """Continuous batching: serve `requests` (sorted by arrival) as they arrive."""
         for r in requests:
             self._alloc_result(r)
-            if r.device_bytes() > self.budget:
-                raise ValueError(f"request {r.rid} needs more device memory than the whole budget")
-        pending = deque(sorted(requests, key=lambda r: r.arrival))
-        free_slots = list(range(self.slots))
-        inflight = {}  # slot -> (request, record)
-        used = 0
-        peak_used, peak_inflight = 0, 0
+        adm = Admission(requests, self.budget, self.slots)
+        records = {}  # slot -> the in-flight request's event and buffers
         t0 = time.perf_counter()
-        while pending or inflight:
+        while not adm.done():
             now = time.perf_counter() - t0
             progressed = False
-            for slot in list(inflight):
-                req, rec = inflight[slot]
-                if rec["event"].query():
-                    req.t_done = time.perf_counter() - t0
-                    used -= req.device_bytes()
-                    del inflight[slot]
-                    free_slots.append(slot)
+            for slot in list(records):
+                if records[slot]["event"].query():
+                    adm.inflight[slot].t_done = time.perf_counter() - t0
+                    adm.complete(slot)
+                    del records[slot]
                     progressed = True
-            # admit in arrival order while the head has arrived and fits
-            while pending and free_slots and pending[0].arrival <= now and used + pending[0].device_bytes() <= self.budget:
-                req = pending.popleft()
-                slot = free_slots.pop()
+            for req, slot in adm.admit(now):
                 req.t_admit = time.perf_counter() - t0
-                inflight[slot] = (req, self._enqueue(req, self.streams[slot]))
-                used += req.device_bytes()
-                peak_used = max(peak_used, used)
-                peak_inflight = max(peak_inflight, len(inflight))
+                records[slot] = self._enqueue(req, self.streams[slot])
                 progressed = True
             if not progressed:
-                if pending and not inflight and pending[0].arrival > now:
-                    time.sleep(min(pending[0].arrival - now, 1e-3))
+                if not adm.inflight and adm.next_arrival() > now:
+                    time.sleep(min(adm.next_arrival() - now, 1e-3))
                 else:
                     time.sleep(20e-6)
         self.torch.cuda.synchronize(self.ctx.device)
         status = self.ctx.status()
         return self._stats(requests, time.perf_counter() - t0, status,
-                           {"peak_device_bytes": peak_used, "peak_in_flight": peak_inflight})
+                           {"peak_device_bytes": adm.peak_used, "peak_in_flight": adm.peak_inflight})
 
     def serve_one_at_a_time(self, requests: list) -> dict:
         """The plain path: requests in arrival order, one at a time on one stream."""
