@@ -19,7 +19,7 @@ OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libpmkrsa.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cpp", "keygen.cpp", "kernels_aux.cu", "modexp_full.cu", "modexp_crt.cu", "modexp_wide.cu", "peak.cu", "noalloc.cu", "tune.cpp", "batch.cpp",
-           "blind.cu", "modexp_latency.cu", "modexp_small.cu"]
+           "blind.cu", "modexp_latency.cu", "modexp_small.cu", "batch_plan.cpp"]
 
 
 def _nvcc() -> str:

@@ -9,6 +9,7 @@
 #include <new>
 #include <vector>
 
+#include "batch_plan.h"
 #include "pmk_internal.h"
 
 struct pmk_batch {
@@ -26,17 +27,9 @@ struct pmk_batch {
 
 namespace {
 
-// A job with at least this many GPU-fulls of exponentiations runs as one
-// plain grid launch inside the graph: it fills the GPU alone, and the grid
-// kernel is a few percent faster than the persistent one on a single large
-// job (measured on 100 MiB).  Smaller jobs share the persistent queues.
-constexpr long long kDirectWaves = 4;
-
+// A planned group with its place in the task array and its grid size.
 struct Group {
-  uint32_t limbs = 0;
-  bool crt = false;
-  pmk::KernelConfig cfg;
-  std::vector<pmk::BatchTask> tasks;
+  pmk::PlanGroup plan;
   size_t offset = 0;
   int blocks = 0;
 };
@@ -59,77 +52,39 @@ void release(pmk_batch *b) {
 }
 
 int plan_and_capture(pmk_ctx *ctx, const pmk_job *jobs, size_t n_jobs, pmk_batch *b) {
-  std::vector<Group> groups;
-  auto group_for = [&](uint32_t limbs, bool crt) -> Group * {
-    for (Group &g : groups)
-      if (g.limbs == limbs && g.crt == crt) return &g;
-    Group g;
-    g.limbs = limbs;
-    g.crt = crt;
-    uint32_t window = 0;
-    if (pmk_get_kernel_config(ctx, limbs, crt ? 1 : 0, &g.cfg.tpi, &g.cfg.form) != PMK_OK ||
-        pmk_get_kernel_window(ctx, limbs, crt ? 1 : 0, &window) != PMK_OK)
-      return nullptr;
-    g.cfg.table = window == pmk::kWindowSmall ? pmk::kTableSmall : pmk::kTableFull;
-    groups.push_back(g);
-    return &groups.back();
-  };
-  int sms = 0;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess) return PMK_ECUDA;
-  struct Direct {
-    size_t job;
-    uint32_t limbs;
-    pmk::KernelConfig cfg;
-  };
-  std::vector<Direct> direct;  // jobs large enough to fill the GPU alone: one plain grid launch each
+  std::vector<pmk::PlanJob> plan_jobs(n_jobs);
   for (size_t j = 0; j < n_jobs; j++) {
     const pmk_job &jb = jobs[j];
-    if (jb.n_chunks == 0) continue;
-    const pmk_keyset *ks = jb.ks;
-    const bool crt = jb.op == PMK_OP_DECRYPT_CRT;
-    const uint32_t S = ks->nbits / 32, limbs = crt ? S / ks->nprimes : S;
-    Group *g = group_for(limbs, crt);
-    if (!g) return PMK_EUNSUPPORTED;
-    const long long wave = pmk::modexp_resident_instances(limbs, g->cfg, crt);  // one GPU-full
-    if (wave <= 0) return PMK_EUNSUPPORTED;
-    const long long instances = (long long)jb.n_chunks * (crt ? ks->nprimes : 1);
-    if (instances >= kDirectWaves * wave) {
-      direct.push_back(Direct{j, limbs, g->cfg});
-      continue;
-    }
-    const uint32_t ipw = 32 / g->cfg.tpi;
-    for (uint32_t k = 0; k < ks->K && k < jb.n_chunks; k++) {
-      const long long count = ((long long)jb.n_chunks - k + ks->K - 1) / ks->K;
-      for (long long i0 = 0; i0 < count; i0 += ipw)
-        for (int prime = 0; prime < (crt ? (int)ks->nprimes : 1); prime++) {
-          pmk::BatchTask t;
-          t.key = ks->d_keys + k;
-          t.in = jb.d_in;
-          t.out = jb.d_out;
-          t.first = k + i0 * ks->K;
-          t.stride = ks->K;
-          t.count = (int)std::min<long long>(ipw, count - i0);
-          t.mode = crt ? 2 + prime : (jb.op == PMK_OP_ENCRYPT ? 0 : 1);
-          g->tasks.push_back(t);
-        }
-    }
+    plan_jobs[j] = pmk::PlanJob{jb.ks->d_keys, jb.ks->K, jb.ks->nbits, jb.ks->nprimes, jb.op,
+                                jb.n_chunks, jb.d_in,  jb.d_out};
   }
-  // longest work first: decryptions before encryptions within a group,
-  // widest groups launched first
-  for (Group &g : groups)
-    std::stable_sort(g.tasks.begin(), g.tasks.end(),
-                     [](const pmk::BatchTask &x, const pmk::BatchTask &y) { return (x.mode != 0) > (y.mode != 0); });
-  std::stable_sort(groups.begin(), groups.end(),
-                   [](const Group &x, const Group &y) { return x.limbs * (x.crt ? 1 : 2) > y.limbs * (y.crt ? 1 : 2); });
-  groups.erase(std::remove_if(groups.begin(), groups.end(), [](const Group &g) { return g.tasks.empty(); }),
-               groups.end());
+  auto config = [ctx](uint32_t limbs, bool crt, pmk::KernelConfig *cfg) {
+    uint32_t window = 0;
+    if (pmk_get_kernel_config(ctx, limbs, crt ? 1 : 0, &cfg->tpi, &cfg->form) != PMK_OK ||
+        pmk_get_kernel_window(ctx, limbs, crt ? 1 : 0, &window) != PMK_OK)
+      return false;
+    cfg->table = window == pmk::kWindowSmall ? pmk::kTableSmall : pmk::kTableFull;
+    return true;
+  };
+  auto resident = [](uint32_t limbs, const pmk::KernelConfig &cfg, bool crt) {
+    return pmk::modexp_resident_instances(limbs, cfg, crt);
+  };
+  std::vector<pmk::PlanGroup> planned;
+  std::vector<pmk::PlanDirect> direct;  // jobs large enough to fill the GPU alone: one plain grid launch each
+  int rc = pmk::plan_batch(plan_jobs, config, resident, planned, direct);
+  if (rc != PMK_OK) return rc;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess) return PMK_ECUDA;
+  std::vector<Group> groups(planned.size());
   std::vector<pmk::BatchTask> all;
-  for (Group &g : groups) {
+  for (size_t gi = 0; gi < planned.size(); gi++) {
+    Group &g = groups[gi];
+    g.plan = std::move(planned[gi]);
     g.offset = all.size();
-    all.insert(all.end(), g.tasks.begin(), g.tasks.end());
-    const int per_sm = pmk::modexp_tasks_blocks_per_sm(g.limbs, g.cfg, g.crt);  // also raises the smem limit
+    all.insert(all.end(), g.plan.tasks.begin(), g.plan.tasks.end());
+    const int per_sm = pmk::modexp_tasks_blocks_per_sm(g.plan.limbs, g.plan.cfg, g.plan.crt);  // raises the smem limit
     if (per_sm <= 0) return PMK_EUNSUPPORTED;
-    const long long need = ((long long)g.tasks.size() + 3) / 4;  // four warps per block
+    const long long need = ((long long)g.plan.tasks.size() + 3) / 4;  // four warps per block
     g.blocks = (int)std::max<long long>(1, std::min<long long>(need, (long long)per_sm * sms));
   }
   b->n_tasks = all.size();
@@ -150,7 +105,6 @@ int plan_and_capture(pmk_ctx *ctx, const pmk_job *jobs, size_t n_jobs, pmk_batch
     if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return PMK_ECUDA;
 
   if (cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return PMK_ECUDA;
-  int rc = PMK_OK;
   if (cudaMemsetAsync(b->d_counters, 0, sizeof(int) * std::max<size_t>(1, groups.size()), b->capture) != cudaSuccess)
     rc = PMK_ECUDA;
   for (size_t j = 0; j < n_jobs && rc == PMK_OK; j++)
@@ -164,8 +118,8 @@ int plan_and_capture(pmk_ctx *ctx, const pmk_job *jobs, size_t n_jobs, pmk_batch
       rc = PMK_ECUDA;
       break;
     }
-    rc = pmk::launch_modexp_tasks(g.limbs, g.cfg, g.crt, b->d_tasks + g.offset, (int)g.tasks.size(),
-                                  b->d_counters + gi, g.blocks, b->side[gi]);
+    rc = pmk::launch_modexp_tasks(g.plan.limbs, g.plan.cfg, g.plan.crt, b->d_tasks + g.offset,
+                                  (int)g.plan.tasks.size(), b->d_counters + gi, g.blocks, b->side[gi]);
     if (rc == PMK_OK && (cudaEventRecord(b->events[gi], b->side[gi]) != cudaSuccess ||
                          cudaStreamWaitEvent(b->capture, b->events[gi], 0) != cudaSuccess))
       rc = PMK_ECUDA;

@@ -225,3 +225,28 @@ def test_unexported_key_constants_from_their_definitions(tmp_path):
     res = subprocess.run([exe], capture_output=True, text=True)
     assert res.returncode == 0, res.stdout
     assert res.stdout.strip().endswith("0 failures") and int(res.stdout.split()[0]) >= 500
+
+
+def test_batch_planner_covers_every_chunk_once(tmp_path):
+    """The batch planner (batch_plan.cpp, built with g++ against
+    tests/c/batch_plan_check.cpp and stand-in geometry / capacity functions)
+    over 300 random job mixes: grid launches exactly for jobs of several
+    GPU-fulls, every other chunk and prime in exactly one task of its key,
+    task sizes within a warp, groups widest first with decryptions first,
+    and refusal of widths without a geometry or capacity."""
+    import shutil
+    import subprocess
+
+    if shutil.which("g++") is None:
+        pytest.skip("g++ not available")
+    from paper_2111_11924_gb300 import _native_build as NB
+
+    cuda_inc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
+    exe = str(tmp_path / "batch_plan_check")
+    subprocess.check_call(["g++", "-std=c++17", "-O2", "-Wall", "-Wextra", "-Werror", "-o", exe,
+                           os.path.join(ROOT, "tests", "c", "batch_plan_check.cpp"),
+                           os.path.join(NB.CSRC, "batch_plan.cpp"), "-I", os.path.join(ROOT, "include"), "-I",
+                           NB.CSRC, "-I", cuda_inc])
+    res = subprocess.run([exe], capture_output=True, text=True)
+    assert res.returncode == 0, res.stdout
+    assert res.stdout.strip().endswith("0 failures") and int(res.stdout.split()[0]) >= 1_000_000
