@@ -63,6 +63,8 @@ void pmk_ctx_destroy(pmk_ctx *ctx);
  *   K: 1..16383 keys.
  *   nbits: 128..8192, a multiple of 128 (EUNSUPPORTED if not built).
  *   e: odd, 3 <= e < 2^32.
+ * EINVAL for a NULL ctx or out, or K, nbits or e out of range; ENOMEM or
+ * ECUDA if the upload fails.  *out is set only on success.
  */
 int pmk_keygen(pmk_ctx *ctx, uint32_t K, uint32_t nbits, uint64_t e, uint64_t seed, pmk_keyset **out);
 
@@ -130,6 +132,8 @@ int pmk_keyset_export(const pmk_keyset *ks, uint32_t *N, uint32_t *d, uint32_t *
  * coef_0 = r_1^-1 mod r_0, coef_1 = 0, coef_i = (r_0 ... r_{i-1})^-1 mod r_i.
  * Any pointer may be NULL. */
 int pmk_keyset_export_primes(const pmk_keyset *ks, uint32_t *primes, uint32_t *dexp, uint32_t *coef);
+/* Key-set properties: primes per modulus (b), key count K, width nbits and
+ * public exponent e.  Each returns 0 for NULL. */
 uint32_t pmk_keyset_num_primes(const pmk_keyset *ks);
 uint32_t pmk_keyset_num_keys(const pmk_keyset *ks);
 uint32_t pmk_keyset_nbits(const pmk_keyset *ks);
@@ -145,15 +149,20 @@ size_t pmk_num_chunks(size_t msg_len, uint32_t nbits);
 /*
  * Split (Section 3.1): chunk t = message bytes [tP, min((t+1)P, L)) read as
  * a little-endian integer, zero-extended to nbits/32 limbs.
- *   d_msg: msg_len bytes (device).  d_chunks: n_chunks x nbits/32 uint32
- *   (device), n_chunks must equal pmk_num_chunks(msg_len, nbits).
+ *   d_msg: msg_len bytes (device), any alignment.  d_chunks: n_chunks x
+ *   nbits/32 uint32 (device, 16-byte aligned), n_chunks must equal
+ *   pmk_num_chunks(msg_len, nbits).
+ * EINVAL for a NULL ctx or buffer, nbits outside 128..8192 or not a multiple
+ * of 128, a chunk count that does not match, or a misaligned d_chunks.
  */
 int pmk_split(pmk_ctx *ctx, uint32_t nbits, const uint8_t *d_msg, size_t msg_len, uint32_t *d_chunks,
               size_t n_chunks, void *stream);
 
 /*
  * Join (the "merge and output" step of Section 3.3): inverse of pmk_split.
- * Writes the low P bytes of every chunk, concatenated and cut to msg_len.
+ * Writes the low P bytes of every chunk, concatenated and cut to msg_len;
+ * nothing outside d_msg[0, msg_len) is written.  Same arguments and errors
+ * as pmk_split (d_chunks 16-byte aligned, d_msg any alignment).
  */
 int pmk_join(pmk_ctx *ctx, uint32_t nbits, const uint32_t *d_chunks, size_t n_chunks, uint8_t *d_msg,
              size_t msg_len, void *stream);
@@ -173,7 +182,11 @@ int pmk_encrypt_chunks(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_in,
  * full-width exponentiation; use_crt = 1: the CRT form of Section 2.1
  * (one exponentiation per prime over nbits/b bits -- two halves for an
  * ordinary key, b for a multi-prime key -- then the CRT recombination
- * sum_i m_i c_i mod N, c_i = (N/r_i) ((N/r_i)^-1 mod r_i)), bit-identical.  With use_crt = 1, d_in and d_out must not overlap.
+ * sum_i m_i c_i mod N, c_i = (N/r_i) ((N/r_i)^-1 mod r_i)), bit-identical.
+ * With use_crt = 0, d_in and d_out may be the same buffer; with use_crt = 1
+ * they must not overlap (EINVAL).  EINVAL also for a NULL or misaligned
+ * argument or a key set of another device; a chunk >= N is reported as
+ * PMK_ERANGE by pmk_status().
  */
 int pmk_decrypt_chunks(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_in, uint32_t *d_out,
                        size_t n_chunks, int use_crt, void *stream);
@@ -298,7 +311,9 @@ const char *pmk_strerror(int code);
  * Integer-pipe peak of this GPU, measured by the library's own
  * dependency-free 32x32->64 multiply-accumulate loop: MACs per clock per SM,
  * the SM clock seen during the loop (MHz) and the SM count.  Used as the
- * roofline denominator of the modular-exponentiation kernels.
+ * roofline denominator of the modular-exponentiation kernels.  Synchronous.
+ * EINVAL for a NULL argument; ENOMEM or ECUDA if its buffers or launches
+ * fail, or if fewer of its blocks fit on an SM than the loop assumes.
  */
 int pmk_measure_int_peak(pmk_ctx *ctx, double *macs_per_clk_per_sm, double *sm_mhz, int *num_sms);
 
@@ -307,7 +322,9 @@ int pmk_measure_int_peak(pmk_ctx *ctx, double *macs_per_clk_per_sm, double *sm_m
  * loop of plain 32-bit multiply-adds (mad.lo, sixteen independent chains per
  * thread): mad.lo per clock per SM, the SM clock seen (MHz) and the SM count.
  * One 32x32->64 MAC is two such operations (low and high halves); this is
- * the denominator of the kernels' "% of INT32 peak".
+ * the denominator of the kernels' "% of INT32 peak".  Like
+ * pmk_measure_int_peak: EINVAL for a NULL argument, ENOMEM or ECUDA if its
+ * buffers or launches fail.
  */
 int pmk_measure_imad_peak(pmk_ctx *ctx, double *mad_lo_per_clk_per_sm, double *sm_mhz, int *num_sms);
 
@@ -324,7 +341,8 @@ int pmk_measure_imad_peak(pmk_ctx *ctx, double *mad_lo_per_clk_per_sm, double *s
  * bit-identical for every geometry; only speed differs.
  */
 int pmk_set_kernel_config(pmk_ctx *ctx, uint32_t limbs, int crt, uint32_t tpi, uint32_t form);
-/* The geometry the context currently uses for (limbs, crt). */
+/* The geometry the context currently uses for (limbs, crt).  EINVAL for a
+ * NULL argument, EUNSUPPORTED if no kernel is compiled for (limbs, crt). */
 int pmk_get_kernel_config(const pmk_ctx *ctx, uint32_t limbs, int crt, uint32_t *tpi, uint32_t *form);
 /* Compiled geometries for (limbs, crt): writes up to `max` (tpi, form) pairs
  * and returns how many exist (a negative code on bad arguments).  Host only. */
@@ -348,7 +366,9 @@ int pmk_list_kernel_configs(uint32_t limbs, int crt, uint32_t *tpi, uint32_t *fo
  * together with the geometry.
  */
 int pmk_set_kernel_window(pmk_ctx *ctx, uint32_t limbs, int crt, uint32_t max_window);
-/* The widest window the context currently uses for (limbs, crt). */
+/* The widest window the context currently uses for (limbs, crt), for its
+ * current geometry.  EINVAL for a NULL argument, EUNSUPPORTED if no kernel
+ * is compiled for (limbs, crt). */
 int pmk_get_kernel_window(const pmk_ctx *ctx, uint32_t limbs, int crt, uint32_t *max_window);
 
 /*
@@ -362,6 +382,10 @@ int pmk_get_kernel_window(const pmk_ctx *ctx, uint32_t limbs, int crt, uint32_t 
  * geometry and its best launch time in ms (any output pointer may be NULL);
  * pmk_get_kernel_window reads the window chosen.  Allocates and frees two
  * temporary device buffers and synchronises the device's legacy stream.
+ * reps is clamped to 1..20.  EINVAL for a NULL ctx or ks, n_chunks = 0 or a
+ * mode outside 0..2; EUNSUPPORTED if no kernel is compiled for the width;
+ * ENOMEM or ECUDA if the temporary buffers or a launch fail (the context's
+ * geometry is then left unchanged).
  */
 int pmk_autotune(pmk_ctx *ctx, const pmk_keyset *ks, size_t n_chunks, int mode, int reps, uint32_t *tpi,
                  uint32_t *form, float *ms);
