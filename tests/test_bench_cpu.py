@@ -1,0 +1,32 @@
+"""bench.py's roofline arithmetic on the CPU: the algorithmic work per chunk
+that the bench line divides by the kernel time, checked against the cost
+model's closed forms (one CIOS Montgomery product = 2 s^2 + s MACs over s
+limbs; one full-d decryption at the fixed w = 5 window count = (n - 1)
+squarings + n/6 multiplies + 16 table entries + 2 conversions)."""
+import pytest
+
+import bench
+
+
+@pytest.mark.parametrize("nbits,macs", [(1024, 2080), (2048, 8256), (3072, 18528), (4096, 32896)])
+def test_montmul_macs(nbits, macs):
+    s = nbits // 32
+    assert bench.macs_per_montmul(nbits) == macs == 2 * s * s + s
+
+
+def test_full_d_count_at_2048_bits():
+    n = 2048
+    assert bench.algorithmic_montmuls(n) == pytest.approx(2047 + 2048 / 6 + 18)
+    assert bench.algorithmic_montmuls(n) == pytest.approx(2406.33, abs=0.01)
+    assert bench.algorithmic_montmuls(n) * bench.macs_per_montmul(n) == pytest.approx(1.987e7, rel=1e-3)
+
+
+def test_crt_count_and_prime_scaling():
+    # two primes at 2048 bits: two 1024-bit exponentiations, 3 input products each, 2 recombination products
+    two = bench.algorithmic_crt_macs(2048, 2)
+    assert two == pytest.approx(2 * (bench.algorithmic_montmuls(1024) + 3) * 2080 + 2 * 8256)
+    assert two == pytest.approx(5.07e6, rel=1e-3)
+    # b primes of n/b bits: each exponentiation costs ~ (n/b)^3, so the total falls ~ b^2 / 4 against two primes
+    for n, b in ((2048, 4), (3072, 3), (4096, 4), (8192, 4)):
+        ratio = bench.algorithmic_crt_macs(n, 2) / bench.algorithmic_crt_macs(n, b)
+        assert 0.8 * b * b / 4 < ratio < 1.05 * b * b / 4, (n, b, ratio)
