@@ -37,6 +37,7 @@ WORKLOAD = W.FILE_1MIB_2048
 METRIC = "2048-bit decrypt chunk-modexps/s"
 UNIT = "chunk-modexps/s"
 L2_FLUSH_BYTES = 256 << 20
+FORM_NAMES = ["chain", "columns"]  # Montgomery product forms (pmk_set_kernel_config)
 KERNELS_PER_STEP = 6  # split, range check + modexp (encrypt), range check + modexp (decrypt), join
 
 # DRAM traffic of the full-d decryption kernel from one ncu capture, valid only
@@ -72,6 +73,18 @@ def algorithmic_crt_macs(nbits: int, primes: int = 2) -> float:
     h = nbits // primes
     per_prime = (algorithmic_montmuls(h) + 2 * primes - 1) * macs_per_montmul(h)
     return primes * per_prime + primes * macs_per_montmul(nbits)
+
+
+def int32_peak_tops(mad_lo_per_clk_per_sm: float, sms: int, mhz: float) -> float:
+    """INT32 multiply-add peak in TOP/s: the measured mad.lo issue rate per
+    clock per SM x SM count x SM clock."""
+    return mad_lo_per_clk_per_sm * sms * mhz * 1e6 / 1e12
+
+
+def int32_ops_per_s(macs: float, ms: float) -> float:
+    """Algorithmic INT32 operations per second: each 32x32->64 MAC is a low
+    and a high multiply-add half."""
+    return 2 * macs / (ms / 1e3)
 
 
 class ClockSampler:
@@ -323,9 +336,12 @@ def run_ours(args):
     clk = clocks.summary()
     sms = peak["num_sms"]
     max_mhz = clk["sm_max_mhz"] or 2070.0
-    peak_tmacs = peak["macs_per_clk_per_sm"] * sms * max_mhz * 1e6 / 1e12
+    # Roofline: algorithmic INT32 multiply-add halves (two per 32x32->64 MAC,
+    # at the fixed w = 5 count) over the mad.lo rate measured in this run.
+    peak_tops = int32_peak_tops(imad["mad_lo_per_clk_per_sm"], sms, max_mhz)
     alg_macs = algorithmic_montmuls(w.nbits) * macs_per_montmul(w.nbits) * n
-    achieved = alg_macs / (dec_ms / 1e3) / 1e12
+    achieved = int32_ops_per_s(alg_macs, dec_ms) / 1e12
+    crt_achieved = int32_ops_per_s(n * algorithmic_crt_macs(w.nbits), crt_dec) / 1e12
     digest = sources_digest()
 
     # the plain GPU formulation on the same ciphertext: one thread per chunk,
@@ -374,17 +390,16 @@ def run_ours(args):
                             "round_trip": mb / (t_step / 1e3)},
         "crt": {"value": world * n / (crt_step / 1e3), "unit": UNIT, "ms_per_step": crt_step,
                 "decrypt_ms": crt_dec, "decrypt_only": n / (crt_dec / 1e3),
-                "roofline": {"bound": "alu", "unit": "TMAC/s", "peak": peak_tmacs,
-                             "achieved": n * algorithmic_crt_macs(w.nbits) / (crt_dec / 1e3) / 1e12,
-                             "frac": n * algorithmic_crt_macs(w.nbits) / (crt_dec / 1e3) / 1e12 / peak_tmacs,
-                             "macs_per_chunk": algorithmic_crt_macs(w.nbits)},
-                "geometry": {"lanes_per_instance": tuned_crt["tpi"], "form": ["chain", "columns"][tuned_crt["form"]],
+                "roofline": {"bound": "alu", "unit": "TOP/s", "peak": peak_tops, "achieved": crt_achieved,
+                             "frac": crt_achieved / peak_tops, "macs_per_chunk": algorithmic_crt_macs(w.nbits),
+                             "int32_ops_per_chunk": 2 * algorithmic_crt_macs(w.nbits)},
+                "geometry": {"lanes_per_instance": tuned_crt["tpi"], "form": FORM_NAMES[tuned_crt["form"]],
                              "max_window": tuned_crt["window"]}},
         "blinded": {"value": world * n / (float(ph_bl.sum(axis=1).mean()) / 1e3), "unit": UNIT,
                     "ms_per_step": float(ph_bl.sum(axis=1).mean()), "encrypt_ms": float(ph_bl[:, 1].mean()),
                     "decrypt_ms": float(ph_bl[:, 2].mean()),
                     "step": "split + Algorithm 1 encryption with R + decryption as (c* c_r^-1)^d + join"},
-        "geometry": {"lanes_per_instance": tuned["tpi"], "form": ["chain", "columns"][tuned["form"]],
+        "geometry": {"lanes_per_instance": tuned["tpi"], "form": FORM_NAMES[tuned["form"]],
                      "max_window": tuned["window"],
                      "chosen_by": "pmk_autotune over every compiled geometry and window bound"},
         "thread_per_chunk_baseline": {"decrypt_only": n / (base_ms / 1e3), "unit": UNIT, "decrypt_ms": base_ms,
@@ -394,19 +409,20 @@ def run_ours(args):
         "split_join_GBps": {"split": (w.msg_bytes + cipher_bytes) / (split_ms / 1e3) / 1e9,
                             "join": (w.msg_bytes + cipher_bytes) / (join_ms / 1e3) / 1e9,
                             "note": "1 MiB step: launch-latency bound; see split_join_hbm for bandwidth"},
-        "int32_ops": {"achieved_tops": 2 * achieved,
-                      "mad_lo_peak_tops": imad["mad_lo_per_clk_per_sm"] * sms * max_mhz * 1e6 / 1e12,
-                      "frac": 2 * achieved / (imad["mad_lo_per_clk_per_sm"] * sms * max_mhz * 1e6 / 1e12),
-                      "mad_lo_per_clk_per_sm": imad["mad_lo_per_clk_per_sm"],
-                      "note": "2 INT32 multiply-add halves per MAC against the mad.lo rate measured in this run "
-                              "(pmk_measure_imad_peak)"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tmacs, "unit": "TMAC/s",
-                     "frac": achieved / peak_tmacs, "traffic": TRAFFIC_MEASURED.get(digest),
-                     "kernel": f"k_modexp<64,{tuned['tpi']},full,{['chain', 'columns'][tuned['form']]}> "
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "TOP/s",
+                     "frac": achieved / peak_tops, "traffic": TRAFFIC_MEASURED.get(digest),
+                     "kernel": f"k_modexp<64,{tuned['tpi']},full,{FORM_NAMES[tuned['form']]}> "
                                "(full-d decrypt; interval includes its ~4 us range check)",
-                     "peak_basis": f"{peak['macs_per_clk_per_sm']:.2f} MAC/clk/SM measured x {sms} SMs x {max_mhz:.0f} MHz",
-                     "frac_at_observed_clock": (achieved / (peak["macs_per_clk_per_sm"] * sms * clk["sm_mhz"] * 1e-6)
-                                                if clk["sm_mhz"] else None)},
+                     "ops_per_launch": 2 * alg_macs, "ops_basis": "2 INT32 multiply-add halves per 32x32->64 MAC; "
+                     f"{algorithmic_montmuls(w.nbits):.1f} Montgomery products x {macs_per_montmul(w.nbits)} MACs "
+                     f"x {n} chunks", "decrypt_ms": dec_ms,
+                     "peak_basis": f"{imad['mad_lo_per_clk_per_sm']:.2f} mad.lo/clk/SM measured x {sms} SMs x "
+                                   f"{max_mhz:.0f} MHz",
+                     "frac_at_observed_clock": (achieved / int32_peak_tops(imad["mad_lo_per_clk_per_sm"], sms,
+                                                                           clk["sm_mhz"]) if clk["sm_mhz"] else None)},
+        "wide_mac_loop": {"macs_per_clk_per_sm": peak["macs_per_clk_per_sm"],
+                          "note": "the library's 32x32->64 multiply loop (pmk_measure_int_peak); context only, "
+                                  "the roofline denominator is the mad.lo rate"},
         "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
         "e2e": {"value": world * n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": w.msg_bytes + cipher_bytes,
                 "d2h_bytes_per_step": cipher_bytes + w.msg_bytes},
@@ -541,7 +557,7 @@ def run_widths(args):
                           "ms": {k: round(v, 4) for k, v in res.items()},
                           "paper_table2_P100_config_D_ms": paper,
                           "chunk_modexps_per_s": {k: round(n / (v / 1e3)) for k, v in res.items()},
-                          "geometry": {m: (t["tpi"], ["chain", "columns"][t["form"]], t["window"])
+                          "geometry": {m: (t["tpi"], FORM_NAMES[t["form"]], t["window"])
                                        for m, t in tuned.items()}}))
         ks.free()
     return 0
@@ -682,7 +698,7 @@ def run_batched(args):
             "batched_chunk_modexps_per_s": n_total / (t_batch / 1e3), "speedup": t_plain / t_batch,
             "payload_MBps_batched": payload / 2**20 / (t_batch / 1e3), "identical_outputs": same,
             "kernels_in_graph": batch.n_kernels, "queued_tasks": batch.n_tasks,
-            "geometry": {f"{nb}-{m}": [t["tpi"], ["chain", "columns"][t["form"]], t["window"]]
+            "geometry": {f"{nb}-{m}": [t["tpi"], FORM_NAMES[t["form"]], t["window"]]
                          for (nb, m), t in tuned.items()}}
     print(json.dumps(line))
     batch.destroy()
@@ -742,7 +758,7 @@ def run_file100(args):
                      "queued_tasks": batch.n_tasks, "outputs_equal_message_chunks": ok_plain and ok_batch,
                      "join_roundtrip": roundtrip,
                      "geometry": [tuned["crt" if crt else "decrypt"]["tpi"],
-                                  ["chain", "columns"][tuned["crt" if crt else "decrypt"]["form"]],
+                                  FORM_NAMES[tuned["crt" if crt else "decrypt"]["form"]],
                                   tuned["crt" if crt else "decrypt"]["window"]]}
         batch.destroy()
     ctx.check()
@@ -882,7 +898,7 @@ def run_multiprime(args):
                           "chunk_modexps_per_s": round(n / (ms / 1e3)),
                           "speedup_vs_two_primes": round(base / ms, 3) if base else None,
                           "model_b2_over_4": b * b / 4,
-                          "geometry": (tuned["tpi"], ["chain", "columns"][tuned["form"]], tuned["window"]),
+                          "geometry": (tuned["tpi"], FORM_NAMES[tuned["form"]], tuned["window"]),
                           "timing": "CUDA events around one pmk_decrypt_chunks call (range check, one "
                                     "exponentiation per prime, recombination); L2 flushed between calls"}))
         ctx.set_kernel_config(nbits // 32 // b, True, 0)

@@ -16,7 +16,7 @@
  *   - Device work is enqueued on `stream` (a cudaStream_t; NULL = legacy
  *     default stream) and returns before it finishes.  Errors detected on
  *     the device (an input chunk >= its modulus) are recorded in the
- *     context and reported by pmk_status().
+ *     context and reported by pmk_sync_status().
  *   - Chunk buffers hold n_chunks x nbits/32 little-endian uint32 limbs,
  *     chunk-major ("limb buffer"), and must be 16-byte aligned (EINVAL).
  *     Chunk t is bound to key t mod K, the row-per-key reshape of the i x j
@@ -48,9 +48,9 @@ typedef struct pmk_keyset pmk_keyset;   /* K key pairs: host copy + device-resid
 
 /* Create a context bound to CUDA device `cuda_device`.  Allocates a small
  * device status word.  *out is set only on success. */
-int pmk_ctx_create(int cuda_device, pmk_ctx **out);
+int pmk_create(pmk_ctx **out, int cuda_device);
 /* Release the context and its device memory.  NULL is ignored. */
-void pmk_ctx_destroy(pmk_ctx *ctx);
+void pmk_destroy(pmk_ctx *ctx);
 
 /*
  * Key initialisation (Section 1.1 steps 1a-1c; Algorithm 1 "Initialization").
@@ -171,7 +171,7 @@ int pmk_join(pmk_ctx *ctx, uint32_t nbits, const uint32_t *d_chunks, size_t n_ch
  * Encryption (Algorithm 1 "Encryption", c = m^e mod N; Algorithm 2 over
  * Algorithm 3 Montgomery products): d_out[t] = d_in[t]^e mod N_{t mod K}.
  * d_in, d_out: n_chunks limb buffers (device); they may be the same buffer.
- * A chunk >= N is reported as PMK_ERANGE by pmk_status().
+ * A chunk >= N is reported as PMK_ERANGE by pmk_sync_status().
  */
 int pmk_encrypt_chunks(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_in, uint32_t *d_out,
                        size_t n_chunks, void *stream);
@@ -186,7 +186,7 @@ int pmk_encrypt_chunks(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_in,
  * With use_crt = 0, d_in and d_out may be the same buffer; with use_crt = 1
  * they must not overlap (EINVAL).  EINVAL also for a NULL or misaligned
  * argument or a key set of another device; a chunk >= N is reported as
- * PMK_ERANGE by pmk_status().
+ * PMK_ERANGE by pmk_sync_status().
  */
 int pmk_decrypt_chunks(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_in, uint32_t *d_out,
                        size_t n_chunks, int use_crt, void *stream);
@@ -219,7 +219,7 @@ int pmk_encrypt_blinded(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_m,
  * Fermat exponentiation per prime (c_r^(r_i - 2) mod r_i: p and q for an
  * ordinary key) and their CRT recombination, followed by one exponentiation
  * by d (full width, or the Section 2.1 CRT form with use_crt = 1).  A c_r sharing a factor
- * with N reports PMK_ENOINV through pmk_status.  Buffers must not overlap.
+ * with N reports PMK_ENOINV through pmk_sync_status.  Buffers must not overlap.
  */
 int pmk_decrypt_blinded(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_cstar, const uint32_t *d_cr,
                         uint32_t *d_m, size_t n_chunks, int use_crt, void *stream);
@@ -227,9 +227,15 @@ int pmk_decrypt_blinded(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_cs
 /*
  * Whole-message calls on HOST buffers: copy in, split/encrypt (or
  * decrypt/join) on the device, copy out, synchronise the stream.  The
- * context keeps grow-only device staging buffers between calls.
+ * context keeps grow-only device staging buffers between calls, allocated
+ * and freed in stream order (cudaMallocAsync / cudaFreeAsync); a call waits
+ * on its own stream for the previous call's use of them, whatever stream
+ * that was.
  *   h_cipher: n_chunks x nbits/32 uint32 with n_chunks = pmk_num_chunks(msg_len, nbits).
- * Returns the device status as pmk_status() would.
+ * Returns the device status as pmk_sync_status() would.  On an error after
+ * the copy of the caller's input was queued, the stream is synchronised
+ * before the call returns, so no copy from or to the caller's buffers is
+ * left in flight.
  */
 int pmk_encrypt_message_host(pmk_ctx *ctx, const pmk_keyset *ks, const uint8_t *h_msg, size_t msg_len,
                              uint32_t *h_cipher, size_t n_chunks, void *stream);
@@ -248,13 +254,26 @@ int pmk_decrypt_message_host(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t 
  * called.  No context is needed: the key set's device is used.
  *   Capacity: 256 + 2 * round_up_256(n_chunks * nbits/8) + round_up_256(msg_len)
  *   bytes must fit in 32 MiB, else PMK_ETOOLARGE and nothing is enqueued.
- *   The first call on a device looks up the array's device address (one-time
- *   set-up per device); make that first call before any stream capture.
+ *   The array is committed when the library's module that holds it is
+ *   loaded.  Under CUDA's lazy module loading (the default) that happens in
+ *   the first call on a device, whose one-time set-up looks up the array's
+ *   device address; if the device's memory is already taken by then, that
+ *   call fails with PMK_ECUDA.  A call with n_chunks = msg_len = 0 (h_cipher
+ *   and h_msg may be NULL) performs only that set-up: make one at start-up,
+ *   before another allocator claims the device's memory.
  *   All calls share the array and it keeps the last call's contents: calls
  *   whose GPU work overlaps (other streams, other host threads) race and
  *   corrupt each other's results.
- *   Synchronises `stream`.  Returns PMK_OK, PMK_ERANGE (a chunk >= its
- *   modulus), PMK_EINVAL, PMK_ETOOLARGE or PMK_ECUDA.
+ *   The call ends by synchronising `stream`, so it must not be made while
+ *   `stream` is being captured into a CUDA graph.  It runs the built-in
+ *   default kernel geometry and odd-power table of each width, not a
+ *   context's autotuned ones (it takes no context), so its speed can differ
+ *   from pmk_decrypt_message_host's.
+ *   Returns PMK_OK, PMK_ERANGE (a chunk >= its modulus), PMK_EINVAL (NULL
+ *   key set or buffer, a chunk count that does not match msg_len, or 2^32
+ *   chunks or more), PMK_ETOOLARGE or PMK_ECUDA.  On an error after the copy
+ *   of h_cipher was queued, the stream is synchronised before the call
+ *   returns, so no copy from or to the caller's buffers is left in flight.
  */
 int pmk_decrypt_message_host_noalloc(const pmk_keyset *ks, const uint32_t *h_cipher, size_t n_chunks,
                                      uint8_t *h_msg, size_t msg_len, int use_crt, void *stream);
@@ -276,7 +295,7 @@ int pmk_decrypt_message_host_noalloc(const pmk_keyset *ks, const uint32_t *h_cip
  *   - range checks, the kernels and CRT recombination are captured once into
  *     a CUDA graph (geometry: the context's current kernel configs).
  * pmk_batch_launch replays that graph on `stream` (asynchronous; errors via
- * pmk_status).  The buffers named by the jobs must stay valid and keep their
+ * pmk_sync_status).  The buffers named by the jobs must stay valid and keep their
  * addresses for the batch's lifetime; their contents may change between
  * launches.  Results are bit-identical to one pmk_*_chunks call per job.
  */
@@ -302,7 +321,7 @@ void pmk_batch_destroy(pmk_batch *batch);
 /* Synchronise `stream`, then return (and clear) the first device-side error
  * recorded since the last call: PMK_OK, PMK_ERANGE or PMK_ENOINV; PMK_ECUDA
  * if a CUDA call fails. */
-int pmk_status(pmk_ctx *ctx, void *stream);
+int pmk_sync_status(pmk_ctx *ctx, void *stream);
 
 /* Static description of an error code. */
 const char *pmk_strerror(int code);

@@ -1,6 +1,7 @@
 // C ABI of the PMKRSA library (include/pmkrsa.h): argument checks, key-set
 // upload, and the order of kernel launches for each call.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <new>
@@ -38,14 +39,39 @@ bool overlap(const void *a, size_t na, const void *b, size_t nb) {
   return x < y + nb && y < x + na;
 }
 
-int grow(void **buf, size_t *cap, size_t bytes) {
-  if (*cap >= bytes) return PMK_OK;
-  if (*buf) cudaFree(*buf);
-  *buf = nullptr;
-  *cap = 0;
-  if (cudaMalloc(buf, bytes) != cudaSuccess) return PMK_ENOMEM;
-  *cap = bytes;
+// Make the staging buffer hold at least `bytes` for work enqueued on `st`:
+// first order `st` after the buffer's last use (on whatever stream), then
+// grow it in stream order if it is too small.  Pair with release().
+int acquire(pmk::Staging &s, size_t bytes, cudaStream_t st) {
+  if (!s.last_use && cudaEventCreateWithFlags(&s.last_use, cudaEventDisableTiming) != cudaSuccess) return PMK_ECUDA;
+  if (cudaStreamWaitEvent(st, s.last_use, 0) != cudaSuccess) return PMK_ECUDA;
+  if (s.cap >= bytes) return PMK_OK;
+  if (s.ptr && cudaFreeAsync(s.ptr, st) != cudaSuccess) return PMK_ECUDA;
+  s.ptr = nullptr;
+  s.cap = 0;
+  if (cudaMallocAsync(&s.ptr, bytes, st) != cudaSuccess) {
+    s.ptr = nullptr;
+    return PMK_ENOMEM;
+  }
+  s.cap = bytes;
   return PMK_OK;
+}
+
+// Mark the end of this call's use of the buffer: everything enqueued on `st`
+// so far.
+void release(pmk::Staging &s, cudaStream_t st) {
+  if (s.last_use) cudaEventRecord(s.last_use, st);
+}
+
+// Wait for the buffer's last use, then free it and its event.
+void drop(pmk::Staging &s) {
+  if (s.last_use) cudaEventSynchronize(s.last_use);
+  if (s.ptr) {
+    cudaFreeAsync(s.ptr, nullptr);
+    cudaStreamSynchronize(nullptr);
+  }
+  if (s.last_use) cudaEventDestroy(s.last_use);
+  s = pmk::Staging{};
 }
 
 // Kernel geometry for an exponentiation over `limbs` limbs: the context's
@@ -173,9 +199,7 @@ bool width_built(uint32_t nbits, uint32_t nprimes = 2) {
 // Most keys per key set: the CRT grid has one row per (key, prime) pair.
 constexpr uint32_t kMaxKeys = 65535 / pmk::kMaxPrimes;
 
-// Most chunks per call: keeps byte counts and grid sizes far from overflow
-// (2^32 chunks of 2048 bits are 1 TiB, beyond any device's memory).
-constexpr size_t kMaxChunks = (size_t)1 << 32;
+using pmk::kMaxChunks;
 
 int check_chunk_call(const pmk_ctx *ctx, const pmk_keyset *ks, const void *in, const void *out, size_t n_chunks) {
   if (!ctx || !ks || n_chunks >= kMaxChunks) return PMK_EINVAL;
@@ -212,9 +236,16 @@ int enqueue_decrypt(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *in, uint
 
 }  // namespace
 
+namespace pmk {
+bool fault_injected(const char *site) {
+  const char *v = std::getenv("PMK_INJECT_FAULT");
+  return v && std::strcmp(v, site) == 0;
+}
+}  // namespace pmk
+
 extern "C" {
 
-int pmk_ctx_create(int cuda_device, pmk_ctx **out) {
+int pmk_create(pmk_ctx **out, int cuda_device) {
   if (!out) return PMK_EINVAL;
   int count = 0;
   if (cudaGetDeviceCount(&count) != cudaSuccess) return PMK_ECUDA;
@@ -229,20 +260,20 @@ int pmk_ctx_create(int cuda_device, pmk_ctx **out) {
   }
   if (cudaMalloc(&ctx->d_status, sizeof(uint32_t)) != cudaSuccess ||
       cudaMemset(ctx->d_status, 0, sizeof(uint32_t)) != cudaSuccess) {
-    pmk_ctx_destroy(ctx);
+    pmk_destroy(ctx);
     return PMK_ENOMEM;
   }
   *out = ctx;
   return PMK_OK;
 }
 
-void pmk_ctx_destroy(pmk_ctx *ctx) {
+void pmk_destroy(pmk_ctx *ctx) {
   if (!ctx) return;
   DeviceGuard g(ctx->device);
+  drop(ctx->msg);
+  drop(ctx->a);
+  drop(ctx->b);
   cudaFree(ctx->d_status);
-  cudaFree(ctx->d_msg);
-  cudaFree(ctx->d_a);
-  cudaFree(ctx->d_b);
   delete ctx;
 }
 
@@ -526,10 +557,12 @@ int pmk_decrypt_blinded(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_cs
   if (!use_crt)
     return pmk::launch_modexp(pmk::ExpMode::kDecrypt, S, cfg_for(ctx, S, false), ks->d_keys, ks->K, d_m, d_m,
                               n_chunks, st);
-  rc = grow(reinterpret_cast<void **>(&ctx->d_b), &ctx->b_cap, n_chunks * S * 4);
-  if (rc == PMK_OK && cudaMemcpyAsync(ctx->d_b, d_m, n_chunks * S * 4, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+  rc = acquire(ctx->b, n_chunks * S * 4, st);
+  uint32_t *x = static_cast<uint32_t *>(ctx->b.ptr);
+  if (rc == PMK_OK && cudaMemcpyAsync(x, d_m, n_chunks * S * 4, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     rc = PMK_ECUDA;
-  if (rc == PMK_OK) rc = enqueue_crt(ctx, ks, pmk::ExpMode::kCrtHalf, ctx->d_b, d_m, n_chunks, st);
+  if (rc == PMK_OK) rc = enqueue_crt(ctx, ks, pmk::ExpMode::kCrtHalf, x, d_m, n_chunks, st);
+  release(ctx->b, st);
   return rc;
 }
 
@@ -548,8 +581,8 @@ int pmk_modexp_chunks_baseline(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_
   return rc;
 }
 
-int pmk_status(pmk_ctx *ctx, void *stream) {
-  pmk::TraceRange trace("pmk_status");
+int pmk_sync_status(pmk_ctx *ctx, void *stream) {
+  pmk::TraceRange trace("pmk_sync_status");
   if (!ctx) return PMK_EINVAL;
   DeviceGuard g(ctx->device);
   if (!g.ok()) return PMK_ECUDA;
@@ -572,16 +605,28 @@ int pmk_encrypt_message_host(pmk_ctx *ctx, const pmk_keyset *ks, const uint8_t *
   DeviceGuard g(ctx->device);
   if (!g.ok()) return PMK_ECUDA;
   const size_t words = n_chunks * (ks->nbits / 32);
-  int rc = grow(reinterpret_cast<void **>(&ctx->d_msg), &ctx->msg_cap, msg_len);
-  if (rc == PMK_OK) rc = grow(reinterpret_cast<void **>(&ctx->d_a), &ctx->a_cap, words * 4);
-  if (rc != PMK_OK) return rc;
   cudaStream_t st = as_stream(stream);
-  if (cudaMemcpyAsync(ctx->d_msg, h_msg, msg_len, cudaMemcpyHostToDevice, st) != cudaSuccess) return PMK_ECUDA;
-  rc = pmk::launch_split(ks->nbits, ctx->d_msg, msg_len, ctx->d_a, n_chunks, st);
-  if (rc == PMK_OK) rc = enqueue_encrypt(ctx, ks, ctx->d_a, ctx->d_a, n_chunks, st);
-  if (rc != PMK_OK) return rc;
-  if (cudaMemcpyAsync(h_cipher, ctx->d_a, words * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) return PMK_ECUDA;
-  return pmk_status(ctx, stream);
+  int rc = acquire(ctx->msg, msg_len, st);
+  if (rc == PMK_OK) rc = acquire(ctx->a, words * 4, st);
+  uint8_t *m = static_cast<uint8_t *>(ctx->msg.ptr);
+  uint32_t *c = static_cast<uint32_t *>(ctx->a.ptr);
+  bool queued = false;  // a copy from or to the caller's host memory is in flight
+  if (rc == PMK_OK) {
+    queued = true;
+    if (cudaMemcpyAsync(m, h_msg, msg_len, cudaMemcpyHostToDevice, st) != cudaSuccess) rc = PMK_ECUDA;
+  }
+  if (rc == PMK_OK && pmk::fault_injected("after_copy")) rc = PMK_ECUDA;
+  if (rc == PMK_OK) rc = pmk::launch_split(ks->nbits, m, msg_len, c, n_chunks, st);
+  if (rc == PMK_OK) rc = enqueue_encrypt(ctx, ks, c, c, n_chunks, st);
+  if (rc == PMK_OK && cudaMemcpyAsync(h_cipher, c, words * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    rc = PMK_ECUDA;
+  release(ctx->msg, st);
+  release(ctx->a, st);
+  if (rc != PMK_OK) {
+    if (queued) cudaStreamSynchronize(st);  // return with no copy of the caller's buffers in flight
+    return rc;
+  }
+  return pmk_sync_status(ctx, stream);
 }
 
 int pmk_decrypt_message_host(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *h_cipher, size_t n_chunks,
@@ -594,17 +639,29 @@ int pmk_decrypt_message_host(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t 
   DeviceGuard g(ctx->device);
   if (!g.ok()) return PMK_ECUDA;
   const size_t words = n_chunks * (ks->nbits / 32);
-  int rc = grow(reinterpret_cast<void **>(&ctx->d_msg), &ctx->msg_cap, msg_len);
-  if (rc == PMK_OK) rc = grow(reinterpret_cast<void **>(&ctx->d_a), &ctx->a_cap, words * 4);
-  if (rc == PMK_OK) rc = grow(reinterpret_cast<void **>(&ctx->d_b), &ctx->b_cap, words * 4);
-  if (rc != PMK_OK) return rc;
   cudaStream_t st = as_stream(stream);
-  if (cudaMemcpyAsync(ctx->d_a, h_cipher, words * 4, cudaMemcpyHostToDevice, st) != cudaSuccess) return PMK_ECUDA;
-  rc = enqueue_decrypt(ctx, ks, ctx->d_a, ctx->d_b, n_chunks, use_crt, st);
-  if (rc == PMK_OK) rc = pmk::launch_join(ks->nbits, ctx->d_b, n_chunks, ctx->d_msg, msg_len, st);
-  if (rc != PMK_OK) return rc;
-  if (cudaMemcpyAsync(h_msg, ctx->d_msg, msg_len, cudaMemcpyDeviceToHost, st) != cudaSuccess) return PMK_ECUDA;
-  return pmk_status(ctx, stream);
+  int rc = acquire(ctx->msg, msg_len, st);
+  if (rc == PMK_OK) rc = acquire(ctx->a, words * 4, st);
+  if (rc == PMK_OK) rc = acquire(ctx->b, words * 4, st);
+  uint8_t *m = static_cast<uint8_t *>(ctx->msg.ptr);
+  uint32_t *c = static_cast<uint32_t *>(ctx->a.ptr), *p = static_cast<uint32_t *>(ctx->b.ptr);
+  bool queued = false;  // a copy from or to the caller's host memory is in flight
+  if (rc == PMK_OK) {
+    queued = true;
+    if (cudaMemcpyAsync(c, h_cipher, words * 4, cudaMemcpyHostToDevice, st) != cudaSuccess) rc = PMK_ECUDA;
+  }
+  if (rc == PMK_OK && pmk::fault_injected("after_copy")) rc = PMK_ECUDA;
+  if (rc == PMK_OK) rc = enqueue_decrypt(ctx, ks, c, p, n_chunks, use_crt, st);
+  if (rc == PMK_OK) rc = pmk::launch_join(ks->nbits, p, n_chunks, m, msg_len, st);
+  if (rc == PMK_OK && cudaMemcpyAsync(h_msg, m, msg_len, cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = PMK_ECUDA;
+  release(ctx->msg, st);
+  release(ctx->a, st);
+  release(ctx->b, st);
+  if (rc != PMK_OK) {
+    if (queued) cudaStreamSynchronize(st);  // return with no copy of the caller's buffers in flight
+    return rc;
+  }
+  return pmk_sync_status(ctx, stream);
 }
 
 const char *pmk_strerror(int code) {

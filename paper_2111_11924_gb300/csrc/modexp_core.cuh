@@ -10,11 +10,15 @@
 // (< N).  Exponentiation is Algorithm 2's square-and-multiply generalised to a
 // left-to-right sliding window of odd powers (schedules built on the host).
 //
-// Cost model on this GPU (measured): a 32x32->64 multiply as one wide IMAD
-// issues at 32 lanes/clk/SM, whereas separate mad.lo + mad.hi cost 1/64 +
-// 1/32 clk; integer adds issue at 128 lanes/clk/SM on another pipe.  So each
-// row forms its L products with wide multiplies and folds them in with two
-// add-with-carry chains (low halves at word j, high halves at word j + 1).
+// Cost model on this GPU (measured with row-shaped loops, one multiplier per
+// row and the multiplicands in registers): mad.lo issues at up to 64
+// lanes/clk/SM but the high half of a 32x32 product at only about 22, and a
+// wide multiply (both halves, with or without a 64-bit addend) at 16-24
+// depending on the warps per SM.  The high half is therefore the cost of a
+// MAC whatever form it takes.  Integer adds issue on the ALU pipe, in
+// parallel.  So each row forms its L products with wide multiplies and folds
+// them in with two add-with-carry chains (low halves at word j, high halves
+// at word j + 1).
 // Lane-to-lane carries are deferred: a lane keeps a small pending word above
 // its L limbs, which the per-row shift moves into its own top limb; after the
 // last row a ballot carry-lookahead resolves them in O(1) warp operations.

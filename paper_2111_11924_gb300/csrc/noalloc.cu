@@ -11,10 +11,15 @@
 // counterpart of this call; it is an interface convenience.
 //
 // The array is a file-scope __device__ variable: every GPU that loads this
-// library reserves kNoAllocBytes of device memory for it until the process
-// exits.  Host code cannot use the array's name as a device address (in host
-// code it denotes a host-side stand-in), so the device address is obtained
-// with cudaGetSymbolAddress once per device and cached.
+// file's module holds kNoAllocBytes of device memory for it until the
+// process exits.  This file has no kernels, so under CUDA's lazy module
+// loading the module (and the array) is loaded by the first call's set-up,
+// cudaGetSymbolAddress, which can then fail with PMK_ECUDA if the device's
+// memory is already taken: a call with n_chunks = msg_len = 0 performs that
+// set-up alone, early in a process.  Host code cannot use the array's name
+// as a device address (in host code it denotes a host-side stand-in), so the
+// device address is obtained with cudaGetSymbolAddress once per device and
+// cached.
 #include <mutex>
 
 #include "pmk_internal.h"
@@ -56,10 +61,12 @@ extern "C" int pmk_decrypt_message_host_noalloc(const pmk_keyset *ks, const uint
   pmk::TraceRange trace("pmk_decrypt_message_host_noalloc");
   using namespace pmk;
   if (!ks) return PMK_EINVAL;
-  if (n_chunks != pmk_num_chunks(msg_len, ks->nbits)) return PMK_EINVAL;
-  if (n_chunks == 0) return PMK_OK;
-  if (!h_cipher || !h_msg) return PMK_EINVAL;
+  if (n_chunks != pmk_num_chunks(msg_len, ks->nbits) || n_chunks >= kMaxChunks) return PMK_EINVAL;
+  if (n_chunks != 0 && (!h_cipher || !h_msg)) return PMK_EINVAL;
+  // Sizes are compared with the capacity one at a time before they are
+  // added, so no sum can wrap around.
   const size_t words = n_chunks * (ks->nbits / 32);
+  if (words > kNoAllocBytes / 4 || msg_len > kNoAllocBytes) return PMK_ETOOLARGE;
   const size_t chunk_bytes = round256(words * 4);
   const size_t need = kStatusBytes + 2 * chunk_bytes + round256(msg_len);
   if (need > kNoAllocBytes) return PMK_ETOOLARGE;
@@ -68,19 +75,25 @@ extern "C" int pmk_decrypt_message_host_noalloc(const pmk_keyset *ks, const uint
   if (cudaGetDevice(&prev) != cudaSuccess) return PMK_ECUDA;
   if (prev != ks->device && cudaSetDevice(ks->device) != cudaSuccess) return PMK_ECUDA;
   int rc = PMK_OK;
+  bool queued = false;  // a copy from or to the caller's host memory is in flight
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   do {
     unsigned char *base = nullptr;
     rc = scratch_base(ks->device, &base);
-    if (rc != PMK_OK) break;
+    if (rc != PMK_OK || n_chunks == 0) break;  // an empty call only performs the set-up
     uint32_t *d_status = reinterpret_cast<uint32_t *>(base);
     uint32_t *d_cipher = reinterpret_cast<uint32_t *>(base + kStatusBytes);
     uint32_t *d_plain = reinterpret_cast<uint32_t *>(base + kStatusBytes + chunk_bytes);
     uint8_t *d_msg = base + kStatusBytes + 2 * chunk_bytes;
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const uint32_t S = ks->nbits / 32, B = ks->nprimes, H = S / B;
     // The array keeps the previous call's contents: the status word must start at zero.
+    queued = true;
     if (cudaMemsetAsync(d_status, 0, sizeof(uint32_t), st) != cudaSuccess ||
         cudaMemcpyAsync(d_cipher, h_cipher, words * 4, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      rc = PMK_ECUDA;
+      break;
+    }
+    if (fault_injected("after_copy")) {
       rc = PMK_ECUDA;
       break;
     }
@@ -102,8 +115,10 @@ extern "C" int pmk_decrypt_message_host_noalloc(const pmk_keyset *ks, const uint
       rc = PMK_ECUDA;
       break;
     }
+    queued = false;  // the stream was synchronised above
     if (status & kStatusRange) rc = PMK_ERANGE;
   } while (false);
+  if (queued && rc != PMK_OK) cudaStreamSynchronize(st);  // return with no copy of the caller's buffers in flight
   if (prev != ks->device) cudaSetDevice(prev);
   return rc;
 }

@@ -28,6 +28,17 @@ class TraceRange {
 // Error bits written by kernels into the context's device status word.
 enum : uint32_t { kStatusRange = 1u, kStatusNotInvertible = 2u };
 
+// Most chunks per call: keeps byte counts and grid sizes far from overflow
+// (2^32 chunks of 2048 bits are 1 TiB, beyond any device's memory).
+constexpr size_t kMaxChunks = (size_t)1 << 32;
+
+// Host-side fault injection for tests: true when the environment variable
+// PMK_INJECT_FAULT names `site`.  The *_host calls consult it right after
+// they queue the copy of the caller's input ("after_copy") and then fail as a
+// failed launch would, so a test can check that an error path leaves no
+// copy of a caller's buffer in flight.  Nothing on the GPU faults.
+bool fault_injected(const char *site);
+
 // Exponent schedule for left-to-right sliding-window exponentiation.
 // steps[0] = index of the first odd power (a load, no squaring);
 // steps[i>0] = (nsq << 8) | idx : nsq squarings, then a multiply by the odd
@@ -193,14 +204,24 @@ struct pmk_keyset {
   pmk::KeyDev *d_keys = nullptr;           // K device key views into d_blob
 };
 
+namespace pmk {
+// A grow-only device buffer owned by a context, allocated and freed in
+// stream order (cudaMallocAsync / cudaFreeAsync).  `last_use` is recorded
+// on the stream of the last call that used it; the next call waits on it on
+// its own stream before reusing, growing or freeing the buffer, so staging
+// never overlaps work still in flight on another stream.
+struct Staging {
+  void *ptr = nullptr;
+  size_t cap = 0;
+  cudaEvent_t last_use = nullptr;
+};
+}  // namespace pmk
+
 // Context: one device, its status word, staging and kernel geometry choices.
 struct pmk_ctx {
   int device = 0;
   uint32_t *d_status = nullptr;            // device-side error bits (pmk::kStatusRange)
-  uint8_t *d_msg = nullptr;                // staging of the *_host calls (grow-only)
-  size_t msg_cap = 0;
-  uint32_t *d_a = nullptr, *d_b = nullptr;
-  size_t a_cap = 0, b_cap = 0;             // in words
+  pmk::Staging msg, a, b;                  // staging of the *_host calls and the blinded CRT path
   std::map<uint32_t, pmk::KernelConfig> cfg;  // (limbs << 1 | crt) -> kernel geometry override
   std::map<uint32_t, int> table;              // (limbs << 1 | crt) -> odd-power table size override
 };

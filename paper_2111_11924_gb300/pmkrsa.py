@@ -46,8 +46,8 @@ def load_library() -> ctypes.CDLL:
     P32 = ctypes.POINTER(ctypes.c_uint32)
     vp, u32, u64, sz, i = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_size_t, ctypes.c_int
     sig = {
-        "pmk_ctx_create": (i, [i, ctypes.POINTER(vp)]),
-        "pmk_ctx_destroy": (None, [vp]),
+        "pmk_create": (i, [ctypes.POINTER(vp), i]),
+        "pmk_destroy": (None, [vp]),
         "pmk_keygen": (i, [vp, u32, u32, u64, u64, ctypes.POINTER(vp)]),
         "pmk_keygen_host": (i, [u32, u32, u64, u64, P32, P32, P32, P32, P32, P32, P32]),
         "pmk_keyset_from_primes": (i, [vp, u32, u32, u64, P32, P32, ctypes.POINTER(vp)]),
@@ -77,7 +77,7 @@ def load_library() -> ctypes.CDLL:
         "pmk_batch_launch": (i, [vp, vp]),
         "pmk_batch_info": (i, [vp, ctypes.POINTER(sz), ctypes.POINTER(i)]),
         "pmk_batch_destroy": (None, [vp]),
-        "pmk_status": (i, [vp, vp]),
+        "pmk_sync_status": (i, [vp, vp]),
         "pmk_strerror": (ctypes.c_char_p, [i]),
         "pmk_measure_int_peak": (i, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(i)]),
@@ -156,6 +156,34 @@ def _torch():
     return torch
 
 
+def host_limb_buffer(t, nbits: int, what: str = "h_cipher"):
+    """Check a host limb buffer for the *_host calls: a contiguous CPU int32
+    (or uint32) tensor of shape (n_chunks, nbits/32).  Returns the chunk
+    count; raises ValueError otherwise, before the library would read past it."""
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or t.device.type != "cpu":
+        raise ValueError(f"{what} must be a CPU tensor")
+    if t.dtype not in (torch.int32, getattr(torch, "uint32", torch.int32)) or not t.is_contiguous():
+        raise ValueError(f"{what} must be a contiguous int32 tensor")
+    if t.dim() != 2 or t.shape[1] != nbits // 32:
+        raise ValueError(f"{what} must have shape (n_chunks, {nbits // 32}) for {nbits}-bit keys")
+    return int(t.shape[0])
+
+
+def host_message_buffer(t, n_chunks: int, nbits: int, what: str = "h_msg"):
+    """Check a host message buffer: a contiguous CPU uint8 tensor whose length
+    gives exactly n_chunks chunks at this width.  Returns its length."""
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or t.device.type != "cpu":
+        raise ValueError(f"{what} must be a CPU tensor")
+    if t.dtype != torch.uint8 or not t.is_contiguous():
+        raise ValueError(f"{what} must be a contiguous uint8 tensor")
+    P = nbits // 8 - 1
+    if (t.numel() + P - 1) // P != n_chunks:
+        raise ValueError(f"{what} of {t.numel()} bytes does not split into {n_chunks} chunks of {P} bytes")
+    return int(t.numel())
+
+
 class KeySet:
     """K key pairs resident on the context's device (pmk_keyset)."""
 
@@ -212,7 +240,7 @@ class Context:
         self.device = int(device)
         torch.cuda.init()
         h = ctypes.c_void_p()
-        _check(load_library().pmk_ctx_create(self.device, ctypes.byref(h)), "pmk_ctx_create")
+        _check(load_library().pmk_create(ctypes.byref(h), self.device), "pmk_create")
         self._h = h
 
     # ------------------------------------------------------------ plumbing
@@ -224,7 +252,7 @@ class Context:
 
     def close(self) -> None:
         if getattr(self, "_h", None):
-            load_library().pmk_ctx_destroy(self._h)
+            load_library().pmk_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -348,15 +376,17 @@ class Context:
 
     def encrypt_message_host(self, ks: KeySet, h_msg, h_cipher, stream=None) -> None:
         """Host buffers (torch CPU tensors, ideally pinned): uint8 message -> int32 limb buffer."""
-        n = h_cipher.shape[0]
+        n = host_limb_buffer(h_cipher, ks.nbits)
+        L = host_message_buffer(h_msg, n, ks.nbits)
         _check(load_library().pmk_encrypt_message_host(self.handle, ks.handle, ctypes.c_void_p(h_msg.data_ptr()),
-                                                       h_msg.numel(), ctypes.c_void_p(h_cipher.data_ptr()), n,
+                                                       L, ctypes.c_void_p(h_cipher.data_ptr()), n,
                                                        self.stream_handle(stream)), "pmk_encrypt_message_host")
 
     def decrypt_message_host(self, ks: KeySet, h_cipher, h_msg, use_crt: bool = False, stream=None) -> None:
-        n = h_cipher.shape[0]
+        n = host_limb_buffer(h_cipher, ks.nbits)
+        L = host_message_buffer(h_msg, n, ks.nbits)
         _check(load_library().pmk_decrypt_message_host(self.handle, ks.handle, ctypes.c_void_p(h_cipher.data_ptr()), n,
-                                                       ctypes.c_void_p(h_msg.data_ptr()), h_msg.numel(), int(use_crt),
+                                                       ctypes.c_void_p(h_msg.data_ptr()), L, int(use_crt),
                                                        self.stream_handle(stream)), "pmk_decrypt_message_host")
 
     def batch(self, jobs) -> "Batch":
@@ -373,7 +403,7 @@ class Context:
 
     def status(self, stream=None) -> int:
         """Synchronise and return (and clear) the device-side error code."""
-        return int(load_library().pmk_status(self.handle, self.stream_handle(stream)))
+        return int(load_library().pmk_sync_status(self.handle, self.stream_handle(stream)))
 
     def check(self, stream=None) -> None:
         _check(self.status(stream), "device status")
@@ -493,10 +523,12 @@ def decrypt_message_host_noalloc(ks: KeySet, h_cipher, h_msg, use_crt: bool = Fa
     """pmk_decrypt_message_host_noalloc: decrypt without any device allocation
     (device staging in the library's fixed array).  Returns the PMK_* code."""
     torch = _torch()
+    n = host_limb_buffer(h_cipher, ks.nbits)
+    L = host_message_buffer(h_msg, n, ks.nbits)
     s = stream if stream is not None else torch.cuda.current_stream(ks._ctx.device)
     return int(load_library().pmk_decrypt_message_host_noalloc(
-        ks.handle, ctypes.c_void_p(h_cipher.data_ptr()), h_cipher.shape[0], ctypes.c_void_p(h_msg.data_ptr()),
-        h_msg.numel(), int(use_crt), ctypes.c_void_p(int(s.cuda_stream))))
+        ks.handle, ctypes.c_void_p(h_cipher.data_ptr()), n, ctypes.c_void_p(h_msg.data_ptr()),
+        L, int(use_crt), ctypes.c_void_p(int(s.cuda_stream))))
 
 
 class Batch:

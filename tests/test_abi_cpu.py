@@ -250,3 +250,28 @@ def test_batch_planner_covers_every_chunk_once(tmp_path):
     res = subprocess.run([exe], capture_output=True, text=True)
     assert res.returncode == 0, res.stdout
     assert res.stdout.strip().endswith("0 failures") and int(res.stdout.split()[0]) >= 1_000_000
+
+
+def test_host_buffer_checks_reject_mismatched_buffers():
+    """The binding checks host buffers before a *_host call would read past
+    them: shape and dtype of the limb buffer, dtype and chunk count of the
+    message, contiguity and device."""
+    import torch
+
+    from paper_2111_11924_gb300 import pmkrsa
+
+    good = torch.zeros((5, 32), dtype=torch.int32)
+    assert pmkrsa.host_limb_buffer(good, 1024) == 5
+    for bad in (torch.zeros((5, 64), dtype=torch.int32),      # another key width
+                torch.zeros((5, 32), dtype=torch.int64),      # wrong dtype
+                torch.zeros((32, 5), dtype=torch.int32).t(),  # not contiguous
+                torch.zeros(160, dtype=torch.int32)):         # not 2-D
+        with pytest.raises(ValueError):
+            pmkrsa.host_limb_buffer(bad, 1024)
+    msg = torch.zeros(5 * 127 - 3, dtype=torch.uint8)
+    assert pmkrsa.host_message_buffer(msg, 5, 1024) == 5 * 127 - 3
+    for bad, n in ((torch.zeros(5 * 127 + 1, dtype=torch.uint8), 5),  # one chunk too many
+                   (torch.zeros(600, dtype=torch.int8), 5),           # wrong dtype
+                   (torch.zeros((2, 300), dtype=torch.uint8)[:, :200], 4)):  # not contiguous
+        with pytest.raises(ValueError):
+            pmkrsa.host_message_buffer(bad, n, 1024)

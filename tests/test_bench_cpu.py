@@ -30,3 +30,15 @@ def test_crt_count_and_prime_scaling():
     for n, b in ((2048, 4), (3072, 3), (4096, 4), (8192, 4)):
         ratio = bench.algorithmic_crt_macs(n, 2) / bench.algorithmic_crt_macs(n, b)
         assert 0.8 * b * b / 4 < ratio < 1.05 * b * b / 4, (n, b, ratio)
+
+
+def test_int32_roofline_recomputes_from_its_inputs():
+    # The headline fraction: 2 INT32 multiply-add halves per MAC over the measured mad.lo rate.  With the
+    # 1 MiB / K = 8 / 2048-bit workload (4,113 chunks), a 17.63 ms decryption and 63.99 mad.lo per clock per
+    # SM on 152 SMs at 2070 MHz, the figure is 9.27 of 20.13 TOP/s.
+    macs = bench.algorithmic_montmuls(2048) * bench.macs_per_montmul(2048) * 4113
+    achieved = bench.int32_ops_per_s(macs, 17.63) / 1e12
+    peak = bench.int32_peak_tops(63.99, 152, 2070.0)
+    assert achieved == pytest.approx(9.27, abs=0.01)
+    assert peak == pytest.approx(20.13, abs=0.01)
+    assert achieved / peak == pytest.approx(0.46, abs=0.005)

@@ -102,3 +102,43 @@ def test_noalloc_multiprime_key_set(setup):
         assert P.pmkrsa.decrypt_message_host_noalloc(ks, cipher, out, use_crt=use_crt) == P.pmkrsa.PMK_OK
         assert torch.equal(out, ref) and torch.equal(out, msg), use_crt
     ks.free()
+
+
+def test_noalloc_empty_call_only_sets_up(setup):
+    """A call with no chunks performs only the one-time set-up (the array's
+    device address), so a caller can commit the array early in a process."""
+    P, ctx, ks, w = setup
+    lib = P.load_library()
+    assert lib.pmk_decrypt_message_host_noalloc(ks.handle, None, 0, None, 0, 0, None) == P.pmkrsa.PMK_OK
+
+
+def test_noalloc_rejects_chunk_counts_beyond_the_bound(setup):
+    """2^32 chunks or more are refused before any size arithmetic, even when
+    (msg_len, n_chunks) agree with each other."""
+    P, ctx, ks, w = setup
+    lib = P.load_library()
+    payload = P.payload_bytes(ks.nbits)
+    length = (1 << 32) * payload  # exactly 2^32 chunks
+    n = P.num_chunks(length, ks.nbits)
+    assert n == 1 << 32
+    dummy = np.zeros(16, np.uint32)
+    rc = lib.pmk_decrypt_message_host_noalloc(ks.handle, ctypes.c_void_p(dummy.ctypes.data), n,
+                                              ctypes.c_void_p(dummy.ctypes.data), length, 0, None)
+    assert rc == P.pmkrsa.PMK_EINVAL
+
+
+def test_noalloc_error_after_copy_leaves_stream_idle(setup, monkeypatch):
+    """A failure injected on the host right after the ciphertext copy is
+    queued: the call reports it and returns with its stream idle; the next
+    call is unaffected."""
+    P, ctx, ks, w = setup
+    msg = torch.from_numpy(np.random.default_rng(9).integers(0, 256, 3 << 20, dtype=np.uint8)).pin_memory()
+    cipher = _cipher_of(ctx, ks, msg)
+    out = torch.zeros_like(msg).pin_memory()
+    stream = torch.cuda.Stream()
+    monkeypatch.setenv("PMK_INJECT_FAULT", "after_copy")
+    assert P.pmkrsa.decrypt_message_host_noalloc(ks, cipher, out, stream=stream) == P.pmkrsa.PMK_ECUDA
+    assert stream.query(), "work left in flight on the caller's stream"
+    monkeypatch.delenv("PMK_INJECT_FAULT")
+    assert P.pmkrsa.decrypt_message_host_noalloc(ks, cipher, out, stream=stream) == P.pmkrsa.PMK_OK
+    assert torch.equal(out, msg)
