@@ -20,8 +20,9 @@
  *   - Chunk buffers hold n_chunks x nbits/32 little-endian uint32 limbs,
  *     chunk-major ("limb buffer"), and must be 16-byte aligned (EINVAL).
  *     Chunk t is bound to key t mod K, the row-per-key reshape of the i x j
- *     plaintext matrix (Section 3.1).  A call takes fewer than 2^32 chunks
- *     (EINVAL otherwise).
+ *     plaintext matrix (Section 3.1), unless the call takes explicit key
+ *     indices (pmk_encrypt_chunks, pmk_decrypt_chunks).  A call takes fewer
+ *     than 2^32 chunks (EINVAL otherwise).
  *   - Calls on one context are not thread-safe; use one context per thread.
  */
 #ifndef PMKRSA_H
@@ -42,6 +43,7 @@ extern "C" {
 #define PMK_EUNSUPPORTED (-5) /* key width not compiled into this build */
 #define PMK_ETOOLARGE (-6)    /* request exceeds the fixed capacity of the allocation-free call */
 #define PMK_ENOINV (-7)       /* a blinding value shares a factor with its modulus (device-detected) */
+#define PMK_EKEYINDEX (-8)    /* an explicit key index was >= K (device-detected) */
 
 typedef struct pmk_ctx pmk_ctx;         /* one GPU: device status word, staging buffers */
 typedef struct pmk_keyset pmk_keyset;   /* K key pairs: host copy + device-resident tables */
@@ -132,6 +134,39 @@ int pmk_keyset_export(const pmk_keyset *ks, uint32_t *N, uint32_t *d, uint32_t *
  * coef_0 = r_1^-1 mod r_0, coef_1 = 0, coef_i = (r_0 ... r_{i-1})^-1 mod r_i.
  * Any pointer may be NULL. */
 int pmk_keyset_export_primes(const pmk_keyset *ks, uint32_t *primes, uint32_t *dexp, uint32_t *coef);
+/*
+ * Versioned key-set serialisation: the Initialization output of Algorithm 1
+ * (public [E, N] and private [D, N] of every key, Section 3.1) with the
+ * primes and CRT values of Section 2.1, for checkpointing a key set and
+ * restoring it in another process.  Layout (every integer little-endian,
+ * whatever the host's byte order):
+ *   bytes 0-3    "PMKK"
+ *   bytes 4-7    version (1)
+ *   bytes 8-11   K
+ *   bytes 12-15  nbits
+ *   bytes 16-19  b, primes per modulus (2 for an ordinary key)
+ *   bytes 20-23  0 (reserved)
+ *   bytes 24-31  e
+ *   then for each key, five rows of s = nbits/32 uint32 limbs: N, d,
+ *   primes, dexp, coef (the last three as pmk_keyset_export_primes writes
+ *   them: b values of s/b limbs each)
+ *   last 8 bytes  FNV-1a 64-bit hash of every byte before it.
+ * Size: 32 + 20 K s + 8 bytes.
+ * pmk_keyset_export_blob: with buf NULL, *len receives the size; otherwise
+ * *len is the buffer's size in bytes (EINVAL, with *len set to the size
+ * needed, if smaller) and receives the bytes written.  EINVAL for a NULL
+ * key set or len.
+ * pmk_keyset_import: checks the magic, version, sizes, hash and ranges,
+ * derives every key again from its primes exactly as
+ * pmk_keyset_from_primes_multi does, and refuses the blob (EINVAL) unless
+ * the stored N, d, dexp and coef equal the derived ones.  With a context the
+ * key tables are uploaded to its device (EUNSUPPORTED if the width is not
+ * built, ENOMEM or ECUDA if the upload fails); with ctx NULL the key set is
+ * host-only: it can be exported and queried, and device calls refuse it
+ * (EINVAL).  *out is set only on success.
+ */
+int pmk_keyset_export_blob(const pmk_keyset *ks, void *buf, size_t *len);
+int pmk_keyset_import(pmk_ctx *ctx, const void *buf, size_t len, pmk_keyset **out);
 /* Key-set properties: primes per modulus (b), key count K, width nbits and
  * public exponent e.  Each returns 0 for NULL. */
 uint32_t pmk_keyset_num_primes(const pmk_keyset *ks);
@@ -169,16 +204,27 @@ int pmk_join(pmk_ctx *ctx, uint32_t nbits, const uint32_t *d_chunks, size_t n_ch
 
 /*
  * Encryption (Algorithm 1 "Encryption", c = m^e mod N; Algorithm 2 over
- * Algorithm 3 Montgomery products): d_out[t] = d_in[t]^e mod N_{t mod K}.
+ * Algorithm 3 Montgomery products): d_out[t] = d_in[t]^e mod N_k.
  * d_in, d_out: n_chunks limb buffers (device); they may be the same buffer.
+ * d_key_idx: NULL binds chunk t to key k = t mod K (the column-by-column
+ *   fill of the i x j matrix with one row per key, Section 3.1); otherwise
+ *   a device array of n_chunks uint32 (4-byte aligned, fewer than 2^31
+ *   chunks), chunk t bound to key d_key_idx[t], any reshape the caller
+ *   chose.  The library groups the chunks by key on the device (a count,
+ *   an offset scan and a scatter into a key-group table in the context's
+ *   stream-ordered staging) so that every block of the exponentiation
+ *   kernel serves one key; results go to each chunk's own position.  An
+ *   index >= K is reported as PMK_EKEYINDEX by pmk_sync_status() and that
+ *   chunk's output is left unwritten.
  * A chunk >= N is reported as PMK_ERANGE by pmk_sync_status().
  */
 int pmk_encrypt_chunks(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_in, uint32_t *d_out,
-                       size_t n_chunks, void *stream);
+                       size_t n_chunks, const uint32_t *d_key_idx, void *stream);
 
 /*
  * Decryption (Algorithm 1 "Decryption", m = c^d mod N):
- * d_out[t] = d_in[t]^{d_k} mod N_k, k = t mod K.  use_crt = 0: one
+ * d_out[t] = d_in[t]^{d_k} mod N_k, with k = t mod K (d_key_idx NULL) or
+ * k = d_key_idx[t], exactly as for pmk_encrypt_chunks.  use_crt = 0: one
  * full-width exponentiation; use_crt = 1: the CRT form of Section 2.1
  * (one exponentiation per prime over nbits/b bits -- two halves for an
  * ordinary key, b for a multi-prime key -- then the CRT recombination
@@ -189,7 +235,7 @@ int pmk_encrypt_chunks(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_in,
  * PMK_ERANGE by pmk_sync_status().
  */
 int pmk_decrypt_chunks(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_in, uint32_t *d_out,
-                       size_t n_chunks, int use_crt, void *stream);
+                       size_t n_chunks, const uint32_t *d_key_idx, int use_crt, void *stream);
 
 /*
  * The plain GPU formulation, kept as a measured baseline for the kernels
@@ -318,10 +364,18 @@ int pmk_batch_launch(pmk_batch *batch, void *stream);
 int pmk_batch_info(const pmk_batch *batch, size_t *n_tasks, int *n_kernels);
 void pmk_batch_destroy(pmk_batch *batch);
 
-/* Synchronise `stream`, then return (and clear) the first device-side error
- * recorded since the last call: PMK_OK, PMK_ERANGE or PMK_ENOINV; PMK_ECUDA
- * if a CUDA call fails. */
+/* Synchronise `stream`, then return (and clear) the device-side errors
+ * recorded since the last call, the most specific one: PMK_EKEYINDEX before
+ * PMK_ERANGE before PMK_ENOINV; PMK_OK if none; PMK_ECUDA if a CUDA call
+ * fails. */
 int pmk_sync_status(pmk_ctx *ctx, void *stream);
+/* pmk_sync_status, and where: *first_chunk (may be NULL) receives the
+ * smallest chunk index that raised a device-side error since the last
+ * status call -- the index within its call (within its job for a batch);
+ * with several calls between status reads, the smallest over them -- or
+ * UINT64_MAX when none did.  Same return values and clearing as
+ * pmk_sync_status. */
+int pmk_sync_status_detail(pmk_ctx *ctx, void *stream, uint64_t *first_chunk);
 
 /* Static description of an error code. */
 const char *pmk_strerror(int code);

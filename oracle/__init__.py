@@ -281,12 +281,31 @@ def modexp_chunks(chunks: np.ndarray, exps: np.ndarray, mods: np.ndarray, thread
     return out
 
 
-def encrypt_chunks(chunks: np.ndarray, keys: OracleKeys, threads: int = 1) -> np.ndarray:
+def keyed(keys: OracleKeys, key_idx) -> OracleKeys:
+    """The key set seen through an explicit chunk-to-key map: row t of every
+    key array is key key_idx[t]'s, so the round-robin loops (chunk t -> row
+    t mod K, here K = len(key_idx)) bind chunk t to key key_idx[t].  This is
+    Algorithm 1 with the i x j reshape of Section 3.1 filled in the caller's
+    order instead of column by column."""
+    idx = np.asarray(key_idx, dtype=np.int64)
+    assert idx.ndim == 1 and (idx >= 0).all() and (idx < keys.K).all()
+    return OracleKeys(len(idx), keys.nbits, keys.e, {f: np.ascontiguousarray(v[idx]) for f, v in keys.a.items()},
+                      keys.b)
+
+
+def encrypt_chunks(chunks: np.ndarray, keys: OracleKeys, threads: int = 1, key_idx=None) -> np.ndarray:
+    """c_t = m_t^e mod N_k, k = t mod K or key_idx[t]."""
+    if key_idx is not None:
+        keys = keyed(keys, key_idx)
     e = np.tile(to_limbs(keys.e, 2), (keys.K, 1))
     return modexp_chunks(chunks, e, keys.a["N"], threads)
 
 
-def decrypt_chunks(chunks: np.ndarray, keys: OracleKeys, use_crt: bool = False, threads: int = 1) -> np.ndarray:
+def decrypt_chunks(chunks: np.ndarray, keys: OracleKeys, use_crt: bool = False, threads: int = 1,
+                   key_idx=None) -> np.ndarray:
+    """m_t = c_t^d mod N_k (full d, or the Section 2.1 CRT form), k = t mod K or key_idx[t]."""
+    if key_idx is not None:
+        keys = keyed(keys, key_idx)
     if not use_crt:
         return modexp_chunks(chunks, keys.a["d"], keys.a["N"], threads)
     if "primes" in keys.a:

@@ -16,6 +16,7 @@ from .pmkrsa import (  # noqa: F401
     KeySet,
     keygen_host,
     keygen_host_multiprime,
+    import_keyset_host,
     TuneCache,
     kernel_configs,
     load_library,
@@ -25,4 +26,4 @@ from .pmkrsa import (  # noqa: F401
 )
 from . import sharding  # noqa: F401
 
-__all__ = ["PMKError", "Context", "KeySet", "keygen_host", "keygen_host_multiprime", "TuneCache", "kernel_configs", "load_library", "num_chunks", "payload_bytes", "strerror", "sharding"]
+__all__ = ["PMKError", "Context", "KeySet", "keygen_host", "keygen_host_multiprime", "import_keyset_host", "TuneCache", "kernel_configs", "load_library", "num_chunks", "payload_bytes", "strerror", "sharding"]

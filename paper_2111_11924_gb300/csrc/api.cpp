@@ -208,30 +208,54 @@ int check_chunk_call(const pmk_ctx *ctx, const pmk_keyset *ks, const void *in, c
   return PMK_OK;
 }
 
-int enqueue_encrypt(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *in, uint32_t *out, size_t n, cudaStream_t st) {
+// key_idx / groups: explicit key indices and their key-group table
+// (launch_key_groups), or both NULL for round robin (chunk t -> key t mod K).
+int enqueue_encrypt(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *in, uint32_t *out, size_t n, cudaStream_t st,
+                    const uint32_t *key_idx = nullptr, const uint32_t *groups = nullptr) {
   const uint32_t S = ks->nbits / 32;
-  int rc = pmk::launch_range_check(ks->d_keys, ks->K, S, in, n, ctx->d_status, st);
-  if (rc == PMK_OK) rc = pmk::launch_modexp(pmk::ExpMode::kEncrypt, S, cfg_for(ctx, S, false), ks->d_keys, ks->K, in, out, n, st);
+  int rc = pmk::launch_range_check(ks->d_keys, ks->K, S, in, n, ctx->d_status, st, key_idx);
+  if (rc == PMK_OK)
+    rc = pmk::launch_modexp(pmk::ExpMode::kEncrypt, S, cfg_for(ctx, S, false), ks->d_keys, ks->K, in, out, n, st,
+                            ks->nprimes, groups);
   return rc;
 }
 
 // One residue per prime of each chunk (exponent d mod (r_i - 1), or r_i - 2
 // for kCrtInverse) into out, then their recombination in place.
 int enqueue_crt(pmk_ctx *ctx, const pmk_keyset *ks, pmk::ExpMode mode, const uint32_t *in, uint32_t *out, size_t n,
-                cudaStream_t st, uint32_t *status_if_zero = nullptr) {
+                cudaStream_t st, uint32_t *status_if_zero = nullptr, const uint32_t *groups = nullptr) {
   const uint32_t b = ks->nprimes, H = ks->nbits / 32 / b;
-  int rc = pmk::launch_modexp(mode, H, cfg_for(ctx, H, true), ks->d_keys, ks->K, in, out, n, st, b);
+  int rc = pmk::launch_modexp(mode, H, cfg_for(ctx, H, true), ks->d_keys, ks->K, in, out, n, st, b, groups);
   if (rc != PMK_OK) return rc;
-  return pmk::launch_crt_sum(ks->nbits / 32, b, ks->d_keys, ks->K, out, n, st, status_if_zero);
+  return pmk::launch_crt_sum(ks->nbits / 32, b, ks->d_keys, ks->K, out, n, st, status_if_zero, groups);
 }
 
 int enqueue_decrypt(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *in, uint32_t *out, size_t n, int use_crt,
-                    cudaStream_t st) {
+                    cudaStream_t st, const uint32_t *key_idx = nullptr, const uint32_t *groups = nullptr) {
   const uint32_t S = ks->nbits / 32;
-  int rc = pmk::launch_range_check(ks->d_keys, ks->K, S, in, n, ctx->d_status, st);
+  int rc = pmk::launch_range_check(ks->d_keys, ks->K, S, in, n, ctx->d_status, st, key_idx);
   if (rc != PMK_OK) return rc;
-  if (!use_crt) return pmk::launch_modexp(pmk::ExpMode::kDecrypt, S, cfg_for(ctx, S, false), ks->d_keys, ks->K, in, out, n, st);
-  return enqueue_crt(ctx, ks, pmk::ExpMode::kCrtHalf, in, out, n, st);
+  if (!use_crt)
+    return pmk::launch_modexp(pmk::ExpMode::kDecrypt, S, cfg_for(ctx, S, false), ks->d_keys, ks->K, in, out, n, st,
+                              ks->nprimes, groups);
+  return enqueue_crt(ctx, ks, pmk::ExpMode::kCrtHalf, in, out, n, st, nullptr, groups);
+}
+
+// Explicit key indices: check them on the host side of the call, then build
+// the key-group table in the context's staging on `st`.  *groups stays NULL
+// for round robin.  Pair with release(ctx->grp, st) once the kernels reading
+// the table are enqueued.
+int key_groups_for(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *key_idx, size_t n, cudaStream_t st,
+                   const uint32_t **groups) {
+  *groups = nullptr;
+  if (!key_idx) return PMK_OK;
+  if (n >= pmk::kMaxGroupedChunks || (reinterpret_cast<uintptr_t>(key_idx) & 3u)) return PMK_EINVAL;
+  int rc = acquire(ctx->grp, pmk::key_groups_words(n, ks->K) * 4, st);
+  if (rc != PMK_OK) return rc;
+  uint32_t *table = static_cast<uint32_t *>(ctx->grp.ptr);
+  rc = pmk::launch_key_groups(key_idx, n, ks->K, table, ctx->d_status, st);
+  if (rc == PMK_OK) *groups = table;
+  return rc;
 }
 
 }  // namespace
@@ -258,8 +282,8 @@ int pmk_create(pmk_ctx **out, int cuda_device) {
     delete ctx;
     return PMK_ECUDA;
   }
-  if (cudaMalloc(&ctx->d_status, sizeof(uint32_t)) != cudaSuccess ||
-      cudaMemset(ctx->d_status, 0, sizeof(uint32_t)) != cudaSuccess) {
+  if (cudaMalloc(&ctx->d_status, pmk::kStatusRecordBytes) != cudaSuccess ||
+      pmk::clear_status(ctx->d_status, nullptr) != PMK_OK || cudaStreamSynchronize(nullptr) != cudaSuccess) {
     pmk_destroy(ctx);
     return PMK_ENOMEM;
   }
@@ -273,6 +297,7 @@ void pmk_destroy(pmk_ctx *ctx) {
   drop(ctx->msg);
   drop(ctx->a);
   drop(ctx->b);
+  drop(ctx->grp);
   cudaFree(ctx->d_status);
   delete ctx;
 }
@@ -432,6 +457,143 @@ int pmk_keyset_export_primes(const pmk_keyset *ks, uint32_t *primes, uint32_t *d
   return PMK_OK;
 }
 
+// ---- key-set blob: a versioned, little-endian serialisation (pmkrsa.h).
+}  // extern "C"
+
+namespace {
+
+constexpr uint32_t kBlobVersion = 1;
+constexpr size_t kBlobHeader = 32, kBlobTrailer = 8;
+constexpr uint32_t kBlobFields = 5;  // N, d, primes, dexp, coef: nbits/32 limbs each
+
+size_t blob_size(uint32_t K, uint32_t nbits) {
+  return kBlobHeader + (size_t)K * kBlobFields * (nbits / 32) * 4 + kBlobTrailer;
+}
+
+void put32(unsigned char *p, uint32_t v) {
+  for (int i = 0; i < 4; i++) p[i] = (unsigned char)(v >> (8 * i));
+}
+void put64(unsigned char *p, uint64_t v) {
+  for (int i = 0; i < 8; i++) p[i] = (unsigned char)(v >> (8 * i));
+}
+uint32_t get32(const unsigned char *p) {
+  uint32_t v = 0;
+  for (int i = 3; i >= 0; i--) v = (v << 8) | p[i];
+  return v;
+}
+uint64_t get64(const unsigned char *p) {
+  uint64_t v = 0;
+  for (int i = 7; i >= 0; i--) v = (v << 8) | p[i];
+  return v;
+}
+
+// FNV-1a, 64-bit (the published offset basis and prime), over a byte range.
+uint64_t fnv1a64(const unsigned char *p, size_t n) {
+  uint64_t h = 0xcbf29ce484222325ull;
+  for (size_t i = 0; i < n; i++) {
+    h ^= p[i];
+    h *= 0x100000001b3ull;
+  }
+  return h;
+}
+
+// The five per-key fields in blob order, as s-limb rows (primes, dexp, coef
+// hold b values of s/b limbs each, the layout of pmk_keyset_export_primes).
+void key_rows(const pmk::HostKey &x, uint32_t nbits, uint32_t b, std::vector<uint32_t> &rows) {
+  const size_t s = nbits / 32, h = s / b;
+  rows.assign(kBlobFields * s, 0u);
+  std::copy(x.N.begin(), x.N.end(), rows.begin());
+  std::copy(x.d.begin(), x.d.end(), rows.begin() + s);
+  for (size_t i = 0; i < b; i++) {
+    std::copy(x.pr[i].begin(), x.pr[i].end(), rows.begin() + 2 * s + i * h);
+    std::copy(x.dpr[i].begin(), x.dpr[i].end(), rows.begin() + 3 * s + i * h);
+    if (i != 1) std::copy(x.coef[i].begin(), x.coef[i].end(), rows.begin() + 4 * s + i * h);
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int pmk_keyset_export_blob(const pmk_keyset *ks, void *buf, size_t *len) {
+  if (!ks || !len) return PMK_EINVAL;
+  const size_t need = blob_size(ks->K, ks->nbits);
+  if (!buf) {
+    *len = need;
+    return PMK_OK;
+  }
+  if (*len < need) {
+    *len = need;
+    return PMK_EINVAL;
+  }
+  unsigned char *p = static_cast<unsigned char *>(buf);
+  std::memcpy(p, "PMKK", 4);
+  put32(p + 4, kBlobVersion);
+  put32(p + 8, ks->K);
+  put32(p + 12, ks->nbits);
+  put32(p + 16, ks->nprimes);
+  put32(p + 20, 0);
+  put64(p + 24, ks->e);
+  size_t off = kBlobHeader;
+  std::vector<uint32_t> rows;
+  for (uint32_t k = 0; k < ks->K; k++) {
+    key_rows(ks->keys[k], ks->nbits, ks->nprimes, rows);
+    for (uint32_t w : rows) {
+      put32(p + off, w);
+      off += 4;
+    }
+  }
+  put64(p + off, fnv1a64(p, off));
+  *len = need;
+  return PMK_OK;
+}
+
+int pmk_keyset_import(pmk_ctx *ctx, const void *buf, size_t len, pmk_keyset **out) {
+  pmk::TraceRange trace("pmk_keyset_import");
+  if (!buf || !out || len < kBlobHeader + kBlobTrailer) return PMK_EINVAL;
+  const unsigned char *p = static_cast<const unsigned char *>(buf);
+  if (std::memcmp(p, "PMKK", 4) != 0 || get32(p + 4) != kBlobVersion || get32(p + 20) != 0) return PMK_EINVAL;
+  const uint32_t K = get32(p + 8), nbits = get32(p + 12), b = get32(p + 16);
+  const uint64_t e = get64(p + 24);
+  if (K == 0 || K > kMaxKeys || !pmk::valid_multiprime(nbits, b) || e < 3 || !(e & 1) || (e >> 32)) return PMK_EINVAL;
+  if (len != blob_size(K, nbits) || get64(p + len - kBlobTrailer) != fnv1a64(p, len - kBlobTrailer))
+    return PMK_EINVAL;
+  if (ctx && !width_built(nbits, b)) return PMK_EUNSUPPORTED;
+  try {
+    pmk_keyset *ks = new pmk_keyset();
+    ks->device = ctx ? ctx->device : -1;
+    ks->K = K;
+    ks->nbits = nbits;
+    ks->e = e;
+    ks->nprimes = b;
+    ks->keys.resize(K);
+    const size_t s = nbits / 32;
+    std::vector<uint32_t> stored(kBlobFields * s), derived;
+    for (uint32_t k = 0; k < K; k++) {
+      const unsigned char *q = p + kBlobHeader + (size_t)k * kBlobFields * s * 4;
+      for (size_t i = 0; i < stored.size(); i++) stored[i] = get32(q + 4 * i);
+      // Everything is derived again from the primes; the stored N, d and CRT
+      // values must agree with it, or the blob is refused.
+      int rc = pmk::host_from_primes_mp(nbits, b, e, stored.data() + 2 * s, ks->keys[k]);
+      if (rc == PMK_OK) {
+        key_rows(ks->keys[k], nbits, b, derived);
+        if (derived != stored) rc = PMK_EINVAL;
+      }
+      if (rc != PMK_OK) {
+        delete ks;
+        return rc;
+      }
+    }
+    if (!ctx) {  // host only: exportable, not usable by device calls
+      *out = ks;
+      return PMK_OK;
+    }
+    return finish_keyset(ctx, ks, out);
+  } catch (const std::bad_alloc &) {
+    return PMK_ENOMEM;
+  }
+}
+
 uint32_t pmk_keyset_num_primes(const pmk_keyset *ks) { return ks ? ks->nprimes : 0; }
 uint32_t pmk_keyset_num_keys(const pmk_keyset *ks) { return ks ? ks->K : 0; }
 uint32_t pmk_keyset_nbits(const pmk_keyset *ks) { return ks ? ks->nbits : 0; }
@@ -439,7 +601,7 @@ uint64_t pmk_keyset_e(const pmk_keyset *ks) { return ks ? ks->e : 0; }
 
 void pmk_keyset_free(pmk_keyset *ks) {
   if (!ks) return;
-  {
+  if (ks->device >= 0) {
     DeviceGuard g(ks->device);
     cudaFree(ks->d_blob);
     cudaFree(ks->d_keys);
@@ -479,18 +641,23 @@ int pmk_join(pmk_ctx *ctx, uint32_t nbits, const uint32_t *d_chunks, size_t n_ch
 }
 
 int pmk_encrypt_chunks(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_in, uint32_t *d_out, size_t n_chunks,
-                       void *stream) {
+                       const uint32_t *d_key_idx, void *stream) {
   pmk::TraceRange trace("pmk_encrypt_chunks");
   if (n_chunks == 0) return (ctx && ks) ? PMK_OK : PMK_EINVAL;
   int rc = check_chunk_call(ctx, ks, d_in, d_out, n_chunks);
   if (rc != PMK_OK) return rc;
   DeviceGuard g(ctx->device);
   if (!g.ok()) return PMK_ECUDA;
-  return enqueue_encrypt(ctx, ks, d_in, d_out, n_chunks, as_stream(stream));
+  cudaStream_t st = as_stream(stream);
+  const uint32_t *groups = nullptr;
+  rc = key_groups_for(ctx, ks, d_key_idx, n_chunks, st, &groups);
+  if (rc == PMK_OK) rc = enqueue_encrypt(ctx, ks, d_in, d_out, n_chunks, st, d_key_idx, groups);
+  if (d_key_idx) release(ctx->grp, st);
+  return rc;
 }
 
 int pmk_decrypt_chunks(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_in, uint32_t *d_out, size_t n_chunks,
-                       int use_crt, void *stream) {
+                       const uint32_t *d_key_idx, int use_crt, void *stream) {
   pmk::TraceRange trace("pmk_decrypt_chunks");
   if (n_chunks == 0) return (ctx && ks) ? PMK_OK : PMK_EINVAL;
   int rc = check_chunk_call(ctx, ks, d_in, d_out, n_chunks);
@@ -499,7 +666,12 @@ int pmk_decrypt_chunks(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_in,
   if (use_crt && overlap(d_in, bytes, d_out, bytes)) return PMK_EINVAL;
   DeviceGuard g(ctx->device);
   if (!g.ok()) return PMK_ECUDA;
-  return enqueue_decrypt(ctx, ks, d_in, d_out, n_chunks, use_crt, as_stream(stream));
+  cudaStream_t st = as_stream(stream);
+  const uint32_t *groups = nullptr;
+  rc = key_groups_for(ctx, ks, d_key_idx, n_chunks, st, &groups);
+  if (rc == PMK_OK) rc = enqueue_decrypt(ctx, ks, d_in, d_out, n_chunks, use_crt, st, d_key_idx, groups);
+  if (d_key_idx) release(ctx->grp, st);
+  return rc;
 }
 
 int pmk_encrypt_blinded(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_m, const uint32_t *d_r,
@@ -581,19 +753,26 @@ int pmk_modexp_chunks_baseline(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_
   return rc;
 }
 
-int pmk_sync_status(pmk_ctx *ctx, void *stream) {
-  pmk::TraceRange trace("pmk_sync_status");
+int pmk_sync_status_detail(pmk_ctx *ctx, void *stream, uint64_t *first_chunk) {
+  pmk::TraceRange trace("pmk_sync_status_detail");
+  if (first_chunk) *first_chunk = UINT64_MAX;
   if (!ctx) return PMK_EINVAL;
   DeviceGuard g(ctx->device);
   if (!g.ok()) return PMK_ECUDA;
   if (cudaStreamSynchronize(as_stream(stream)) != cudaSuccess) return PMK_ECUDA;
-  uint32_t st = 0;
-  if (cudaMemcpy(&st, ctx->d_status, sizeof st, cudaMemcpyDeviceToHost) != cudaSuccess) return PMK_ECUDA;
+  uint32_t rec[4] = {0, 0, 0, 0};
+  if (cudaMemcpy(rec, ctx->d_status, sizeof rec, cudaMemcpyDeviceToHost) != cudaSuccess) return PMK_ECUDA;
+  const uint32_t st = rec[0];
   if (st == 0) return PMK_OK;
-  if (cudaMemset(ctx->d_status, 0, sizeof st) != cudaSuccess) return PMK_ECUDA;
+  if (first_chunk) *first_chunk = (uint64_t)rec[2] | ((uint64_t)rec[3] << 32);
+  if (pmk::clear_status(ctx->d_status, nullptr) != PMK_OK || cudaStreamSynchronize(nullptr) != cudaSuccess)
+    return PMK_ECUDA;
+  if (st & pmk::kStatusKeyIndex) return PMK_EKEYINDEX;
   if (st & pmk::kStatusRange) return PMK_ERANGE;
   return (st & pmk::kStatusNotInvertible) ? PMK_ENOINV : PMK_ECUDA;
 }
+
+int pmk_sync_status(pmk_ctx *ctx, void *stream) { return pmk_sync_status_detail(ctx, stream, nullptr); }
 
 int pmk_encrypt_message_host(pmk_ctx *ctx, const pmk_keyset *ks, const uint8_t *h_msg, size_t msg_len,
                              uint32_t *h_cipher, size_t n_chunks, void *stream) {
@@ -674,6 +853,7 @@ const char *pmk_strerror(int code) {
     case PMK_EUNSUPPORTED: return "key width or launch geometry not built";
     case PMK_ETOOLARGE: return "request exceeds the fixed capacity of the allocation-free call";
     case PMK_ENOINV: return "blinding value not invertible modulo its key";
+    case PMK_EKEYINDEX: return "key index not below the key set's key count";
     default: return "unknown error";
   }
 }

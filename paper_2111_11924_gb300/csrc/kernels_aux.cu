@@ -146,14 +146,21 @@ __global__ void __launch_bounds__(kAuxThreads) k_join(const uint32_t *__restrict
   }
 }
 
-// Flags chunks whose value is >= the modulus of their key (t mod K).
+// Flags chunks whose value is >= the modulus of their key (t mod K, or
+// key_idx[t]); a key index >= K flags kStatusKeyIndex instead.
 __global__ void __launch_bounds__(kAuxThreads) k_range(const KeyDev *__restrict__ keys, uint32_t K, int S,
                                                        const uint32_t *__restrict__ in, long long n,
-                                                       uint32_t *__restrict__ status) {
+                                                       uint32_t *__restrict__ status,
+                                                       const uint32_t *__restrict__ key_idx) {
   const long long t = (long long)blockIdx.x * kAuxThreads + threadIdx.x;
   if (t >= n) return;
   const uint32_t *x = in + t * S;
-  const uint32_t *N = keys[t % K].N;
+  const uint32_t k = key_idx ? __ldg(key_idx + t) : (uint32_t)(t % K);
+  if (k >= K) {
+    report(status, kStatusKeyIndex, t);
+    return;
+  }
+  const uint32_t *N = keys[k].N;
   int ge = 1;  // x == N counts as out of range
   for (int i = S - 1; i >= 0; i--) {
     const uint32_t xi = __ldg(x + i), ni = __ldg(N + i);
@@ -162,7 +169,79 @@ __global__ void __launch_bounds__(kAuxThreads) k_range(const KeyDev *__restrict_
       break;
     }
   }
-  if (ge) atomicOr(status, kStatusRange);
+  if (ge) report(status, kStatusRange, t);
+}
+
+// Key groups for explicit key indices, in three passes.
+//   count:   histogram of the indices (a shared-memory histogram per block,
+//            added into count[0..K) once per bin);
+//   offsets: poff[k] = sum over j < k of count[j] rounded up to kGroupAlign
+//            slots, poff[K] the total (one block; also cursor[k] = poff[k]);
+//   scatter: slot[cursor[k]++] = t for every chunk t of key k.  The lanes of
+//            a warp with equal keys take consecutive slots with one atomic.
+// The slot table starts filled with kNoChunk (the padding).  Slot order
+// within a key follows the atomics, so it may vary from call to call; each
+// chunk's result does not depend on it.
+__global__ void __launch_bounds__(kAuxThreads) k_key_count(const uint32_t *__restrict__ key_idx, long long n,
+                                                           uint32_t K, uint32_t *__restrict__ count,
+                                                           uint32_t *__restrict__ status) {
+  extern __shared__ uint32_t hist[];
+  for (uint32_t k = threadIdx.x; k < K; k += kAuxThreads) hist[k] = 0;
+  __syncthreads();
+  for (long long t = (long long)blockIdx.x * kAuxThreads + threadIdx.x; t < n; t += (long long)gridDim.x * kAuxThreads) {
+    const uint32_t k = __ldg(key_idx + t);
+    if (k < K) atomicAdd(&hist[k], 1u); else report(status, kStatusKeyIndex, t);
+  }
+  __syncthreads();
+  for (uint32_t k = threadIdx.x; k < K; k += kAuxThreads)
+    if (hist[k]) atomicAdd(count + k, hist[k]);
+}
+
+constexpr int kScanThreads = 1024;
+
+__global__ void __launch_bounds__(kScanThreads) k_key_offsets(const uint32_t *__restrict__ count, uint32_t K,
+                                                              uint32_t *__restrict__ poff,
+                                                              uint32_t *__restrict__ cursor) {
+  __shared__ uint32_t part[kScanThreads];
+  const uint32_t per = (K + kScanThreads - 1) / kScanThreads;  // keys per thread, contiguous
+  const uint32_t k0 = threadIdx.x * per, k1 = min(K, k0 + per);
+  uint32_t sum = 0;
+  for (uint32_t k = k0; k < k1; k++) sum += (count[k] + kGroupAlign - 1) / kGroupAlign * kGroupAlign;
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  for (int d = 1; d < kScanThreads; d <<= 1) {  // inclusive scan (Hillis-Steele)
+    const uint32_t v = threadIdx.x >= (unsigned)d ? part[threadIdx.x - d] : 0u;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  uint32_t off = part[threadIdx.x] - sum;  // exclusive prefix of this thread's keys
+  for (uint32_t k = k0; k < k1; k++) {
+    poff[k] = off;
+    cursor[k] = off;
+    off += (count[k] + kGroupAlign - 1) / kGroupAlign * kGroupAlign;
+  }
+  if (threadIdx.x == kScanThreads - 1) poff[K] = part[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kAuxThreads) k_key_scatter(const uint32_t *__restrict__ key_idx, long long n,
+                                                             uint32_t K, uint32_t *__restrict__ cursor,
+                                                             uint32_t *__restrict__ slot) {
+  const long long base = (long long)blockIdx.x * kAuxThreads;
+  for (long long t0 = base; t0 < n; t0 += (long long)gridDim.x * kAuxThreads) {
+    const long long t = t0 + threadIdx.x;
+    const bool live = t < n;  // uniform loop bound: every lane of the warp reaches the match below
+    const uint32_t k = live ? __ldg(key_idx + t) : kNoChunk;
+    const uint32_t peers = __match_any_sync(dev::kFull, k);
+    if (!live || k >= K) continue;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+    uint32_t pos = 0;
+    if (lane == leader) pos = atomicAdd(cursor + k, (uint32_t)__popc(peers));
+    pos = __shfl_sync(peers, pos, leader);
+    slot[pos + rank] = (uint32_t)t;
+  }
 }
 
 // The plain GPU formulation, kept as a measured baseline: one thread per
@@ -274,6 +353,12 @@ const ModexpEntry *find_entry(uint32_t limbs, KernelConfig cfg, bool crt) {
 
 }  // namespace
 
+int clear_status(uint32_t *status, cudaStream_t st) {
+  if (cudaMemsetAsync(status, 0, 8, st) != cudaSuccess || cudaMemsetAsync(status + 2, 0xff, 8, st) != cudaSuccess)
+    return PMK_ECUDA;
+  return PMK_OK;
+}
+
 int launch_split(uint32_t nbits, const uint8_t *msg, size_t len, uint32_t *chunks, size_t n, cudaStream_t st) {
   const int P = (int)(nbits / 8 - 1), S = (int)(nbits / 32);
   const long long nvec = (long long)n * (S / 4);
@@ -308,10 +393,38 @@ int launch_join(uint32_t nbits, const uint32_t *chunks, size_t n, uint8_t *msg, 
 }
 
 int launch_range_check(const KeyDev *keys, uint32_t K, uint32_t s, const uint32_t *in, size_t n, uint32_t *status,
-                       cudaStream_t st) {
+                       cudaStream_t st, const uint32_t *key_idx) {
   if (n == 0) return PMK_OK;
   k_range<<<(unsigned)((n + kAuxThreads - 1) / kAuxThreads), kAuxThreads, 0, st>>>(keys, K, (int)s, in, (long long)n,
-                                                                                   status);
+                                                                                   status, key_idx);
+  return cuda_rc(cudaGetLastError());
+}
+
+// Layout of a key-group table: poff[K + 1], slot[n + kGroupAlign K] (the
+// padding of K segments is below kGroupAlign K), count[K], cursor[K].
+size_t key_groups_words(size_t n, uint32_t K) {
+  return (size_t)(K + 1) + (n + (size_t)kGroupAlign * K) + 2 * (size_t)K;
+}
+
+int launch_key_groups(const uint32_t *key_idx, size_t n, uint32_t K, uint32_t *table, uint32_t *status,
+                      cudaStream_t st) {
+  if (K == 0 || K > 16383 || n >= kMaxGroupedChunks) return PMK_EINVAL;
+  const size_t nslot = n + (size_t)kGroupAlign * K;
+  uint32_t *poff = table, *slot = table + K + 1, *count = slot + nslot, *cursor = count + K;
+  if (cudaMemsetAsync(slot, 0xff, nslot * 4, st) != cudaSuccess ||
+      cudaMemsetAsync(count, 0, (size_t)K * 4, st) != cudaSuccess)
+    return PMK_ECUDA;
+  if (n == 0) {
+    k_key_offsets<<<1, kScanThreads, 0, st>>>(count, K, poff, cursor);
+    return cuda_rc(cudaGetLastError());
+  }
+  const size_t hist_bytes = (size_t)K * 4;
+  int rc = configure_smem(reinterpret_cast<const void *>(&k_key_count), 16383 * 4);  // the largest K, set once
+  if (rc != PMK_OK) return rc;
+  const int g = (int)std::min<long long>(grid_for((long long)n, kAuxThreads), 152LL * 4);
+  k_key_count<<<g, kAuxThreads, hist_bytes, st>>>(key_idx, (long long)n, K, count, status);
+  k_key_offsets<<<1, kScanThreads, 0, st>>>(count, K, poff, cursor);
+  k_key_scatter<<<grid_for((long long)n, kAuxThreads), kAuxThreads, 0, st>>>(key_idx, (long long)n, K, cursor, slot);
   return cuda_rc(cudaGetLastError());
 }
 
@@ -336,7 +449,7 @@ const MulmodEntry *crt_sum_entries(int *count) {
 }
 
 int launch_crt_sum(uint32_t limbs, uint32_t parts, const KeyDev *keys, uint32_t K, uint32_t *out, size_t n,
-                   cudaStream_t st, uint32_t *status_if_zero_residue) {
+                   cudaStream_t st, uint32_t *status_if_zero_residue, const uint32_t *groups) {
   if (n == 0) return PMK_OK;
   if (parts < 2 || parts > (uint32_t)kMaxPrimes || limbs % parts || K == 0 || K > 65535) return PMK_EINVAL;
   int cnt = 0;
@@ -348,11 +461,12 @@ int launch_crt_sum(uint32_t limbs, uint32_t parts, const KeyDev *keys, uint32_t 
   if (rc != PMK_OK) return rc;
   const long long per_key = ((long long)n + K - 1) / K;
   const int ipb = dev::kThreads / e->tpi;
-  dim3 grid((unsigned)((per_key + ipb - 1) / ipb), K);
+  dim3 grid = groups ? dim3((unsigned)(((long long)n + (long long)kGroupAlign * K + ipb - 1) / ipb), 1)
+                     : dim3((unsigned)((per_key + ipb - 1) / ipb), K);
   long long nl = (long long)n;
   int B = (int)parts;
   uint32_t *status = status_if_zero_residue;
-  void *args[] = {(void *)&keys, (void *)&K, (void *)&out, (void *)&nl, (void *)&B, (void *)&status};
+  void *args[] = {(void *)&keys, (void *)&K, (void *)&out, (void *)&nl, (void *)&B, (void *)&status, (void *)&groups};
   return cuda_rc(cudaLaunchKernel(e->fn, grid, dim3(dev::kThreads), args, e->smem, st));
 }
 
@@ -466,22 +580,25 @@ int launch_modexp_tasks(uint32_t limbs, KernelConfig cfg, bool crt, const BatchT
 }
 
 int launch_modexp(ExpMode mode, uint32_t limbs, KernelConfig cfg, const KeyDev *keys, uint32_t K, const uint32_t *in,
-                  uint32_t *out, size_t n, cudaStream_t st, uint32_t parts) {
+                  uint32_t *out, size_t n, cudaStream_t st, uint32_t parts, const uint32_t *groups) {
   if (n == 0) return PMK_OK;
   const bool crt = mode == ExpMode::kCrtHalf || mode == ExpMode::kCrtInverse;
   if (crt && (parts < 2 || parts > (uint32_t)kMaxPrimes)) return PMK_EINVAL;
-  if ((unsigned long long)K * (crt ? parts : 1) > 65535ull) return PMK_EINVAL;  // grid.y
+  if (!groups && (unsigned long long)K * (crt ? parts : 1) > 65535ull) return PMK_EINVAL;  // grid.y
   const ModexpEntry *e = find_entry(limbs, cfg, crt);
   if (!e) return PMK_EUNSUPPORTED;
   const int rc = configure_smem(e->fn, e->smem);
   if (rc != PMK_OK) return rc;
   const long long per_key = ((long long)n + K - 1) / K;
   const int ipb = e->threads / e->tpi;
-  dim3 grid((unsigned)((per_key + ipb - 1) / ipb), crt ? parts * K : K);
+  if (groups && kGroupAlign % ipb) return PMK_EUNSUPPORTED;  // a block must not straddle two keys' slots
+  dim3 grid = groups ? dim3((unsigned)(((long long)n + (long long)kGroupAlign * K + ipb - 1) / ipb), crt ? parts : 1)
+                     : dim3((unsigned)((per_key + ipb - 1) / ipb), crt ? parts * K : K);
   long long nl = (long long)n;
   int sel = (mode == ExpMode::kEncrypt || mode == ExpMode::kCrtInverse) ? 1 : 0;
   int np = crt ? (int)parts : 1;
-  void *args[] = {(void *)&keys, (void *)&K, (void *)&in, (void *)&out, (void *)&nl, (void *)&sel, (void *)&np};
+  void *args[] = {(void *)&keys, (void *)&K,   (void *)&in, (void *)&out,
+                  (void *)&nl,   (void *)&sel, (void *)&np, (void *)&groups};
   return cuda_rc(cudaLaunchKernel(e->fn, grid, dim3(e->threads), args, e->smem, st));
 }
 

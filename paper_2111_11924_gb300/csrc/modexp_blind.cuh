@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(NT) k_blind_crt(const KeyDev *__restrict__ key
 #pragma unroll
     for (int o = 1; o < TPI; o <<= 1) any |= __shfl_xor_sync(kFull, any, o, TPI);
   }
-  if (status && active && r == 0 && any == 0) atomicOr(status, kStatusNotInvertible);
+  if (status && active && r == 0 && any == 0) report(status, kStatusNotInvertible, t);
   store_slice<L>(tbl + 8 * ROW, a, r);
   exp2_window<S, TPI, FORM>(a, tbl, ybuf, kd.sched_blind[prime], kd.nsteps_blind[prime], kd.maxa_blind[prime],
                             kd.maxb_blind[prime], nn, n0, r);

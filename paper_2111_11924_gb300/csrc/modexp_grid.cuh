@@ -41,10 +41,53 @@ __device__ __forceinline__ void crt_input(uint32_t (&a)[S / TPI], const uint32_t
   }
 }
 
-// Grid: blockIdx.y selects the key (full width) or key * parts + i (CRT,
-// residue mod prime r_i); blockIdx.x * IPB + instance slot selects the j-th
-// chunk of that key, chunk t = key + j K.  Every block therefore serves one
-// key: schedules, modulus and control flow are uniform across it.
+// Which chunks a block serves, and under which key.  Every block serves one
+// key, so schedules, modulus and control flow are uniform across it.
+//   Round robin (grp == nullptr): blockIdx.y is the key (full width) or
+//     key * parts + i (CRT, residue mod prime r_i); instance slot g of block
+//     x takes the j-th chunk of that key, j = x IPB + g, chunk t = key + j K.
+//   Key groups (grp != nullptr, explicit key indices): grp holds the padded
+//     segment offsets poff[0..K] followed by the slot table (see
+//     launch_key_groups); key k owns slots [poff[k], poff[k+1]), a multiple
+//     of 64 long, each holding a chunk index or kNoChunk.  Block x takes
+//     slots [x IPB, (x + 1) IPB) (IPB divides 64, so one key's), its key is
+//     found by binary search over poff, and blockIdx.y is the prime.
+struct BlockChunks {
+  uint32_t key;
+  long long first_slot;  // round robin: the block's first chunk; groups: its first slot
+  bool any;              // the block has at least one chunk
+};
+__device__ __forceinline__ BlockChunks block_chunks(const uint32_t *__restrict__ grp, uint32_t K, long long n,
+                                                    int ipb, uint32_t grid_key) {
+  BlockChunks b;
+  if (!grp) {
+    b.key = grid_key;
+    b.first_slot = grid_key + (long long)blockIdx.x * ipb * K;
+    b.any = b.first_slot < n;
+    return b;
+  }
+  const uint32_t s0 = blockIdx.x * (uint32_t)ipb;
+  b.first_slot = s0;
+  b.any = s0 < __ldg(grp + K);
+  uint32_t lo = 0, hi = K;  // poff[lo] <= s0 < poff[hi]
+  while (b.any && hi - lo > 1) {
+    const uint32_t mid = (lo + hi) / 2;
+    if (__ldg(grp + mid) <= s0) lo = mid; else hi = mid;
+  }
+  b.key = lo;
+  return b;
+}
+// Chunk of instance slot g (negative: none).
+__device__ __forceinline__ long long slot_chunk(const uint32_t *__restrict__ grp, uint32_t K, long long n,
+                                                const BlockChunks &b, uint32_t g) {
+  if (!grp) {
+    const long long t = b.first_slot + (long long)g * K;
+    return t < n ? t : -1;
+  }
+  const uint32_t c = __ldg(grp + K + 1 + b.first_slot + g);
+  return c == kNoChunk ? -1 : (long long)c;
+}
+
 //
 // FULL: out[t] = in[t]^E mod N_key, E = e (sel != 0) or d, S = nbits / 32.
 // CRT:  out[t][i] = in[t]^E mod r_i over S = nbits / (32 parts) limbs, with
@@ -58,7 +101,7 @@ __device__ __forceinline__ void crt_input(uint32_t (&a)[S / TPI], const uint32_t
 template <int S, int TPI, bool CRT, int FORM, int NT = kThreads, int TABLE = kTableFull>
 __global__ void __launch_bounds__(NT) k_modexp(const KeyDev *__restrict__ keys, uint32_t K,
                                                const uint32_t *__restrict__ in, uint32_t *__restrict__ out,
-                                               long long n, int sel, int parts) {
+                                               long long n, int sel, int parts, const uint32_t *__restrict__ grp) {
   constexpr int L = S / TPI;
   constexpr int IPB = NT / TPI;
   constexpr int ROW = Layout<S>::kRow;
@@ -71,10 +114,10 @@ __global__ void __launch_bounds__(NT) k_modexp(const KeyDev *__restrict__ keys, 
   uint32_t *tbl = smem + Layout<S>::kConstRows * ROW + g * INST;
   uint32_t *ybuf = tbl + ROWS * ROW;
 
-  const uint32_t key = CRT ? blockIdx.y / (uint32_t)parts : blockIdx.y;
-  const uint32_t prime = CRT ? blockIdx.y % (uint32_t)parts : 0;
-  const long long first = key + (long long)blockIdx.x * IPB * K;
-  if (first >= n) return;  // block-uniform: no instance of this block has a chunk
+  const uint32_t prime = CRT ? (grp ? blockIdx.y : blockIdx.y % (uint32_t)parts) : 0;
+  const BlockChunks bc = block_chunks(grp, K, n, IPB, CRT ? blockIdx.y / (uint32_t)parts : blockIdx.y);
+  if (!bc.any) return;  // block-uniform: no instance of this block has a chunk
+  const uint32_t key = bc.key;
   const KeyDev &kd = keys[key];
   const uint32_t *M = CRT ? kd.P[prime] : kd.N;
   const uint32_t *R2 = CRT ? kd.R2h[prime] : kd.R2;
@@ -93,11 +136,12 @@ __global__ void __launch_bounds__(NT) k_modexp(const KeyDev *__restrict__ keys, 
   }
   __syncthreads();
   // After the barrier the warps are independent: a warp whose instances all
-  // lie past the last chunk (the tail block of a key) leaves.
-  if (first + (long long)((threadIdx.x / 32) * (32 / TPI)) * K >= n) return;
+  // lie past the last chunk of the key leaves (chunks and slots of a key are
+  // in order, padding last, so its first instance decides).
+  if (slot_chunk(grp, K, n, bc, (threadIdx.x / 32) * (32 / TPI)) < 0) return;
 
-  const long long t = first + (long long)g * K;
-  const bool active = t < n;
+  const long long t = slot_chunk(grp, K, n, bc, g);
+  const bool active = t >= 0;
   uint32_t nn[L], a[L];
   load_slice_global<L>(nn, M, r);
   if (!CRT) {

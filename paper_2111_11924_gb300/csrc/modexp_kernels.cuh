@@ -131,23 +131,24 @@ __global__ void __launch_bounds__(kThreads) k_mulmod(const KeyDev *__restrict__ 
 // residue before the group's shuffles inside that product, so the stores
 // cannot overtake another lane's loads.  With `status`, a residue equal to
 // zero (the input shares the prime r_i: no inverse exists) sets
-// kStatusNotInvertible.  Grid as k_mulmod.
+// kStatusNotInvertible.  Grid as k_mulmod, or over key groups as k_modexp
+// (block_chunks) when grp is given.
 template <int S, int TPI>
 __global__ void __launch_bounds__(kThreads) k_crt_sum(const KeyDev *__restrict__ keys, uint32_t K,
-                                                      uint32_t *out, long long n, int B, uint32_t *status) {
+                                                      uint32_t *out, long long n, int B, uint32_t *status,
+                                                      const uint32_t *__restrict__ grp) {
   constexpr int L = S / TPI;
   constexpr int IPB = kThreads / TPI;
   constexpr int ROW = Layout<S>::kRow;
   extern __shared__ __align__(16) uint32_t smem[];  // B rows: c_i R mod N
   const uint32_t r = threadIdx.x % TPI, g = threadIdx.x / TPI;
-  const uint32_t key = blockIdx.y;
-  const long long first = key + (long long)blockIdx.x * IPB * K;
-  if (first >= n) return;
-  const KeyDev &kd = keys[key];
+  const BlockChunks bc = block_chunks(grp, K, n, IPB, blockIdx.y);
+  if (!bc.any) return;
+  const KeyDev &kd = keys[bc.key];
   for (int i = threadIdx.x; i < B * S; i += kThreads) smem[(i / S) * ROW + i % S] = __ldg(kd.crt_sum[i / S] + i % S);
   __syncthreads();
-  const long long t = first + (long long)g * K;
-  const bool active = t < n;
+  const long long t = slot_chunk(grp, K, n, bc, g);
+  const bool active = t >= 0;
   const int H = S / B;
   uint32_t nn[L], acc[L], a[L];
   load_slice_global<L>(nn, kd.N, r);
@@ -171,7 +172,7 @@ __global__ void __launch_bounds__(kThreads) k_crt_sum(const KeyDev *__restrict__
     mod_add<L, TPI>(acc, a, nn, r);
   }
   if (active) {
-    if (status && zero && r == 0) atomicOr(status, kStatusNotInvertible);
+    if (status && zero && r == 0) report(status, kStatusNotInvertible, t);
     uint32_t *o = out + t * S + r * L;
 #pragma unroll
     for (int j = 0; j < L; j++) o[j] = acc[j];

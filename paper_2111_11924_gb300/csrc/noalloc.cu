@@ -29,7 +29,7 @@ namespace {
 
 // 32 MiB: a 2048-bit message of up to ~11 MB (4 + 256 + 256 + 255 bytes per chunk).
 constexpr size_t kNoAllocBytes = 32u << 20;
-constexpr size_t kStatusBytes = 256;  // first 256 bytes: the status word
+constexpr size_t kStatusBytes = 256;  // first 256 bytes: the status record
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
@@ -88,7 +88,7 @@ extern "C" int pmk_decrypt_message_host_noalloc(const pmk_keyset *ks, const uint
     const uint32_t S = ks->nbits / 32, B = ks->nprimes, H = S / B;
     // The array keeps the previous call's contents: the status word must start at zero.
     queued = true;
-    if (cudaMemsetAsync(d_status, 0, sizeof(uint32_t), st) != cudaSuccess ||
+    if (clear_status(d_status, st) != PMK_OK ||
         cudaMemcpyAsync(d_cipher, h_cipher, words * 4, cudaMemcpyHostToDevice, st) != cudaSuccess) {
       rc = PMK_ECUDA;
       break;

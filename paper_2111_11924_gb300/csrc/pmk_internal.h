@@ -26,7 +26,29 @@ class TraceRange {
 };
 
 // Error bits written by kernels into the context's device status word.
-enum : uint32_t { kStatusRange = 1u, kStatusNotInvertible = 2u };
+enum : uint32_t { kStatusRange = 1u, kStatusNotInvertible = 2u, kStatusKeyIndex = 4u };
+
+// The device status record of a context (16 bytes, 8-byte aligned): word 0
+// holds the error bits, words 2-3 the smallest chunk index (within its call)
+// that raised one, all ones when none.  Kernels receive a pointer to word 0.
+constexpr size_t kStatusRecordBytes = 16;
+constexpr unsigned long long kNoErrorChunk = ~0ull;
+#ifdef __CUDACC__
+// Record error `flag` for chunk t.
+__device__ __forceinline__ void report(uint32_t *status, uint32_t flag, long long t) {
+  atomicOr(status, flag);
+  atomicMin(reinterpret_cast<unsigned long long *>(status + 2), (unsigned long long)t);
+}
+#endif
+// Clear a status record on `st` (error bits 0, no failing chunk).
+int clear_status(uint32_t *status, cudaStream_t st);
+
+// Key groups (explicit key indices): each key's chunks occupy a segment of
+// slots padded to a multiple of kGroupAlign; a padding slot holds kNoChunk.
+constexpr uint32_t kGroupAlign = 64;
+constexpr uint32_t kNoChunk = 0xffffffffu;
+// Most chunks of a call with explicit key indices (slot numbers stay 32-bit).
+constexpr size_t kMaxGroupedChunks = (size_t)1 << 31;
 
 // Most chunks per call: keeps byte counts and grid sizes far from overflow
 // (2^32 chunks of 2048 bits are 1 TiB, beyond any device's memory).
@@ -141,8 +163,18 @@ Schedule2 make_schedule2(const uint32_t *expa, const uint32_t *expb, int nlimbs)
 enum class ExpMode : int { kEncrypt = 0, kDecrypt = 1, kCrtHalf = 2, kCrtInverse = 3 };
 int launch_split(uint32_t nbits, const uint8_t *msg, size_t len, uint32_t *chunks, size_t n, cudaStream_t st);
 int launch_join(uint32_t nbits, const uint32_t *chunks, size_t n, uint8_t *msg, size_t len, cudaStream_t st);
+// Flags chunks >= their key's modulus (kStatusRange); with key_idx, the key
+// of chunk t is key_idx[t], and an index >= K sets kStatusKeyIndex instead.
 int launch_range_check(const KeyDev *keys, uint32_t K, uint32_t s, const uint32_t *in, size_t n,
-                       uint32_t *status, cudaStream_t st);
+                       uint32_t *status, cudaStream_t st, const uint32_t *key_idx = nullptr);
+// Key groups for explicit key indices (key_idx[t] = key of chunk t): builds
+// in `table` (key_groups_words(n, K) words) the padded segment offsets
+// poff[0..K] followed by the slot table, chunks of key k in slots
+// [poff[k], poff[k + 1]).  Indices >= K set kStatusKeyIndex in *status and
+// their chunks get no slot.  K <= 16383.
+size_t key_groups_words(size_t n, uint32_t K);
+int launch_key_groups(const uint32_t *key_idx, size_t n, uint32_t K, uint32_t *table, uint32_t *status,
+                      cudaStream_t st);
 // Launch geometry of an exponentiation kernel: lanes per instance, Montgomery
 // form (0 = one carry chain per lane, 1 = independent columns) and the
 // odd-power table size (kTableFull or kTableSmall; a geometry compiled only
@@ -153,13 +185,15 @@ struct KernelConfig {
 };
 // CRT modes run `parts` residues per chunk (the key's prime count) over
 // `limbs` = s / parts limbs each; residue i of chunk t goes to out[t][i * limbs].
+// With `groups` (a table of launch_key_groups) chunks are taken by key group
+// instead of round robin.
 int launch_modexp(ExpMode mode, uint32_t limbs, KernelConfig cfg, const KeyDev *keys, uint32_t K, const uint32_t *in,
-                  uint32_t *out, size_t n, cudaStream_t st, uint32_t parts = 2);
+                  uint32_t *out, size_t n, cudaStream_t st, uint32_t parts = 2, const uint32_t *groups = nullptr);
 // CRT recombination of `parts` residues per chunk (limbs / parts limbs
 // each) in place at full width `limbs`: out[t] holds the residues and
 // receives the value mod N.
 int launch_crt_sum(uint32_t limbs, uint32_t parts, const KeyDev *keys, uint32_t K, uint32_t *out, size_t n,
-                   cudaStream_t st, uint32_t *status_if_zero_residue = nullptr);
+                   cudaStream_t st, uint32_t *status_if_zero_residue = nullptr, const uint32_t *groups = nullptr);
 // Fused blinded CRT decryption: out[t][i] = c*[t]^(d_i) c_r[t]^(r_i - 1 - d_i)
 // mod r_i for each of the key's `parts` primes (prime_limbs limbs each); the
 // residues of (c* c_r^-1)^d, to be recombined by launch_crt_sum.  A c_r
@@ -222,6 +256,7 @@ struct pmk_ctx {
   int device = 0;
   uint32_t *d_status = nullptr;            // device-side error bits (pmk::kStatusRange)
   pmk::Staging msg, a, b;                  // staging of the *_host calls and the blinded CRT path
+  pmk::Staging grp;                        // key-group table of calls with explicit key indices
   std::map<uint32_t, pmk::KernelConfig> cfg;  // (limbs << 1 | crt) -> kernel geometry override
   std::map<uint32_t, int> table;              // (limbs << 1 | crt) -> odd-power table size override
 };

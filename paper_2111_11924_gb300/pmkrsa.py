@@ -14,8 +14,8 @@ import numpy as np
 
 from . import _native_build
 
-PMK_OK, PMK_EINVAL, PMK_ERANGE, PMK_ENOMEM, PMK_ECUDA, PMK_EUNSUPPORTED, PMK_ETOOLARGE, PMK_ENOINV = (
-    0, -1, -2, -3, -4, -5, -6, -7)
+PMK_OK, PMK_EINVAL, PMK_ERANGE, PMK_ENOMEM, PMK_ECUDA, PMK_EUNSUPPORTED, PMK_ETOOLARGE, PMK_ENOINV, PMK_EKEYINDEX = (
+    0, -1, -2, -3, -4, -5, -6, -7, -8)
 
 _lib = None
 
@@ -56,6 +56,8 @@ def load_library() -> ctypes.CDLL:
         "pmk_keygen_host_multiprime": (i, [u32, u32, u32, u64, u64, P32, P32, P32, P32, P32]),
         "pmk_keyset_export_primes": (i, [vp, P32, P32, P32]),
         "pmk_keyset_from_primes_multi": (i, [vp, u32, u32, u32, u64, P32, ctypes.POINTER(vp)]),
+        "pmk_keyset_export_blob": (i, [vp, vp, ctypes.POINTER(sz)]),
+        "pmk_keyset_import": (i, [vp, vp, sz, ctypes.POINTER(vp)]),
         "pmk_keyset_num_primes": (u32, [vp]),
         "pmk_keyset_num_keys": (u32, [vp]),
         "pmk_keyset_nbits": (u32, [vp]),
@@ -65,8 +67,8 @@ def load_library() -> ctypes.CDLL:
         "pmk_num_chunks": (sz, [sz, u32]),
         "pmk_split": (i, [vp, u32, vp, sz, vp, sz, vp]),
         "pmk_join": (i, [vp, u32, vp, sz, vp, sz, vp]),
-        "pmk_encrypt_chunks": (i, [vp, vp, vp, vp, sz, vp]),
-        "pmk_decrypt_chunks": (i, [vp, vp, vp, vp, sz, i, vp]),
+        "pmk_encrypt_chunks": (i, [vp, vp, vp, vp, sz, vp, vp]),
+        "pmk_decrypt_chunks": (i, [vp, vp, vp, vp, sz, vp, i, vp]),
         "pmk_modexp_chunks_baseline": (i, [vp, vp, vp, vp, sz, i, vp]),
         "pmk_encrypt_blinded": (i, [vp, vp, vp, vp, vp, vp, sz, vp]),
         "pmk_decrypt_blinded": (i, [vp, vp, vp, vp, vp, sz, i, vp]),
@@ -78,6 +80,7 @@ def load_library() -> ctypes.CDLL:
         "pmk_batch_info": (i, [vp, ctypes.POINTER(sz), ctypes.POINTER(i)]),
         "pmk_batch_destroy": (None, [vp]),
         "pmk_sync_status": (i, [vp, vp]),
+        "pmk_sync_status_detail": (i, [vp, vp, ctypes.POINTER(u64)]),
         "pmk_strerror": (ctypes.c_char_p, [i]),
         "pmk_measure_int_peak": (i, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(i)]),
@@ -218,6 +221,15 @@ class KeySet:
         _check(lib.pmk_keyset_export(self.handle, *[_p32(arrs[f]) for f in _KEY_FIELDS]), "export")
         return arrs
 
+    def export_blob(self) -> bytes:
+        """The key set as a versioned little-endian blob (pmk_keyset_export_blob)."""
+        lib = load_library()
+        n = ctypes.c_size_t(0)
+        _check(lib.pmk_keyset_export_blob(self.handle, None, ctypes.byref(n)), "pmk_keyset_export_blob")
+        buf = ctypes.create_string_buffer(n.value)
+        _check(lib.pmk_keyset_export_blob(self.handle, buf, ctypes.byref(n)), "pmk_keyset_export_blob")
+        return buf.raw[: n.value]
+
     def free(self) -> None:
         if self._h:
             load_library().pmk_keyset_free(self._h)
@@ -286,6 +298,12 @@ class Context:
                                                         ctypes.byref(h)), "pmk_keygen_multiprime")
         return KeySet(self, h)
 
+    def import_keyset(self, blob: bytes) -> KeySet:
+        """A key set restored from pmk_keyset_export_blob's bytes, on this context's device."""
+        h = ctypes.c_void_p()
+        _check(load_library().pmk_keyset_import(self.handle, blob, len(blob), ctypes.byref(h)), "pmk_keyset_import")
+        return KeySet(self, h)
+
     def keyset_from_primes(self, nbits: int, e: int, p: np.ndarray, q: np.ndarray) -> KeySet:
         p = np.ascontiguousarray(p, np.uint32)
         q = np.ascontiguousarray(q, np.uint32)
@@ -324,21 +342,34 @@ class Context:
                "pmk_join")
         return out
 
-    def encrypt_chunks(self, ks: KeySet, chunks, out=None, stream=None):
+    def _key_idx(self, key_idx, n: int):
+        """Device pointer of an explicit key-index vector (int32 CUDA tensor of n), or None."""
+        if key_idx is None:
+            return None
+        torch = _torch()
+        if key_idx.numel() != n:
+            raise ValueError(f"key_idx must hold one key index per chunk ({n})")
+        return self._dev(key_idx, torch.int32, "key_idx")
+
+    def encrypt_chunks(self, ks: KeySet, chunks, out=None, stream=None, key_idx=None):
+        """c[t] = m[t]^e mod N_k with k = t mod K, or k = key_idx[t] when given."""
         torch = _torch()
         if out is None:
             out = torch.empty_like(chunks)
         _check(load_library().pmk_encrypt_chunks(self.handle, ks.handle, self._dev(chunks, torch.int32, "in"),
                                                  self._dev(out, torch.int32, "out"), chunks.shape[0],
+                                                 self._key_idx(key_idx, chunks.shape[0]),
                                                  self.stream_handle(stream)), "pmk_encrypt_chunks")
         return out
 
-    def decrypt_chunks(self, ks: KeySet, chunks, use_crt: bool = False, out=None, stream=None):
+    def decrypt_chunks(self, ks: KeySet, chunks, use_crt: bool = False, out=None, stream=None, key_idx=None):
+        """m[t] = c[t]^d mod N_k with k = t mod K, or k = key_idx[t] when given."""
         torch = _torch()
         if out is None:
             out = torch.empty_like(chunks)
         _check(load_library().pmk_decrypt_chunks(self.handle, ks.handle, self._dev(chunks, torch.int32, "in"),
-                                                 self._dev(out, torch.int32, "out"), chunks.shape[0], int(use_crt),
+                                                 self._dev(out, torch.int32, "out"), chunks.shape[0],
+                                                 self._key_idx(key_idx, chunks.shape[0]), int(use_crt),
                                                  self.stream_handle(stream)), "pmk_decrypt_chunks")
         return out
 
@@ -405,6 +436,12 @@ class Context:
         """Synchronise and return (and clear) the device-side error code."""
         return int(load_library().pmk_sync_status(self.handle, self.stream_handle(stream)))
 
+    def status_detail(self, stream=None) -> tuple:
+        """(code, first failing chunk or None): pmk_sync_status_detail."""
+        first = ctypes.c_uint64(0)
+        code = int(load_library().pmk_sync_status_detail(self.handle, self.stream_handle(stream), ctypes.byref(first)))
+        return code, (None if first.value == 2**64 - 1 else int(first.value))
+
     def check(self, stream=None) -> None:
         _check(self.status(stream), "device status")
 
@@ -464,6 +501,15 @@ class Context:
             cache.put(key, res)
         return res
 
+    def copy_kernel_configs_from(self, other: "Context", keysets: dict) -> None:
+        """Take other's kernel geometry and window bound for every limb count
+        the key sets use (full width and CRT residues)."""
+        for ks in keysets.values():
+            for limbs, crt in ((ks.nbits // 32, False), (ks.nbits // 32 // ks.nprimes, True)):
+                tpi, form = other.get_kernel_config(limbs, crt)
+                self.set_kernel_config(limbs, crt, tpi, form)
+                self.set_kernel_window(limbs, crt, other.get_kernel_window(limbs, crt))
+
     def get_kernel_config(self, limbs: int, crt: bool) -> tuple:
         tpi, form = np.zeros(1, np.uint32), np.zeros(1, np.uint32)
         _check(load_library().pmk_get_kernel_config(self.handle, limbs, int(crt), _p32(tpi), _p32(form)),
@@ -517,6 +563,14 @@ def kernel_configs(limbs: int, crt: bool) -> list:
     tpi, form = np.zeros(n, np.uint32), np.zeros(n, np.uint32)
     lib.pmk_list_kernel_configs(limbs, int(crt), _p32(tpi), _p32(form), n)
     return list(zip(tpi.tolist(), form.tolist()))
+
+
+def import_keyset_host(blob: bytes) -> KeySet:
+    """A host-only key set from a blob (pmk_keyset_import with no context):
+    it can be exported and inspected but not used by device calls."""
+    h = ctypes.c_void_p()
+    _check(load_library().pmk_keyset_import(None, blob, len(blob), ctypes.byref(h)), "pmk_keyset_import")
+    return KeySet(None, h)
 
 
 def decrypt_message_host_noalloc(ks: KeySet, h_cipher, h_msg, use_crt: bool = False, stream=None) -> int:

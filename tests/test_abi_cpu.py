@@ -275,3 +275,80 @@ def test_host_buffer_checks_reject_mismatched_buffers():
                    (torch.zeros((2, 300), dtype=torch.uint8)[:, :200], 4)):  # not contiguous
         with pytest.raises(ValueError):
             pmkrsa.host_message_buffer(bad, n, 1024)
+
+
+def test_blob_round_trip_from_c(P, tmp_path):
+    """A C99 program writes a key-set blob with its own writer, imports it
+    host-only, exports it and gets the same bytes; a corrupted or
+    inconsistent blob is refused."""
+    import shutil
+    import subprocess
+
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    from paper_2111_11924_gb300 import _native_build as NB
+
+    exe = str(tmp_path / "blob_roundtrip")
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-o", exe,
+                           os.path.join(ROOT, "tests", "c", "blob_roundtrip.c"), "-I", os.path.join(ROOT, "include"),
+                           NB.LIB, "-Wl,-rpath," + os.path.dirname(NB.LIB)])
+    out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split("\n")
+    einval = P.pmkrsa.PMK_EINVAL
+    assert out[0] == "keygen 0" and out[1] == "import 0"
+    assert out[2] == f"export 0 0 size {32 + 20 * 3 * 24 + 8} same"
+    assert out[3] == f"corrupt {einval}" and out[4] == f"inconsistent {einval}"
+
+
+def _fnv1a64(b: bytes) -> int:
+    h = 0xCBF29CE484222325
+    for x in b:
+        h = ((h ^ x) * 0x100000001B3) & (2**64 - 1)
+    return h
+
+
+def _oracle_blob(ok, b: int) -> bytes:
+    """The documented blob layout written from the oracle's key material."""
+    import struct
+
+    s = ok.nbits // 32
+    rows = []
+    for k in range(ok.K):
+        if b == 2:
+            primes = np.concatenate([ok.a["p"][k], ok.a["q"][k]])
+            dexp = np.concatenate([ok.a["dp"][k], ok.a["dq"][k]])
+            coef = np.concatenate([ok.a["qinv"][k], np.zeros(s // 2, np.uint32)])
+        else:
+            primes, dexp, coef = ok.a["primes"][k], ok.a["dexp"][k], ok.a["coef"][k]
+        rows += [ok.a["N"][k], ok.a["d"][k], primes, dexp, coef]
+    body = b"PMKK" + struct.pack("<5IQ", 1, ok.K, ok.nbits, b, 0, ok.e) + \
+        b"".join(np.asarray(r, dtype="<u4").tobytes() for r in rows)
+    return body + struct.pack("<Q", _fnv1a64(body))
+
+
+@pytest.mark.parametrize("K,nbits,b,seed", [(3, 512, 2, 11), (2, 768, 3, 12), (2, 1024, 4, 13)])
+def test_blob_matches_oracle_key_material(P, K, nbits, b, seed):
+    """A blob written from the oracle's keys imports into a key set whose
+    exported material is the oracle's, and exports back to the same bytes."""
+    ok = oracle.keygen(K, nbits, 65537, seed) if b == 2 else oracle.keygen_mp(K, nbits, b, 65537, seed)
+    blob = _oracle_blob(ok, b)
+    ks = P.import_keyset_host(blob)
+    assert (ks.K, ks.nbits, ks.nprimes, ks.e) == (K, nbits, b, 65537)
+    assert ks.export_blob() == blob
+    ex = ks.export()
+    for f in ok.a:
+        assert np.array_equal(ex[f], ok.a[f]), f
+    ks.free()
+
+
+def test_blob_rejections(P):
+    ok = oracle.keygen(2, 512, 65537, 21)
+    blob = bytearray(_oracle_blob(ok, 2))
+    for mutate in (lambda x: x.__setitem__(0, ord("Q")),              # magic
+                   lambda x: x.__setitem__(4, 2),                     # version
+                   lambda x: x.__setitem__(len(x) - 1, x[-1] ^ 1),    # hash
+                   lambda x: x.__setitem__(slice(len(x) - 9, len(x) - 8), b"")):  # length
+        bad = bytearray(blob)
+        mutate(bad)
+        with pytest.raises(P.PMKError) as err:
+            P.import_keyset_host(bytes(bad))
+        assert err.value.code == P.pmkrsa.PMK_EINVAL

@@ -318,6 +318,32 @@ def test_out_of_range_chunk_reported(ctx, P):
     assert ctx.status() == P.pmkrsa.PMK_ERANGE
 
 
+def test_failing_chunk_is_attributed(ctx, P):
+    """pmk_sync_status_detail names the smallest failing chunk of the call:
+    a range error (chunk >= its modulus), a key index >= K, and a blinding
+    value sharing a prime with its modulus; and none after clearing."""
+    ks, ok = keys_for(ctx, 3, 512, seed=31)
+    rng = np.random.default_rng(31)
+    m = oracle.split(rng.integers(0, 256, 400 * 63, dtype=np.uint8), 512)
+    bad = m.copy()
+    for t in (271, 90, 305):  # three bad chunks; 90 is the first
+        bad[t] = ok.a["N"][t % 3]
+    ctx.encrypt_chunks(ks, dev(bad))
+    assert ctx.status_detail() == (P.pmkrsa.PMK_ERANGE, 90)
+    assert ctx.status_detail() == (P.pmkrsa.PMK_OK, None)
+    idx = rng.integers(0, 3, m.shape[0]).astype(np.uint32)
+    idx[[333, 17]] = 9
+    ctx.encrypt_chunks(ks, dev(m), key_idx=dev(idx))
+    assert ctx.status_detail() == (P.pmkrsa.PMK_EKEYINDEX, 17)
+    # blinded decryption: r of chunk 44 is a multiple of key (44 mod 3)'s first prime
+    c = ctx.encrypt_chunks(ks, dev(m))
+    r = oracle.split(rng.integers(0, 256, 400 * 63, dtype=np.uint8), 512)
+    r[44] = oracle.to_limbs(3 * oracle.from_limbs(ok.a["p"][44 % 3]), 16)
+    cstar, cr = ctx.encrypt_blinded(ks, c, dev(r))
+    ctx.decrypt_blinded(ks, cstar, cr, use_crt=True)
+    assert ctx.status_detail() == (P.pmkrsa.PMK_ENOINV, 44)
+
+
 def test_argument_errors(ctx, P):
     ks, _ = keys_for(ctx, 2, 256, seed=8)
     m = torch.zeros((4, 8), dtype=torch.int32, device="cuda")
@@ -676,7 +702,7 @@ def test_chunk_count_bound(ctx, P):
     ks, _ = keys_for(ctx, 2, 512, seed=3)
     x = torch.zeros((4, 16), dtype=torch.int32, device="cuda")
     rc = P.load_library().pmk_encrypt_chunks(ctx.handle, ks.handle, ctypes.c_void_p(x.data_ptr()),
-                                             ctypes.c_void_p(x.data_ptr()), 1 << 32, None)
+                                             ctypes.c_void_p(x.data_ptr()), 1 << 32, None, None)
     assert rc == P.pmkrsa.PMK_EINVAL
 
 

@@ -349,3 +349,26 @@ def test_blinded_decrypt_rejects_non_invertible_r():
     cr = np.stack([oracle.to_limbs(kd["p"] * 3 % kd["N"], 8)])  # shares the factor p with N
     with pytest.raises(ValueError):
         oracle.blind_decrypt_chunks(m, cr, keys)
+
+
+def test_keyed_chunk_loops_follow_an_explicit_key_map():
+    """Explicit chunk-to-key map (the i x j reshape of Section 3.1 in any
+    order): chunk t under key key_idx[t], checked with Python pow per chunk;
+    the map t mod K gives the round-robin result."""
+    K, nbits = 3, 256
+    keys = oracle.keygen(K, nbits, 65537, 0x50444D4B0000C0DE)
+    rng = np.random.default_rng(77)
+    n = 40
+    m = oracle.split(rng.integers(0, 256, n * (nbits // 8 - 1), dtype=np.uint8), nbits)
+    idx = rng.integers(0, K, n)
+    idx[:5] = 2  # a run on one key
+    c = oracle.encrypt_chunks(m, keys, key_idx=idx)
+    Ns, ds = keys.ints("N"), keys.ints("d")
+    for t in range(n):
+        assert oracle.from_limbs(c[t]) == pow(oracle.from_limbs(m[t]), 65537, Ns[idx[t]])
+    back = oracle.decrypt_chunks(c, keys, key_idx=idx)
+    assert np.array_equal(back, m)
+    assert np.array_equal(oracle.decrypt_chunks(c, keys, use_crt=True, key_idx=idx), m)
+    for t in (0, 17, n - 1):
+        assert oracle.from_limbs(back[t]) == pow(oracle.from_limbs(c[t]), ds[idx[t]], Ns[idx[t]])
+    assert np.array_equal(oracle.encrypt_chunks(m, keys, key_idx=np.arange(n) % K), oracle.encrypt_chunks(m, keys))
