@@ -10,6 +10,13 @@ so L2 is flushed (a 256 MiB write) between timed steps, outside the timed
 intervals.  The CRT form of decryption is timed the same way and reported
 beside it.
 
+After the headline, rank 0 adds the other workloads to the same line, each
+under its own key with its configuration named: ``file100`` (100 MiB, K = 16,
+one plain launch per call against the persistent graph path), ``batched``
+(64 messages of mixed sizes and widths at a stated scale, one call per job
+against pmk_batch) and ``serving`` (the request mix at loads below its
+measured capacity, p50 / p99, against one request at a time).
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun every rank processes its own message (weak scaling); rank 0
 prints one JSON line.  ``--impl reference`` times the CPU oracle instead.
@@ -432,6 +439,12 @@ def run_ours(args):
     }
     if rank == 0:  # outside the timed region: split / join bandwidth on the 100 MiB file
         line["split_join_hbm"] = hbm_split_join(ctx, 10)
+    if rank == 0 and not args.no_extra_configs:
+        # the other workloads, each on its own config, after the headline's timed region
+        line["file100"] = _guarded(lambda: file100_leg(ctx, reps=1, tune_chunks=50000))
+        line["batched"] = _guarded(lambda: batched_leg(ctx, scale=0.2, reps=2, tune_chunks=5000))
+        line["serving"] = _guarded(lambda: serving_leg(ctx, n_requests=120, loads=(0.5, 0.9), scale=1.0,
+                                                       plain_at=0.5))
     if rank == 0 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
         r = oracle_sample(args.ref_sample, threads)
@@ -629,23 +642,33 @@ def run_table3(args):
 
 
 def run_batched(args):
-    """Many messages of mixed sizes and key widths in one batch: 64 messages,
-    sizes log-uniform over 4 KB - 25 MB (times --batch-scale), each with its
-    own K in {2, 4, 8, 16} and key width in {1024, 2048, 3072, 4096} bits;
-    ops 70% full-d decrypt, 10% CRT decrypt, 20% encrypt.  Times the plain
-    path (one call, one launch per job, on one stream) against the batched
-    path (pmk_batch: one persistent kernel per width, graph-replayed), after
-    autotuning every (width, mode), and checks both give identical output."""
+    """Many messages of mixed sizes and key widths in one batch (config 4);
+    see batched_leg."""
+    import paper_2111_11924_gb300 as P
+
+    ctx = P.Context(0)
+    res = batched_leg(ctx, args.batch_scale, args.steps, tune_chunks=50000)
+    print(json.dumps({"mode": "batched"} | res))
+    return 0 if res["identical_outputs"] else 1
+
+
+def batched_leg(ctx, scale: float, reps: int, tune_chunks: int) -> dict:
+    """Config 4: 64 messages, sizes log-uniform over 4 KB - 25 MB (times
+    scale), each with its own K in {2, 4, 8, 16} and key width in {1024, 2048,
+    3072, 4096} bits; ops 70% full-d decrypt, 10% CRT decrypt, 20% encrypt.
+    Times the plain path (one call, one launch per job, on one stream)
+    against the batched path (pmk_batch: persistent kernels per width and
+    grid launches for large jobs, graph-replayed), after autotuning every
+    (width, mode) on up to tune_chunks chunks, and checks both give
+    identical output."""
     import torch
 
-    import paper_2111_11924_gb300 as P
     from paper_2111_11924_gb300 import pmkrsa as B
 
     rng = np.random.default_rng(0x50444D4B0000C000)
-    ctx = P.Context(0)
     keysets, jobs, payload = {}, [], 0
     for m in range(64):
-        size = int(np.exp(rng.uniform(np.log(4096), np.log(25e6))) * args.batch_scale)
+        size = int(np.exp(rng.uniform(np.log(4096), np.log(25e6))) * scale)
         K = int(rng.choice([2, 4, 8, 16]))
         nbits = int(rng.choice([1024, 2048, 3072, 4096]))
         op = int(rng.choice([B.OP_DECRYPT, B.OP_DECRYPT_CRT, B.OP_ENCRYPT], p=[0.7, 0.1, 0.2]))
@@ -664,7 +687,7 @@ def run_batched(args):
         for mode, op in (("encrypt", B.OP_ENCRYPT), ("decrypt", B.OP_DECRYPT), ("crt", B.OP_DECRYPT_CRT)):
             n = sum(j[1].shape[0] for j in jobs if j[0].nbits == nbits and j[3] == op)
             if n and (nbits, mode) not in tuned:
-                tuned[nbits, mode] = ctx.autotune(ks, min(n, 50000), mode, reps=1)
+                tuned[nbits, mode] = ctx.autotune(ks, min(n, tune_chunks), mode, reps=1)
 
     def per_call():
         for ks, x, out, op in jobs:
@@ -673,36 +696,24 @@ def run_batched(args):
             else:
                 ctx.decrypt_chunks(ks, x, use_crt=(op == B.OP_DECRYPT_CRT), out=out)
 
-    def timed(fn, reps):
-        fn()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ts = []
-        for _ in range(reps):
-            e0.record()
-            fn()
-            e1.record()
-            torch.cuda.synchronize()
-            ts.append(e0.elapsed_time(e1))
-        return statistics.median(ts)
-
-    t_plain = timed(per_call, args.steps)
+    t_plain = _median_ms(per_call, reps)
     ref = [j[2].clone() for j in jobs]
     batch = ctx.batch(jobs)
-    t_batch = timed(batch.launch, args.steps)
+    t_batch = _median_ms(batch.launch, reps)
     ctx.check()
     same = all(torch.equal(j[2], r) for j, r in zip(jobs, ref))
-    line = {"mode": "batched", "messages": len(jobs), "payload_bytes": payload, "chunk_modexps": n_total,
-            "scale": args.batch_scale, "per_call_ms": t_plain, "batched_ms": t_batch,
-            "per_call_chunk_modexps_per_s": n_total / (t_plain / 1e3),
-            "batched_chunk_modexps_per_s": n_total / (t_batch / 1e3), "speedup": t_plain / t_batch,
-            "payload_MBps_batched": payload / 2**20 / (t_batch / 1e3), "identical_outputs": same,
-            "kernels_in_graph": batch.n_kernels, "queued_tasks": batch.n_tasks,
-            "geometry": {f"{nb}-{m}": [t["tpi"], FORM_NAMES[t["form"]], t["window"]]
-                         for (nb, m), t in tuned.items()}}
-    print(json.dumps(line))
+    res = {"messages": len(jobs), "payload_bytes": payload, "chunk_modexps": n_total,
+           "scale": scale, "reps": reps, "per_call_ms": t_plain, "batched_ms": t_batch,
+           "per_call_chunk_modexps_per_s": n_total / (t_plain / 1e3),
+           "batched_chunk_modexps_per_s": n_total / (t_batch / 1e3), "speedup": t_plain / t_batch,
+           "payload_MBps_batched": payload / 2**20 / (t_batch / 1e3), "identical_outputs": same,
+           "kernels_in_graph": batch.n_kernels, "queued_tasks": batch.n_tasks,
+           "geometry": {f"{nb}-{m}": [t["tpi"], FORM_NAMES[t["form"]], t["window"]]
+                        for (nb, m), t in tuned.items()}}
     batch.destroy()
-    return 0 if same else 1
+    for ks in keysets.values():
+        ks.free()
+    return res
 
 
 def run_file100(args):
@@ -710,100 +721,194 @@ def run_file100(args):
     of all 411,207 chunks as one plain launch per call, and the same job
     through the persistent graph-replayed batch path (pmk_batch), with the
     full round trip (split, encrypt, decrypt, join) checked on both."""
+    import paper_2111_11924_gb300 as P
+
+    ctx = P.Context(0)
+    res = file100_leg(ctx, args.steps, tune_chunks=W.FILE_100MIB_2048.n_chunks)
+    print(json.dumps({"mode": "file100"} | res))
+    return 0 if res["ok"] else 1
+
+
+def _guarded(fn) -> dict:
+    """Run one extra bench leg; a failure is reported in its own object
+    instead of costing the whole line."""
+    try:
+        return fn()
+    except Exception as exc:  # noqa: BLE001 - reported in the line
+        return {"error": f"{type(exc).__name__}: {exc}"[:400]}
+
+
+def _median_ms(fn, reps: int) -> float:
+    """Median CUDA-event time of fn() over reps runs (one untimed run first)."""
     import torch
 
-    import paper_2111_11924_gb300 as P
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def file100_leg(ctx, reps: int, tune_chunks: int) -> dict:
+    """Config 3 (100 MiB, K = 16, 2048 bits, inputs larger than L2): full-d
+    and CRT decryption of all 411,207 chunks, one plain launch per call
+    against the same job through the persistent graph path (pmk_batch), with
+    the round trip checked on both; geometry autotuned on tune_chunks chunks."""
+    import torch
+
     from paper_2111_11924_gb300 import pmkrsa as B
 
     w = W.FILE_100MIB_2048
-    ctx = P.Context(0)
     ks = ctx.keygen(w.K, w.nbits, w.e, w.key_seed)
     d_msg = torch.from_numpy(w.message()).cuda()
     n = w.n_chunks
     chunks = ctx.split(w.nbits, d_msg)
     cipher = ctx.encrypt_chunks(ks, chunks)
     out = torch.empty_like(chunks)
-    tuned = {m: ctx.autotune(ks, n, m, reps=1) for m in ("decrypt", "crt")}
-
-    def timed(fn, reps):
-        fn()
-        torch.cuda.synchronize()
-        ts = []
-        for _ in range(reps):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            fn()
-            e1.record()
-            torch.cuda.synchronize()
-            ts.append(e0.elapsed_time(e1))
-        return statistics.median(ts)
-
-    res = {}
+    tuned = {m: ctx.autotune(ks, min(n, tune_chunks), m, reps=1) for m in ("decrypt", "crt")}
+    res = {"workload": w.name, "chunks": n, "keys": w.K, "key_bits": w.nbits,
+           "inputs": "resident in HBM (larger than L2)", "reps": reps}
+    ok = True
     for name, crt, op in (("full_d", False, B.OP_DECRYPT), ("crt", True, B.OP_DECRYPT_CRT)):
         out.zero_()
-        t_plain = timed(lambda: ctx.decrypt_chunks(ks, cipher, use_crt=crt, out=out), args.steps)
+        t_plain = _median_ms(lambda: ctx.decrypt_chunks(ks, cipher, use_crt=crt, out=out), reps)
         ok_plain = bool(torch.equal(out, chunks))
-        back = ctx.join(w.nbits, out, w.msg_bytes)
-        roundtrip = bool(torch.equal(back, d_msg))
+        roundtrip = bool(torch.equal(ctx.join(w.nbits, out, w.msg_bytes), d_msg))
         out.zero_()
         batch = ctx.batch([(ks, cipher, out, op)])
-        t_batch = timed(batch.launch, args.steps)
+        t_batch = _median_ms(batch.launch, reps)
         ok_batch = bool(torch.equal(out, chunks))
+        macs = n * (algorithmic_crt_macs(w.nbits) if crt else algorithmic_montmuls(w.nbits) * macs_per_montmul(w.nbits))
+        t = tuned["crt" if crt else "decrypt"]
         res[name] = {"plain_ms": round(t_plain, 3), "batched_ms": round(t_batch, 3),
                      "plain_chunk_modexps_per_s": round(n / (t_plain / 1e3)),
                      "batched_chunk_modexps_per_s": round(n / (t_batch / 1e3)),
                      "plain_MBps": round(w.msg_bytes / 2**20 / (t_plain / 1e3), 2),
                      "batched_MBps": round(w.msg_bytes / 2**20 / (t_batch / 1e3), 2),
+                     "plain_int32_TOPs": round(int32_ops_per_s(macs, t_plain) / 1e12, 3),
                      "batched_over_plain": round(t_plain / t_batch, 3), "kernels_in_graph": batch.n_kernels,
                      "queued_tasks": batch.n_tasks, "outputs_equal_message_chunks": ok_plain and ok_batch,
-                     "join_roundtrip": roundtrip,
-                     "geometry": [tuned["crt" if crt else "decrypt"]["tpi"],
-                                  FORM_NAMES[tuned["crt" if crt else "decrypt"]["form"]],
-                                  tuned["crt" if crt else "decrypt"]["window"]]}
+                     "join_roundtrip": roundtrip, "geometry": [t["tpi"], FORM_NAMES[t["form"]], t["window"]]}
+        ok = ok and ok_plain and ok_batch and roundtrip
         batch.destroy()
     ctx.check()
-    print(json.dumps({"mode": "file100", "workload": w.name, "chunks": n, "keys": w.K, "key_bits": w.nbits,
-                      "inputs": "resident in HBM (larger than L2)"} | res))
-    ok = all(r["outputs_equal_message_chunks"] and r["join_roundtrip"] for r in res.values())
-    return 0 if ok else 1
+    ks.free()
+    res["ok"] = ok
+    return res
 
 
 def run_serving(args):
-    """The serving workload: Poisson arrivals (--serve-rate per second) of
-    encrypt / decrypt requests (70% decrypt, CRT form), payloads log-uniform
-    over 1 KB - 25 MB times --serve-scale, key widths uniform over {2048, 3072,
-    4096} with resident key tables, admission by a 40 GB device budget.
-    Reports p50 / p99 latency and MB/s for continuous batching on streams and
-    for the plain one-request-at-a-time path on the same requests."""
-    import torch
-
+    """The serving workload (config 5) swept over offered load; see serving_leg."""
     import paper_2111_11924_gb300 as P
-    from paper_2111_11924_gb300 import serving as SV
 
     ctx = P.Context(0)
+    loads = tuple(float(x) for x in args.serve_loads.split(","))
+    res = serving_leg(ctx, args.serve_requests, loads, args.serve_scale, plain_at=loads[0])
+    print(json.dumps({"mode": "serving"} | res))
+    return 0 if res["ok"] else 1
+
+
+def serving_leg(ctx, n_requests: int, loads: tuple, scale: float, plain_at: float | None) -> dict:
+    """Config 5: encrypt / decrypt requests (70% decrypt, CRT form), payloads
+    log-uniform over 1 KB - 25 MB times `scale`, key widths uniform over
+    {2048, 3072, 4096} with resident key tables (K = 8 each), admission by a
+    40 GB device budget, Poisson arrivals.
+
+    At the configured 2,000 requests/s the offered load is ~4.9 GB/s (mean
+    payload (b - a) / ln(b / a) = 2.47 MB), far above what the GPU decrypts,
+    so no steady state exists there.  The leg therefore measures:
+      - capacity: the same requests all arriving at once, served by the
+        coalescing loop (saturation throughput, MB/s of payload);
+      - kernels: the same work as one launch per (operation, width), data
+        resident, no copies (the kernels' own rate on this mix);
+      - p50 / p99 latency and achieved MB/s at each offered load rho (arrival
+        rate = rho x capacity / mean payload), one Poisson draw rescaled;
+      - the plain one-request-at-a-time path at load plain_at.
+    Every decryption must give back its message."""
+    import torch
+
+    from paper_2111_11924_gb300 import pmkrsa as B
+    from paper_2111_11924_gb300 import serving as SV
+
     widths = (2048, 3072, 4096)
     keysets = {nb: ctx.keygen(8, nb, 65537, 0x50444D4B0000F000 + nb) for nb in widths}
-    for nb, ks in keysets.items():
+    for ks in keysets.values():
         for mode in ("encrypt", "crt"):
-            ctx.autotune(ks, 2000, mode, reps=1)
-    reqs = SV.poisson_requests(args.serve_rate, args.serve_requests, seed=5, widths=widths, scale=args.serve_scale)
+            ctx.autotune(ks, 4000, mode, reps=1)
+    reqs = SV.poisson_requests(1.0, n_requests, seed=5, widths=widths, scale=scale)  # unit rate, rescaled below
+    unit_arrival = [r.arrival for r in reqs]
     SV.prepare_payloads(ctx, keysets, reqs)
-    server = SV.Server(ctx, keysets, budget_bytes=40 << 30, slots=args.serve_slots, use_crt=True)
-    server.serve(reqs[: min(16, len(reqs))])  # warm-up
-    for r in reqs:
-        r.result = None
-    cb = server.serve(reqs)
-    ok_cb = all(torch.equal(r.result, r.extra["message"]) for r in reqs if r.op == "decrypt")
-    for r in reqs:
-        r.result = None
-    plain = server.serve_one_at_a_time(reqs)
     payload = sum(r.msg_len for r in reqs)
-    line = {"mode": "serving", "requests": len(reqs), "arrival_rate_per_s": args.serve_rate,
-            "payload_scale": args.serve_scale, "payload_MB": payload / 2**20,
-            "offered_MBps": payload / 2**20 / reqs[-1].arrival, "decrypt_form": "CRT",
-            "continuous_batching": cb, "one_at_a_time": plain, "decryptions_round_trip": ok_cb}
-    print(json.dumps(line))
-    return 0 if ok_cb else 1
+    mean_payload = payload / len(reqs)
+    server = SV.Server(ctx, keysets, budget_bytes=40 << 30, slots=256, use_crt=True, lanes=4)
+
+    def run(rate, plain=False):
+        for r, a in zip(reqs, unit_arrival):
+            r.arrival = a / rate if rate else 0.0
+            r.result = None
+        st = server.serve_one_at_a_time(reqs) if plain else server.serve(reqs)
+        ok = all(torch.equal(r.result, r.extra["message"]) for r in reqs if r.op == "decrypt")
+        return st, ok
+
+    run(0.0)  # warm-up
+    cap, ok = run(0.0)
+    cap_MBps = cap["payload_MBps"]
+    # the kernels' own rate on the same work: one launch per (op, width), data resident
+    groups = {}
+    for r in reqs:
+        groups.setdefault((r.op, r.nbits), []).append(r)
+    dev_jobs = []
+    for (op, nb), rs in groups.items():
+        if op == "encrypt":
+            x = torch.cat([ctx.split(nb, r.payload.cuda()) for r in rs])
+        else:
+            x = torch.cat([r.payload.cuda() for r in rs])
+        dev_jobs.append((keysets[nb], x, torch.empty_like(x), B.OP_ENCRYPT if op == "encrypt" else B.OP_DECRYPT_CRT))
+
+    def kernels():
+        for ks, x, out, op in dev_jobs:
+            if op == B.OP_ENCRYPT:
+                ctx.encrypt_chunks(ks, x, out=out)
+            else:
+                ctx.decrypt_chunks(ks, x, use_crt=True, out=out)
+
+    k_ms = _median_ms(kernels, 2)
+    kern_MBps = payload / 2**20 / (k_ms / 1e3)
+    sweep = []
+    for rho in loads:
+        rate = rho * cap_MBps * 2**20 / mean_payload
+        st, ok_r = run(rate)
+        ok = ok and ok_r
+        sweep.append({"load": rho, "arrival_rate_per_s": round(rate, 2),
+                      "offered_MBps": round(payload / 2**20 / max(r.arrival for r in reqs), 2),
+                      "achieved_MBps": round(st["payload_MBps"], 2), "p50_ms": round(st["p50_ms"], 2),
+                      "p99_ms": round(st["p99_ms"], 2), "max_ms": round(st["max_ms"], 2),
+                      "batches": st["batches"], "mean_batch_requests": round(st["mean_batch_requests"], 2),
+                      "status": st["status"]})
+    res = {"workload": "serving: Poisson arrivals, 70% decrypt (CRT), payloads log-uniform 1 KB-25 MB x scale, "
+                       "widths 2048/3072/4096, K = 8, 40 GB budget",
+           "requests": len(reqs), "payload_scale": scale, "payload_MB": round(payload / 2**20, 2),
+           "mean_payload_MB": round(mean_payload / 2**20, 3),
+           "configured_rate_offered_GBps": round(2000 * mean_payload / 2**30, 2),
+           "capacity_MBps": round(cap_MBps, 2), "kernels_MBps": round(kern_MBps, 2),
+           "capacity_over_kernels": round(cap_MBps / kern_MBps, 3), "lanes": 4, "sweep": sweep}
+    if plain_at is not None:
+        rate = plain_at * cap_MBps * 2**20 / mean_payload
+        st, ok_p = run(rate, plain=True)
+        ok = ok and ok_p
+        res["one_at_a_time"] = {"load": plain_at, "achieved_MBps": round(st["payload_MBps"], 2),
+                                "p50_ms": round(st["p50_ms"], 2), "p99_ms": round(st["p99_ms"], 2)}
+    server.close()
+    for ks in keysets.values():
+        ks.free()
+    res["ok"] = ok
+    return res
 
 
 def hbm_split_join(ctx, steps: int) -> dict:
@@ -927,11 +1032,13 @@ def main(argv=None):
                     help="time the mixed-size 64-message batch (plain per-call vs persistent batch) and exit")
     ap.add_argument("--batch-scale", type=float, default=1.0, help="scale of the batch's message sizes")
     ap.add_argument("--hbm", action="store_true", help="time split / join on the 100 MiB file and exit")
-    ap.add_argument("--serve", action="store_true", help="run the serving workload and exit")
-    ap.add_argument("--serve-rate", type=float, default=2000.0)
-    ap.add_argument("--serve-requests", type=int, default=400)
-    ap.add_argument("--serve-scale", type=float, default=0.01, help="scale of the request payload sizes")
-    ap.add_argument("--serve-slots", type=int, default=32)
+    ap.add_argument("--serve", action="store_true", help="run the serving workload over a load sweep and exit")
+    ap.add_argument("--serve-requests", type=int, default=240)
+    ap.add_argument("--serve-scale", type=float, default=1.0, help="scale of the request payload sizes")
+    ap.add_argument("--serve-loads", default="0.25,0.5,0.75,0.9,1.0,1.2",
+                    help="offered loads as fractions of the measured capacity; the first also runs the plain path")
+    ap.add_argument("--no-extra-configs", action="store_true",
+                    help="leave the 100 MiB, batched and serving objects out of the default line")
     ap.add_argument("--widths", action="store_true",
                     help="time the 100 KB / K=16 workload at each key length and exit")
     ap.add_argument("--width-list", type=int, nargs="*", default=[1024, 2048, 3072, 4096, 6144, 8192])

@@ -1,15 +1,27 @@
-"""Request serving over the PMKRSA kernels: continuous batching on streams.
+"""Request serving over the PMKRSA kernels: continuous batching.
 
 Requests (encrypt a message, or decrypt a ciphertext back to its message)
 arrive over time with uneven sizes and key widths.  The key tables of every
 width stay resident on the device.  A request is admitted as soon as it has
-arrived, an in-flight slot is free and its device memory fits the budget;
-its whole pipeline (host-to-device copy, split + encrypt or decrypt + join,
-device-to-host copy) is enqueued on the slot's own CUDA stream, so requests
-admitted while others are still running execute concurrently on the GPU.
-Completion is detected with CUDA events, which frees the slot and the memory
-for the next arrivals.  The host thread never blocks on the device while
-others are in flight.
+arrived, an in-flight slot is free and its device memory fits the budget.
+Admitted requests wait for a lane (a CUDA stream with its own library
+context, hence its own device status record).  When a lane is free, the
+oldest waiting request and every other waiting request of the same
+operation and key width are packed into one batch:
+  - one host-to-device copy per request into one chunk buffer;
+  - one exponentiation launch over all the batch's chunks, with explicit key
+    indices so that chunk t of every request keeps key t mod K, exactly as
+    if the request ran alone (the ciphertext of a request does not depend on
+    what it was batched with);
+  - one split (encrypt) or join (decrypt) and one device-to-host copy per
+    request.
+Batches on different lanes overlap on the GPU, and requests arriving while
+they run are admitted and batched as lanes free up.  Completion is detected
+with CUDA events; the host never blocks on the device while work is in
+flight.  Each request ends with its own status: a batch whose lane reports a
+device-side error names its first failing chunk, which names the request;
+that request is marked failed and the rest of the batch is run again
+without it, until no error is left.
 
 This is host orchestration only: every step of every request runs in the
 library's kernels through the C ABI.
@@ -37,6 +49,7 @@ class Request:
     result: object = None   # pinned host tensor, filled when done
     t_admit: float = math.nan
     t_done: float = math.nan
+    status: int = 0         # PMK_* code of this request's device-side checks
     extra: dict = field(default_factory=dict)
 
     @property
@@ -97,10 +110,46 @@ class Admission:
         return out
 
 
-class Server:
-    """Admits requests by arrival time, in-flight slot and device-memory budget."""
+def pack_batch(ready: list, max_chunks: int = 1 << 30) -> list:
+    """The next batch from the admitted requests waiting for a lane (in
+    arrival order): the oldest one and every later one of the same operation
+    and key width, while the batch stays within max_chunks chunks (the
+    oldest is always taken)."""
+    if not ready:
+        return []
+    head = ready[0]
+    out, total = [], 0
+    for r in ready:
+        if r.op != head.op or r.nbits != head.nbits:
+            continue
+        n = num_chunks(r.msg_len, r.nbits)
+        if out and total + n > max_chunks:
+            continue
+        out.append(r)
+        total += n
+    return out
 
-    def __init__(self, ctx: Context, keysets: dict, budget_bytes: int, slots: int = 16, use_crt: bool = True):
+
+def batch_layout(requests: list, K: int):
+    """Chunk offsets of the requests in one batch buffer and the explicit key
+    index of every chunk: chunk t of a request keeps key t mod K."""
+    counts = np.array([num_chunks(r.msg_len, r.nbits) for r in requests], dtype=np.int64)
+    offsets = np.concatenate([[0], np.cumsum(counts)])
+    key_idx = np.concatenate([np.arange(c, dtype=np.int64) % K for c in counts]) if len(counts) else np.zeros(0)
+    return offsets, key_idx.astype(np.int32)
+
+
+def request_of_chunk(offsets, chunk: int) -> int:
+    """Index (within the batch) of the request that holds batch chunk `chunk`."""
+    return int(np.searchsorted(offsets, chunk, side="right") - 1)
+
+
+class Server:
+    """Admits requests by arrival time, in-flight slot and device-memory
+    budget, and runs them in coalesced batches on `lanes` streams."""
+
+    def __init__(self, ctx: Context, keysets: dict, budget_bytes: int, slots: int = 16, use_crt: bool = True,
+                 lanes: int = 4, max_batch_chunks: int = 1 << 30):
         import torch
 
         self.torch = torch
@@ -109,7 +158,17 @@ class Server:
         self.budget = int(budget_bytes)
         self.slots = int(slots)
         self.use_crt = use_crt
-        self.streams = [torch.cuda.Stream(device=ctx.device) for _ in range(self.slots)]
+        self.max_batch_chunks = int(max_batch_chunks)
+        self.streams = [torch.cuda.Stream(device=ctx.device) for _ in range(max(self.slots, lanes))]
+        # one library context per lane: its own status record and staging
+        self.lane_ctx = [Context(ctx.device) for _ in range(int(lanes))]
+        for lc in self.lane_ctx:  # the serving geometry: what the caller tuned on ctx
+            lc.copy_kernel_configs_from(ctx, keysets)
+
+    def close(self) -> None:
+        for lc in self.lane_ctx:
+            lc.close()
+        self.lane_ctx = []
 
     # ------------------------------------------------------------------ one request
     def _enqueue(self, req: Request, stream) -> dict:
@@ -142,11 +201,125 @@ class Server:
             else:
                 req.result = torch.empty(req.msg_len, dtype=torch.uint8).pin_memory()
 
+    # ------------------------------------------------------------------ one coalesced batch
+    def _enqueue_batch(self, batch: list, lane: int) -> dict:
+        """One batch (same op and width) on lane `lane`: copies in, one
+        exponentiation launch with explicit key indices, split / join per
+        request, copies out, then an event."""
+        torch = self.torch
+        ctx, stream = self.lane_ctx[lane], self.streams[lane]
+        nbits = batch[0].nbits
+        ks: KeySet = self.keysets[nbits]
+        dev = f"cuda:{self.ctx.device}"
+        offsets, key_idx = batch_layout(batch, ks.K)
+        n = int(offsets[-1])
+        h_idx = torch.from_numpy(key_idx).pin_memory()
+        with torch.cuda.stream(stream):
+            d_idx = h_idx.to(dev, non_blocking=True)
+            chunks = torch.empty((n, nbits // 32), dtype=torch.int32, device=dev)
+            keep = [h_idx, d_idx, chunks]
+            if batch[0].op == "encrypt":
+                for r, a, b in zip(batch, offsets[:-1], offsets[1:]):
+                    d_msg = r.payload.to(dev, non_blocking=True)
+                    ctx.split(nbits, d_msg, out=chunks[a:b], stream=stream)
+                    keep.append(d_msg)
+                ctx.encrypt_chunks(ks, chunks, out=chunks, stream=stream, key_idx=d_idx)
+                for r, a, b in zip(batch, offsets[:-1], offsets[1:]):
+                    r.result.copy_(chunks[a:b], non_blocking=True)
+            else:
+                for r, a, b in zip(batch, offsets[:-1], offsets[1:]):
+                    chunks[a:b].copy_(r.payload, non_blocking=True)
+                plain = ctx.decrypt_chunks(ks, chunks, use_crt=self.use_crt, stream=stream, key_idx=d_idx)
+                keep.append(plain)
+                for r, a, b in zip(batch, offsets[:-1], offsets[1:]):
+                    d_msg = ctx.join(nbits, plain[a:b], r.msg_len, stream=stream)
+                    r.result.copy_(d_msg, non_blocking=True)
+                    keep.append(d_msg)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+        return {"event": ev, "bufs": keep, "batch": batch, "offsets": offsets, "lane": lane}
+
+    def _settle(self, rec: dict) -> list:
+        """After a batch's event: read its lane's status; on an error, mark the
+        request of the first failing chunk and run the others again (same
+        lane, waiting) until none fails.  Returns the batch's requests."""
+        from .pmkrsa import PMK_OK
+
+        ctx, stream = self.lane_ctx[rec["lane"]], self.streams[rec["lane"]]
+        batch, offsets = rec["batch"], rec["offsets"]
+        while True:
+            code, first = ctx.status_detail(stream)
+            if code == PMK_OK:
+                return rec["batch"]
+            bad = request_of_chunk(offsets, first) if first is not None else 0
+            batch[bad].status = code
+            rest = [r for i, r in enumerate(batch) if i != bad]
+            if not rest:
+                return rec["batch"]
+            again = self._enqueue_batch(rest, rec["lane"])
+            again["event"].synchronize()
+            batch, offsets = again["batch"], again["offsets"]
+
     # ------------------------------------------------------------------ serving loops
-    def serve(self, requests: list) -> dict:
-        """Continuous batching: serve `requests` (sorted by arrival) as they arrive."""
+    def serve(self, requests: list, coalesce: bool = True) -> dict:
+        """Continuous batching: serve `requests` as they arrive.  coalesce=False
+        runs every admitted request on its own stream (no packing), for
+        comparison."""
+        if not coalesce:
+            return self._serve_per_request(requests)
         for r in requests:
             self._alloc_result(r)
+            r.status = 0
+        adm = Admission(requests, self.budget, self.slots)
+        slot_of = {}                      # rid -> admission slot
+        ready = []                        # admitted, waiting for a lane
+        free_lanes = list(range(len(self.lane_ctx)))
+        running = []                      # records of batches in flight
+        batches, batch_sizes = 0, []
+        t0 = time.perf_counter()
+        while not adm.done():
+            now = time.perf_counter() - t0
+            progressed = False
+            for rec in list(running):
+                if rec["event"].query():
+                    done_at = time.perf_counter() - t0
+                    for r in self._settle(rec):
+                        r.t_done = done_at
+                        adm.complete(slot_of.pop(r.rid))
+                    free_lanes.append(rec["lane"])
+                    running.remove(rec)
+                    progressed = True
+            for req, slot in adm.admit(now):
+                req.t_admit = time.perf_counter() - t0
+                slot_of[req.rid] = slot
+                ready.append(req)
+                progressed = True
+            while ready and free_lanes:
+                batch = pack_batch(ready, self.max_batch_chunks)
+                ids = {r.rid for r in batch}
+                ready = [r for r in ready if r.rid not in ids]
+                running.append(self._enqueue_batch(batch, free_lanes.pop()))
+                batches += 1
+                batch_sizes.append(len(batch))
+                progressed = True
+            if not progressed:
+                if not adm.inflight and adm.next_arrival() > now:
+                    time.sleep(min(adm.next_arrival() - now, 1e-3))
+                else:
+                    time.sleep(20e-6)
+        self.torch.cuda.synchronize(self.ctx.device)
+        statuses = [r.status for r in requests]
+        status = next((s for s in statuses if s != 0), 0)
+        return self._stats(requests, time.perf_counter() - t0, status,
+                           {"peak_device_bytes": adm.peak_used, "peak_in_flight": adm.peak_inflight,
+                            "batches": batches, "mean_batch_requests": float(np.mean(batch_sizes)) if batch_sizes else 0.0,
+                            "failed_requests": [r.rid for r in requests if r.status != 0]})
+
+    def _serve_per_request(self, requests: list) -> dict:
+        """Every admitted request on its own slot stream, without packing."""
+        for r in requests:
+            self._alloc_result(r)
+            r.status = 0
         adm = Admission(requests, self.budget, self.slots)
         records = {}  # slot -> the in-flight request's event and buffers
         t0 = time.perf_counter()

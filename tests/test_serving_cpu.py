@@ -75,3 +75,31 @@ def test_request_larger_than_the_budget_is_refused():
     reqs = requests(10, 13)
     with pytest.raises(ValueError):
         SV.Admission(reqs, budget_bytes=max(r.device_bytes() for r in reqs) - 1, slots=4)
+
+
+def test_pack_batch_takes_the_oldest_and_its_kind():
+    reqs = requests(40, 21)
+    ready = sorted(reqs, key=lambda r: r.arrival)[:25]
+    batch = SV.pack_batch(ready)
+    head = ready[0]
+    assert batch[0] is head
+    assert all(r.op == head.op and r.nbits == head.nbits for r in batch)
+    assert [r.rid for r in batch] == [r.rid for r in ready if r.op == head.op and r.nbits == head.nbits]
+    # a chunk cap keeps the head and skips what does not fit
+    cap = SV.num_chunks(head.msg_len, head.nbits)
+    assert SV.pack_batch(ready, max_chunks=cap)[0] is head
+    small = SV.pack_batch(ready, max_chunks=cap)
+    assert sum(SV.num_chunks(r.msg_len, r.nbits) for r in small) <= max(cap, 0) or len(small) == 1
+    assert SV.pack_batch([]) == []
+
+
+def test_batch_layout_keeps_each_requests_key_binding():
+    reqs = requests(12, 22, max_bytes=50_000)
+    K = 7
+    offsets, key_idx = SV.batch_layout(reqs, K)
+    counts = [SV.num_chunks(r.msg_len, r.nbits) for r in reqs]
+    assert list(np.diff(offsets)) == counts and offsets[0] == 0 and len(key_idx) == offsets[-1]
+    for i, (a, b) in enumerate(zip(offsets[:-1], offsets[1:])):
+        assert list(key_idx[a:b]) == [t % K for t in range(b - a)]  # chunk t of every request: key t mod K
+        for c in (a, b - 1):
+            assert SV.request_of_chunk(offsets, c) == i
