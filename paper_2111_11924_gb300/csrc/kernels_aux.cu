@@ -522,11 +522,17 @@ KernelConfig default_config(uint32_t limbs, bool crt) {
 
 int list_configs(uint32_t limbs, bool crt, KernelConfig *out, int max) {
   int k = 0;
-  for (const ModexpEntry &e : entries(crt))
-    if (e.limbs == (int)limbs && e.table == kTableFull) {  // geometries; the small-table twins are not listed
-      if (k < max && out) out[k] = KernelConfig{(uint32_t)e.tpi, (uint32_t)e.form};
-      k++;
-    }
+  const std::vector<ModexpEntry> all = entries(crt);
+  for (size_t i = 0; i < all.size(); i++) {
+    const ModexpEntry &e = all[i];
+    if (e.limbs != (int)limbs || e.table != kTableFull) continue;  // geometries; small-table twins are not listed
+    bool seen = false;  // block-size twins are one geometry
+    for (size_t j = 0; j < i && !seen; j++)
+      seen = all[j].limbs == e.limbs && all[j].tpi == e.tpi && all[j].form == e.form && all[j].table == kTableFull;
+    if (seen) continue;
+    if (k < max && out) out[k] = KernelConfig{(uint32_t)e.tpi, (uint32_t)e.form};
+    k++;
+  }
   return k;
 }
 

@@ -52,6 +52,9 @@ __global__ void __launch_bounds__(kThreads) k_modexp_tasks(const BatchTask *__re
     const uint32_t *sR2 = R2, *sR3 = CRT ? kd.R3h[prime] : R2, *sOne = g_one_row;
     const bool active = (int)g < tk.count;
     const long long t = tk.first + (long long)g * tk.stride;
+    // The output address is formed before the exponentiation, so that only
+    // this pointer (not the task's fields) stays live across it.
+    uint32_t *const o = active ? tk.out + t * W + (CRT ? prime * S : 0) + r * L : nullptr;
     uint32_t nn[L], a[L];
     load_slice_global<L>(nn, M, r);
     if (!CRT) {
@@ -67,8 +70,7 @@ __global__ void __launch_bounds__(kThreads) k_modexp_tasks(const BatchTask *__re
     }
     exp_window<S, TPI, FORM>(a, tbl, ybuf, sched, nsteps, maxidx, nn, n0, r);
     mont<S, TPI, FORM>(a, sOne, nn, n0, r);
-    if (active) {
-      uint32_t *o = tk.out + t * W + (CRT ? prime * S : 0) + r * L;
+    if (o) {
       if constexpr (L % 4 == 0) {
 #pragma unroll
         for (int j = 0; j < L; j += 4) *reinterpret_cast<uint4 *>(o + j) = make_uint4(a[j], a[j + 1], a[j + 2], a[j + 3]);

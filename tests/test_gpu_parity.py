@@ -440,51 +440,60 @@ def test_6144_8192_bit_keys(ctx, P, nbits):
 
 
 def test_batched_persistent_graph_matches_per_call(ctx, P):
-    """A mixed batch (three key sets and widths, encrypt / full d / CRT, ragged
-    sizes) replayed from its CUDA graph equals one call per job, bit for bit,
-    and keeps doing so when the input contents change between launches."""
+    """A mixed batch (five key sets at 512-4096 bits, encrypt / full d / CRT,
+    ragged sizes) replayed from its CUDA graph equals one call per job, bit
+    for bit, and keeps doing so when the input contents change between
+    launches.  Every job of both launches is also checked against the oracle
+    on a sample of at least 8 chunks that includes its last one."""
     from paper_2111_11924_gb300 import pmkrsa as B
 
     sets = [keys_for(ctx, K, nb, seed=700 + nb) for K, nb in ((3, 1024), (2, 2048), (5, 512))]
-    ks4096, keys4096 = _checked_wide_keys(ctx, 2, 4096, seed=0x50444D4B0000B000)
+    wide = []  # library keys at 3072 / 4096 bits, checked with Python integers; the oracle computes with them
+    for K, nb, seed in ((2, 4096, 0x50444D4B0000B000), (3, 3072, 0x50444D4B0000B100)):
+        ks_w, keys_w = _checked_wide_keys(ctx, K, nb, seed=seed)
+        wide.append((ks_w, keys_w, oracle.OracleKeys(K, nb, 65537, ks_w.export())))
     rng = np.random.default_rng(77)
 
     def chunks_for(Ns, n, s):
         return np.stack([oracle.to_limbs(W.random_below(rng, Ns[t % len(Ns)]), s) for t in range(n)])
 
-    jobs, refs = [], []
-    plan = [(0, 41, B.OP_DECRYPT), (0, 7, B.OP_ENCRYPT), (1, 33, B.OP_DECRYPT_CRT), (2, 3, B.OP_DECRYPT),
-            (1, 1, B.OP_DECRYPT), (2, 90, B.OP_ENCRYPT), (3, 5, B.OP_DECRYPT_CRT), (3, 4, B.OP_DECRYPT)]
-    for si, n, op in plan:
+    def key_set(si):
         if si < 3:
             ks, ok = sets[si]
-            Ns = ok.ints("N")
-        else:
-            ks, Ns = ks4096, [k["N"] for k in keys4096]
+            return ks, ok, ok.ints("N")
+        ks_w, keys_w, ok_w = wide[si - 3]
+        return ks_w, ok_w, [k["N"] for k in keys_w]
+
+    jobs = []
+    plan = [(0, 41, B.OP_DECRYPT), (0, 7, B.OP_ENCRYPT), (1, 33, B.OP_DECRYPT_CRT), (2, 3, B.OP_DECRYPT),
+            (1, 1, B.OP_DECRYPT), (2, 90, B.OP_ENCRYPT), (3, 5, B.OP_DECRYPT_CRT), (3, 4, B.OP_DECRYPT),
+            (4, 12, B.OP_DECRYPT), (4, 9, B.OP_DECRYPT_CRT), (4, 10, B.OP_ENCRYPT)]
+    for si, n, op in plan:
+        ks, _, Ns = key_set(si)
         x = dev(chunks_for(Ns, n, ks.nbits // 32))
-        out = torch.zeros_like(x)
-        jobs.append((ks, x, out, op))
+        jobs.append((ks, x, torch.zeros_like(x), op))
     batch = ctx.batch(jobs)
     assert batch.n_kernels >= 4 and batch.n_tasks > 0
     for rep in range(2):
         if rep == 1:  # new contents, same buffers
             for (ks, x, out, op), (si, n, _) in zip(jobs, plan):
-                Ns = sets[si][1].ints("N") if si < 3 else [k["N"] for k in keys4096]
-                x.copy_(dev(chunks_for(Ns, n, ks.nbits // 32)))
+                x.copy_(dev(chunks_for(key_set(si)[2], n, ks.nbits // 32)))
         for _, _, out, _ in jobs:
             out.zero_()
         batch.launch()
         ctx.check()
-        for ks, x, out, op in jobs:
+        for (ks, x, out, op), (si, n, _) in zip(jobs, plan):
             if op == B.OP_ENCRYPT:
                 ref = ctx.encrypt_chunks(ks, x)
             else:
                 ref = ctx.decrypt_chunks(ks, x, use_crt=(op == B.OP_DECRYPT_CRT))
-            assert torch.equal(out, ref), (ks.nbits, op, x.shape[0])
-    # one job against the oracle directly
-    ks, x, out, op = jobs[0]
-    ok = sets[0][1]
-    assert np.array_equal(host(out)[:6], oracle.decrypt_chunks(host(x)[:6], ok))
+            assert torch.equal(out, ref), (ks.nbits, op, n)
+            ok = key_set(si)[1]
+            sample = np.unique(np.concatenate([rng.choice(n, min(n, 8), replace=False), [n - 1]]))
+            xin = host(x)[sample]
+            want = (oracle.encrypt_chunks(xin, ok, key_idx=sample % ok.K) if op == B.OP_ENCRYPT
+                    else oracle.decrypt_chunks(xin, ok, key_idx=sample % ok.K))
+            assert np.array_equal(host(out)[sample], want), (ks.nbits, op, n, rep)
     batch.destroy()
 
 
@@ -506,6 +515,41 @@ def test_blinded_algorithm1_parity(ctx, nbits, K, length):
         assert np.array_equal(host(back), m), use_crt
     sample = slice(0, 10)
     assert np.array_equal(oracle.blind_decrypt_chunks(cstar_ref[sample], cr_ref[sample], ok, threads=8), m[sample])
+    assert ctx.status() == 0
+
+
+@pytest.mark.parametrize("nbits,K", [(512, 3), (2048, 4)])
+def test_blinded_values_across_their_whole_range(ctx, nbits, K):
+    """Algorithm 1 allows any r in Z*_N.  Blinding values at the top of the
+    range -- N - 1, N - 2, and random values in [2^(n-8), N) -- and at the
+    bottom (1, 2): C*, C_R equal the oracle's, and both decryption paths
+    (full d, and CRT: the fused joint exponentiation at 2048 bits, Fermat
+    inverses and recombination at 512 bits) recover every chunk."""
+    ks, ok = keys_for(ctx, K, nbits, seed=0x50444D4B0000D200 + nbits)
+    Ns = ok.ints("N")
+    s = nbits // 32
+    rng = np.random.default_rng(nbits + 5)
+    n = 40
+    m = oracle.split(rng.integers(0, 256, n * (nbits // 8 - 1), dtype=np.uint8), nbits)
+    vals = []
+    for t in range(n):
+        N = Ns[t % K]
+        special = {0: N - 1, 1: N - 2, 2: 1, 3: 2, 4: N - 1, 5: N - 2}
+        if t in special:
+            vals.append(special[t])
+        else:  # uniform in [2^(n-8), N): above what the default blinding generator draws
+            lo = 1 << (nbits - 8)
+            vals.append(lo + W.random_below(rng, N - lo))
+    r = np.stack([oracle.to_limbs(v, s) for v in vals])
+    assert all(v >= 1 << (nbits - 8) for t, v in enumerate(vals) if t not in (2, 3))
+    cstar_ref, cr_ref = oracle.blind_encrypt_chunks(m, r, ok, threads=8)
+    cstar, cr = ctx.encrypt_blinded(ks, dev(m), dev(r))
+    assert np.array_equal(host(cstar), cstar_ref)
+    assert np.array_equal(host(cr), cr_ref)
+    for use_crt in (False, True):
+        back = ctx.decrypt_blinded(ks, cstar, cr, use_crt=use_crt)
+        assert np.array_equal(host(back), m), use_crt
+    assert np.array_equal(oracle.blind_decrypt_chunks(cstar_ref[:8], cr_ref[:8], ok, threads=8), m[:8])
     assert ctx.status() == 0
 
 
