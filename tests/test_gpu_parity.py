@@ -196,8 +196,13 @@ def test_every_kernel_geometry(ctx, P, nbits, crt):
     rng = np.random.default_rng(1)
     Ns = ok.ints("N")
     n = 37  # ragged: several blocks per key and a partial one
-    c = np.stack([oracle.to_limbs(W.random_below(rng, Ns[t % K]), nbits // 32) for t in range(n)])
-    ref = oracle.decrypt_chunks(c[:6], ok)
+    vals = [W.random_below(rng, Ns[t % K]) for t in range(n)]
+    # edge values among them: 0, 1, 2, N - 1, N - 2 and all-ones low limbs, for every product form
+    for t, f in ((6, lambda N: 0), (7, lambda N: 1), (8, lambda N: 2), (9, lambda N: N - 1), (10, lambda N: N - 2),
+                 (11, lambda N: (1 << (nbits - 2)) - 1)):
+        vals[t] = f(Ns[t % K])
+    c = np.stack([oracle.to_limbs(v, nbits // 32) for v in vals])
+    ref = oracle.decrypt_chunks(c[:12], ok)
     limbs = nbits // 64 if crt else nbits // 32
     configs = P.kernel_configs(limbs, crt)
     assert len(configs) >= 1
@@ -213,7 +218,7 @@ def test_every_kernel_geometry(ctx, P, nbits, crt):
                 ctx.set_kernel_config(limbs, crt, 0)
                 ctx.set_kernel_window(limbs, crt, 0)
     for o, cfg in zip(outs, tried):
-        assert np.array_equal(o[:6], ref), cfg
+        assert np.array_equal(o[:12], ref), cfg
         assert np.array_equal(o, outs[0]), cfg
     assert ctx.get_kernel_config(limbs, crt)[0] in {t for t, _ in configs}
     assert ctx.get_kernel_window(limbs, crt) == 5
