@@ -50,7 +50,7 @@ KERNELS_PER_STEP = 6  # split, range check + modexp (encrypt), range check + mod
 # DRAM traffic of the full-d decryption kernel from one ncu capture, valid only
 # for the kernel sources it was measured on (see profiles/).
 TRAFFIC_SOURCES = ["paper_2111_11924_gb300/csrc/modexp_core.cuh", "paper_2111_11924_gb300/csrc/modexp_grid.cuh"]
-TRAFFIC_MEASURED = {"50b7422931fdff94": 1680896}  # source digest -> bytes per launch (profiles/)
+TRAFFIC_MEASURED = {"a9fe84bae498f3d7": 1451008}  # source digest -> bytes per launch (profiles/)
 
 
 def sources_digest() -> str:
