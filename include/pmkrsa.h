@@ -89,7 +89,7 @@ int pmk_keygen_multiprime(pmk_ctx *ctx, uint32_t K, uint32_t nbits, uint32_t npr
 
 /*
  * pmk_keygen_multiprime on the host only, with the output layout of
- * pmk_keyset_export (N, d) and pmk_keyset_export_primes (primes, dexp,
+ * pmk_keyset_export_fields (N, d) and pmk_keyset_export_primes (primes, dexp,
  * coef).  Any output pointer may be NULL.
  */
 int pmk_keygen_host_multiprime(uint32_t K, uint32_t nbits, uint32_t nprimes, uint64_t e, uint64_t seed, uint32_t *N,
@@ -98,7 +98,7 @@ int pmk_keygen_host_multiprime(uint32_t K, uint32_t nbits, uint32_t nprimes, uin
 /*
  * The same key initialisation as pmk_keygen, on the host only (no device,
  * no context): writes the key material to caller-owned host arrays with the
- * layout of pmk_keyset_export.  Any output pointer may be NULL.
+ * layout of pmk_keyset_export_fields.  Any output pointer may be NULL.
  */
 int pmk_keygen_host(uint32_t K, uint32_t nbits, uint64_t e, uint64_t seed, uint32_t *N, uint32_t *d, uint32_t *p,
                     uint32_t *q, uint32_t *dp, uint32_t *dq, uint32_t *qinv);
@@ -123,11 +123,12 @@ int pmk_keyset_from_primes(pmk_ctx *ctx, uint32_t K, uint32_t nbits, uint64_t e,
 int pmk_keyset_from_primes_multi(pmk_ctx *ctx, uint32_t K, uint32_t nbits, uint32_t nprimes, uint64_t e,
                                  const uint32_t *primes, pmk_keyset **out);
 
-/* Copy the key material out (host arrays, key-major, little-endian limbs):
- * N, d: K x nbits/32;  p, q, dp, dq, qinv: K x nbits/64.  Any pointer may be
- * NULL.  For a key set with more than two primes p .. qinv must be NULL
- * (EINVAL): use pmk_keyset_export_primes. */
-int pmk_keyset_export(const pmk_keyset *ks, uint32_t *N, uint32_t *d, uint32_t *p, uint32_t *q, uint32_t *dp,
+/* Copy the key material out field by field (host arrays, key-major,
+ * little-endian limbs): N, d: K x nbits/32;  p, q, dp, dq, qinv: K x nbits/64.
+ * Any pointer may be NULL.  For a key set with more than two primes p .. qinv
+ * must be NULL (EINVAL): use pmk_keyset_export_primes.  The serialised form
+ * of the whole key set is pmk_keyset_export. */
+int pmk_keyset_export_fields(const pmk_keyset *ks, uint32_t *N, uint32_t *d, uint32_t *p, uint32_t *q, uint32_t *dp,
                       uint32_t *dq, uint32_t *qinv);
 /* The primes of every key and their CRT values, K x b x nbits/(32 b) limbs
  * each (b = pmk_keyset_num_primes): primes r_i, dexp_i = d mod (r_i - 1),
@@ -152,7 +153,7 @@ int pmk_keyset_export_primes(const pmk_keyset *ks, uint32_t *primes, uint32_t *d
  *   them: b values of s/b limbs each)
  *   last 8 bytes  FNV-1a 64-bit hash of every byte before it.
  * Size: 32 + 20 K s + 8 bytes.
- * pmk_keyset_export_blob: with buf NULL, *len receives the size; otherwise
+ * pmk_keyset_export: with buf NULL, *len receives the size; otherwise
  * *len is the buffer's size in bytes (EINVAL, with *len set to the size
  * needed, if smaller) and receives the bytes written.  EINVAL for a NULL
  * key set or len.
@@ -165,7 +166,7 @@ int pmk_keyset_export_primes(const pmk_keyset *ks, uint32_t *primes, uint32_t *d
  * host-only: it can be exported and queried, and device calls refuse it
  * (EINVAL).  *out is set only on success.
  */
-int pmk_keyset_export_blob(const pmk_keyset *ks, void *buf, size_t *len);
+int pmk_keyset_export(const pmk_keyset *ks, void *buf, size_t *len);
 int pmk_keyset_import(pmk_ctx *ctx, const void *buf, size_t len, pmk_keyset **out);
 /* Key-set properties: primes per modulus (b), key count K, width nbits and
  * public exponent e.  Each returns 0 for NULL. */

@@ -342,7 +342,7 @@ int pmk_keygen_host_multiprime(uint32_t K, uint32_t nbits, uint32_t nprimes, uin
     ks.e = e;
     ks.nprimes = nprimes;
     int rc = pmk::host_keygen_mp(K, nbits, nprimes, e, seed, ks.keys);
-    if (rc == PMK_OK) rc = pmk_keyset_export(&ks, N, d, nullptr, nullptr, nullptr, nullptr, nullptr);
+    if (rc == PMK_OK) rc = pmk_keyset_export_fields(&ks, N, d, nullptr, nullptr, nullptr, nullptr, nullptr);
     if (rc == PMK_OK) rc = pmk_keyset_export_primes(&ks, primes, dexp, coef);
     return rc;
   } catch (const std::bad_alloc &) {
@@ -361,7 +361,7 @@ int pmk_keygen_host(uint32_t K, uint32_t nbits, uint64_t e, uint64_t seed, uint3
     ks.e = e;
     int rc = pmk::host_keygen(K, nbits, e, seed, ks.keys);
     if (rc != PMK_OK) return rc;
-    return pmk_keyset_export(&ks, N, d, p, q, dp, dq, qinv);
+    return pmk_keyset_export_fields(&ks, N, d, p, q, dp, dq, qinv);
   } catch (const std::bad_alloc &) {
     return PMK_ENOMEM;
   }
@@ -422,7 +422,7 @@ int pmk_keyset_from_primes_multi(pmk_ctx *ctx, uint32_t K, uint32_t nbits, uint3
   }
 }
 
-int pmk_keyset_export(const pmk_keyset *ks, uint32_t *N, uint32_t *d, uint32_t *p, uint32_t *q, uint32_t *dp,
+int pmk_keyset_export_fields(const pmk_keyset *ks, uint32_t *N, uint32_t *d, uint32_t *p, uint32_t *q, uint32_t *dp,
                       uint32_t *dq, uint32_t *qinv) {
   if (!ks) return PMK_EINVAL;
   if (ks->nprimes != 2 && (p || q || dp || dq || qinv)) return PMK_EINVAL;  // primes: pmk_keyset_export_primes
@@ -515,7 +515,7 @@ void key_rows(const pmk::HostKey &x, uint32_t nbits, uint32_t b, std::vector<uin
 
 extern "C" {
 
-int pmk_keyset_export_blob(const pmk_keyset *ks, void *buf, size_t *len) {
+int pmk_keyset_export(const pmk_keyset *ks, void *buf, size_t *len) {
   if (!ks || !len) return PMK_EINVAL;
   const size_t need = blob_size(ks->K, ks->nbits);
   if (!buf) {

@@ -51,12 +51,12 @@ def load_library() -> ctypes.CDLL:
         "pmk_keygen": (i, [vp, u32, u32, u64, u64, ctypes.POINTER(vp)]),
         "pmk_keygen_host": (i, [u32, u32, u64, u64, P32, P32, P32, P32, P32, P32, P32]),
         "pmk_keyset_from_primes": (i, [vp, u32, u32, u64, P32, P32, ctypes.POINTER(vp)]),
-        "pmk_keyset_export": (i, [vp, P32, P32, P32, P32, P32, P32, P32]),
+        "pmk_keyset_export_fields": (i, [vp, P32, P32, P32, P32, P32, P32, P32]),
         "pmk_keygen_multiprime": (i, [vp, u32, u32, u32, u64, u64, ctypes.POINTER(vp)]),
         "pmk_keygen_host_multiprime": (i, [u32, u32, u32, u64, u64, P32, P32, P32, P32, P32]),
         "pmk_keyset_export_primes": (i, [vp, P32, P32, P32]),
         "pmk_keyset_from_primes_multi": (i, [vp, u32, u32, u32, u64, P32, ctypes.POINTER(vp)]),
-        "pmk_keyset_export_blob": (i, [vp, vp, ctypes.POINTER(sz)]),
+        "pmk_keyset_export": (i, [vp, vp, ctypes.POINTER(sz)]),
         "pmk_keyset_import": (i, [vp, vp, sz, ctypes.POINTER(vp)]),
         "pmk_keyset_num_primes": (u32, [vp]),
         "pmk_keyset_num_keys": (u32, [vp]),
@@ -212,22 +212,22 @@ class KeySet:
         lib = load_library()
         if self.nprimes != 2:
             arrs = {f: np.zeros((self.K, self.limbs), np.uint32) for f in _MP_FIELDS}
-            _check(lib.pmk_keyset_export(self.handle, _p32(arrs["N"]), _p32(arrs["d"]), None, None, None, None, None),
+            _check(lib.pmk_keyset_export_fields(self.handle, _p32(arrs["N"]), _p32(arrs["d"]), None, None, None, None, None),
                    "export")
             _check(lib.pmk_keyset_export_primes(self.handle, _p32(arrs["primes"]), _p32(arrs["dexp"]),
                                                 _p32(arrs["coef"])), "export_primes")
             return arrs
         arrs = _key_arrays(self.K, self.nbits)
-        _check(lib.pmk_keyset_export(self.handle, *[_p32(arrs[f]) for f in _KEY_FIELDS]), "export")
+        _check(lib.pmk_keyset_export_fields(self.handle, *[_p32(arrs[f]) for f in _KEY_FIELDS]), "export")
         return arrs
 
     def export_blob(self) -> bytes:
-        """The key set as a versioned little-endian blob (pmk_keyset_export_blob)."""
+        """The key set as a versioned little-endian blob (pmk_keyset_export)."""
         lib = load_library()
         n = ctypes.c_size_t(0)
-        _check(lib.pmk_keyset_export_blob(self.handle, None, ctypes.byref(n)), "pmk_keyset_export_blob")
+        _check(lib.pmk_keyset_export(self.handle, None, ctypes.byref(n)), "pmk_keyset_export")
         buf = ctypes.create_string_buffer(n.value)
-        _check(lib.pmk_keyset_export_blob(self.handle, buf, ctypes.byref(n)), "pmk_keyset_export_blob")
+        _check(lib.pmk_keyset_export(self.handle, buf, ctypes.byref(n)), "pmk_keyset_export")
         return buf.raw[: n.value]
 
     def free(self) -> None:
@@ -299,7 +299,7 @@ class Context:
         return KeySet(self, h)
 
     def import_keyset(self, blob: bytes) -> KeySet:
-        """A key set restored from pmk_keyset_export_blob's bytes, on this context's device."""
+        """A key set restored from pmk_keyset_export's bytes, on this context's device."""
         h = ctypes.c_void_p()
         _check(load_library().pmk_keyset_import(self.handle, blob, len(blob), ctypes.byref(h)), "pmk_keyset_import")
         return KeySet(self, h)

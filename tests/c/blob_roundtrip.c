@@ -45,8 +45,8 @@ int main(void) {
   rc = pmk_keyset_import(NULL, mine, size, &ks);
   printf("import %d\n", rc);
   size_t len = 0;
-  int rc2 = rc == PMK_OK ? pmk_keyset_export_blob(ks, NULL, &len) : rc;
-  int rc3 = rc2 == PMK_OK ? pmk_keyset_export_blob(ks, back, &len) : rc2;
+  int rc2 = rc == PMK_OK ? pmk_keyset_export(ks, NULL, &len) : rc;
+  int rc3 = rc2 == PMK_OK ? pmk_keyset_export(ks, back, &len) : rc2;
   printf("export %d %d size %zu %s\n", rc2, rc3, len, (len == size && !memcmp(mine, back, size)) ? "same" : "differs");
   pmk_keyset_free(ks);
   mine[40] ^= 1;  /* a flipped bit in key 0's N: the hash no longer matches */

@@ -258,7 +258,7 @@ def test_multiprime_autotune_and_errors(ctx, P):
     lib = P.load_library()
     buf = np.zeros(2 * 2048 // 32, np.uint32)
     p32 = buf.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
-    assert lib.pmk_keyset_export(ks.handle, None, None, p32, None, None, None, None) == P.pmkrsa.PMK_EINVAL
+    assert lib.pmk_keyset_export_fields(ks.handle, None, None, p32, None, None, None, None) == P.pmkrsa.PMK_EINVAL
 
 
 def test_multiprime_keyset_from_oracle_primes(ctx, P):
