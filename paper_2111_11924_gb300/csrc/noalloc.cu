@@ -86,7 +86,7 @@ extern "C" int pmk_decrypt_message_host_noalloc(const pmk_keyset *ks, const uint
     uint32_t *d_plain = reinterpret_cast<uint32_t *>(base + kStatusBytes + chunk_bytes);
     uint8_t *d_msg = base + kStatusBytes + 2 * chunk_bytes;
     const uint32_t S = ks->nbits / 32, B = ks->nprimes, H = S / B;
-    // The array keeps the previous call's contents: the status word must start at zero.
+    // The array keeps the previous call's contents: the status record must start cleared.
     queued = true;
     if (clear_status(d_status, st) != PMK_OK ||
         cudaMemcpyAsync(d_cipher, h_cipher, words * 4, cudaMemcpyHostToDevice, st) != cudaSuccess) {

@@ -25,7 +25,7 @@ class TraceRange {
   TraceRange &operator=(const TraceRange &) = delete;
 };
 
-// Error bits written by kernels into the context's device status word.
+// Error bits written by kernels into word 0 of the context's device status record.
 enum : uint32_t { kStatusRange = 1u, kStatusNotInvertible = 2u, kStatusKeyIndex = 4u };
 
 // The device status record of a context (16 bytes, 8-byte aligned): word 0
@@ -251,10 +251,10 @@ struct Staging {
 };
 }  // namespace pmk
 
-// Context: one device, its status word, staging and kernel geometry choices.
+// Context: one device, its status record, staging and kernel geometry choices.
 struct pmk_ctx {
   int device = 0;
-  uint32_t *d_status = nullptr;            // device-side error bits (pmk::kStatusRange)
+  uint32_t *d_status = nullptr;            // status record: error bits, smallest failing chunk
   pmk::Staging msg, a, b;                  // staging of the *_host calls and the blinded CRT path
   pmk::Staging grp;                        // key-group table of calls with explicit key indices
   std::map<uint32_t, pmk::KernelConfig> cfg;  // (limbs << 1 | crt) -> kernel geometry override
