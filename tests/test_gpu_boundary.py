@@ -157,3 +157,47 @@ def test_blob_import_on_device_decrypts_alike(env):
         ctx.check()
         ks.free()
         ks2.free()
+
+
+def test_batched_workload_at_full_scale_against_the_oracle(env):
+    """The batched workload at its stated size: 64 messages, sizes log-uniform
+    over 4 KB - 25 MB, each with its own K in {2, 4, 8, 16} and width in
+    {1024, 2048, 3072, 4096} bits, 70% full-d decryption, 10% CRT decryption,
+    20% encryption.  The graph-replayed batch equals one call per job, and
+    every job is checked against the oracle on 4 chunks including its last
+    (the oracle computes with the library's exported keys)."""
+    P, oracle, ctx = env
+    from paper_2111_11924_gb300 import pmkrsa as B
+
+    rng = np.random.default_rng(0x50444D4B0000C000)
+    keysets, okeys, jobs = {}, {}, []
+    for msg_i in range(64):
+        size = int(np.exp(rng.uniform(np.log(4096), np.log(25e6))))
+        K = int(rng.choice([2, 4, 8, 16]))
+        nbits = int(rng.choice([1024, 2048, 3072, 4096]))
+        op = int(rng.choice([B.OP_DECRYPT, B.OP_DECRYPT_CRT, B.OP_ENCRYPT], p=[0.7, 0.1, 0.2]))
+        if (K, nbits) not in keysets:
+            keysets[K, nbits] = ctx.keygen(K, nbits, 65537, 0x50444D4B0000C100 + 16 * K + nbits)
+            okeys[K, nbits] = oracle.OracleKeys(K, nbits, 65537, keysets[K, nbits].export())
+        ks = keysets[K, nbits]
+        msg = torch.from_numpy(np.random.default_rng(msg_i).integers(0, 256, size, dtype=np.uint8)).cuda()
+        plain = ctx.split(nbits, msg)
+        src = plain if op == B.OP_ENCRYPT else ctx.encrypt_chunks(ks, plain)
+        jobs.append((ks, src, torch.empty_like(src), op, okeys[K, nbits]))
+    batch = ctx.batch([j[:4] for j in jobs])
+    batch.launch()
+    ctx.check()
+    assert sum(j[1].shape[0] for j in jobs) > 250_000
+    for ks, x, out, op, ok in jobs:
+        ref = (ctx.encrypt_chunks(ks, x) if op == B.OP_ENCRYPT
+               else ctx.decrypt_chunks(ks, x, use_crt=(op == B.OP_DECRYPT_CRT)))
+        assert torch.equal(out, ref), (ks.nbits, ks.K, op, x.shape[0])
+        n = x.shape[0]
+        sample = np.unique(np.concatenate([rng.integers(0, n, 3), [n - 1]]))
+        xin = x.cpu().numpy().view(np.uint32)[sample]
+        want = (oracle.encrypt_chunks(xin, ok, threads=8, key_idx=sample % ok.K) if op == B.OP_ENCRYPT
+                else oracle.decrypt_chunks(xin, ok, threads=8, key_idx=sample % ok.K))
+        assert np.array_equal(out.cpu().numpy().view(np.uint32)[sample], want), (ks.nbits, ks.K, op, n)
+    batch.destroy()
+    for ks in keysets.values():
+        ks.free()
