@@ -50,7 +50,7 @@ KERNELS_PER_STEP = 6  # split, range check + modexp (encrypt), range check + mod
 # DRAM traffic of the full-d decryption kernel from one ncu capture, valid only
 # for the kernel sources it was measured on (see profiles/).
 TRAFFIC_SOURCES = ["paper_2111_11924_gb300/csrc/modexp_core.cuh", "paper_2111_11924_gb300/csrc/modexp_grid.cuh"]
-TRAFFIC_MEASURED = {"a9fe84bae498f3d7": 1451008}  # source digest -> bytes per launch (profiles/)
+TRAFFIC_MEASURED = {"0fe715b73419553d": 1444096}  # source digest -> bytes per launch (profiles/)
 
 
 def sources_digest() -> str:
@@ -911,10 +911,15 @@ def serving_leg(ctx, n_requests: int, loads: tuple, scale: float, plain_at: floa
     return res
 
 
-def hbm_split_join(ctx, steps: int) -> dict:
+def hbm_split_join(ctx, steps: int, back_to_back: int = 20) -> dict:
     """Split and join (the HBM-bound rows) on the 100 MiB / 2048-bit file:
     GB/s of algorithmic bytes (message bytes + limb-buffer bytes) against the
-    measured copy bandwidth of this GPU; both buffers are larger than L2."""
+    measured copy bandwidth of this GPU.  Both buffers (205 MB) are larger
+    than L2, so every launch streams them from HBM.  Two timings: CUDA events
+    around one launch (median of `steps`; this includes the launch latency,
+    about 6 us against a ~30 us kernel), and around `back_to_back` launches
+    in a row divided by their number (the kernel's own rate, which the
+    fraction of copy bandwidth uses)."""
     import torch
 
     w = W.FILE_100MIB_2048
@@ -939,9 +944,18 @@ def hbm_split_join(ctx, steps: int) -> dict:
             fn()
             ev[2 * i + 1].record()
         torch.cuda.synchronize()
-        ms = statistics.median(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(steps))
+        ms_one = statistics.median(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(steps))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(back_to_back):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / back_to_back
         gbs = bytes_moved / (ms / 1e3) / 1e9
-        res[name] = {"ms": ms, "GBps": gbs, "frac_of_measured_copy": gbs / peak if peak else None}
+        res[name] = {"ms": ms, "GBps": gbs, "frac_of_measured_copy": gbs / peak if peak else None,
+                     "back_to_back_launches": back_to_back, "ms_single_launch": ms_one,
+                     "GBps_single_launch": bytes_moved / (ms_one / 1e3) / 1e9}
     assert torch.equal(back, d_msg)
     return res
 

@@ -97,9 +97,11 @@ __device__ __forceinline__ long long slot_chunk(const uint32_t *__restrict__ grp
 // NT threads per block (128, or 64 where smaller blocks fit more
 // instances in an SM's shared memory).  TABLE (kTableFull or kTableSmall)
 // sizes the odd-power tables in shared memory and selects the key's
-// schedules built for it.
-template <int S, int TPI, bool CRT, int FORM, int NT = kThreads, int TABLE = kTableFull>
-__global__ void __launch_bounds__(NT) k_modexp(const KeyDev *__restrict__ keys, uint32_t K,
+// schedules built for it.  MINB: the minimum resident blocks per SM declared
+// to ptxas (0: none); 1 lets it use more registers, which pays for one
+// geometry (see the CRT instantiations).
+template <int S, int TPI, bool CRT, int FORM, int NT = kThreads, int TABLE = kTableFull, int MINB = 0>
+__global__ void __launch_bounds__(NT, MINB) k_modexp(const KeyDev *__restrict__ keys, uint32_t K,
                                                const uint32_t *__restrict__ in, uint32_t *__restrict__ out,
                                                long long n, int sel, int parts, const uint32_t *__restrict__ grp) {
   constexpr int L = S / TPI;

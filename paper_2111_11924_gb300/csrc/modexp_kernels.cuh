@@ -211,14 +211,14 @@ struct ModexpEntry {
 // instances per SM): 3.4% faster CRT decryption at 2048 bits and 100 MiB.
 // Other geometries measured no gain or a loss (64 limbs at 4 lanes: 12%
 // slower at 1 MiB) and keep 128.
-template <int S, int TPI, bool CRT, int FORM, int NT = dev::kThreads, int TABLE = kTableFull>
+template <int S, int TPI, bool CRT, int FORM, int NT = dev::kThreads, int TABLE = kTableFull, int MINB = 0>
 ModexpEntry make_entry() {
   constexpr size_t warp_area = (size_t)(32 / TPI) * dev::Layout<S>::inst(dev::table_rows(TABLE));
   return ModexpEntry{S,
                      TPI,
                      CRT,
                      FORM,
-                     reinterpret_cast<const void *>(&dev::k_modexp<S, TPI, CRT, FORM, NT, TABLE>),
+                     reinterpret_cast<const void *>(&dev::k_modexp<S, TPI, CRT, FORM, NT, TABLE, MINB>),
                      dev::modexp_smem_bytes<S>(TPI, NT, TABLE),
                      reinterpret_cast<const void *>(&dev::k_modexp_tasks<S, TPI, CRT, FORM, TABLE>),
                      sizeof(uint32_t) * warp_area * (dev::kThreads / 32),
