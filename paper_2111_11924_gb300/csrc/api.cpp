@@ -643,7 +643,7 @@ int pmk_join(pmk_ctx *ctx, uint32_t nbits, const uint32_t *d_chunks, size_t n_ch
 int pmk_encrypt_chunks(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_in, uint32_t *d_out, size_t n_chunks,
                        const uint32_t *d_key_idx, void *stream) {
   pmk::TraceRange trace("pmk_encrypt_chunks");
-  if (n_chunks == 0) return (ctx && ks) ? PMK_OK : PMK_EINVAL;
+  if (n_chunks == 0) return (ctx && ks && ks->device == ctx->device) ? PMK_OK : PMK_EINVAL;
   int rc = check_chunk_call(ctx, ks, d_in, d_out, n_chunks);
   if (rc != PMK_OK) return rc;
   DeviceGuard g(ctx->device);
@@ -659,7 +659,7 @@ int pmk_encrypt_chunks(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_in,
 int pmk_decrypt_chunks(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_in, uint32_t *d_out, size_t n_chunks,
                        const uint32_t *d_key_idx, int use_crt, void *stream) {
   pmk::TraceRange trace("pmk_decrypt_chunks");
-  if (n_chunks == 0) return (ctx && ks) ? PMK_OK : PMK_EINVAL;
+  if (n_chunks == 0) return (ctx && ks && ks->device == ctx->device) ? PMK_OK : PMK_EINVAL;
   int rc = check_chunk_call(ctx, ks, d_in, d_out, n_chunks);
   if (rc != PMK_OK) return rc;
   const size_t bytes = n_chunks * (ks->nbits / 8);
@@ -677,7 +677,7 @@ int pmk_decrypt_chunks(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_in,
 int pmk_encrypt_blinded(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_m, const uint32_t *d_r,
                         uint32_t *d_cstar, uint32_t *d_cr, size_t n_chunks, void *stream) {
   pmk::TraceRange trace("pmk_encrypt_blinded");
-  if (n_chunks == 0) return (ctx && ks) ? PMK_OK : PMK_EINVAL;
+  if (n_chunks == 0) return (ctx && ks && ks->device == ctx->device) ? PMK_OK : PMK_EINVAL;
   int rc = check_chunk_call(ctx, ks, d_m, d_cstar, n_chunks);
   if (rc == PMK_OK) rc = check_chunk_call(ctx, ks, d_r, d_cr, n_chunks);
   if (rc != PMK_OK) return rc;
@@ -699,7 +699,7 @@ int pmk_encrypt_blinded(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_m,
 int pmk_decrypt_blinded(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_cstar, const uint32_t *d_cr,
                         uint32_t *d_m, size_t n_chunks, int use_crt, void *stream) {
   pmk::TraceRange trace("pmk_decrypt_blinded");
-  if (n_chunks == 0) return (ctx && ks) ? PMK_OK : PMK_EINVAL;
+  if (n_chunks == 0) return (ctx && ks && ks->device == ctx->device) ? PMK_OK : PMK_EINVAL;
   int rc = check_chunk_call(ctx, ks, d_cstar, d_m, n_chunks);
   if (rc == PMK_OK) rc = check_chunk_call(ctx, ks, d_cr, d_m, n_chunks);
   if (rc != PMK_OK) return rc;
@@ -741,7 +741,7 @@ int pmk_decrypt_blinded(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_cs
 int pmk_modexp_chunks_baseline(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_in, uint32_t *d_out,
                                size_t n_chunks, int decrypt, void *stream) {
   pmk::TraceRange trace("pmk_modexp_chunks_baseline");
-  if (n_chunks == 0) return (ctx && ks) ? PMK_OK : PMK_EINVAL;
+  if (n_chunks == 0) return (ctx && ks && ks->device == ctx->device) ? PMK_OK : PMK_EINVAL;
   int rc = check_chunk_call(ctx, ks, d_in, d_out, n_chunks);
   if (rc != PMK_OK) return rc;
   DeviceGuard g(ctx->device);

@@ -60,7 +60,7 @@ extern "C" int pmk_decrypt_message_host_noalloc(const pmk_keyset *ks, const uint
                                                 uint8_t *h_msg, size_t msg_len, int use_crt, void *stream) {
   pmk::TraceRange trace("pmk_decrypt_message_host_noalloc");
   using namespace pmk;
-  if (!ks) return PMK_EINVAL;
+  if (!ks || ks->device < 0 || !ks->d_keys) return PMK_EINVAL;  // a host-only key set has no device tables
   if (n_chunks != pmk_num_chunks(msg_len, ks->nbits) || n_chunks >= kMaxChunks) return PMK_EINVAL;
   if (n_chunks != 0 && (!h_cipher || !h_msg)) return PMK_EINVAL;
   // Sizes are compared with the capacity one at a time before they are

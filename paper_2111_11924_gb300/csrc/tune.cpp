@@ -19,7 +19,7 @@
 extern "C" int pmk_autotune(pmk_ctx *ctx, const pmk_keyset *ks, size_t n_chunks, int mode, int reps, uint32_t *tpi,
                             uint32_t *form, float *ms) {
   pmk::TraceRange trace("pmk_autotune");
-  if (!ctx || !ks || n_chunks == 0 || mode < 0 || mode > 2) return PMK_EINVAL;
+  if (!ctx || !ks || ks->device != ctx->device || n_chunks == 0 || mode < 0 || mode > 2) return PMK_EINVAL;
   const bool crt = mode == 2;
   const uint32_t S = ks->nbits / 32;
   const uint32_t limbs = crt ? S / ks->nprimes : S;

@@ -159,6 +159,17 @@ def _torch():
     return torch
 
 
+def chunk_shape(t, nbits: int, n_chunks=None, what: str = "chunks") -> int:
+    """Check that a limb buffer has shape (n_chunks, nbits/32) (any n_chunks
+    when None).  Returns its chunk count; raises ValueError otherwise, so
+    that no call reads or writes past a buffer of another width or length."""
+    if not isinstance(t, _torch().Tensor) or t.dim() != 2 or t.shape[1] != nbits // 32:
+        raise ValueError(f"{what} must have shape (n_chunks, {nbits // 32}) for {nbits}-bit keys")
+    if n_chunks is not None and t.shape[0] != n_chunks:
+        raise ValueError(f"{what} holds {t.shape[0]} chunks, {n_chunks} expected")
+    return int(t.shape[0])
+
+
 def host_limb_buffer(t, nbits: int, what: str = "h_cipher"):
     """Check a host limb buffer for the *_host calls: a contiguous CPU int32
     (or uint32) tensor of shape (n_chunks, nbits/32).  Returns the chunk
@@ -168,9 +179,7 @@ def host_limb_buffer(t, nbits: int, what: str = "h_cipher"):
         raise ValueError(f"{what} must be a CPU tensor")
     if t.dtype not in (torch.int32, getattr(torch, "uint32", torch.int32)) or not t.is_contiguous():
         raise ValueError(f"{what} must be a contiguous int32 tensor")
-    if t.dim() != 2 or t.shape[1] != nbits // 32:
-        raise ValueError(f"{what} must have shape (n_chunks, {nbits // 32}) for {nbits}-bit keys")
-    return int(t.shape[0])
+    return chunk_shape(t, nbits, None, what)
 
 
 def host_message_buffer(t, n_chunks: int, nbits: int, what: str = "h_msg"):
@@ -286,6 +295,20 @@ class Context:
             raise ValueError(f"{what} must be a contiguous {dtype} tensor")
         return ctypes.c_void_p(t.data_ptr())
 
+    def _limbs(self, t, nbits: int, n_chunks, what):
+        """Device pointer of a chunk buffer: a contiguous int32 CUDA tensor on
+        this device of shape (n_chunks, nbits/32)."""
+        p = self._dev(t, _torch().int32, what)
+        chunk_shape(t, nbits, n_chunks, what)
+        return p
+
+    def _bytes(self, t, n_bytes: int, what):
+        """Device pointer of a contiguous uint8 CUDA tensor of n_bytes bytes."""
+        p = self._dev(t, _torch().uint8, what)
+        if t.numel() != n_bytes:
+            raise ValueError(f"{what} holds {t.numel()} bytes, {n_bytes} expected")
+        return p
+
     # ------------------------------------------------------------ keys
     def keygen(self, K: int, nbits: int, e: int = 65537, seed: int = 0, nprimes: int = 2) -> KeySet:
         """K key pairs; nprimes > 2 gives multi-prime keys (Section 2.1)."""
@@ -329,7 +352,7 @@ class Context:
         if out is None:
             out = torch.empty((n, nbits // 32), dtype=torch.int32, device=msg.device)
         _check(load_library().pmk_split(self.handle, nbits, self._dev(msg, torch.uint8, "msg"), msg.numel(),
-                                        self._dev(out, torch.int32, "chunks"), n, self.stream_handle(stream)),
+                                        self._limbs(out, nbits, n, "chunks"), n, self.stream_handle(stream)),
                "pmk_split")
         return out
 
@@ -337,8 +360,8 @@ class Context:
         torch = _torch()
         if out is None:
             out = torch.empty(msg_len, dtype=torch.uint8, device=chunks.device)
-        _check(load_library().pmk_join(self.handle, nbits, self._dev(chunks, torch.int32, "chunks"), chunks.shape[0],
-                                       self._dev(out, torch.uint8, "msg"), msg_len, self.stream_handle(stream)),
+        _check(load_library().pmk_join(self.handle, nbits, self._limbs(chunks, nbits, None, "chunks"), chunks.shape[0],
+                                       self._bytes(out, msg_len, "msg"), msg_len, self.stream_handle(stream)),
                "pmk_join")
         return out
 
@@ -346,18 +369,19 @@ class Context:
         """Device pointer of an explicit key-index vector (int32 CUDA tensor of n), or None."""
         if key_idx is None:
             return None
-        torch = _torch()
+        p = self._dev(key_idx, _torch().int32, "key_idx")
         if key_idx.numel() != n:
             raise ValueError(f"key_idx must hold one key index per chunk ({n})")
-        return self._dev(key_idx, torch.int32, "key_idx")
+        return p
 
     def encrypt_chunks(self, ks: KeySet, chunks, out=None, stream=None, key_idx=None):
         """c[t] = m[t]^e mod N_k with k = t mod K, or k = key_idx[t] when given."""
         torch = _torch()
         if out is None:
             out = torch.empty_like(chunks)
-        _check(load_library().pmk_encrypt_chunks(self.handle, ks.handle, self._dev(chunks, torch.int32, "in"),
-                                                 self._dev(out, torch.int32, "out"), chunks.shape[0],
+        n = chunk_shape(chunks, ks.nbits, None, "in")
+        _check(load_library().pmk_encrypt_chunks(self.handle, ks.handle, self._limbs(chunks, ks.nbits, n, "in"),
+                                                 self._limbs(out, ks.nbits, n, "out"), n,
                                                  self._key_idx(key_idx, chunks.shape[0]),
                                                  self.stream_handle(stream)), "pmk_encrypt_chunks")
         return out
@@ -367,8 +391,9 @@ class Context:
         torch = _torch()
         if out is None:
             out = torch.empty_like(chunks)
-        _check(load_library().pmk_decrypt_chunks(self.handle, ks.handle, self._dev(chunks, torch.int32, "in"),
-                                                 self._dev(out, torch.int32, "out"), chunks.shape[0],
+        n = chunk_shape(chunks, ks.nbits, None, "in")
+        _check(load_library().pmk_decrypt_chunks(self.handle, ks.handle, self._limbs(chunks, ks.nbits, n, "in"),
+                                                 self._limbs(out, ks.nbits, n, "out"), n,
                                                  self._key_idx(key_idx, chunks.shape[0]), int(use_crt),
                                                  self.stream_handle(stream)), "pmk_decrypt_chunks")
         return out
@@ -377,8 +402,9 @@ class Context:
         """The plain thread-per-chunk, binary-exponent kernel (a measured baseline)."""
         torch = _torch()
         out = torch.empty_like(chunks) if out is None else out
-        _check(load_library().pmk_modexp_chunks_baseline(self.handle, ks.handle, self._dev(chunks, torch.int32, "in"),
-                                                         self._dev(out, torch.int32, "out"), chunks.shape[0],
+        n = chunk_shape(chunks, ks.nbits, None, "in")
+        _check(load_library().pmk_modexp_chunks_baseline(self.handle, ks.handle, self._limbs(chunks, ks.nbits, n, "in"),
+                                                         self._limbs(out, ks.nbits, n, "out"), n,
                                                          int(decrypt), self.stream_handle(stream)),
                "pmk_modexp_chunks_baseline")
         return out
@@ -388,10 +414,11 @@ class Context:
         torch = _torch()
         out_cstar = torch.empty_like(chunks) if out_cstar is None else out_cstar
         out_cr = torch.empty_like(chunks) if out_cr is None else out_cr
-        _check(load_library().pmk_encrypt_blinded(self.handle, ks.handle, self._dev(chunks, torch.int32, "m"),
-                                                  self._dev(rnd, torch.int32, "r"),
-                                                  self._dev(out_cstar, torch.int32, "cstar"),
-                                                  self._dev(out_cr, torch.int32, "cr"), chunks.shape[0],
+        n = chunk_shape(chunks, ks.nbits, None, "m")
+        _check(load_library().pmk_encrypt_blinded(self.handle, ks.handle, self._limbs(chunks, ks.nbits, n, "m"),
+                                                  self._limbs(rnd, ks.nbits, n, "r"),
+                                                  self._limbs(out_cstar, ks.nbits, n, "cstar"),
+                                                  self._limbs(out_cr, ks.nbits, n, "cr"), n,
                                                   self.stream_handle(stream)), "pmk_encrypt_blinded")
         return out_cstar, out_cr
 
@@ -399,9 +426,10 @@ class Context:
         """Algorithm 1 decryption with R: m = (c* c_r^-1)^d mod N."""
         torch = _torch()
         out = torch.empty_like(cstar) if out is None else out
-        _check(load_library().pmk_decrypt_blinded(self.handle, ks.handle, self._dev(cstar, torch.int32, "cstar"),
-                                                  self._dev(cr, torch.int32, "cr"), self._dev(out, torch.int32, "m"),
-                                                  cstar.shape[0], int(use_crt), self.stream_handle(stream)),
+        n = chunk_shape(cstar, ks.nbits, None, "cstar")
+        _check(load_library().pmk_decrypt_blinded(self.handle, ks.handle, self._limbs(cstar, ks.nbits, n, "cstar"),
+                                                  self._limbs(cr, ks.nbits, n, "cr"), self._limbs(out, ks.nbits, n, "m"),
+                                                  n, int(use_crt), self.stream_handle(stream)),
                "pmk_decrypt_blinded")
         return out
 
@@ -426,8 +454,9 @@ class Context:
         torch = _torch()
         arr = (_Job * max(1, len(jobs)))()
         for k, (ks, t_in, t_out, op) in enumerate(jobs):
-            arr[k] = _Job(ks.handle, self._dev(t_in, torch.int32, "in").value, self._dev(t_out, torch.int32, "out").value,
-                          t_in.shape[0], int(op))
+            n = chunk_shape(t_in, ks.nbits, None, "in")
+            arr[k] = _Job(ks.handle, self._limbs(t_in, ks.nbits, n, "in").value,
+                          self._limbs(t_out, ks.nbits, n, "out").value, n, int(op))
         h = ctypes.c_void_p()
         _check(load_library().pmk_batch_create(self.handle, arr, len(jobs), ctypes.byref(h)), "pmk_batch_create")
         return Batch(self, h, jobs)
@@ -579,10 +608,15 @@ def decrypt_message_host_noalloc(ks: KeySet, h_cipher, h_msg, use_crt: bool = Fa
     torch = _torch()
     n = host_limb_buffer(h_cipher, ks.nbits)
     L = host_message_buffer(h_msg, n, ks.nbits)
-    s = stream if stream is not None else torch.cuda.current_stream(ks._ctx.device)
+    if stream is not None:
+        s = int(stream.cuda_stream)
+    elif ks._ctx is not None:
+        s = int(torch.cuda.current_stream(ks._ctx.device).cuda_stream)
+    else:
+        s = 0  # a host-only key set: the library refuses it before any device work
     return int(load_library().pmk_decrypt_message_host_noalloc(
         ks.handle, ctypes.c_void_p(h_cipher.data_ptr()), n, ctypes.c_void_p(h_msg.data_ptr()),
-        L, int(use_crt), ctypes.c_void_p(int(s.cuda_stream))))
+        L, int(use_crt), ctypes.c_void_p(s)))
 
 
 class Batch:

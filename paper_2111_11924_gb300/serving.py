@@ -21,7 +21,7 @@ with CUDA events; the host never blocks on the device while work is in
 flight.  Each request ends with its own status: a batch whose lane reports a
 device-side error names its first failing chunk, which names the request;
 that request is marked failed and the rest of the batch is run again
-without it, until no error is left.
+without it, until no error is left (this error path waits for each re-run).
 
 This is host orchestration only: every step of every request runs in the
 library's kernels through the C ABI.
@@ -57,8 +57,12 @@ class Request:
         return self.t_done - self.arrival
 
     def device_bytes(self) -> int:
+        """Device memory the request holds while in flight: its message, its
+        input and output chunks, and in a coalesced batch its chunks' key
+        indices and key-group slots (4 + 4 bytes a chunk).  The per-key part
+        of a batch's key-group table (268 bytes a key) is not counted."""
         n = num_chunks(self.msg_len, self.nbits)
-        return self.msg_len + 2 * n * (self.nbits // 8)
+        return self.msg_len + 2 * n * (self.nbits // 8) + 8 * n
 
 
 def _percentile(xs, q):

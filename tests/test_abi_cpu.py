@@ -268,6 +268,10 @@ def test_host_buffer_checks_reject_mismatched_buffers():
                 torch.zeros(160, dtype=torch.int32)):         # not 2-D
         with pytest.raises(ValueError):
             pmkrsa.host_limb_buffer(bad, 1024)
+    assert pmkrsa.chunk_shape(good, 1024, 5) == 5
+    for bad, n in ((good, 4), (torch.zeros((5, 64), dtype=torch.int32), 5), (torch.zeros(160), None), ([0], None)):
+        with pytest.raises(ValueError):
+            pmkrsa.chunk_shape(bad, 1024, n)
     msg = torch.zeros(5 * 127 - 3, dtype=torch.uint8)
     assert pmkrsa.host_message_buffer(msg, 5, 1024) == 5 * 127 - 3
     for bad, n in ((torch.zeros(5 * 127 + 1, dtype=torch.uint8), 5),  # one chunk too many
@@ -352,3 +356,21 @@ def test_blob_rejections(P):
         with pytest.raises(P.PMKError) as err:
             P.import_keyset_host(bytes(bad))
         assert err.value.code == P.pmkrsa.PMK_EINVAL
+
+
+def test_host_only_key_set_is_refused_by_device_calls(P):
+    """A key set imported without a context has no device tables: the
+    allocation-free decryption refuses it (EINVAL) before any device work,
+    so the refusal is visible on a machine with no GPU."""
+    import torch
+
+    ok = oracle.keygen(2, 512, 65537, 22)
+    ks = P.import_keyset_host(_oracle_blob(ok, 2))
+    n = 3
+    cipher = torch.zeros((n, 512 // 32), dtype=torch.int32)
+    msg = torch.zeros(n * (512 // 8 - 1), dtype=torch.uint8)
+    for crt in (False, True):
+        assert P.pmkrsa.decrypt_message_host_noalloc(ks, cipher, msg, use_crt=crt) == P.pmkrsa.PMK_EINVAL
+    empty = torch.zeros((0, 512 // 32), dtype=torch.int32)
+    assert P.pmkrsa.decrypt_message_host_noalloc(ks, empty, torch.zeros(0, dtype=torch.uint8)) == P.pmkrsa.PMK_EINVAL
+    ks.free()

@@ -159,6 +159,41 @@ def test_blob_import_on_device_decrypts_alike(env):
         ks2.free()
 
 
+def test_buffers_of_another_shape_and_host_only_keys_are_refused(env):
+    """The binding refuses, before any launch, chunk buffers whose width is
+    not the key set's or whose length differs from the input's, a message
+    buffer of another length, and a key-index vector of another length; the
+    library refuses a host-only key set (EINVAL) in the device calls."""
+    P, oracle, ctx = env
+    ks = ctx.keygen(2, 2048, 65537, 0x50444D4B0000E700)
+    good = torch.zeros((5, 64), dtype=torch.int32, device="cuda")
+    narrow = torch.zeros((5, 32), dtype=torch.int32, device="cuda")    # 1024-bit chunks
+    short = torch.zeros((4, 64), dtype=torch.int32, device="cuda")
+    idx = torch.zeros(4, dtype=torch.int32, device="cuda")
+    for call in (lambda: ctx.encrypt_chunks(ks, narrow),
+                 lambda: ctx.decrypt_chunks(ks, good, out=short),
+                 lambda: ctx.decrypt_chunks(ks, good, key_idx=idx),
+                 lambda: ctx.encrypt_blinded(ks, good, short),
+                 lambda: ctx.decrypt_blinded(ks, good, good, out=narrow),
+                 lambda: ctx.modexp_chunks_baseline(ks, narrow),
+                 lambda: ctx.split(2048, torch.zeros(600, dtype=torch.uint8, device="cuda"), out=good),
+                 lambda: ctx.join(2048, good, 1000, out=torch.zeros(999, dtype=torch.uint8, device="cuda")),
+                 lambda: ctx.batch([(ks, good, short, P.pmkrsa.OP_ENCRYPT)])):
+        with pytest.raises(ValueError):
+            call()
+    host_only = P.import_keyset_host(ks.export_blob())
+    for call in (lambda: ctx.encrypt_chunks(host_only, good),
+                 lambda: ctx.decrypt_chunks(host_only, good, use_crt=True),
+                 lambda: ctx.encrypt_chunks(host_only, good[:0]),
+                 lambda: ctx.autotune(host_only, 100, "decrypt", reps=1)):
+        with pytest.raises(P.PMKError) as err:
+            call()
+        assert err.value.code == P.pmkrsa.PMK_EINVAL
+    assert ctx.status() == 0
+    host_only.free()
+    ks.free()
+
+
 def test_batched_workload_at_full_scale_against_the_oracle(env):
     """The batched workload at its stated size: 64 messages, sizes log-uniform
     over 4 KB - 25 MB, each with its own K in {2, 4, 8, 16} and width in
