@@ -47,10 +47,29 @@ L2_FLUSH_BYTES = 256 << 20
 FORM_NAMES = ["chain", "columns"]  # Montgomery product forms (pmk_set_kernel_config)
 KERNELS_PER_STEP = 6  # split, range check + modexp (encrypt), range check + modexp (decrypt), join
 
-# DRAM traffic of the full-d decryption kernel from one ncu capture, valid only
-# for the kernel sources it was measured on (see profiles/).
+# ncu counters of the full-d decryption kernel on the 1 MiB workload, valid
+# only for the kernel sources they were measured on (see profiles/): DRAM
+# bytes per launch, and the issue-slot and pipe utilisation that the
+# algorithmic count does not see (carry adds and column shifts take issue
+# slots of their own).
 TRAFFIC_SOURCES = ["paper_2111_11924_gb300/csrc/modexp_core.cuh", "paper_2111_11924_gb300/csrc/modexp_grid.cuh"]
-TRAFFIC_MEASURED = {"0fe715b73419553d": 1444096}  # source digest -> bytes per launch (profiles/)
+COUNTERS_MEASURED = {  # source digest -> counters of one launch
+    "0fe715b73419553d": {"traffic": 1444096, "issue_active_pct": 51.06, "warps_active_per_sm": 6.91,
+                         "alu_pipe_pct": 56.93, "fmaheavy_pipe_pct": 61.13, "warp_instructions": 10071705714},
+}
+
+
+def issue_slots(counters: dict, alg_macs: float):
+    """Issue-slot use of the dominant kernel beside its roofline: the ncu
+    counters of the same kernel sources, and the thread instructions it
+    executes per algorithmic MAC (None when no capture matches the sources)."""
+    if "issue_active_pct" not in counters:
+        return None
+    return {"issue_active_pct": counters["issue_active_pct"],
+            "warps_active_per_sm": counters["warps_active_per_sm"],
+            "alu_pipe_pct": counters["alu_pipe_pct"], "fmaheavy_pipe_pct": counters["fmaheavy_pipe_pct"],
+            "thread_instructions_per_mac": 32 * counters["warp_instructions"] / alg_macs,
+            "source": "ncu counters of one launch on this workload (profiles/modexp_fulld_1MiB_K8_2048bit.md)"}
 
 
 def sources_digest() -> str:
@@ -350,6 +369,7 @@ def run_ours(args):
     achieved = int32_ops_per_s(alg_macs, dec_ms) / 1e12
     crt_achieved = int32_ops_per_s(n * algorithmic_crt_macs(w.nbits), crt_dec) / 1e12
     digest = sources_digest()
+    counters = COUNTERS_MEASURED.get(digest, {})
 
     # the plain GPU formulation on the same ciphertext: one thread per chunk,
     # binary exponent, one launch per call
@@ -417,7 +437,8 @@ def run_ours(args):
                             "join": (w.msg_bytes + cipher_bytes) / (join_ms / 1e3) / 1e9,
                             "note": "1 MiB step: launch-latency bound; see split_join_hbm for bandwidth"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "TOP/s",
-                     "frac": achieved / peak_tops, "traffic": TRAFFIC_MEASURED.get(digest),
+                     "frac": achieved / peak_tops, "traffic": counters.get("traffic"),
+                     "issue_slots": issue_slots(counters, alg_macs),
                      "kernel": f"k_modexp<64,{tuned['tpi']},full,{FORM_NAMES[tuned['form']]}> "
                                "(full-d decrypt; interval includes its ~4 us range check)",
                      "ops_per_launch": 2 * alg_macs, "ops_basis": "2 INT32 multiply-add halves per 32x32->64 MAC; "

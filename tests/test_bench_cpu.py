@@ -42,3 +42,16 @@ def test_int32_roofline_recomputes_from_its_inputs():
     assert achieved == pytest.approx(9.27, abs=0.01)
     assert peak == pytest.approx(20.13, abs=0.01)
     assert achieved / peak == pytest.approx(0.46, abs=0.005)
+
+
+def test_issue_slots_follow_the_current_kernel_sources():
+    # The stored counters are reported only for the kernel sources they were captured on, and the
+    # instructions per MAC come from the capture's warp instruction count: 1.007e10 warp instructions
+    # for 8.17e10 algorithmic MACs are 3.94 thread instructions per MAC.
+    macs = bench.algorithmic_montmuls(2048) * bench.macs_per_montmul(2048) * 4113
+    got = bench.issue_slots({"issue_active_pct": 51.06, "warps_active_per_sm": 6.91, "alu_pipe_pct": 56.93,
+                             "fmaheavy_pipe_pct": 61.13, "warp_instructions": 10071705714}, macs)
+    assert got["thread_instructions_per_mac"] == pytest.approx(3.94, abs=0.01)
+    assert bench.issue_slots({}, macs) is None
+    for counters in bench.COUNTERS_MEASURED.values():
+        assert set(counters) >= {"traffic", "issue_active_pct", "warp_instructions"}
