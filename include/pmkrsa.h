@@ -335,8 +335,9 @@ int pmk_decrypt_message_host_noalloc(const pmk_keyset *ks, const uint32_t *h_cip
  *   - jobs are grouped by exponentiation width and mode; each group runs as
  *     one persistent kernel whose warps take tasks (up to 32/TPI chunks of
  *     one key) from a device queue, longest tasks first;
- *   - a job with at least four GPU-fulls of exponentiations instead gets
- *     its own grid launch (the kernel of pmk_*_chunks);
+ *   - a job with at least one GPU-full of exponentiations (as many as the
+ *     GPU holds resident at once) instead gets its own grid launch (the
+ *     kernel of pmk_*_chunks);
  *   - groups and such jobs run concurrently on internal streams, widest
  *     first;
  *   - range checks, the kernels and CRT recombination are captured once into

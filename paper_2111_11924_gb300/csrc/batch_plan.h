@@ -37,9 +37,11 @@ struct PlanDirect {
 
 // A job with at least this many GPU-fulls of exponentiations runs as one
 // plain grid launch inside the graph: it fills the GPU alone, and the grid
-// kernel is a few percent faster than the persistent one on a single large
-// job (measured on 100 MiB).  Smaller jobs share the persistent queues.
-constexpr long long kDirectWaves = 4;
+// kernel is 3-8% faster than the persistent one on a single job of one to
+// four GPU-fulls (measured from 8,000 to 28,000 2048-bit chunks), while
+// mixed batches measured the same with this threshold as with four.
+// Smaller jobs share the persistent queues.
+constexpr long long kDirectWaves = 1;
 
 // config(limbs, crt, &cfg): the geometry for that width and mode (false if
 // none); resident(limbs, cfg, crt): the exponentiations the whole GPU holds

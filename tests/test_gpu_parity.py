@@ -651,8 +651,8 @@ def test_integer_peak_measurements_are_sane(ctx):
 
 
 def test_batch_large_jobs_take_a_grid_launch(ctx, P):
-    """Jobs that fill the GPU several times over run as plain grid launches
-    inside the batch graph, next to queued small jobs; every output equals the
+    """Jobs that fill the GPU at least once run as plain grid launches inside
+    the batch graph, next to queued small jobs; every output equals the
     per-call result, and a batch of one large job holds no queued tasks."""
     from paper_2111_11924_gb300 import pmkrsa as B
 
