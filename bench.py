@@ -54,8 +54,8 @@ KERNELS_PER_STEP = 6  # split, range check + modexp (encrypt), range check + mod
 # slots of their own).
 TRAFFIC_SOURCES = ["paper_2111_11924_gb300/csrc/modexp_core.cuh", "paper_2111_11924_gb300/csrc/modexp_grid.cuh"]
 COUNTERS_MEASURED = {  # source digest -> counters of one launch
-    "0fe715b73419553d": {"traffic": 1444096, "issue_active_pct": 51.06, "warps_active_per_sm": 6.91,
-                         "alu_pipe_pct": 56.93, "fmaheavy_pipe_pct": 61.13, "warp_instructions": 10071705714},
+    "aaf81f9378ddee50": {"traffic": 1273600, "issue_active_pct": 50.80, "warps_active_per_sm": 6.93,
+                         "alu_pipe_pct": 57.16, "fmaheavy_pipe_pct": 60.34, "warp_instructions": 10037561520},
 }
 
 

@@ -593,7 +593,8 @@ int launch_modexp(ExpMode mode, uint32_t limbs, KernelConfig cfg, const KeyDev *
   if (!groups && (unsigned long long)K * (crt ? parts : 1) > 65535ull) return PMK_EINVAL;  // grid.y
   const ModexpEntry *e = find_entry(limbs, cfg, crt);
   if (!e) return PMK_EUNSUPPORTED;
-  const int rc = configure_smem(e->fn, e->smem);
+  const void *fn = groups ? e->fn_grp : e->fn;
+  const int rc = configure_smem(fn, e->smem);
   if (rc != PMK_OK) return rc;
   const long long per_key = ((long long)n + K - 1) / K;
   const int ipb = e->threads / e->tpi;
@@ -605,7 +606,7 @@ int launch_modexp(ExpMode mode, uint32_t limbs, KernelConfig cfg, const KeyDev *
   int np = crt ? (int)parts : 1;
   void *args[] = {(void *)&keys, (void *)&K,   (void *)&in, (void *)&out,
                   (void *)&nl,   (void *)&sel, (void *)&np, (void *)&groups};
-  return cuda_rc(cudaLaunchKernel(e->fn, grid, dim3(e->threads), args, e->smem, st));
+  return cuda_rc(cudaLaunchKernel(fn, grid, dim3(e->threads), args, e->smem, st));
 }
 
 }  // namespace pmk

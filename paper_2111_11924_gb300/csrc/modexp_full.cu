@@ -6,6 +6,9 @@ namespace pmk {
 using dev::kChain;
 using dev::kCols;
 
+// The 64-limb, 16-lane column geometry serves its round-robin launches with
+// the key-group instantiation, measured 1.8% faster at 1 MiB and 1.0% at
+// 10 MiB.
 const ModexpEntry *modexp_entries_full(int *count) {
   static const ModexpEntry entries[] = {
       make_entry<4, 2, false, kChain>(),    make_entry<8, 2, false, kChain>(),
@@ -13,7 +16,7 @@ const ModexpEntry *modexp_entries_full(int *count) {
       make_entry<32, 8, false, kChain>(),   make_entry<32, 4, false, kCols, 64>(),
       make_entry<32, 8, false, kCols>(),    make_entry<64, 4, false, kChain>(),
       make_entry<64, 8, false, kChain>(),   make_entry<64, 16, false, kChain>(),
-      make_entry<64, 8, false, kCols>(),    make_entry<64, 16, false, kCols>(),
+      make_entry<64, 8, false, kCols>(),    make_entry<64, 16, false, kCols, dev::kThreads, kTableFull, 0, true>(),
       make_entry<96, 8, false, kChain>(),   make_entry<96, 8, false, kCols>(),
       make_entry<128, 16, false, kChain>(), make_entry<128, 16, false, kCols>(),
   };

@@ -99,8 +99,16 @@ __device__ __forceinline__ long long slot_chunk(const uint32_t *__restrict__ grp
 // sizes the odd-power tables in shared memory and selects the key's
 // schedules built for it.  MINB: the minimum resident blocks per SM declared
 // to ptxas (0: none); 1 lets it use more registers, which pays for one
-// geometry (see the CRT instantiations).
-template <int S, int TPI, bool CRT, int FORM, int NT = kThreads, int TABLE = kTableFull, int MINB = 0>
+// geometry (see the CRT instantiations).  GRP = false: round robin only.
+// GRP = true: a key group table (grp, explicit key indices) when grp is
+// given, round robin when it is null.  Two instantiations because the table
+// lookup in the prologue, though outside the exponentiation, changes how
+// ptxas compiles the whole kernel: 38 instead of 32 registers at 64 limbs
+// and 32 lanes, round-robin launches up to 18% slower at 100 KB, and a few
+// column-form geometries 1-2% faster (measured); each geometry names the
+// instantiation that serves its round-robin launches (make_entry).
+template <int S, int TPI, bool CRT, int FORM, int NT = kThreads, int TABLE = kTableFull, int MINB = 0,
+          bool GRP = false>
 __global__ void __launch_bounds__(NT, MINB) k_modexp(const KeyDev *__restrict__ keys, uint32_t K,
                                                const uint32_t *__restrict__ in, uint32_t *__restrict__ out,
                                                long long n, int sel, int parts, const uint32_t *__restrict__ grp) {
@@ -116,10 +124,20 @@ __global__ void __launch_bounds__(NT, MINB) k_modexp(const KeyDev *__restrict__ 
   uint32_t *tbl = smem + Layout<S>::kConstRows * ROW + g * INST;
   uint32_t *ybuf = tbl + ROWS * ROW;
 
-  const uint32_t prime = CRT ? (grp ? blockIdx.y : blockIdx.y % (uint32_t)parts) : 0;
-  const BlockChunks bc = block_chunks(grp, K, n, IPB, CRT ? blockIdx.y / (uint32_t)parts : blockIdx.y);
-  if (!bc.any) return;  // block-uniform: no instance of this block has a chunk
-  const uint32_t key = bc.key;
+  uint32_t key, prime;
+  long long first = 0;  // round robin: the block's first chunk
+  BlockChunks bc{};     // key groups: the block's key and first slot
+  if constexpr (GRP) {
+    prime = CRT ? (grp ? blockIdx.y : blockIdx.y % (uint32_t)parts) : 0;
+    bc = block_chunks(grp, K, n, IPB, CRT ? blockIdx.y / (uint32_t)parts : blockIdx.y);
+    if (!bc.any) return;  // block-uniform: no instance of this block has a chunk
+    key = bc.key;
+  } else {
+    key = CRT ? blockIdx.y / (uint32_t)parts : blockIdx.y;
+    prime = CRT ? blockIdx.y % (uint32_t)parts : 0;
+    first = key + (long long)blockIdx.x * IPB * K;
+    if (first >= n) return;  // block-uniform: no instance of this block has a chunk
+  }
   const KeyDev &kd = keys[key];
   const uint32_t *M = CRT ? kd.P[prime] : kd.N;
   const uint32_t *R2 = CRT ? kd.R2h[prime] : kd.R2;
@@ -140,10 +158,17 @@ __global__ void __launch_bounds__(NT, MINB) k_modexp(const KeyDev *__restrict__ 
   // After the barrier the warps are independent: a warp whose instances all
   // lie past the last chunk of the key leaves (chunks and slots of a key are
   // in order, padding last, so its first instance decides).
-  if (slot_chunk(grp, K, n, bc, (threadIdx.x / 32) * (32 / TPI)) < 0) return;
-
-  const long long t = slot_chunk(grp, K, n, bc, g);
-  const bool active = t >= 0;
+  long long t;
+  bool active;
+  if constexpr (GRP) {
+    if (slot_chunk(grp, K, n, bc, (threadIdx.x / 32) * (32 / TPI)) < 0) return;
+    t = slot_chunk(grp, K, n, bc, g);
+    active = t >= 0;
+  } else {
+    if (first + (long long)((threadIdx.x / 32) * (32 / TPI)) * K >= n) return;
+    t = first + (long long)g * K;
+    active = t < n;
+  }
   uint32_t nn[L], a[L];
   load_slice_global<L>(nn, M, r);
   if (!CRT) {

@@ -191,13 +191,15 @@ constexpr size_t modexp_smem_bytes(int tpi, int threads = kThreads, int table = 
 
 // One compiled instantiation: limb count, lanes per instance, CRT or full
 // width, Montgomery form (dev::kChain / dev::kCols), odd-power table size
-// (kTableFull / kTableSmall); the one-launch-per-call kernel and the
-// persistent batch kernel with their shared-memory sizes.
+// (kTableFull / kTableSmall); the one-launch-per-call kernel (round robin,
+// and its twin over key groups) and the persistent batch kernel with their
+// shared-memory sizes.
 struct ModexpEntry {
   int limbs, tpi;
   bool crt;
   int form;
   const void *fn;
+  const void *fn_grp;  // fn over a key group table (same shared memory)
   size_t smem;
   const void *fn_tasks;
   size_t smem_tasks;
@@ -211,14 +213,18 @@ struct ModexpEntry {
 // instances per SM): 3.4% faster CRT decryption at 2048 bits and 100 MiB.
 // Other geometries measured no gain or a loss (64 limbs at 4 lanes: 12%
 // slower at 1 MiB) and keep 128.
-template <int S, int TPI, bool CRT, int FORM, int NT = dev::kThreads, int TABLE = kTableFull, int MINB = 0>
+// RR_GRP: round-robin launches also take the key-group instantiation (the
+// geometries where it measured faster; see k_modexp).
+template <int S, int TPI, bool CRT, int FORM, int NT = dev::kThreads, int TABLE = kTableFull, int MINB = 0,
+          bool RR_GRP = false>
 ModexpEntry make_entry() {
   constexpr size_t warp_area = (size_t)(32 / TPI) * dev::Layout<S>::inst(dev::table_rows(TABLE));
   return ModexpEntry{S,
                      TPI,
                      CRT,
                      FORM,
-                     reinterpret_cast<const void *>(&dev::k_modexp<S, TPI, CRT, FORM, NT, TABLE, MINB>),
+                     reinterpret_cast<const void *>(&dev::k_modexp<S, TPI, CRT, FORM, NT, TABLE, MINB, RR_GRP>),
+                     reinterpret_cast<const void *>(&dev::k_modexp<S, TPI, CRT, FORM, NT, TABLE, MINB, true>),
                      dev::modexp_smem_bytes<S>(TPI, NT, TABLE),
                      reinterpret_cast<const void *>(&dev::k_modexp_tasks<S, TPI, CRT, FORM, TABLE>),
                      sizeof(uint32_t) * warp_area * (dev::kThreads / 32),
