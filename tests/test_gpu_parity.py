@@ -190,7 +190,10 @@ def test_1mib_2048_encrypt_all_decrypt_sampled(ctx):
                                        (3072, True)])
 def test_every_kernel_geometry(ctx, P, nbits, crt):
     """Every compiled (lanes, form) geometry gives the same bit-exact result;
-    for the CRT residues also with the small odd-power table (window <= 4)."""
+    for the CRT residues also with the small odd-power table (window <= 4).
+    Each geometry runs in both of its instantiations: round robin, and over
+    key groups (explicit key indices in a random order, checked against the
+    oracle with the same indices)."""
     K = 3
     ks, ok = keys_for(ctx, K, nbits, seed=4242 + nbits)
     rng = np.random.default_rng(1)
@@ -203,23 +206,30 @@ def test_every_kernel_geometry(ctx, P, nbits, crt):
         vals[t] = f(Ns[t % K])
     c = np.stack([oracle.to_limbs(v, nbits // 32) for v in vals])
     ref = oracle.decrypt_chunks(c[:12], ok)
+    idx = rng.integers(0, K, n)  # explicit key indices: chunk t under key idx[t]
+    c2 = np.stack([oracle.to_limbs(W.random_below(rng, Ns[k]), nbits // 32) for k in idx])
+    ref2 = oracle.decrypt_chunks(c2[:12], ok, key_idx=idx[:12])
+    d_idx = torch.from_numpy(idx.astype(np.int32)).cuda()
     limbs = nbits // 64 if crt else nbits // 32
     configs = P.kernel_configs(limbs, crt)
     assert len(configs) >= 1
-    outs, tried = [], []
+    outs, outs2, tried = [], [], []
     for window in ((5, 4) if crt else (5,)):
         for tpi, form in configs:
             ctx.set_kernel_config(limbs, crt, tpi, form)
             ctx.set_kernel_window(limbs, crt, window)
             try:
                 outs.append(host(ctx.decrypt_chunks(ks, dev(c), use_crt=crt)))
+                outs2.append(host(ctx.decrypt_chunks(ks, dev(c2), use_crt=crt, key_idx=d_idx)))
                 tried.append((tpi, form, window))
             finally:
                 ctx.set_kernel_config(limbs, crt, 0)
                 ctx.set_kernel_window(limbs, crt, 0)
-    for o, cfg in zip(outs, tried):
+    for o, o2, cfg in zip(outs, outs2, tried):
         assert np.array_equal(o[:12], ref), cfg
         assert np.array_equal(o, outs[0]), cfg
+        assert np.array_equal(o2[:12], ref2), cfg
+        assert np.array_equal(o2, outs2[0]), cfg
     assert ctx.get_kernel_config(limbs, crt)[0] in {t for t, _ in configs}
     assert ctx.get_kernel_window(limbs, crt) == 5
 
