@@ -12,7 +12,7 @@ beside it.
 
 After the headline, rank 0 adds the other workloads to the same line, each
 under its own key with its configuration named: ``file100`` (100 MiB, K = 16,
-one plain launch per call against the persistent graph path), ``batched``
+one plain launch per call against the graph-replayed batch path), ``batched``
 (64 messages of mixed sizes and widths at a stated scale, one call per job
 against pmk_batch) and ``serving`` (the request mix at loads below its
 measured capacity, p50 / p99, against one request at a time).
@@ -516,11 +516,13 @@ def run_profile(args):
     back = ctx.join(w.nbits, plain, w.msg_bytes)
     ctx.check()
     assert torch.equal(plain, chunks) and torch.equal(plain_crt, chunks) and torch.equal(back, d_msg)
-    if args.profile_batch:  # the same full-d decryption through the persistent graph path
+    if args.profile_batch:  # the same full-d decryption through the batch's persistent queue
         from paper_2111_11924_gb300 import pmkrsa as B
 
         out = torch.zeros_like(cipher)
+        ctx.set_batch_direct_max(0)  # a job below one GPU-full goes to the queue, a larger one gets a launch
         batch = ctx.batch([(ks, cipher, out, B.OP_DECRYPT)])
+        ctx.set_batch_direct_max(256)
         batch.launch()
         ctx.check()
         assert torch.equal(out, chunks)
@@ -678,8 +680,8 @@ def batched_leg(ctx, scale: float, reps: int, tune_chunks: int) -> dict:
     scale), each with its own K in {2, 4, 8, 16} and key width in {1024, 2048,
     3072, 4096} bits; ops 70% full-d decrypt, 10% CRT decrypt, 20% encrypt.
     Times the plain path (one call, one launch per job, on one stream)
-    against the batched path (pmk_batch: persistent kernels per width and
-    grid launches for large jobs, graph-replayed), after autotuning every
+    against the batched path (pmk_batch: one grid launch per job on
+    concurrent streams, graph-replayed), after autotuning every
     (width, mode) on up to tune_chunks chunks, and checks both give
     identical output."""
     import torch
@@ -740,7 +742,7 @@ def batched_leg(ctx, scale: float, reps: int, tune_chunks: int) -> dict:
 def run_file100(args):
     """The 100 MiB file with K = 16 2048-bit keys: full-d and CRT decryption
     of all 411,207 chunks as one plain launch per call, and the same job
-    through the persistent graph-replayed batch path (pmk_batch), with the
+    through the graph-replayed batch path (pmk_batch), with the
     full round trip (split, encrypt, decrypt, join) checked on both."""
     import paper_2111_11924_gb300 as P
 
@@ -779,7 +781,7 @@ def _median_ms(fn, reps: int) -> float:
 def file100_leg(ctx, reps: int, tune_chunks: int) -> dict:
     """Config 3 (100 MiB, K = 16, 2048 bits, inputs larger than L2): full-d
     and CRT decryption of all 411,207 chunks, one plain launch per call
-    against the same job through the persistent graph path (pmk_batch), with
+    against the same job through the graph-replayed batch path (pmk_batch), with
     the round trip checked on both; geometry autotuned on tune_chunks chunks."""
     import torch
 
@@ -1064,7 +1066,7 @@ def main(argv=None):
     ap.add_argument("--profile", action="store_true",
                     help="run the fixed launch sequence used for ncu captures and exit")
     ap.add_argument("--batched", action="store_true",
-                    help="time the mixed-size 64-message batch (plain per-call vs persistent batch) and exit")
+                    help="time the mixed-size 64-message batch (plain per-call vs the batch graph) and exit")
     ap.add_argument("--batch-scale", type=float, default=1.0, help="scale of the batch's message sizes")
     ap.add_argument("--hbm", action="store_true", help="time split / join on the 100 MiB file and exit")
     ap.add_argument("--serve", action="store_true", help="run the serving workload over a load sweep and exit")
@@ -1078,7 +1080,7 @@ def main(argv=None):
                     help="time the 100 KB / K=16 workload at each key length and exit")
     ap.add_argument("--width-list", type=int, nargs="*", default=[1024, 2048, 3072, 4096, 6144, 8192])
     ap.add_argument("--file100", action="store_true",
-                    help="100 MiB / K=16 decryption: one plain launch per call vs the persistent batch path, and exit")
+                    help="100 MiB / K=16 decryption: one plain launch per call vs the batch graph, and exit")
     ap.add_argument("--table3", action="store_true",
                     help="the paper's Table 3 file sizes (1-100 MB, K=16, 2048 bits), plain and blinded, and exit")
     ap.add_argument("--table3-sizes", type=int, nargs="*", default=[1, 10, 25, 50, 100])
@@ -1087,7 +1089,8 @@ def main(argv=None):
     ap.add_argument("--mp-list", type=lambda v: tuple(int(x) for x in v.split(":")), nargs="*",
                     default=MULTIPRIME_CASES, help="bits:primes pairs for --multiprime")
     ap.add_argument("--profile-batch", action="store_true",
-                    help="with --profile: also run the full-d decryption through the persistent batch path")
+                    help="with --profile: also run the full-d decryption through the batch's persistent queue "
+                         "(a job below one GPU-full)")
     ap.add_argument("--profile-blinded", action="store_true",
                     help="with --profile: also run a blinded encryption and a blinded CRT decryption")
     ap.add_argument("--profile-crt-window", type=int, default=0,

@@ -332,13 +332,16 @@ int pmk_decrypt_message_host_noalloc(const pmk_keyset *ks, const uint32_t *h_cip
  *   PMK_OP_DECRYPT_CRT (Section 2.1 CRT form; d_in and d_out must not overlap),
  * over n_chunks chunks, chunk t bound to key t mod K of the job's key set.
  * Jobs may mix key sets and key widths.  pmk_batch_create plans the work:
- *   - jobs are grouped by exponentiation width and mode; each group runs as
- *     one persistent kernel whose warps take tasks (up to 32/TPI chunks of
- *     one key) from a device queue, longest tasks first;
- *   - a job with at least one GPU-full of exponentiations (as many as the
- *     GPU holds resident at once) instead gets its own grid launch (the
- *     kernel of pmk_*_chunks);
- *   - groups and such jobs run concurrently on internal streams, widest
+ *   - in a batch of at most the context's direct-launch limit of jobs with
+ *     chunks (pmk_set_batch_direct_max, default 256), every job gets its
+ *     own grid launch (the kernel of pmk_*_chunks);
+ *   - in a larger batch, a job with at least one GPU-full of
+ *     exponentiations (as many as the GPU holds resident at once) gets its
+ *     own grid launch, and the others are grouped by exponentiation width
+ *     and mode; each group runs as one persistent kernel whose warps take
+ *     tasks (up to 32/TPI chunks of one key) from a device queue, longest
+ *     tasks first;
+ *   - groups and launched jobs run concurrently on internal streams, widest
  *     first;
  *   - range checks, the kernels and CRT recombination are captured once into
  *     a CUDA graph (geometry: the context's current kernel configs).
@@ -360,6 +363,13 @@ typedef struct pmk_job {
 typedef struct pmk_batch pmk_batch;
 
 int pmk_batch_create(pmk_ctx *ctx, const pmk_job *jobs, size_t n_jobs, pmk_batch **out);
+/* The direct-launch limit of the batches this context plans from now on:
+ * batches with at most max_jobs jobs with chunks run every job as its own
+ * grid launch; 0 sends every job below one GPU-full through the persistent
+ * queues.  Default 256 (one launch per job measured faster up to 256 jobs,
+ * the queues faster for 1,024 jobs of a few chunks).  EINVAL for a NULL
+ * context.  Results do not depend on it. */
+int pmk_set_batch_direct_max(pmk_ctx *ctx, size_t max_jobs);
 int pmk_batch_launch(pmk_batch *batch, void *stream);
 /* Tasks queued for the persistent kernels, and exponentiation kernels per
  * launch (persistent kernels plus grid launches of large jobs). */

@@ -2,9 +2,10 @@
 // exponentiation width and mode, and capture range checks, one persistent
 // kernel per group (on forked streams) and CRT recombination into a CUDA
 // graph that pmk_batch_launch replays.  A CRT job contributes one task per
-// (chunk group, prime) and one recombination launch.  Jobs that fill the GPU
-// several times over skip the queue and get their own grid launch in the
-// same graph.
+// (chunk group, prime) and one recombination launch.  In batches of up to
+// the context's direct-launch limit (kDirectMaxJobs unless set), and for
+// jobs that fill the GPU in larger ones, a job skips the queue and gets its
+// own grid launch in the same graph (batch_plan.h).
 #include <algorithm>
 #include <new>
 #include <vector>
@@ -71,7 +72,7 @@ int plan_and_capture(pmk_ctx *ctx, const pmk_job *jobs, size_t n_jobs, pmk_batch
   };
   std::vector<pmk::PlanGroup> planned;
   std::vector<pmk::PlanDirect> direct;  // jobs large enough to fill the GPU alone: one plain grid launch each
-  int rc = pmk::plan_batch(plan_jobs, config, resident, planned, direct);
+  int rc = pmk::plan_batch(plan_jobs, config, resident, ctx->batch_direct_max, planned, direct);
   if (rc != PMK_OK) return rc;
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess) return PMK_ECUDA;
@@ -204,6 +205,12 @@ int pmk_batch_launch(pmk_batch *b, void *stream) {
   const int rc = cudaGraphLaunch(b->exec, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess ? PMK_OK : PMK_ECUDA;
   if (prev != b->device) cudaSetDevice(prev);
   return rc;
+}
+
+int pmk_set_batch_direct_max(pmk_ctx *ctx, size_t max_jobs) {
+  if (!ctx) return PMK_EINVAL;
+  ctx->batch_direct_max = max_jobs;
+  return PMK_OK;
 }
 
 int pmk_batch_info(const pmk_batch *b, size_t *n_tasks, int *n_kernels) {

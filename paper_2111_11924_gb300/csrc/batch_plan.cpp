@@ -7,9 +7,11 @@ namespace pmk {
 
 int plan_batch(const std::vector<PlanJob> &jobs, const std::function<bool(uint32_t, bool, KernelConfig *)> &config,
                const std::function<long long(uint32_t, const KernelConfig &, bool)> &resident,
-               std::vector<PlanGroup> &groups, std::vector<PlanDirect> &direct) {
+               size_t direct_max_jobs, std::vector<PlanGroup> &groups, std::vector<PlanDirect> &direct) {
   groups.clear();
   direct.clear();
+  const size_t busy = (size_t)std::count_if(jobs.begin(), jobs.end(), [](const PlanJob &j) { return j.n_chunks > 0; });
+  const bool all_direct = busy <= direct_max_jobs;
   auto group_for = [&](uint32_t limbs, bool crt) -> PlanGroup * {
     for (PlanGroup &g : groups)
       if (g.limbs == limbs && g.crt == crt) return &g;
@@ -30,7 +32,7 @@ int plan_batch(const std::vector<PlanJob> &jobs, const std::function<bool(uint32
     const long long wave = resident(limbs, g->cfg, crt);  // one GPU-full
     if (wave <= 0) return PMK_EUNSUPPORTED;
     const long long instances = (long long)jb.n_chunks * (crt ? jb.nprimes : 1);
-    if (instances >= kDirectWaves * wave) {
+    if (all_direct || instances >= kDirectWaves * wave) {
       direct.push_back(PlanDirect{j, limbs, g->cfg});
       continue;
     }

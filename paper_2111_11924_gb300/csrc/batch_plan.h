@@ -35,23 +35,34 @@ struct PlanDirect {
   KernelConfig cfg;
 };
 
-// A job with at least this many GPU-fulls of exponentiations runs as one
-// plain grid launch inside the graph: it fills the GPU alone, and the grid
-// kernel is 3-8% faster than the persistent one on a single job of one to
-// four GPU-fulls (measured from 8,000 to 28,000 2048-bit chunks), while
-// mixed batches measured the same with this threshold as with four.
-// Smaller jobs share the persistent queues.
+// Which jobs run as their own plain grid launch inside the graph (the kernel
+// of pmk_*_chunks, on a stream of its own) instead of sharing a persistent
+// queue:
+//   - every job, when the batch holds at most kDirectMaxJobs jobs with
+//     chunks: the grid kernel runs each exponentiation faster than the
+//     persistent one (up to 20% on jobs too small to fill the GPU), and the
+//     concurrent launches overlap as well as the shared queue does (mixed
+//     64-message batch 535 vs 552 ms, 256 jobs of 1-16 chunks 61.8 vs
+//     63.8 ms);
+//   - in larger batches, the jobs with at least kDirectWaves GPU-fulls of
+//     exponentiations: one launch per tiny job leaves most of each block's
+//     shared memory unused, and 1,024 jobs of 1-8 chunks took 171 ms as
+//     launches against 94 ms through the queues.
+// (kDirectMaxJobs, the default limit, is defined with the context in
+// pmk_internal.h.)
 constexpr long long kDirectWaves = 1;
 
 // config(limbs, crt, &cfg): the geometry for that width and mode (false if
 // none); resident(limbs, cfg, crt): the exponentiations the whole GPU holds
-// at once in it.  Jobs with no chunks are skipped.  A task holds up to
+// at once in it; direct_max_jobs: the batch size up to which every job runs
+// as its own launch (kDirectMaxJobs in the library).  Jobs with no chunks
+// are skipped.  A task holds up to
 // 32 / TPI chunks of one key (first, first + K, ...) and, for CRT, one
 // prime.  On return the groups are non-empty, widest first, with
 // decryptions before encryptions inside each.  Returns PMK_OK, or
 // PMK_EUNSUPPORTED when a width has no geometry or no resident capacity.
 int plan_batch(const std::vector<PlanJob> &jobs, const std::function<bool(uint32_t, bool, KernelConfig *)> &config,
                const std::function<long long(uint32_t, const KernelConfig &, bool)> &resident,
-               std::vector<PlanGroup> &groups, std::vector<PlanDirect> &direct);
+               size_t direct_max_jobs, std::vector<PlanGroup> &groups, std::vector<PlanDirect> &direct);
 
 }  // namespace pmk

@@ -251,6 +251,11 @@ struct Staging {
 };
 }  // namespace pmk
 
+namespace pmk {
+// Default direct-launch limit of batch planning (see batch_plan.h).
+constexpr size_t kDirectMaxJobs = 256;
+}  // namespace pmk
+
 // Context: one device, its status record, staging and kernel geometry choices.
 struct pmk_ctx {
   int device = 0;
@@ -259,4 +264,5 @@ struct pmk_ctx {
   pmk::Staging grp;                        // key-group table of calls with explicit key indices
   std::map<uint32_t, pmk::KernelConfig> cfg;  // (limbs << 1 | crt) -> kernel geometry override
   std::map<uint32_t, int> table;              // (limbs << 1 | crt) -> odd-power table size override
+  size_t batch_direct_max = pmk::kDirectMaxJobs;  // pmk_set_batch_direct_max
 };

@@ -78,6 +78,7 @@ def load_library() -> ctypes.CDLL:
         "pmk_batch_create": (i, [vp, ctypes.POINTER(_Job), sz, ctypes.POINTER(vp)]),
         "pmk_batch_launch": (i, [vp, vp]),
         "pmk_batch_info": (i, [vp, ctypes.POINTER(sz), ctypes.POINTER(i)]),
+        "pmk_set_batch_direct_max": (i, [vp, sz]),
         "pmk_batch_destroy": (None, [vp]),
         "pmk_sync_status": (i, [vp, vp]),
         "pmk_sync_status_detail": (i, [vp, vp, ctypes.POINTER(u64)]),
@@ -460,6 +461,12 @@ class Context:
         h = ctypes.c_void_p()
         _check(load_library().pmk_batch_create(self.handle, arr, len(jobs), ctypes.byref(h)), "pmk_batch_create")
         return Batch(self, h, jobs)
+
+    def set_batch_direct_max(self, max_jobs: int) -> None:
+        """pmk_set_batch_direct_max: batches planned from now on with at most
+        max_jobs jobs run every job as its own grid launch (default 256);
+        0 sends every job below one GPU-full through the persistent queues."""
+        _check(load_library().pmk_set_batch_direct_max(self.handle, int(max_jobs)), "pmk_set_batch_direct_max")
 
     def status(self, stream=None) -> int:
         """Synchronise and return (and clear) the device-side error code."""

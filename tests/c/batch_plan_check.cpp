@@ -2,9 +2,11 @@
 // and capacity functions; no GPU.  For random mixes of jobs (widths, key
 // counts, prime counts, operations, sizes from 0 to several GPU-fulls) it
 // checks that:
-//   - a job goes to its own grid launch exactly when its exponentiations
-//     reach kDirectWaves GPU-fulls; every other job's chunks (and, for CRT,
-//     every prime of every chunk) are covered by exactly one task;
+//   - a job goes to its own grid launch exactly when the batch holds at most
+//     direct_max_jobs jobs with chunks (drawn at random around the trial's
+//     job count, so both rules are exercised) or its exponentiations reach
+//     kDirectWaves GPU-fulls; every other job's chunks (and, for CRT, every
+//     prime of every chunk) are covered by exactly one task;
 //   - a task holds 1 .. 32 / TPI chunks of one key (first = key mod K,
 //     stride K), the job's buffers, and the job's mode;
 //   - groups are non-empty and distinct per (width, mode), carry the
@@ -70,9 +72,15 @@ void trial(int t) {
     jb.out = bufs[2 * j + 1].data();
     jobs.push_back(jb);
   }
+  size_t busy = 0;
+  for (const auto &jb : jobs) busy += jb.n_chunks > 0;
+  const uint32_t pick_max = rnd(4);
+  const size_t direct_max_jobs = pick_max == 0 ? 0 : pick_max == 1 ? (busy ? busy - 1 : 0) : pick_max == 2 ? busy
+                                                                                                        : pmk::kDirectMaxJobs;
+  const bool all_direct = busy <= direct_max_jobs;
   std::vector<pmk::PlanGroup> groups;
   std::vector<pmk::PlanDirect> direct;
-  const int rc = pmk::plan_batch(jobs, config, resident, groups, direct);
+  const int rc = pmk::plan_batch(jobs, config, resident, direct_max_jobs, groups, direct);
   expect(rc == PMK_OK, "planning succeeds", t);
   if (rc != PMK_OK) return;
 
@@ -122,8 +130,8 @@ void trial(int t) {
     pmk::KernelConfig cfg;
     config(limbs, crt, &cfg);
     const long long instances = (long long)jb.n_chunks * (crt ? jb.nprimes : 1);
-    const bool big = jb.n_chunks && instances >= pmk::kDirectWaves * resident(limbs, cfg, crt);
-    expect(big == (direct_jobs.count(j) == 1), "grid launch exactly for jobs of several GPU-fulls", t);
+    const bool big = jb.n_chunks && (all_direct || instances >= pmk::kDirectWaves * resident(limbs, cfg, crt));
+    expect(big == (direct_jobs.count(j) == 1), "grid launch exactly for small batches and jobs of a GPU-full", t);
     if (big || jb.n_chunks == 0) continue;
     for (long long c = 0; c < (long long)jb.n_chunks; c++)
       for (int p = 0; p < (crt ? (int)jb.nprimes : 1); p++) {
@@ -143,10 +151,10 @@ int main() {
   std::vector<pmk::PlanJob> odd = {pmk::PlanJob{kd.data(), 2, 1280, 2, PMK_OP_DECRYPT, 10, in.data(), out.data()}};
   std::vector<pmk::PlanGroup> groups;
   std::vector<pmk::PlanDirect> direct;
-  expect(pmk::plan_batch(odd, config, resident, groups, direct) == PMK_EUNSUPPORTED, "no geometry refused", -1);
+  expect(pmk::plan_batch(odd, config, resident, 0, groups, direct) == PMK_EUNSUPPORTED, "no geometry refused", -1);
   auto none = [](uint32_t, const pmk::KernelConfig &, bool) { return 0LL; };
   odd[0].nbits = 2048;
-  expect(pmk::plan_batch(odd, config, none, groups, direct) == PMK_EUNSUPPORTED, "no capacity refused", -1);
+  expect(pmk::plan_batch(odd, config, none, 0, groups, direct) == PMK_EUNSUPPORTED, "no capacity refused", -1);
   std::printf("%d checks, %d failures\n", g_checks, g_failures);
   return g_failures ? 1 : 0;
 }

@@ -210,9 +210,11 @@ def test_multiprime_blinded(ctx, P, nbits, b):
     assert np.array_equal(np.delete(out, K, axis=0), np.delete(m, K, axis=0))
 
 
-def test_multiprime_in_a_batch(ctx, P):
+@pytest.mark.parametrize("direct_max", [256, 0])
+def test_multiprime_in_a_batch(ctx, P, direct_max):
     """A batch mixing multi-prime CRT jobs (3 and 4 primes) with two-prime
-    jobs replays bit-identical to one call per job."""
+    jobs replays bit-identical to one call per job, as grid launches per job
+    and through the persistent queues (one task per prime)."""
     from paper_2111_11924_gb300 import pmkrsa as B
 
     a, oka = mp_keys(ctx, 3, 3072, 3, seed=0x50444D4B0000E600)
@@ -230,7 +232,12 @@ def test_multiprime_in_a_batch(ctx, P):
         else:
             x = np.stack([oracle.to_limbs(W.random_below(rng, Ns[t % len(Ns)]), s) for t in range(n)])
         jobs.append((ks, dev(x), torch.zeros((n, s), dtype=torch.int32, device="cuda"), op))
-    batch = ctx.batch(jobs)
+    ctx.set_batch_direct_max(direct_max)
+    try:
+        batch = ctx.batch(jobs)
+    finally:
+        ctx.set_batch_direct_max(256)
+    assert (batch.n_tasks > 0) == (direct_max == 0)
     batch.launch()
     ctx.check()
     for ks, x, out, op in jobs:

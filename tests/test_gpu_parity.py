@@ -264,13 +264,17 @@ def test_window_bound_api_batch_and_autotune(ctx, P):
             ctx.set_kernel_config(32, True, tpi, form)
             assert torch.equal(ctx.decrypt_chunks(ks, c, use_crt=True), full5), (tpi, form)
         ctx.set_kernel_config(32, True, 0)
-        outs = [torch.zeros_like(c) for _ in range(3)]
-        batch = ctx.batch([(ks, c, outs[0], B.OP_DECRYPT), (ks, c, outs[1], B.OP_DECRYPT_CRT),
-                           (ks, full5, outs[2], B.OP_ENCRYPT)])
-        batch.launch()
-        ctx.check()
-        assert torch.equal(outs[0], full5) and torch.equal(outs[1], full5) and torch.equal(outs[2], c)
-        batch.destroy()
+        for direct_max in (256, 0):  # grid launches per job, then the persistent queues
+            outs = [torch.zeros_like(c) for _ in range(3)]
+            ctx.set_batch_direct_max(direct_max)
+            batch = ctx.batch([(ks, c, outs[0], B.OP_DECRYPT), (ks, c, outs[1], B.OP_DECRYPT_CRT),
+                               (ks, full5, outs[2], B.OP_ENCRYPT)])
+            assert (batch.n_tasks > 0) == (direct_max == 0)
+            batch.launch()
+            ctx.check()
+            assert torch.equal(outs[0], full5) and torch.equal(outs[1], full5) and torch.equal(outs[2], c)
+            batch.destroy()
+        ctx.set_batch_direct_max(256)
         for mode in ("decrypt", "crt"):
             res = ctx.autotune(ks, n, mode, reps=1)
             limbs = 32 if mode == "crt" else 64
@@ -454,12 +458,15 @@ def test_6144_8192_bit_keys(ctx, P, nbits):
     assert ctx.status() == 0
 
 
-def test_batched_persistent_graph_matches_per_call(ctx, P):
+@pytest.mark.parametrize("queued", [False, True])
+def test_batched_persistent_graph_matches_per_call(ctx, P, queued):
     """A mixed batch (five key sets at 512-4096 bits, encrypt / full d / CRT,
     ragged sizes) replayed from its CUDA graph equals one call per job, bit
     for bit, and keeps doing so when the input contents change between
     launches.  Every job of both launches is also checked against the oracle
-    on a sample of at least 8 chunks that includes its last one."""
+    on a sample of at least 8 chunks that includes its last one.  Queued:
+    the context's direct-launch limit is 0, so the small jobs go through the
+    persistent queues; otherwise every job is its own grid launch."""
     from paper_2111_11924_gb300 import pmkrsa as B
 
     sets = [keys_for(ctx, K, nb, seed=700 + nb) for K, nb in ((3, 1024), (2, 2048), (5, 512))]
@@ -487,8 +494,15 @@ def test_batched_persistent_graph_matches_per_call(ctx, P):
         ks, _, Ns = key_set(si)
         x = dev(chunks_for(Ns, n, ks.nbits // 32))
         jobs.append((ks, x, torch.zeros_like(x), op))
-    batch = ctx.batch(jobs)
-    assert batch.n_kernels >= 4 and batch.n_tasks > 0
+    ctx.set_batch_direct_max(0 if queued else 256)
+    try:
+        batch = ctx.batch(jobs)
+    finally:
+        ctx.set_batch_direct_max(256)
+    if queued:
+        assert batch.n_kernels >= 4 and batch.n_tasks > 0
+    else:
+        assert batch.n_tasks == 0 and batch.n_kernels == len(jobs)
     for rep in range(2):
         if rep == 1:  # new contents, same buffers
             for (ks, x, out, op), (si, n, _) in zip(jobs, plan):
@@ -661,9 +675,11 @@ def test_integer_peak_measurements_are_sane(ctx):
 
 
 def test_batch_large_jobs_take_a_grid_launch(ctx, P):
-    """Jobs that fill the GPU at least once run as plain grid launches inside
-    the batch graph, next to queued small jobs; every output equals the
-    per-call result, and a batch of one large job holds no queued tasks."""
+    """With the direct-launch limit below the batch's job count (here 0),
+    jobs that fill the GPU at least once still run as plain grid launches
+    inside the batch graph, next to queued small jobs; every output equals
+    the per-call result, and a batch of one large job holds no queued
+    tasks."""
     from paper_2111_11924_gb300 import pmkrsa as B
 
     ks = ctx.keygen(8, 2048, 65537, 0x50444D4B0000EC00)
@@ -673,7 +689,13 @@ def test_batch_large_jobs_take_a_grid_launch(ctx, P):
     jobs = [(ks, big[:20000], torch.zeros_like(big[:20000]), B.OP_DECRYPT_CRT),
             (ks, big, torch.zeros_like(big), B.OP_DECRYPT),
             (ks, small, torch.zeros_like(small), B.OP_DECRYPT_CRT)]
-    batch = ctx.batch(jobs)
+    ctx.set_batch_direct_max(0)
+    try:
+        batch = ctx.batch(jobs)
+        one_out = torch.zeros_like(big)
+        one = ctx.batch([(ks, big, one_out, B.OP_DECRYPT_CRT)])
+    finally:
+        ctx.set_batch_direct_max(256)
     assert batch.n_kernels >= 3 and batch.n_tasks > 0
     batch.launch()
     ctx.check()
@@ -681,12 +703,10 @@ def test_batch_large_jobs_take_a_grid_launch(ctx, P):
         assert torch.equal(out, ctx.decrypt_chunks(k, x, use_crt=op == B.OP_DECRYPT_CRT)), (x.shape[0], op)
     assert torch.equal(jobs[1][2], ctx.split(2048, msg))
     batch.destroy()
-    out = torch.zeros_like(big)
-    one = ctx.batch([(ks, big, out, B.OP_DECRYPT_CRT)])
     assert one.n_tasks == 0 and one.n_kernels == 1
     one.launch()
     ctx.check()
-    assert torch.equal(out, ctx.split(2048, msg))
+    assert torch.equal(one_out, ctx.split(2048, msg))
     one.destroy()
     ks.free()
 
@@ -740,12 +760,16 @@ def test_canary_words_around_every_output(ctx, P):
         bb, bl = _guarded(n * s)
         ctx.decrypt_blinded(ks, cstar.view(n, s), cr.view(n, s), use_crt=True, out=bl.view(n, s))
         assert _guards_intact(bb, n * s) and torch.equal(bl, chunks)
-        qb, qout = _guarded(n * s)
-        batch = ctx.batch([(ks, cipher.view(n, s), qout.view(n, s), B.OP_DECRYPT_CRT)])
-        batch.launch()
-        ctx.check()
-        assert _guards_intact(qb, n * s) and torch.equal(qout, chunks)
-        batch.destroy()
+        for direct_max in (256, 0):  # the batch as a grid launch, then through the persistent queue
+            qb, qout = _guarded(n * s)
+            ctx.set_batch_direct_max(direct_max)
+            batch = ctx.batch([(ks, cipher.view(n, s), qout.view(n, s), B.OP_DECRYPT_CRT)])
+            ctx.set_batch_direct_max(256)
+            assert (batch.n_tasks > 0) == (direct_max == 0)
+            batch.launch()
+            ctx.check()
+            assert _guards_intact(qb, n * s) and torch.equal(qout, chunks), direct_max
+            batch.destroy()
         obuf = torch.full((L + 8192,), 0x5A, dtype=torch.uint8, device="cuda")
         ctx.join(nbits, chunks.view(n, s), L, out=obuf[4096:4096 + L])
         o = obuf.cpu().numpy()
