@@ -42,12 +42,24 @@ bool overlap(const void *a, size_t na, const void *b, size_t nb) {
   return x < y + nb && y < x + na;
 }
 
-void release(pmk_batch *b) {
-  if (b->exec) cudaGraphExecDestroy(b->exec);
+// The streams and events exist only to record the graph (cross-stream waits
+// become dependency edges), and the instantiated graph is independent of the
+// recorded one: all of them go as soon as the graph is instantiated, so a
+// batch of many jobs does not hold a stream per job for its lifetime.
+void drop_capture(pmk_batch *b) {
   if (b->graph) cudaGraphDestroy(b->graph);
   for (cudaEvent_t e : b->events) cudaEventDestroy(e);
   for (cudaStream_t s : b->side) cudaStreamDestroy(s);
   if (b->capture) cudaStreamDestroy(b->capture);
+  b->graph = nullptr;
+  b->events.clear();
+  b->side.clear();
+  b->capture = nullptr;
+}
+
+void release(pmk_batch *b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  drop_capture(b);
   cudaFree(b->d_tasks);
   cudaFree(b->d_counters);
 }
@@ -153,6 +165,7 @@ int plan_and_capture(pmk_ctx *ctx, const pmk_job *jobs, size_t n_jobs, pmk_batch
   if (rc != PMK_OK) return rc;
   if (end != cudaSuccess || !graph) return PMK_ECUDA;
   if (cudaGraphInstantiate(&b->exec, graph, 0) != cudaSuccess) return PMK_ECUDA;
+  drop_capture(b);
   return PMK_OK;
 }
 
