@@ -175,8 +175,8 @@ __global__ void __launch_bounds__(kAuxThreads) k_range(const KeyDev *__restrict_
 // Key groups for explicit key indices, in three passes.
 //   count:   histogram of the indices (a shared-memory histogram per block,
 //            added into count[0..K) once per bin);
-//   offsets: poff[k] = sum over j < k of count[j] rounded up to kGroupAlign
-//            slots, poff[K] the total (one block; also cursor[k] = poff[k]);
+//   offsets: poff[k] = sum over j < k of count[j] rounded up to the table's
+//            alignment, poff[K] the total (one block; also cursor[k] = poff[k]);
 //   scatter: slot[cursor[k]++] = t for every chunk t of key k.  The lanes of
 //            a warp with equal keys take consecutive slots with one atomic.
 // The slot table starts filled with kNoChunk (the padding).  Slot order
@@ -200,13 +200,13 @@ __global__ void __launch_bounds__(kAuxThreads) k_key_count(const uint32_t *__res
 constexpr int kScanThreads = 1024;
 
 __global__ void __launch_bounds__(kScanThreads) k_key_offsets(const uint32_t *__restrict__ count, uint32_t K,
-                                                              uint32_t *__restrict__ poff,
+                                                              uint32_t align, uint32_t *__restrict__ poff,
                                                               uint32_t *__restrict__ cursor) {
   __shared__ uint32_t part[kScanThreads];
   const uint32_t per = (K + kScanThreads - 1) / kScanThreads;  // keys per thread, contiguous
   const uint32_t k0 = threadIdx.x * per, k1 = min(K, k0 + per);
   uint32_t sum = 0;
-  for (uint32_t k = k0; k < k1; k++) sum += (count[k] + kGroupAlign - 1) / kGroupAlign * kGroupAlign;
+  for (uint32_t k = k0; k < k1; k++) sum += (count[k] + align - 1) / align * align;
   part[threadIdx.x] = sum;
   __syncthreads();
   for (int d = 1; d < kScanThreads; d <<= 1) {  // inclusive scan (Hillis-Steele)
@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(kScanThreads) k_key_offsets(const uint32_t *__
   for (uint32_t k = k0; k < k1; k++) {
     poff[k] = off;
     cursor[k] = off;
-    off += (count[k] + kGroupAlign - 1) / kGroupAlign * kGroupAlign;
+    off += (count[k] + align - 1) / align * align;
   }
   if (threadIdx.x == kScanThreads - 1) poff[K] = part[threadIdx.x];
 }
@@ -406,16 +406,17 @@ size_t key_groups_words(size_t n, uint32_t K) {
   return (size_t)(K + 1) + (n + (size_t)kGroupAlign * K) + 2 * (size_t)K;
 }
 
-int launch_key_groups(const uint32_t *key_idx, size_t n, uint32_t K, uint32_t *table, uint32_t *status,
-                      cudaStream_t st) {
+int launch_key_groups(const uint32_t *key_idx, size_t n, uint32_t K, uint32_t align, uint32_t *table,
+                      uint32_t *status, cudaStream_t st) {
   if (K == 0 || K > 16383 || n >= kMaxGroupedChunks) return PMK_EINVAL;
+  if (align == 0 || align > kGroupAlign || (align & (align - 1))) return PMK_EINVAL;
   const size_t nslot = n + (size_t)kGroupAlign * K;
   uint32_t *poff = table, *slot = table + K + 1, *count = slot + nslot, *cursor = count + K;
   if (cudaMemsetAsync(slot, 0xff, nslot * 4, st) != cudaSuccess ||
       cudaMemsetAsync(count, 0, (size_t)K * 4, st) != cudaSuccess)
     return PMK_ECUDA;
   if (n == 0) {
-    k_key_offsets<<<1, kScanThreads, 0, st>>>(count, K, poff, cursor);
+    k_key_offsets<<<1, kScanThreads, 0, st>>>(count, K, align, poff, cursor);
     return cuda_rc(cudaGetLastError());
   }
   const size_t hist_bytes = (size_t)K * 4;
@@ -423,7 +424,7 @@ int launch_key_groups(const uint32_t *key_idx, size_t n, uint32_t K, uint32_t *t
   if (rc != PMK_OK) return rc;
   const int g = (int)std::min<long long>(grid_for((long long)n, kAuxThreads), 152LL * 4);
   k_key_count<<<g, kAuxThreads, hist_bytes, st>>>(key_idx, (long long)n, K, count, status);
-  k_key_offsets<<<1, kScanThreads, 0, st>>>(count, K, poff, cursor);
+  k_key_offsets<<<1, kScanThreads, 0, st>>>(count, K, align, poff, cursor);
   k_key_scatter<<<grid_for((long long)n, kAuxThreads), kAuxThreads, 0, st>>>(key_idx, (long long)n, K, cursor, slot);
   return cuda_rc(cudaGetLastError());
 }
@@ -449,7 +450,8 @@ const MulmodEntry *crt_sum_entries(int *count) {
 }
 
 int launch_crt_sum(uint32_t limbs, uint32_t parts, const KeyDev *keys, uint32_t K, uint32_t *out, size_t n,
-                   cudaStream_t st, uint32_t *status_if_zero_residue, const uint32_t *groups) {
+                   cudaStream_t st, uint32_t *status_if_zero_residue, const uint32_t *groups,
+                   uint32_t groups_align) {
   if (n == 0) return PMK_OK;
   if (parts < 2 || parts > (uint32_t)kMaxPrimes || limbs % parts || K == 0 || K > 65535) return PMK_EINVAL;
   int cnt = 0;
@@ -461,7 +463,9 @@ int launch_crt_sum(uint32_t limbs, uint32_t parts, const KeyDev *keys, uint32_t 
   if (rc != PMK_OK) return rc;
   const long long per_key = ((long long)n + K - 1) / K;
   const int ipb = dev::kThreads / e->tpi;
-  dim3 grid = groups ? dim3((unsigned)(((long long)n + (long long)kGroupAlign * K + ipb - 1) / ipb), 1)
+  if (groups && (groups_align == 0 || groups_align > kGroupAlign || groups_align % ipb))
+    return PMK_EUNSUPPORTED;  // a block must not straddle two keys' slots
+  dim3 grid = groups ? dim3((unsigned)(((long long)n + (long long)(groups_align - 1) * K + ipb - 1) / ipb), 1)
                      : dim3((unsigned)((per_key + ipb - 1) / ipb), K);
   long long nl = (long long)n;
   int B = (int)parts;
@@ -502,6 +506,19 @@ int launch_modexp_naive(bool enc, uint32_t limbs, const KeyDev *keys, uint32_t K
 }
 
 bool modexp_built(uint32_t limbs, KernelConfig cfg, bool crt) { return find_entry(limbs, cfg, crt) != nullptr; }
+
+uint32_t modexp_block_instances(uint32_t limbs, KernelConfig cfg, bool crt) {
+  const ModexpEntry *e = find_entry(limbs, cfg, crt);
+  return e ? (uint32_t)(e->threads / e->tpi) : 0u;
+}
+
+uint32_t crt_sum_block_instances(uint32_t limbs) {
+  int cnt = 0;
+  const MulmodEntry *list = crt_sum_entries(&cnt);
+  for (int i = 0; i < cnt; i++)
+    if (list[i].limbs == (int)limbs) return (uint32_t)(dev::kThreads / list[i].tpi);
+  return 0u;
+}
 
 // Defaults measured on GB300 (1 MiB and 100 MiB workloads at 2048 bits):
 // 64-limb full-width and 32-limb CRT residues run fastest with independent
@@ -586,7 +603,8 @@ int launch_modexp_tasks(uint32_t limbs, KernelConfig cfg, bool crt, const BatchT
 }
 
 int launch_modexp(ExpMode mode, uint32_t limbs, KernelConfig cfg, const KeyDev *keys, uint32_t K, const uint32_t *in,
-                  uint32_t *out, size_t n, cudaStream_t st, uint32_t parts, const uint32_t *groups) {
+                  uint32_t *out, size_t n, cudaStream_t st, uint32_t parts, const uint32_t *groups,
+                  uint32_t groups_align) {
   if (n == 0) return PMK_OK;
   const bool crt = mode == ExpMode::kCrtHalf || mode == ExpMode::kCrtInverse;
   if (crt && (parts < 2 || parts > (uint32_t)kMaxPrimes)) return PMK_EINVAL;
@@ -598,8 +616,9 @@ int launch_modexp(ExpMode mode, uint32_t limbs, KernelConfig cfg, const KeyDev *
   if (rc != PMK_OK) return rc;
   const long long per_key = ((long long)n + K - 1) / K;
   const int ipb = e->threads / e->tpi;
-  if (groups && kGroupAlign % ipb) return PMK_EUNSUPPORTED;  // a block must not straddle two keys' slots
-  dim3 grid = groups ? dim3((unsigned)(((long long)n + (long long)kGroupAlign * K + ipb - 1) / ipb), crt ? parts : 1)
+  if (groups && (groups_align == 0 || groups_align > kGroupAlign || groups_align % ipb))
+    return PMK_EUNSUPPORTED;  // a block must not straddle two keys' slots
+  dim3 grid = groups ? dim3((unsigned)(((long long)n + (long long)(groups_align - 1) * K + ipb - 1) / ipb), crt ? parts : 1)
                      : dim3((unsigned)((per_key + ipb - 1) / ipb), crt ? parts * K : K);
   long long nl = (long long)n;
   int sel = (mode == ExpMode::kEncrypt || mode == ExpMode::kCrtInverse) ? 1 : 0;

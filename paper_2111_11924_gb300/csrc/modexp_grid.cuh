@@ -49,9 +49,10 @@ __device__ __forceinline__ void crt_input(uint32_t (&a)[S / TPI], const uint32_t
 //   Key groups (grp != nullptr, explicit key indices): grp holds the padded
 //     segment offsets poff[0..K] followed by the slot table (see
 //     launch_key_groups); key k owns slots [poff[k], poff[k+1]), a multiple
-//     of 64 long, each holding a chunk index or kNoChunk.  Block x takes
-//     slots [x IPB, (x + 1) IPB) (IPB divides 64, so one key's), its key is
-//     found by binary search over poff, and blockIdx.y is the prime.
+//     of the table's alignment long, each holding a chunk index or
+//     kNoChunk.  Block x takes slots [x IPB, (x + 1) IPB) (IPB divides the
+//     alignment, so one key's), its key is found by binary search over
+//     poff, and blockIdx.y is the prime.
 struct BlockChunks {
   uint32_t key;
   long long first_slot;  // round robin: the block's first chunk; groups: its first slot

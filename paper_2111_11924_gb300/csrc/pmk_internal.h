@@ -44,7 +44,8 @@ __device__ __forceinline__ void report(uint32_t *status, uint32_t flag, long lon
 int clear_status(uint32_t *status, cudaStream_t st);
 
 // Key groups (explicit key indices): each key's chunks occupy a segment of
-// slots padded to a multiple of kGroupAlign; a padding slot holds kNoChunk.
+// slots padded to a multiple of the table's alignment (a power of two, at
+// most kGroupAlign); a padding slot holds kNoChunk.
 constexpr uint32_t kGroupAlign = 64;
 constexpr uint32_t kNoChunk = 0xffffffffu;
 // Most chunks of a call with explicit key indices (slot numbers stay 32-bit).
@@ -172,9 +173,14 @@ int launch_range_check(const KeyDev *keys, uint32_t K, uint32_t s, const uint32_
 // poff[0..K] followed by the slot table, chunks of key k in slots
 // [poff[k], poff[k + 1]).  Indices >= K set kStatusKeyIndex in *status and
 // their chunks get no slot.  K <= 16383.
+// Each key's segment is padded to a multiple of `align` slots (a power of
+// two, 1 .. kGroupAlign): the largest instances-per-block of the kernels
+// that will read the table, so that a block never straddles two keys and a
+// key has at most one partly filled block per kernel.
 size_t key_groups_words(size_t n, uint32_t K);
-int launch_key_groups(const uint32_t *key_idx, size_t n, uint32_t K, uint32_t *table, uint32_t *status,
-                      cudaStream_t st);
+int launch_key_groups(const uint32_t *key_idx, size_t n, uint32_t K, uint32_t align, uint32_t *table,
+                      uint32_t *status, cudaStream_t st);
+
 // Launch geometry of an exponentiation kernel: lanes per instance, Montgomery
 // form (0 = one carry chain per lane, 1 = independent columns) and the
 // odd-power table size (kTableFull or kTableSmall; a geometry compiled only
@@ -183,17 +189,24 @@ struct KernelConfig {
   uint32_t tpi = 0, form = 0;
   int table = kTableFull;
 };
+// Instances per block of the exponentiation kernel of a geometry, and of the
+// CRT recombination at a full width (0 if not built): the alignment a key
+// group table needs for them.
+uint32_t modexp_block_instances(uint32_t limbs, KernelConfig cfg, bool crt);
+uint32_t crt_sum_block_instances(uint32_t limbs);
 // CRT modes run `parts` residues per chunk (the key's prime count) over
 // `limbs` = s / parts limbs each; residue i of chunk t goes to out[t][i * limbs].
-// With `groups` (a table of launch_key_groups) chunks are taken by key group
-// instead of round robin.
+// With `groups` (a table of launch_key_groups built with alignment
+// groups_align) chunks are taken by key group instead of round robin.
 int launch_modexp(ExpMode mode, uint32_t limbs, KernelConfig cfg, const KeyDev *keys, uint32_t K, const uint32_t *in,
-                  uint32_t *out, size_t n, cudaStream_t st, uint32_t parts = 2, const uint32_t *groups = nullptr);
+                  uint32_t *out, size_t n, cudaStream_t st, uint32_t parts = 2, const uint32_t *groups = nullptr,
+                  uint32_t groups_align = kGroupAlign);
 // CRT recombination of `parts` residues per chunk (limbs / parts limbs
 // each) in place at full width `limbs`: out[t] holds the residues and
 // receives the value mod N.
 int launch_crt_sum(uint32_t limbs, uint32_t parts, const KeyDev *keys, uint32_t K, uint32_t *out, size_t n,
-                   cudaStream_t st, uint32_t *status_if_zero_residue = nullptr, const uint32_t *groups = nullptr);
+                   cudaStream_t st, uint32_t *status_if_zero_residue = nullptr, const uint32_t *groups = nullptr,
+                   uint32_t groups_align = kGroupAlign);
 // Fused blinded CRT decryption: out[t][i] = c*[t]^(d_i) c_r[t]^(r_i - 1 - d_i)
 // mod r_i for each of the key's `parts` primes (prime_limbs limbs each); the
 // residues of (c* c_r^-1)^d, to be recombined by launch_crt_sum.  A c_r

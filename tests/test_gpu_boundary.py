@@ -74,6 +74,31 @@ def test_key_index_every_chunk_matches_oracle(env, nbits, K, n, pattern):
     ks.free()
 
 
+def test_key_index_where_the_kernels_differ_in_block_size(env):
+    """4096-bit keys: the CRT residue kernel holds 16 instances per block and
+    the recombination 8, so the key-group table is aligned to the larger;
+    random and one-key maps give the oracle's results for full d and CRT
+    (the oracle computes with the library's exported keys)."""
+    P, oracle, ctx = env
+    K, nbits = 4, 4096
+    ks = ctx.keygen(K, nbits, 65537, 0x50444D4B0000E800)
+    ok = oracle.OracleKeys(K, nbits, 65537, ks.export())
+    rng = np.random.default_rng(48)
+    n = 301
+    m = oracle.split(rng.integers(0, 256, n * (nbits // 8 - 1) - 11, dtype=np.uint8), nbits)
+    for idx in (rng.integers(0, K, n), np.full(n, 2)):
+        idx = idx.astype(np.uint32)
+        d_idx = _dev(idx)
+        c = ctx.encrypt_chunks(ks, _dev(m), key_idx=d_idx)
+        ctx.check()
+        assert np.array_equal(c.cpu().numpy().view(np.uint32), oracle.encrypt_chunks(m, ok, threads=8, key_idx=idx))
+        for use_crt in (False, True):
+            back = ctx.decrypt_chunks(ks, c, use_crt=use_crt, key_idx=d_idx)
+            ctx.check()
+            assert np.array_equal(back.cpu().numpy().view(np.uint32), m), use_crt
+    ks.free()
+
+
 def test_key_index_round_robin_map_equals_null(env):
     """key_idx[t] = t mod K reproduces the call without indices bit for bit,
     in place as well."""
