@@ -27,6 +27,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -54,8 +55,8 @@ KERNELS_PER_STEP = 6  # split, range check + modexp (encrypt), range check + mod
 # slots of their own).
 TRAFFIC_SOURCES = ["paper_2111_11924_gb300/csrc/modexp_core.cuh", "paper_2111_11924_gb300/csrc/modexp_grid.cuh"]
 COUNTERS_MEASURED = {  # source digest -> counters of one launch
-    "aaf81f9378ddee50": {"traffic": 1273600, "issue_active_pct": 50.80, "warps_active_per_sm": 6.93,
-                         "alu_pipe_pct": 57.16, "fmaheavy_pipe_pct": 60.34, "warp_instructions": 10037561520},
+    "5829c9343745b4f4": {"traffic": 1273600, "issue_active_pct": 50.80, "warps_active_per_sm": 6.93,
+                         "alu_pipe_pct": 57.17, "fmaheavy_pipe_pct": 60.34, "warp_instructions": 10037561520},
 }
 
 
@@ -72,11 +73,19 @@ def issue_slots(counters: dict, alg_macs: float):
             "source": "ncu counters of one launch on this workload (profiles/modexp_fulld_1MiB_K8_2048bit.md)"}
 
 
-def sources_digest() -> str:
+def code_digest(texts) -> str:
+    """Digest of C++ sources with comments and whitespace removed, so that a
+    change of wording in a comment keeps the counters of the same code."""
     h = hashlib.sha256()
-    for f in TRAFFIC_SOURCES:
-        h.update(open(os.path.join(ROOT, f), "rb").read())
+    for text in texts:
+        code = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        code = re.sub(r"//[^\n]*", " ", code)
+        h.update(" ".join(code.split()).encode())
     return h.hexdigest()[:16]
+
+
+def sources_digest() -> str:
+    return code_digest(open(os.path.join(ROOT, f)).read() for f in TRAFFIC_SOURCES)
 
 
 def algorithmic_montmuls(nbits: int) -> float:

@@ -55,3 +55,11 @@ def test_issue_slots_follow_the_current_kernel_sources():
     assert bench.issue_slots({}, macs) is None
     for counters in bench.COUNTERS_MEASURED.values():
         assert set(counters) >= {"traffic", "issue_active_pct", "warp_instructions"}
+
+
+def test_counter_digest_ignores_comments_only():
+    a = "int f(int x) {  // add one\n  return x + 1; /* plain */ }\n"
+    b = "int f(int x) {\n  // adds 1 to x\n  return x + 1;\n}\n"
+    c = "int f(int x) { return x + 2; }"
+    assert bench.code_digest([a]) == bench.code_digest([b])
+    assert bench.code_digest([a]) != bench.code_digest([c])
