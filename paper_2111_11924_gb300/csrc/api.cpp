@@ -668,7 +668,7 @@ int pmk_encrypt_chunks(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_in,
   if (!g.ok()) return PMK_ECUDA;
   cudaStream_t st = as_stream(stream);
   const uint32_t *groups = nullptr;
-  const uint32_t align = group_align(ctx, ks, false);
+  const uint32_t align = d_key_idx ? group_align(ctx, ks, false) : pmk::kGroupAlign;
   rc = key_groups_for(ctx, ks, d_key_idx, n_chunks, st, align, &groups);
   if (rc == PMK_OK) rc = enqueue_encrypt(ctx, ks, d_in, d_out, n_chunks, st, d_key_idx, groups, align);
   if (d_key_idx) release(ctx->grp, st);
@@ -687,7 +687,7 @@ int pmk_decrypt_chunks(pmk_ctx *ctx, const pmk_keyset *ks, const uint32_t *d_in,
   if (!g.ok()) return PMK_ECUDA;
   cudaStream_t st = as_stream(stream);
   const uint32_t *groups = nullptr;
-  const uint32_t align = group_align(ctx, ks, use_crt != 0);
+  const uint32_t align = d_key_idx ? group_align(ctx, ks, use_crt != 0) : pmk::kGroupAlign;
   rc = key_groups_for(ctx, ks, d_key_idx, n_chunks, st, align, &groups);
   if (rc == PMK_OK) rc = enqueue_decrypt(ctx, ks, d_in, d_out, n_chunks, use_crt, st, d_key_idx, groups, align);
   if (d_key_idx) release(ctx->grp, st);

@@ -83,7 +83,7 @@ int plan_and_capture(pmk_ctx *ctx, const pmk_job *jobs, size_t n_jobs, pmk_batch
     return pmk::modexp_resident_instances(limbs, cfg, crt);
   };
   std::vector<pmk::PlanGroup> planned;
-  std::vector<pmk::PlanDirect> direct;  // jobs large enough to fill the GPU alone: one plain grid launch each
+  std::vector<pmk::PlanDirect> direct;  // jobs with a grid launch of their own
   int rc = pmk::plan_batch(plan_jobs, config, resident, ctx->batch_direct_max, planned, direct);
   if (rc != PMK_OK) return rc;
   int sms = 0;
@@ -221,6 +221,7 @@ int pmk_batch_launch(pmk_batch *b, void *stream) {
 }
 
 int pmk_set_batch_direct_max(pmk_ctx *ctx, size_t max_jobs) {
+  pmk::TraceRange trace("pmk_set_batch_direct_max");
   if (!ctx) return PMK_EINVAL;
   ctx->batch_direct_max = max_jobs;
   return PMK_OK;
