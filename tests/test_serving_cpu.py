@@ -103,3 +103,25 @@ def test_batch_layout_keeps_each_requests_key_binding():
         assert list(key_idx[a:b]) == [t % K for t in range(b - a)]  # chunk t of every request: key t mod K
         for c in (a, b - 1):
             assert SV.request_of_chunk(offsets, c) == i
+
+
+def test_dispatch_keeps_priority_lanes_for_small_batches():
+    """Lanes 0-1 are priority lanes for batches of at most 100 chunks: a small
+    head takes one, a large head takes an ordinary lane or waits, and when
+    only priority lanes are free the oldest small requests go ahead of a
+    large one; without priority lanes any lane takes the head."""
+    def req(rid, n, nbits=1024):
+        return SV.Request(rid=rid, op="decrypt", nbits=nbits, arrival=rid, msg_len=n * 127, payload=None)
+
+    big, small1, small2 = req(0, 500), req(1, 10), req(2, 20)
+    lane, batch = SV.dispatch([small1, big], [0, 1, 2, 3], 2, 100, 1 << 30)
+    assert lane in (0, 1) and [r.rid for r in batch] == [1]
+    lane, batch = SV.dispatch([big, small1], [0, 1, 2, 3], 2, 100, 1 << 30)
+    assert lane in (2, 3) and 0 in [r.rid for r in batch]
+    lane, batch = SV.dispatch([big, small1, small2], [0, 1], 2, 100, 1 << 30)
+    assert lane in (0, 1) and [r.rid for r in batch] == [1, 2]
+    assert SV.dispatch([big], [0, 1], 2, 100, 1 << 30) is None
+    lane, batch = SV.dispatch([small1], [2], 2, 100, 1 << 30)  # no priority lane free: an ordinary one
+    assert lane == 2 and [r.rid for r in batch] == [1]
+    lane, batch = SV.dispatch([big, small1], [0, 1, 2], 0, 100, 1 << 30)
+    assert lane == 2 and [r.rid for r in batch] == [0, 1]
