@@ -847,7 +847,7 @@ def run_serving(args):
 
 
 def serving_leg(ctx, n_requests: int, loads: tuple, scale: float, plain_at: float | None,
-                priority_lanes: int | None = None) -> dict:
+                priority_lanes: int | None = None, lanes: int = 4, small_chunks: int = 4096) -> dict:
     """Config 5: encrypt / decrypt requests (70% decrypt, CRT form), payloads
     log-uniform over 1 KB - 25 MB times `scale`, key widths uniform over
     {2048, 3072, 4096} with resident key tables (K = 8 each), admission by a
@@ -879,8 +879,8 @@ def serving_leg(ctx, n_requests: int, loads: tuple, scale: float, plain_at: floa
     SV.prepare_payloads(ctx, keysets, reqs)
     payload = sum(r.msg_len for r in reqs)
     mean_payload = payload / len(reqs)
-    server = SV.Server(ctx, keysets, budget_bytes=40 << 30, slots=256, use_crt=True, lanes=4,
-                       priority_lanes=priority_lanes)
+    server = SV.Server(ctx, keysets, budget_bytes=40 << 30, slots=256, use_crt=True, lanes=lanes,
+                       priority_lanes=priority_lanes, small_chunks=small_chunks)
 
     def run(rate, plain=False):
         for r, a in zip(reqs, unit_arrival):
@@ -931,7 +931,7 @@ def serving_leg(ctx, n_requests: int, loads: tuple, scale: float, plain_at: floa
            "mean_payload_MB": round(mean_payload / 2**20, 3),
            "configured_rate_offered_GBps": round(2000 * mean_payload / 2**30, 2),
            "capacity_MBps": round(cap_MBps, 2), "kernels_MBps": round(kern_MBps, 2),
-           "capacity_over_kernels": round(cap_MBps / kern_MBps, 3), "lanes": 4,
+           "capacity_over_kernels": round(cap_MBps / kern_MBps, 3), "lanes": lanes,
            "priority_lanes": server.priority_lanes, "small_batch_chunks": server.small_chunks, "sweep": sweep}
     if plain_at is not None:
         rate = plain_at * cap_MBps * 2**20 / mean_payload
