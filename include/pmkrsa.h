@@ -372,7 +372,7 @@ int pmk_batch_create(pmk_ctx *ctx, const pmk_job *jobs, size_t n_jobs, pmk_batch
 int pmk_set_batch_direct_max(pmk_ctx *ctx, size_t max_jobs);
 int pmk_batch_launch(pmk_batch *batch, void *stream);
 /* Tasks queued for the persistent kernels, and exponentiation kernels per
- * launch (persistent kernels plus grid launches of large jobs). */
+ * launch (persistent kernels plus the jobs' own grid launches). */
 int pmk_batch_info(const pmk_batch *batch, size_t *n_tasks, int *n_kernels);
 void pmk_batch_destroy(pmk_batch *batch);
 
