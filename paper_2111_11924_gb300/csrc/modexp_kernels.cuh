@@ -214,17 +214,20 @@ struct ModexpEntry {
 // Other geometries measured no gain or a loss (64 limbs at 4 lanes: 12%
 // slower at 1 MiB) and keep 128.
 // RR_GRP: round-robin launches also take the key-group instantiation (the
-// geometries where it measured faster; see k_modexp).
+// geometries where it measured faster; see k_modexp).  GRP_MINB: the
+// key-group instantiation's minimum resident blocks per SM, where it differs
+// from MINB (the geometries where it measured faster that way).
 template <int S, int TPI, bool CRT, int FORM, int NT = dev::kThreads, int TABLE = kTableFull, int MINB = 0,
-          bool RR_GRP = false>
+          bool RR_GRP = false, int GRP_MINB = MINB>
 ModexpEntry make_entry() {
   constexpr size_t warp_area = (size_t)(32 / TPI) * dev::Layout<S>::inst(dev::table_rows(TABLE));
   return ModexpEntry{S,
                      TPI,
                      CRT,
                      FORM,
-                     reinterpret_cast<const void *>(&dev::k_modexp<S, TPI, CRT, FORM, NT, TABLE, MINB, RR_GRP>),
-                     reinterpret_cast<const void *>(&dev::k_modexp<S, TPI, CRT, FORM, NT, TABLE, MINB, true>),
+                     reinterpret_cast<const void *>(
+                         &dev::k_modexp<S, TPI, CRT, FORM, NT, TABLE, RR_GRP ? GRP_MINB : MINB, RR_GRP>),
+                     reinterpret_cast<const void *>(&dev::k_modexp<S, TPI, CRT, FORM, NT, TABLE, GRP_MINB, true>),
                      dev::modexp_smem_bytes<S>(TPI, NT, TABLE),
                      reinterpret_cast<const void *>(&dev::k_modexp_tasks<S, TPI, CRT, FORM, TABLE>),
                      sizeof(uint32_t) * warp_area * (dev::kThreads / 32),

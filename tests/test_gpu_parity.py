@@ -187,7 +187,7 @@ def test_1mib_2048_encrypt_all_decrypt_sampled(ctx):
 # ------------------------------------------------------------------ launch geometries
 
 @pytest.mark.parametrize("nbits,crt", [(2048, False), (2048, True), (1024, False), (1024, True), (4096, False),
-                                       (3072, True)])
+                                       (3072, True), (3072, False)])
 def test_every_kernel_geometry(ctx, P, nbits, crt):
     """Every compiled (lanes, form) geometry gives the same bit-exact result;
     for the CRT residues also with the small odd-power table (window <= 4).
