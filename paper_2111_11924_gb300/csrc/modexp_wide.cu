@@ -8,9 +8,13 @@ namespace pmk {
 using dev::kChain;
 using dev::kCols;
 
+// The 192-limb, 16-lane chain geometry (the 6144-bit default) serves its
+// round-robin launches with the key-group instantiation, measured 7% faster
+// at 100 KB and 2.8% at 4 MiB.
 const ModexpEntry *modexp_entries_wide(int *count) {
   static const ModexpEntry entries[] = {
-      make_entry<192, 16, false, kChain>(), make_entry<192, 16, false, kCols>(),
+      make_entry<192, 16, false, kChain, dev::kThreads, kTableFull, 0, true>(),
+      make_entry<192, 16, false, kCols>(),
       make_entry<256, 16, false, kChain>(), make_entry<256, 16, false, kCols>(),
       make_entry<256, 32, false, kChain>(), make_entry<96, 8, true, kChain>(),
       make_entry<96, 16, true, kChain>(),   make_entry<96, 16, true, kCols>(),
